@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the VEG splatting hot path on GB300.
+
+Default workload (the training step): 1M Gaussians sampled from an 8-blob
+scalar field, one 1024x1024 view, 4 transfer functions, L1 loss against a
+target rendered from a perturbed copy.  A step is one pass of the whole hot
+path: projection, tile binning + radix sort, compositing of all 4 TFs, L1
+loss, compositing backward, projection backward.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (512 MB write) between timed
+steps, outside the timed spans.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (launched by torchrun) every rank runs the same step on its own
+GPU (independent replicas, weak scaling); the time is the max over ranks.
+`--impl reference` times the CPU oracle on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s render & train steps/s, p50/p99 serve latency vs plain path, same GB300"
+WORKLOAD = ("train step: 1M blob-field Gaussians (8 blobs), 1024x1024, 4 TFs, L1 vs "
+            "perturbed-copy target; project+bin/sort+composite fwd+L1+composite bwd+project bwd")
+FP32_LANES_PER_SM = 128
+
+# FP32 operations per work unit (an FMA counts 2), taken from the kernels'
+# per-pair arithmetic; the instrumented kernels count the units.
+FWD_FLOPS = {"visited": 11, "alpha": 3, "blended": 10}
+BWD_FLOPS = {"replayed": 11, "alpha": 3, "blended": 21, "free": 7, "grad": 26}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-tiles", type=int, default=6)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--width", type=int, default=1024)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def setup_train(args, device):
+    import torch
+
+    from paper_2504_13339_gb300 import scenes as S
+    from paper_2504_13339_gb300.render import SplatPipeline, lut_tensor
+
+    g, tgt_g, cams, tfs = S.train_scene(n=args.n, width=args.width)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=device)
+    tens = (t(g.mean_v), t(g.logscale_w), t(g.quat))
+    luts = lut_tensor(tfs, device)
+    p = SplatPipeline(g.n, cams, n_tf=len(tfs), capacity=8 * g.n)
+    # target: render of the perturbed copy (synthetic input data)
+    target = p.render(t(tgt_g.mean_v), t(tgt_g.logscale_w), t(tgt_g.quat), luts).clone()
+    p.render(*tens, luts)  # sizes the instance capacity for this scene
+    _, m = p.status()
+    p.set_capacity(int(m * 1.15) + 4096)
+    grads = [torch.zeros_like(x) for x in tens]
+    return p, tens, luts, target, grads, cams, tfs, g, m
+
+
+def gpu_step(p, tens, luts, target, grads, ev=None):
+    for gb in grads:
+        gb.zero_()
+    p.project(*tens, luts)
+    p.bin_sort()
+    if ev is not None:
+        ev[0].record()
+    p.composite(luts)
+    if ev is not None:
+        ev[1].record()
+    p.l1(target)
+    if ev is not None:
+        ev[2].record()
+    p.backward_2d(p.loss_grad)
+    if ev is not None:
+        ev[3].record()
+    p.project_backward(*grads)
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2504_13339_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """DRAM bytes per launch recorded from an ncu capture of the same kernel
+    source (profiles/traffic.json); None when absent or stale."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha") != source_hash("composite.cu", "veg_internal.cuh"):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2504_13339_gb300 import _lib
+    import __graft_entry__
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    _lib.load()
+
+    p, tens, luts, target, grads, cams, tfs, g, m = setup_train(args, device)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        gpu_step(p, tens, luts, target, grads)
+    st, m2 = p.status()
+    assert st == _lib.VEG_OK, "instance capacity overflow during warm-up"
+
+    # ---- device-timed loop -------------------------------------------------
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = _lib.veg_kernel_launches()
+    for k in range(K):
+        flush.zero_()
+        e = evs[k]
+        e[4].record(stream)
+        gpu_step(p, tens, luts, target, grads, ev=e[:4])
+        e[5].record(stream)
+    barrier()
+    launches = _lib.veg_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [e[4].elapsed_time(e[5]) for e in evs]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers ---------------
+    tgt_host = target.cpu().pin_memory()
+    lut_host = luts.cpu().pin_memory()
+    loss_host = torch.empty(1).pin_memory()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    barrier()
+    for k in range(K):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        target.copy_(tgt_host, non_blocking=True)
+        luts.copy_(lut_host, non_blocking=True)
+        gpu_step(p, tens, luts, target, grads)
+        loss_host.copy_(p.loss, non_blocking=True)
+        ev2[k][1].record(stream)
+    barrier()
+    e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in ev2]))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = tgt_host.numel() * 4 + lut_host.numel() * 4
+    d2h = 4
+
+    # ---- work counts for the roofline (instrumented launches, untimed) -----
+    fst = torch.zeros(3, dtype=torch.int64, device=device)
+    bst = torch.zeros(5, dtype=torch.int64, device=device)
+    p.project(*tens, luts)
+    p.bin_sort()
+    p.composite(luts, stats=fst)
+    p.l1(target)
+    p.backward_2d(p.loss_grad, stats=bst)
+    torch.cuda.synchronize()
+    f = fst.cpu().numpy().astype(float)
+    b = bst.cpu().numpy().astype(float)
+    fwd_flops = FWD_FLOPS["visited"] * f[0] + FWD_FLOPS["alpha"] * f[1] + FWD_FLOPS["blended"] * f[2]
+    bwd_flops = (BWD_FLOPS["replayed"] * b[0] + BWD_FLOPS["alpha"] * b[1] +
+                 BWD_FLOPS["blended"] * b[2] + BWD_FLOPS["free"] * b[3] + BWD_FLOPS["grad"] * b[4])
+    props = torch.cuda.get_device_properties(device)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fwd_avg, bwd_avg = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
+    if bwd_avg >= fwd_avg:
+        dom, dom_ms, dom_flops, key = "composite_bwd_kernel", bwd_avg, bwd_flops, "composite_bwd"
+    else:
+        dom, dom_ms, dom_flops, key = "composite_fwd_kernel", fwd_avg, fwd_flops, "composite_fwd"
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tflops, 4), "traffic": profiled_traffic(key),
+                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
+                              f"x 2 (FMA) x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                "avg_launch_ms": round(dom_ms, 4), "flops_per_launch": dom_flops}
+
+    steps_per_s = world * K / (total_ms * 1e-3)
+    mpix = world * K * p.out.numel() // 4 / (total_ms * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": round(steps_per_s, 3), "unit": "steps/s",
+        "n_gpus": world, "steps": K, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": g.n, "width": cams[0].width,
+                   "height": cams[0].height, "n_tf": len(tfs), "views": len(cams),
+                   "tile_instances": int(m), "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "mpix_per_s": round(mpix, 2),
+        "stages_ms": {"composite_fwd": round(fwd_avg, 4), "composite_bwd": round(bwd_avg, 4),
+                      "other": round(total_ms / K - fwd_avg - bwd_avg, 4)},
+        "work": {"fwd": {"visited": int(f[0]), "alpha": int(f[1]), "blended": int(f[2])},
+                 "bwd": {"replayed": int(b[0]), "alpha": int(b[1]), "blended": int(b[2]),
+                         "free": int(b[3]), "grad": int(b[4])},
+                 "fwd_tflops": round(fwd_flops / (fwd_avg * 1e-3) / 1e12, 3)},
+        "clocks": clk,
+        "e2e": {"value": round(world * K / (e2e_ms * 1e-3), 3), "unit": "steps/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+    }
+    if (rank == 0) and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# ----------------------------------------------------------------------------
+
+class OracleSample:
+    """The oracle on a bounded sample of the training step: the projection of
+    the whole scene is prepared once; a sampled step projects a 1/n_occ
+    slice of the Gaussians and runs binning, the blend of all TFs, the L1
+    loss, the blend backward and the projection backward for one occupied
+    tile; its time x n_occ estimates one full step."""
+
+    def __init__(self, args, seed=7):
+        from oracle import veg_oracle as O
+        from paper_2504_13339_gb300 import scenes as S
+        self.O = O
+        self.g, tgt, self.cams, self.tfs = S.train_scene(n=args.n, width=args.width)
+        cam = self.cams[0]
+        self.proj = O.project32(cam, self.g, self.tfs)
+        self.tproj = O.project32(cam, tgt, self.tfs)
+        # splats per tile from the rectangles (2D difference array)
+        d = np.zeros((cam.tiles_y + 1, cam.tiles_x + 1), np.int64)
+        ok = self.proj["count"] > 0
+        x0, y0, x1, y1 = (self.proj["rect"][ok, c] for c in range(4))
+        np.add.at(d, (y0, x0), 1)
+        np.add.at(d, (y0, x1), -1)
+        np.add.at(d, (y1, x0), -1)
+        np.add.at(d, (y1, x1), 1)
+        per_tile = np.cumsum(np.cumsum(d, 0), 1)[:-1, :-1].ravel()
+        occ = np.nonzero(per_tile)[0]
+        self.occupied = int(occ.size)
+        self.order = np.random.default_rng(seed).permutation(occ)
+        self.k = 0
+
+    def step(self):
+        O, cam, g = self.O, self.cams[0], self.g
+        tile = int(self.order[self.k % len(self.order)])
+        self.k += 1
+        sl = slice(0, max(1, g.n // self.occupied))
+        O.project32(cam, g.subset(np.arange(g.n)[sl]), self.tfs)
+        lists = O.tile_lists(self.proj, cam, [tile])
+        bins = O.bins_from_lists([lists], 1, cam.tiles_x * cam.tiles_y)
+        fwd = O.composite_fwd([self.proj], self.cams, bins, self.tfs, tiles=[tile], record=True)
+        tl = O.tile_lists(self.tproj, cam, [tile])
+        tb = O.bins_from_lists([tl], 1, cam.tiles_x * cam.tiles_y)
+        tgt = O.composite_fwd([self.tproj], self.cams, tb, self.tfs, tiles=[tile])
+        px, py = O._tile_pixels(cam, tile)
+        a = fwd["out"][0][:, py, px]
+        b = tgt["out"][0][:, py, px]
+        dout = np.zeros_like(fwd["out"])
+        dout[0][:, py, px, :3] = np.sign(a - b)[..., :3] / dout[..., :3].size
+        g2 = O.composite_bwd([self.proj], self.cams, bins, self.tfs, (0, 0, 0), fwd, dout,
+                             tiles=[tile])
+        touched = np.nonzero(np.abs(g2[0]).sum(1))[0]
+        if touched.size:
+            prs = {k: (v[touched] if isinstance(v, np.ndarray) and v.shape[:1] == (g.n,) else v)
+                   for k, v in self.proj.items()}
+            O.params_grad(self.cams, g.subset(touched), [prs], g2[:, touched])
+
+
+def cpu_baseline(args):
+    s = OracleSample(args)
+    t0 = time.perf_counter()
+    n = 0
+    while n < args.cpu_tiles:
+        s.step()
+        n += 1
+    dt = (time.perf_counter() - t0) / n
+    full = dt * s.occupied
+    return {"value": round(1.0 / full, 6), "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} of {s.occupied} occupied tiles (each: 1/{s.occupied} of the "
+                      f"projection, the tile's lists, blend of {len(s.tfs)} TFs, target, L1, "
+                      f"blend backward, projection backward), scaled by {s.occupied}; "
+                      f"numpy single thread"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    s = OracleSample(args)
+    for _ in range(max(args.warmup, 3)):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = (time.perf_counter() - t0) / args.steps
+    full = dt * s.occupied
+    val = 1.0 / full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(full * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": s.g.n, "width": s.cams[0].width,
+                   "n_tf": len(s.tfs)},
+        "cpu_baseline": {"value": round(val, 6), "unit": "steps/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"per step one of {s.occupied} occupied tiles (+1/{s.occupied}"
+                                   f" of the projection), time x {s.occupied}"},
+        "e2e": {"value": round(val, 6), "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

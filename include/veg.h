@@ -1,0 +1,256 @@
+/*
+ * veg.h -- C ABI of the GB300 splatting core for Volume Encoding Gaussians
+ * (VEG, arXiv 2504.13339).
+ *
+ * Each 3D Gaussian carries a scalar value v instead of a colour (Sec. 3.2).
+ * Rendering (Sec. 3.3) maps v through a transfer function (TF) to colour
+ * C(v) and opacity O(v), forms alpha = O(v) * w with a trainable weight w,
+ * projects the Gaussian to a 2D screen covariance (EWA splatting), bins the
+ * splats into 16x16 pixel tiles, orders each tile's splats by depth and
+ * blends them front to back with Eq. 1:
+ *     P = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j).
+ * The backward pass (Sec. 3.3, "gradients are computed manually") carries
+ * dL/dP back through the blend, the TF and the projection.
+ *
+ * Conventions shared by every entry point
+ *   - Memory: every array argument is DEVICE memory owned by the caller,
+ *     unless marked "host".  The library never allocates or frees: scratch
+ *     memory is a caller-provided workspace sized by the *_workspace_size
+ *     query.  Arrays of 4-float records must be 16-byte aligned.
+ *   - Streams: all work is enqueued on `stream`; calls return before it
+ *     runs.  Inputs must stay valid until the stream reaches the call.
+ *   - Errors: a call returns VEG_ERR_INVALID_ARGUMENT before launching
+ *     anything when an argument is malformed, VEG_ERR_CUDA when a launch
+ *     fails.  Errors found on the device (instance capacity overflow) are
+ *     recorded in the workspace header and reported by veg_sync_status.
+ *     Nothing aborts, traps or prints.
+ *   - Cameras (host structs, copied into kernel parameters): pinhole with
+ *     OpenCV axes (x right, y down, z forward), world_to_cam = [R | t]
+ *     row-major 3x4; pixel (i, j) is evaluated at the point (i, j) in
+ *     pixel units.  All views of one call share width and height.
+ *   - Gaussians: three float4 arrays of n rows: (mu_x, mu_y, mu_z, v),
+ *     (log s_x, log s_y, log s_z, w), (q_w, q_x, q_y, q_z).  v and w are
+ *     already activated into [0, 1] (the paper stores them via a sigmoid).
+ *   - Transfer functions: n_tf tables of lut_size RGBA float4 entries over
+ *     v in [0, 1]: entry k sits at v = k/(lut_size-1), values in between are
+ *     linearly interpolated (Sec. 3.3, last paragraph).
+ */
+#ifndef VEG_H
+#define VEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum veg_status {
+  VEG_OK = 0,
+  VEG_ERR_INVALID_ARGUMENT = 1,
+  VEG_ERR_CAPACITY = 2,    /* more tile instances than the caller's capacity */
+  VEG_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
+  VEG_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  VEG_ERR_UNSUPPORTED = 5  /* valid request this build does not handle */
+} veg_status;
+
+#define VEG_MAX_VIEWS 64
+#define VEG_MAX_IMAGE 16384
+#define VEG_TILE 16
+
+typedef struct veg_camera {
+  float world_to_cam[12]; /* 3x4 row-major [R | t] */
+  float fx, fy, cx, cy;   /* focal lengths and principal point, pixels */
+  int32_t width, height;  /* image size, pixels, 1..16384 */
+  float near_plane;       /* Gaussians with camera z <= near are culled */
+} veg_camera;
+
+typedef struct veg_gaussians {
+  const float* mean_v;     /* device [n][4]: mu, v */
+  const float* logscale_w; /* device [n][4]: log-scale, w */
+  const float* quat;       /* device [n][4]: q_w, q_x, q_y, q_z (any norm > 0) */
+  int64_t n;
+} veg_gaussians;
+
+typedef struct veg_tf {
+  const float* lut; /* device [n_tf][lut_size][4] RGBA, straight alpha */
+  int32_t lut_size; /* >= 2 */
+  int32_t n_tf;     /* >= 1 */
+} veg_tf;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* veg_status_string(veg_status status);
+
+/* Number of kernels this library has launched in the process so far
+ * (a diagnostic counter, incremented on the host at every launch). */
+uint64_t veg_kernel_launches(void);
+
+/*
+ * veg_project -- per-Gaussian projection (Sec. 3.3: covariance from S and R,
+ * projected to 2D "using the method of Zwicker et al."; TF applied first so
+ * that Gaussians mapped to low opacity are culled immediately).
+ *
+ * For every view v < n_views and Gaussian i < g.n, writes record v*n + i:
+ *   splat_geo [V][n][4]: (u_x, u_y, depth, w)  screen mean, camera z, weight
+ *   splat_aux [V][n][4]: (a, b, c, v)  conic = inverse 2D covariance
+ *       [[a, b], [b, c]] of Sigma' = J W Sigma W^T J^T + 0.3 I
+ *   tiles_touched [V][n]: number of 16x16 tiles in the splat's rectangle
+ *   rect [V][n][4] int16: tile rectangle (x0, y0, x1, y1), ends exclusive:
+ *       the tiles holding a pixel centre inside [u - r, u + r]^2 with
+ *       r = ceil(3 sqrt(lambda_max(Sigma')))
+ * A culled Gaussian gets tiles_touched = 0 and all-zero records.  Culling:
+ * camera z <= near_plane, zero quaternion, det(Sigma') <= 0, empty rectangle,
+ * and -- only when cull_tf is non-NULL -- O_t(v) w < 1/255 for every table t
+ * of cull_tf (lossless: such a Gaussian can never reach alpha >= 1/255).
+ * Depth, screen mean, radius, rectangle and the opacity test are evaluated in
+ * IEEE float32 with a fixed operation order (no fused multiply-add) so that
+ * tile lists are reproducible bit for bit.
+ * cams: host [n_views], 1 <= n_views <= VEG_MAX_VIEWS.  cull_tf: host pointer
+ * to a descriptor (its lut is device memory) or NULL.
+ */
+veg_status veg_project(const veg_camera* cams, int32_t n_views, veg_gaussians g,
+                       const veg_tf* cull_tf, float* splat_geo, float* splat_aux,
+                       int32_t* tiles_touched, int16_t* rect, cudaStream_t stream);
+
+/*
+ * veg_bin_sort -- tile binning and depth ordering (Sec. 3.3: "the efficient
+ * tile-based rasterizer", alpha-blending "in front-to-back order").
+ *
+ * Produces, for every view and tile, the list of splats touching the tile in
+ * increasing (depth, Gaussian index) order; equivalently the stable sort of
+ * one key per (Gaussian, tile) pair,
+ *     key = (view << (tb + 32)) | (tile << 32) | bits(depth_f32),
+ * tb = max(1, ceil(log2(tiles per view))), emitted in Gaussian index order
+ * with tiles row-major.  Outputs:
+ *   vals [capacity]: record index v*n + i of each instance, sorted
+ *   keys [capacity] (optional, may be NULL): the sorted 64-bit keys above
+ *   tile_ranges [V][tiles][2] int32: [start, end) of each tile's run in vals
+ *       ((0, 0) for an empty tile); tiles = ceil(W/16) * ceil(H/16), row-major
+ * The number of instances M is known only on the device; when M > capacity
+ * only the first `capacity` instances (in emission order) are binned, the
+ * header flag is set and veg_sync_status returns VEG_ERR_CAPACITY.
+ * workspace: device, >= veg_bin_sort_workspace_size(...) bytes, 256-byte
+ * aligned; its first 256 bytes are a status header read by veg_sync_status.
+ * n, capacity >= 0; capacity < 2^31.
+ */
+veg_status veg_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t capacity,
+                                       int32_t width, int32_t height, size_t* bytes);
+veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int64_t n,
+                        const float* splat_geo, const int32_t* tiles_touched,
+                        const int16_t* rect, void* workspace, size_t workspace_bytes,
+                        int64_t capacity, uint64_t* keys, uint32_t* vals,
+                        int32_t* tile_ranges, cudaStream_t stream);
+
+/*
+ * veg_sync_status -- waits for `stream`, then reads the status header of a
+ * bin_sort / render workspace.  Writes the instance count M (even when it
+ * exceeded the capacity) to *n_instances (host, may be NULL).  Returns
+ * VEG_ERR_CAPACITY if the last binning overflowed, VEG_ERR_CUDA if the
+ * stream reported an error, else VEG_OK.
+ */
+veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* n_instances);
+
+/*
+ * veg_composite_fwd -- Eq. 1 per pixel, for n_tf transfer functions at once.
+ *
+ * For each view, tile, pixel and TF t, walks the tile's list front to back:
+ *   G = exp(-1/2 d^T Sigma'^-1 d), d = u - pixel (skip the splat if the
+ *       exponent is positive);
+ *   (rgb, A) = TF_t(v) by linear interpolation; alpha = min(0.99, A w G);
+ *   skip if alpha < 1/255; stop this TF at this pixel if T (1 - alpha) <
+ *   1e-4 (that splat not blended); else C += rgb alpha T, T *= 1 - alpha.
+ * Writes out [V][n_tf][H][W][4] = (C + T bg, T_final) and n_contrib
+ * [V][n_tf][H][W] = 1 + list position of the last blended splat (0 if none).
+ * The scene representation is TF-independent, so one sort serves every TF.
+ * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default).
+ * bg: host float[3].  stats: optional device uint64[3] accumulating
+ * (visited pixel-splat pairs, alpha evaluations, blended pairs), NULL to skip
+ * the instrumented kernel.  n is the per-view record count used by
+ * veg_project.
+ */
+veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
+                             const float* splat_geo, const float* splat_aux,
+                             const uint32_t* vals, const int32_t* tile_ranges, veg_tf tf,
+                             const float* bg, int32_t tf_group, float* out,
+                             int32_t* n_contrib, unsigned long long* stats,
+                             cudaStream_t stream);
+
+/*
+ * veg_composite_bwd -- manual gradients of the render (Sec. 3.3, backward
+ * pass through "the rasterizer", the transfer function and the projection).
+ *
+ * Given the forward inputs/outputs and dL_dout [V][n_tf][H][W][4] (gradient
+ * with respect to (R, G, B, T_final)), replays each pixel's blend front to
+ * back and ACCUMULATES (+=) into the caller's gradient arrays, packed like
+ * the Gaussians: grad_mean_v [n][4] = (dL/dmu, dL/dv), grad_logscale_w
+ * [n][4] = (dL/dlog s, dL/dw), grad_quat [n][4] = dL/dq, summed over views
+ * and TFs.  Derivatives are exact: zero through the 0.99 clamp, the skips and
+ * the clamped Jacobian entries.  grad2d (optional, may be NULL) receives the
+ * per-record screen-space gradients [V][n][8] = (du_x, du_y, da, db, dc, dv,
+ * dw, 0) (overwritten).  workspace >= veg_composite_bwd_workspace_size.
+ * If grad_mean_v, grad_logscale_w and grad_quat are all NULL, only grad2d
+ * (then required) is computed; veg_project_bwd completes the chain.
+ * stats: optional device uint64[5] accumulating (replayed pixel-splat pairs,
+ * alpha evaluations, blended pairs, blended pairs below the 0.99 clamp,
+ * pairs with a nonzero screen-space gradient); NULL skips the instrumented
+ * kernel.
+ */
+veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views, size_t* bytes);
+veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
+                             const float* splat_geo, const float* splat_aux,
+                             const int32_t* tiles_touched, const uint32_t* vals,
+                             const int32_t* tile_ranges, veg_tf tf, const float* bg,
+                             int32_t tf_group, const float* out, const int32_t* n_contrib,
+                             const float* dL_dout, void* workspace, size_t workspace_bytes,
+                             float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
+                             float* grad2d, unsigned long long* stats, cudaStream_t stream);
+
+/*
+ * veg_project_bwd -- the projection part of the backward pass (Sec. 3.3):
+ * chains per-record screen-space gradients grad2d [V][n][8] = (du_x, du_y,
+ * da, db, dc, dv, dw, 0) -- as written by veg_composite_bwd -- through the
+ * EWA projection, the covariance construction, the scale exponential and the
+ * quaternion normalisation, and ACCUMULATES (+=) the sum over views into
+ * grad_mean_v, grad_logscale_w and grad_quat [n][4].  Records with
+ * tiles_touched == 0 (culled) contribute nothing.  One thread per Gaussian,
+ * no atomics: the result is deterministic.
+ */
+veg_status veg_project_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
+                           const int32_t* tiles_touched, const float* grad2d,
+                           float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
+                           cudaStream_t stream);
+
+/*
+ * veg_l1_loss -- the L1 part of the training loss (Sec. 4.2:
+ * (1 - lambda) L1 + lambda L_SSIM): loss = mean |out.rgb - target.rgb| over
+ * n_records RGBA records (the fourth channel ignored), and
+ * grad = dloss/dout (sign(out - target) / (3 n_records) on RGB, 0 on the
+ * fourth channel; sign(0) = 0).  loss: device float, overwritten.
+ * workspace >= veg_l1_loss_workspace_size bytes; the sum is reduced in a
+ * fixed order, so the result is deterministic.
+ */
+veg_status veg_l1_loss_workspace_size(size_t* bytes);
+veg_status veg_l1_loss(const float* out, const float* target, int64_t n_records, float* grad,
+                       float* loss, void* workspace, size_t workspace_bytes,
+                       cudaStream_t stream);
+
+/*
+ * veg_render -- convenience forward: veg_project (with the TF cull), then
+ * veg_bin_sort, then veg_composite_fwd, all scratch in `workspace`
+ * (>= veg_render_workspace_size bytes).  Same outputs as
+ * veg_composite_fwd.  Overflow of `capacity` is reported by veg_sync_status
+ * on the same workspace.
+ */
+veg_status veg_render_workspace_size(int64_t n, int32_t n_views, int64_t capacity,
+                                     int32_t width, int32_t height, size_t* bytes);
+veg_status veg_render(const veg_camera* cams, int32_t n_views, veg_gaussians g, veg_tf tf,
+                      const float* bg, int64_t capacity, void* workspace,
+                      size_t workspace_bytes, float* out, int32_t* n_contrib,
+                      cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VEG_H */

@@ -38,8 +38,9 @@ Readings where the paper is silent (each listed in the design notes):
      blending that splat.
   R8 output RGB = sum c a T + T_final bg and the final transmittance T_final.
   R9 derivatives are the true ones: zero through the 0.99 clamp and the skips.
-  R12 pixels whose decisions sit within a relative 1e-4 of a threshold are
-     flagged; float32 and float64 may legitimately decide them differently.
+  R12 pixels whose decisions sit within a relative 1e-5 (alpha tests) or 1e-3
+     (transmittance stop) of a threshold are flagged; float32 and float64 may
+     legitimately decide them differently.
 """
 from __future__ import annotations
 
@@ -56,6 +57,12 @@ DILATION = 0.3
 FRUSTUM_SLACK = 1.3
 LAMBDA_FLOOR = 0.1
 TILE = 16
+# Relative half-widths of the threshold windows of reading R12.  Float32
+# alpha carries up to a few 1e-6 relative error (the exponent's rounding
+# times |power| <= ~6, plus the hardware exp2 approximation); float32
+# transmittance accumulates up to ~1e-5 per high-opacity step.
+FLAG_ALPHA = 1e-5
+FLAG_T = 1e-3
 
 # Cody-Waite split of ln 2: the high part has 15 significant bits so that
 # n * LN2_HI is exact for |n| <= 2^8; LN2_LO = ln 2 - LN2_HI.
@@ -355,8 +362,8 @@ def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False):
             blend = ok & ~term
             clamped = blend & (raw > ALPHA_MAX)
             with np.errstate(divide="ignore", invalid="ignore"):
-                near = (_flag_near(alpha, ALPHA_MIN, 1e-4) | _flag_near(raw, ALPHA_MAX, 1e-4)
-                        | (ok & _flag_near(test, T_MIN, 1e-3)))
+                near = (_flag_near(alpha, ALPHA_MIN, FLAG_ALPHA) | _flag_near(raw, ALPHA_MAX, FLAG_ALPHA)
+                        | (ok & _flag_near(test, T_MIN, FLAG_T)))
                 scale = np.abs(qa) + np.abs(qc) + 2 * np.abs(qb)
                 near |= (np.abs(power) <= 1e-5 * scale)[:, None] & (scale > 0)[:, None]
             flag |= active & near
@@ -728,3 +735,33 @@ def render_frozen(cams, mean, logscale, quat, v, w, luts, bg, bins, recs, tiles)
                                frozen=recs[vi, tile])
             out[vi, :, py, px] = r["out"]
     return out
+
+
+def tile_lists(proj, cam, tiles, view=0):
+    """Lists of the given tiles by a direct rectangle test on every visible
+    Gaussian, ordered by (float32 depth, index) -- no keys or global sort.
+    Values are record indices view * n + i."""
+    n = proj["geo"].shape[0]
+    valid = proj["count"] > 0
+    r = proj["rect"]
+    depth = proj["geo"][:, 2]
+    out = {}
+    for tile in tiles:
+        tx, ty = tile % cam.tiles_x, tile // cam.tiles_x
+        m = valid & (r[:, 0] <= tx) & (tx < r[:, 2]) & (r[:, 1] <= ty) & (ty < r[:, 3])
+        idx = np.nonzero(m)[0]
+        idx = idx[np.lexsort((idx, depth[idx]))]
+        out[tile] = idx + view * n
+    return out
+
+
+def bins_from_lists(lists_per_view, n_views, n_tiles):
+    """A bins dict (vals, ranges) holding only the listed tiles."""
+    vals, ranges, pos = [], np.zeros((n_views, n_tiles, 2), np.int64), 0
+    for vi in range(n_views):
+        for tile, lst in sorted(lists_per_view[vi].items()):
+            ranges[vi, tile] = (pos, pos + len(lst)) if len(lst) else (0, 0)
+            vals.append(np.asarray(lst, np.uint32))
+            pos += len(lst)
+    vals = np.concatenate(vals) if vals else np.zeros(0, np.uint32)
+    return {"vals": vals, "ranges": ranges}

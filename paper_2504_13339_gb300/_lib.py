@@ -1,0 +1,237 @@
+"""ctypes binding of libveg.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch CUDA tensors (device memory) plus plain numbers; nothing is computed in
+Python.  Importing this module fails loudly if the library has not been built:
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libveg.so")
+
+VEG_OK = 0
+VEG_ERR_CAPACITY = 2
+STATUS_NAMES = {0: "VEG_OK", 1: "VEG_ERR_INVALID_ARGUMENT", 2: "VEG_ERR_CAPACITY",
+                3: "VEG_ERR_CUDA", 4: "VEG_ERR_TIMEOUT", 5: "VEG_ERR_UNSUPPORTED"}
+MAX_VIEWS = 64
+
+
+class VegError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} failed: {STATUS_NAMES.get(status, status)}")
+
+
+class veg_camera(ctypes.Structure):
+    _fields_ = [("world_to_cam", ctypes.c_float * 12), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("near_plane", ctypes.c_float)]
+
+
+class veg_gaussians(ctypes.Structure):
+    _fields_ = [("mean_v", ctypes.c_void_p), ("logscale_w", ctypes.c_void_p),
+                ("quat", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class veg_tf(ctypes.Structure):
+    _fields_ = [("lut", ctypes.c_void_p), ("lut_size", ctypes.c_int32), ("n_tf", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_CAMS = ctypes.POINTER(veg_camera)
+_SIGS = {
+    "veg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "veg_kernel_launches": (ctypes.c_uint64, []),
+    "veg_project": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, ctypes.POINTER(veg_tf), _P, _P, _P,
+                                   _P, _P]),
+    "veg_bin_sort_workspace_size": (ctypes.c_int, [_I64, _I32, _I64, _I32, _I32,
+                                                   ctypes.POINTER(_SZ)]),
+    "veg_bin_sort": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, _SZ, _I64, _P, _P, _P, _P]),
+    "veg_sync_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I64)]),
+    "veg_composite_fwd": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, veg_tf, _P, _I32, _P,
+                                         _P, _P, _P]),
+    "veg_composite_bwd_workspace_size": (ctypes.c_int, [_I64, _I32, ctypes.POINTER(_SZ)]),
+    "veg_composite_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, veg_tf,
+                                         _P, _I32, _P, _P, _P, _P, _SZ, _P, _P, _P, _P, _P, _P]),
+    "veg_project_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P]),
+    "veg_l1_loss_workspace_size": (ctypes.c_int, [ctypes.POINTER(_SZ)]),
+    "veg_l1_loss": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),
+    "veg_render_workspace_size": (ctypes.c_int, [_I64, _I32, _I64, _I32, _I32,
+                                                 ctypes.POINTER(_SZ)]),
+    "veg_render": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, veg_tf, _P, _I64, _P, _SZ, _P, _P,
+                                  _P]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libveg.so (raises if it is missing) and declares every symbol."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libveg.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(name, status):
+    if status != VEG_OK:
+        raise VegError(name, status)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def cameras(cams):
+    """ctypes array of veg_camera from scene cameras."""
+    arr = (veg_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].world_to_cam[:] = [float(x) for x in np.asarray(c.world_to_cam, np.float32).ravel()]
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = c.fx, c.fy, c.cx, c.cy
+        arr[i].width, arr[i].height, arr[i].near_plane = c.width, c.height, c.near
+    return arr
+
+
+def gaussians(mean_v, logscale_w, quat):
+    return veg_gaussians(mean_v.data_ptr(), logscale_w.data_ptr(), quat.data_ptr(),
+                         mean_v.shape[0])
+
+
+def tf_desc(luts):
+    return veg_tf(luts.data_ptr(), luts.shape[-2], luts.shape[0])
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def veg_status_string(status: int) -> str:
+    return load().veg_status_string(status).decode()
+
+
+def veg_kernel_launches() -> int:
+    return int(load().veg_kernel_launches())
+
+
+def veg_project(cams, g, cull_tf, splat_geo, splat_aux, tiles_touched, rect, stream=None):
+    lib = load()
+    tf = ctypes.byref(cull_tf) if cull_tf is not None else None
+    _check("veg_project", lib.veg_project(cams, len(cams), g, tf, _ptr(splat_geo), _ptr(splat_aux),
+                                          _ptr(tiles_touched), _ptr(rect), _stream(stream)))
+
+
+def veg_bin_sort_workspace_size(n, n_views, capacity, width, height) -> int:
+    out = _SZ()
+    _check("veg_bin_sort_workspace_size",
+           load().veg_bin_sort_workspace_size(n, n_views, capacity, width, height,
+                                              ctypes.byref(out)))
+    return out.value
+
+
+def veg_bin_sort(cams, n, splat_geo, tiles_touched, rect, workspace, capacity, keys, vals,
+                 tile_ranges, stream=None):
+    _check("veg_bin_sort",
+           load().veg_bin_sort(cams, len(cams), n, _ptr(splat_geo), _ptr(tiles_touched),
+                               _ptr(rect), _ptr(workspace), workspace.numel(), capacity,
+                               _ptr(keys), _ptr(vals), _ptr(tile_ranges), _stream(stream)))
+
+
+def veg_sync_status(workspace, stream=None):
+    """Returns (status, n_instances); does not raise on VEG_ERR_CAPACITY."""
+    n = _I64()
+    st = load().veg_sync_status(_ptr(workspace), _stream(stream), ctypes.byref(n))
+    if st not in (VEG_OK, 2):
+        raise VegError("veg_sync_status", st)
+    return st, n.value
+
+
+def veg_composite_fwd(cams, n, splat_geo, splat_aux, vals, tile_ranges, tf, bg, tf_group, out,
+                      n_contrib, stats=None, stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    _check("veg_composite_fwd",
+           load().veg_composite_fwd(cams, len(cams), n, _ptr(splat_geo), _ptr(splat_aux),
+                                    _ptr(vals), _ptr(tile_ranges), tf,
+                                    ctypes.cast(bgc, ctypes.c_void_p), tf_group, _ptr(out),
+                                    _ptr(n_contrib), _ptr(stats), _stream(stream)))
+
+
+def veg_composite_bwd_workspace_size(n, n_views) -> int:
+    out = _SZ()
+    _check("veg_composite_bwd_workspace_size",
+           load().veg_composite_bwd_workspace_size(n, n_views, ctypes.byref(out)))
+    return out.value
+
+
+def veg_composite_bwd(cams, g, splat_geo, splat_aux, tiles_touched, vals, tile_ranges, tf, bg,
+                      tf_group, out, n_contrib, dL_dout, workspace, grad_mean_v, grad_logscale_w,
+                      grad_quat, grad2d=None, stats=None, stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check("veg_composite_bwd",
+           load().veg_composite_bwd(cams, len(cams), g, _ptr(splat_geo), _ptr(splat_aux),
+                                    _ptr(tiles_touched), _ptr(vals), _ptr(tile_ranges), tf,
+                                    ctypes.cast(bgc, ctypes.c_void_p), tf_group, _ptr(out),
+                                    _ptr(n_contrib), _ptr(dL_dout), _ptr(workspace), ws_bytes,
+                                    _ptr(grad_mean_v), _ptr(grad_logscale_w), _ptr(grad_quat),
+                                    _ptr(grad2d), _ptr(stats), _stream(stream)))
+
+
+def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,
+                    stream=None):
+    _check("veg_project_bwd",
+           load().veg_project_bwd(cams, len(cams), g, _ptr(tiles_touched), _ptr(grad2d),
+                                  _ptr(grad_mean_v), _ptr(grad_logscale_w), _ptr(grad_quat),
+                                  _stream(stream)))
+
+
+def veg_l1_loss_workspace_size() -> int:
+    out = _SZ()
+    _check("veg_l1_loss_workspace_size", load().veg_l1_loss_workspace_size(ctypes.byref(out)))
+    return out.value
+
+
+def veg_l1_loss(out, target, n_records, grad, loss, workspace, stream=None):
+    _check("veg_l1_loss",
+           load().veg_l1_loss(_ptr(out), _ptr(target), n_records, _ptr(grad), _ptr(loss),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream(stream)))
+
+
+def veg_render_workspace_size(n, n_views, capacity, width, height) -> int:
+    out = _SZ()
+    _check("veg_render_workspace_size",
+           load().veg_render_workspace_size(n, n_views, capacity, width, height,
+                                            ctypes.byref(out)))
+    return out.value
+
+
+def veg_render(cams, g, tf, bg, capacity, workspace, out, n_contrib, stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    _check("veg_render",
+           load().veg_render(cams, len(cams), g, tf, ctypes.cast(bgc, ctypes.c_void_p), capacity,
+                             _ptr(workspace), workspace.numel(), _ptr(out), _ptr(n_contrib),
+                             _stream(stream)))

@@ -1,0 +1,539 @@
+// Tile binning and depth ordering for the tile rasteriser (Sec. 3.3).
+//
+// The required order is the stable sort of one 64-bit key per
+// (Gaussian, tile) pair, key = (view, tile, depth bits), emitted in Gaussian
+// index order.  Rather than radix-sorting 44-60 bit keys over all M pairs,
+// the path sorts in two stages that give the same order:
+//   1. sort the V*n (view, Gaussian) records by their float32 depth bits
+//      (stable, so ties keep index order) -- 4 passes over V*n items;
+//   2. emit the pairs in that depth order with key = view * tiles + tile and
+//      stable-sort them by that key alone -- ceil(bits/8) passes over M.
+// A stable sort by tile of a sequence already ordered by (depth, index)
+// yields (view, tile, depth, index) order.  Both stages use one hand-written
+// LSD radix sort (reduce / scan / stable scatter, 8-bit digits, 4096 items
+// per block).  The instance count M lives only on the device; later kernels
+// read it from the workspace header, so no host round trip is needed.
+#include <algorithm>
+
+#include "veg_internal.cuh"
+
+namespace veg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTileItems = kThreads * kItems;  // 4096 items per radix block
+
+// Number of items to process: a fixed count, or min(*dev, cap).
+struct Count {
+  int64_t fixed;
+  const unsigned long long* dev;
+  int64_t cap;
+  __device__ __forceinline__ int64_t get() const {
+    if (dev == nullptr) return fixed;
+    unsigned long long m = *dev;
+    return (int64_t)(m < (unsigned long long)cap ? m : (unsigned long long)cap);
+  }
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan256(T x, T* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < 8 ? s_warp[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < 8) s_warp[lane] = wi - w;
+  }
+  __syncthreads();
+  T r = s_warp[warp] + inc - x;
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// radix sort kernels (u32 keys, u32 values, one 1..8-bit digit per pass)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads)
+    radix_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, int shift, int nbits,
+                      uint32_t* __restrict__ hist, int nblocks) {
+  __shared__ uint32_t s_hist[256];
+  s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t n = cnt.get();
+  const int64_t base = (int64_t)blockIdx.x * kTileItems;
+  const uint32_t mask = (1u << nbits) - 1u;
+  if (base < n) {
+#pragma unroll 4
+    for (int j = 0; j < kItems; ++j) {
+      int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+      if (i < n) atomicAdd(&s_hist[(__ldg(&keys[i]) >> shift) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
+}
+
+// One block per digit: exclusive scan in place of that digit's per-block
+// counts, and the digit total.
+__global__ void __launch_bounds__(1024)
+    radix_scan_rows_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_total;
+  uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (int base = 0; base < nblocks; base += 1024 * 4) {
+    uint32_t v[4];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int i = base + threadIdx.x * 4 + k;
+      v[k] = i < nblocks ? row[i] : 0u;
+      sum += v[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_warp[lane];
+      uint32_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      s_warp[lane] = wi - w;
+      if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    uint32_t run = carry + s_warp[warp] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int i = base + threadIdx.x * 4 + k;
+      if (i < nblocks) row[i] = run;
+      run += v[k];
+    }
+    carry += s_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+// Stable scatter: rank every item among equal digits of its block (warp
+// order, then lane order = item order), stage the block in digit order in
+// shared memory, then write each digit run out contiguously.
+__global__ void __launch_bounds__(kThreads)
+    radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, Count cnt,
+                         int shift, int nbits, const uint32_t* __restrict__ hist,
+                         const uint32_t* __restrict__ totals, int nblocks) {
+  __shared__ uint32_t s_whist[8][256];
+  __shared__ uint32_t s_dbase[256];
+  __shared__ uint32_t s_bstart[256];
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_keys[kTileItems];
+  __shared__ uint32_t s_vals[kTileItems];
+  const int64_t n = cnt.get();
+  const int64_t base = (int64_t)blockIdx.x * kTileItems;
+  if (base >= n) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t mask = (1u << nbits) - 1u;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) s_whist[w][tid] = 0;
+  uint32_t dpre = block_exclusive_scan256<uint32_t>(totals[tid], s_warp);
+  s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + blockIdx.x];
+  __syncthreads();
+
+  uint32_t k[kItems], v[kItems], r[kItems];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+    bool valid = i < n;
+    k[j] = valid ? kin[i] : 0u;
+    v[j] = valid ? vin[i] : 0u;
+    uint32_t d = valid ? ((k[j] >> shift) & mask) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
+    r[j] = before + __popc(peers & lt);
+    __syncwarp();
+    if (d < 256u && (peers & lt) == 0) s_whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over warps, and the block's digit count
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    uint32_t c = s_whist[w][tid];
+    s_whist[w][tid] = run;
+    run += c;
+  }
+  s_bstart[tid] = block_exclusive_scan256<uint32_t>(run, s_warp);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+    if (i < n) {
+      uint32_t d = (k[j] >> shift) & mask;
+      uint32_t pos = s_bstart[d] + s_whist[warp][d] + r[j];
+      s_keys[pos] = k[j];
+      s_vals[pos] = v[j];
+    }
+  }
+  __syncthreads();
+  const int cnt_valid = (int)min((int64_t)kTileItems, n - base);
+  for (int p = tid; p < cnt_valid; p += kThreads) {
+    uint32_t key = s_keys[p];
+    uint32_t d = (key >> shift) & mask;
+    uint32_t g = s_dbase[d] + (uint32_t)p - s_bstart[d];
+    kout[g] = key;
+    vout[g] = s_vals[p];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// binning kernels
+// ---------------------------------------------------------------------------
+
+__global__ void depth_keys_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
+                                  int64_t nrec, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrec) return;
+  keys[i] = tiles[i] > 0 ? __float_as_uint(geo[i].z) : 0xffffffffu;
+  vals[i] = (uint32_t)i;
+}
+
+// Per-block sums of tiles_touched taken in depth order.
+__global__ void __launch_bounds__(kThreads)
+    count_reduce_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
+                        int64_t nrec, unsigned long long* __restrict__ bsum) {
+  __shared__ unsigned long long s[kThreads];
+  const int64_t base = (int64_t)blockIdx.x * kTileItems;
+  unsigned long long acc = 0;
+  for (int j = 0; j < kItems; ++j) {
+    int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+    if (i < nrec) acc += (unsigned)tiles[order[i]];
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
+}
+
+// Exclusive scan of the block sums (one block of 1024 threads); writes the
+// instance total and the capacity flag into the header.
+__global__ void __launch_bounds__(1024)
+    count_top_kernel(unsigned long long* __restrict__ bsum, int nb, WsHeader* __restrict__ hdr,
+                     int64_t capacity) {
+  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned long long s_total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    unsigned long long x = i < nb ? bsum[i] : 0ull;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = s_warp[lane];
+      unsigned long long wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      s_warp[lane] = wi - w;
+      if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    if (i < nb) bsum[i] = carry + s_warp[warp] + inc - x;
+    carry += s_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    hdr->n_instances = carry;
+    hdr->flags = carry > (unsigned long long)capacity ? FLAG_CAPACITY : 0u;
+  }
+}
+
+// Instance offsets (exclusive prefix of tiles_touched in depth order),
+// saturated to 0xffffffff (any value >= capacity is never emitted).
+__global__ void __launch_bounds__(kThreads)
+    count_down_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
+                      int64_t nrec, const unsigned long long* __restrict__ bsum,
+                      uint32_t* __restrict__ offsets) {
+  __shared__ unsigned long long s_warp[8];
+  const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
+  uint32_t c[kItems];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    int64_t i = base + k;
+    c[k] = i < nrec ? (uint32_t)tiles[order[i]] : 0u;
+    sum += c[k];
+  }
+  unsigned long long run = bsum[blockIdx.x] + block_exclusive_scan256<unsigned long long>(sum, s_warp);
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    int64_t i = base + k;
+    if (i < nrec) offsets[i] = run < 0xffffffffull ? (uint32_t)run : 0xffffffffu;
+    run += c[k];
+  }
+}
+
+// One thread per record in depth order: write its (view*tiles + tile, record)
+// pairs, tiles row-major, while below capacity.
+__global__ void emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
+                            const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+                            int64_t nrec, int64_t n_per_view, int tiles_x, int tiles_per_view,
+                            int64_t capacity, uint32_t* __restrict__ ikeys,
+                            uint32_t* __restrict__ ivals) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrec) return;
+  uint32_t g = order[i];
+  if (tiles[g] == 0) return;
+  int64_t off = offsets[i];
+  if (off >= capacity) return;
+  short4 rc = rect[g];
+  uint32_t kb = (uint32_t)(g / n_per_view) * (uint32_t)tiles_per_view;
+  for (int ty = rc.y; ty < rc.w; ++ty)
+    for (int tx = rc.x; tx < rc.z; ++tx) {
+      if (off >= capacity) return;
+      ikeys[off] = kb + (uint32_t)(ty * tiles_x + tx);
+      ivals[off] = g;
+      ++off;
+    }
+}
+
+__global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) ranges[i] = make_int2(0, 0);
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
+                              int2* __restrict__ ranges) {
+  const int64_t n = cnt.get();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = keys[i];
+  if (i == 0 || keys[i - 1] != k) ranges[k].x = (int)i;
+  if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (int)(i + 1);
+}
+
+__global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
+                              Count cnt, const float4* __restrict__ geo, int tiles_per_view, int tb,
+                              uint64_t* __restrict__ keys64) {
+  const int64_t n = cnt.get();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t tk = tkeys[i];
+  uint32_t view = tk / (uint32_t)tiles_per_view;
+  uint32_t tile = tk - view * (uint32_t)tiles_per_view;
+  uint32_t depth = __float_as_uint(geo[vals[i]].z);
+  keys64[i] = ((uint64_t)view << (tb + 32)) | ((uint64_t)tile << 32) | (uint64_t)depth;
+}
+
+struct Layout {
+  WsHeader* hdr;
+  uint32_t *dk0, *dv0, *dk1, *dv1, *offsets;
+  unsigned long long* bsum;
+  uint32_t *ik0, *ik1, *iv0;
+  uint32_t *hist, *totals;
+  int nb_rec, nb_hist;
+  size_t bytes;
+};
+
+Layout carve(void* ws, int64_t nrec, int64_t capacity) {
+  Carver c(ws);
+  Layout L;
+  L.hdr = c.take<WsHeader>(1);
+  L.dk0 = c.take<uint32_t>(nrec);
+  L.dv0 = c.take<uint32_t>(nrec);
+  L.dk1 = c.take<uint32_t>(nrec);
+  L.dv1 = c.take<uint32_t>(nrec);
+  L.offsets = c.take<uint32_t>(nrec);
+  L.nb_rec = (int)std::max<int64_t>(1, (nrec + kTileItems - 1) / kTileItems);
+  L.bsum = c.take<unsigned long long>(L.nb_rec);
+  L.ik0 = c.take<uint32_t>(capacity);
+  L.ik1 = c.take<uint32_t>(capacity);
+  L.iv0 = c.take<uint32_t>(capacity);
+  L.nb_hist = (int)std::max<int64_t>(L.nb_rec, (capacity + kTileItems - 1) / kTileItems);
+  L.hist = c.take<uint32_t>((size_t)256 * L.nb_hist);
+  L.totals = c.take<uint32_t>(256);
+  L.bytes = c.bytes();
+  return L;
+}
+
+void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
+                Count cnt, int shift, int nbits, int nblocks, const Layout& L,
+                cudaStream_t stream) {
+  radix_hist_kernel<<<nblocks, kThreads, 0, stream>>>(kin, cnt, shift, nbits, L.hist, nblocks);
+  radix_scan_rows_kernel<<<256, 1024, 0, stream>>>(L.hist, nblocks, L.totals);
+  radix_scatter_kernel<<<nblocks, kThreads, 0, stream>>>(kin, vin, kout, vout, cnt, shift, nbits,
+                                                         L.hist, L.totals, nblocks);
+  count_launch(3);
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  return (unsigned)std::max<int64_t>(1, (n + threads - 1) / threads);
+}
+
+}  // namespace
+
+size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity, int tiles_per_view) {
+  (void)tiles_per_view;
+  return carve(nullptr, n * n_views, capacity).bytes;
+}
+
+veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const float4* geo,
+                          const int32_t* tiles, const short4* rect, void* ws, int64_t capacity,
+                          uint64_t* keys, uint32_t* vals, int2* ranges, cudaStream_t stream) {
+  const int W = cams[0].width, H = cams[0].height;
+  const int tiles_x = tiles_x_of(W), tiles_per_view = tiles_x * tiles_x_of(H);
+  const int64_t nrec = n * n_views;
+  const int64_t nranges = (int64_t)tiles_per_view * n_views;
+  Layout L = carve(ws, nrec, capacity);
+
+  zero_ranges_kernel<<<grid_for(nranges, 256), 256, 0, stream>>>(ranges, nranges);
+  count_launch();
+  if (nrec == 0) {
+    cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), stream);
+    return launch_status();
+  }
+  // 1. depth sort of all (view, Gaussian) records
+  depth_keys_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(geo, tiles, nrec, L.dk0, L.dv0);
+  count_launch();
+  Count cr{nrec, nullptr, 0};
+  radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 0, 8, L.nb_rec, L, stream);
+  radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 8, 8, L.nb_rec, L, stream);
+  radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 16, 8, L.nb_rec, L, stream);
+  radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 24, 8, L.nb_rec, L, stream);
+  const uint32_t* order = L.dv0;
+  // 2. instance offsets in depth order, total into the header
+  count_reduce_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, nrec, L.bsum);
+  count_top_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, L.hdr, capacity);
+  count_down_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, nrec, L.bsum, L.offsets);
+  count_launch(3);
+  // 3. emit (tile key, record) pairs, then stable sort by tile key
+  int bits = 1;
+  while (((int64_t)1 << bits) < nranges) ++bits;
+  const int passes = (bits + 7) / 8;
+  uint32_t* kbuf[2] = {L.ik0, L.ik1};
+  uint32_t* vbuf[2];
+  if (passes % 2 == 0) {
+    vbuf[0] = vals;
+    vbuf[1] = L.iv0;
+  } else {
+    vbuf[0] = L.iv0;
+    vbuf[1] = vals;
+  }
+  emit_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(tiles, rect, order, L.offsets, nrec, n,
+                                                       tiles_x, tiles_per_view, capacity, kbuf[0],
+                                                       vbuf[0]);
+  count_launch();
+  Count ci{0, &L.hdr->n_instances, capacity};
+  const int nb_inst = (int)std::max<int64_t>(1, (capacity + kTileItems - 1) / kTileItems);
+  int shift = 0;
+  for (int p = 0; p < passes; ++p) {
+    int nb = (bits - shift + (passes - p) - 1) / (passes - p);  // balanced digit widths
+    radix_pass(kbuf[p & 1], vbuf[p & 1], kbuf[(p + 1) & 1], vbuf[(p + 1) & 1], ci, shift, nb,
+               nb_inst, L, stream);
+    shift += nb;
+  }
+  const uint32_t* fkeys = kbuf[passes & 1];
+  // 4. per-tile ranges and optional 64-bit keys
+  ranges_kernel<<<grid_for(capacity, 256), 256, 0, stream>>>(fkeys, ci, ranges);
+  count_launch();
+  if (keys) {
+    keys64_kernel<<<grid_for(capacity, 256), 256, 0, stream>>>(
+        fkeys, vals, ci, geo, tiles_per_view, tile_bits_of(tiles_per_view), keys);
+    count_launch();
+  }
+  return launch_status();
+}
+
+}  // namespace veg
+
+extern "C" veg_status veg_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t capacity,
+                                                  int32_t width, int32_t height, size_t* bytes) {
+  if (!bytes || n < 0 || n_views < 1 || n_views > VEG_MAX_VIEWS || capacity < 0 ||
+      capacity >= ((int64_t)1 << 31) || width < 1 || height < 1 || width > VEG_MAX_IMAGE ||
+      height > VEG_MAX_IMAGE)
+    return VEG_ERR_INVALID_ARGUMENT;
+  *bytes = veg::binsort_ws_bytes(n, n_views, capacity,
+                                 veg::tiles_x_of(width) * veg::tiles_x_of(height));
+  return VEG_OK;
+}
+
+extern "C" veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int64_t n,
+                                   const float* splat_geo, const int32_t* tiles_touched,
+                                   const int16_t* rect, void* workspace, size_t workspace_bytes,
+                                   int64_t capacity, uint64_t* keys, uint32_t* vals,
+                                   int32_t* tile_ranges, cudaStream_t stream) {
+  using namespace veg;
+  veg_status st = check_cameras(cams, n_views);
+  if (st != VEG_OK) return st;
+  if (n < 0 || capacity < 0 || capacity >= ((int64_t)1 << 31) || !workspace || !tile_ranges ||
+      (capacity > 0 && !vals) || (n > 0 && (!splat_geo || !tiles_touched || !rect)))
+    return VEG_ERR_INVALID_ARGUMENT;
+  if (n * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) || !aligned16(splat_geo) ||
+      (reinterpret_cast<uintptr_t>(rect) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+    return VEG_ERR_INVALID_ARGUMENT;
+  const int tpv = tiles_x_of(cams[0].width) * tiles_x_of(cams[0].height);
+  if ((int64_t)tpv * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
+  if (workspace_bytes < binsort_ws_bytes(n, n_views, capacity, tpv))
+    return VEG_ERR_INVALID_ARGUMENT;
+  return binsort_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
+                        tiles_touched, reinterpret_cast<const short4*>(rect), workspace, capacity,
+                        keys, vals, reinterpret_cast<int2*>(tile_ranges), stream);
+}
+
+extern "C" veg_status veg_sync_status(const void* workspace, cudaStream_t stream,
+                                      int64_t* n_instances) {
+  if (!workspace) return VEG_ERR_INVALID_ARGUMENT;
+  veg::WsHeader h;
+  if (cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return VEG_ERR_CUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return VEG_ERR_CUDA;
+  if (n_instances) *n_instances = (int64_t)h.n_instances;
+  return (h.flags & veg::FLAG_CAPACITY) ? VEG_ERR_CAPACITY : VEG_OK;
+}

@@ -1,0 +1,153 @@
+// Shared internals of the VEG CUDA library: host-side launch bookkeeping,
+// workspace carving, and the device-side float32 helpers whose operation
+// order defines the binning-critical arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "veg.h"
+
+namespace veg {
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+void count_launch(int k = 1);
+
+// Returns VEG_ERR_CUDA if the last launch failed to enqueue.
+veg_status launch_status();
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller-provided workspace (256-byte aligned pieces).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = round_up(off, 256);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t bytes() const { return round_up(off, 256); }
+};
+
+// Status header at the start of a bin_sort / render workspace.
+struct WsHeader {
+  unsigned long long n_instances;  // total tile instances of the last binning
+  unsigned int flags;              // VEG_FLAG_* bits
+  unsigned int pad[61];
+};
+static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
+constexpr unsigned int FLAG_CAPACITY = 1u;
+
+struct CamParam {
+  float r[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float near_plane;
+  int width, height, tiles_x, tiles_y;
+};
+
+struct CamSet {
+  CamParam c[VEG_MAX_VIEWS];
+};
+
+veg_status check_cameras(const veg_camera* cams, int32_t n_views);
+void fill_camset(const veg_camera* cams, int32_t n_views, CamSet* out);
+
+inline int tiles_x_of(int w) { return (w + VEG_TILE - 1) / VEG_TILE; }
+inline int tile_bits_of(int tiles) {
+  int b = 1;
+  while ((1 << b) < tiles) ++b;
+  return b;
+}
+
+// Entry points shared between translation units (no argument validation).
+veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const veg_tf* cull_tf,
+                          float4* geo, float4* aux, int32_t* tiles, short4* rect,
+                          cudaStream_t stream);
+size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity, int tiles_per_view);
+veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const float4* geo,
+                          const int32_t* tiles, const short4* rect, void* ws, int64_t capacity,
+                          uint64_t* keys, uint32_t* vals, int2* ranges, cudaStream_t stream);
+veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
+                                const float4* geo, const float4* aux, const uint32_t* vals,
+                                const int2* ranges, veg_tf tf, const float* bg, int tf_group,
+                                float4* out, int32_t* n_contrib, unsigned long long* stats,
+                                cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// device side: float32 operations in a fixed order (no contraction)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float dv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, float b1,
+                                      float b2) {
+  return add(add(mul(a0, b0), mul(a1, b1)), mul(a2, b2));
+}
+
+// exp(x) by Cody-Waite reduction with ln 2 split into a 15-bit high part
+// (exact products n * hi for |n| <= 256) and the remainder, then a degree-7
+// Taylor polynomial in Horner form; scaling by 2^n through the exponent
+// field.  Input clamped to [-80, 80].  Error <= 2 ulp (checked on the host
+// against a float64 reference by the test suite).
+__device__ __forceinline__ float exp_cw(float x) {
+  const float kLog2e = 1.44269502162933349609375f;  // float32(log2 e)
+  const float kLn2Hi = 0.693145751953125f;
+  const float kLn2Lo = 1.428606765330187045037746429443359375e-06f;  // float32(ln2 - hi)
+  x = fminf(fmaxf(x, -80.0f), 80.0f);
+  float n = rintf(mul(x, kLog2e));
+  float r = sub(x, mul(n, kLn2Hi));
+  r = sub(r, mul(n, kLn2Lo));
+  float p = 1.0f / 5040.0f;
+  p = add(mul(p, r), 1.0f / 720.0f);
+  p = add(mul(p, r), 1.0f / 120.0f);
+  p = add(mul(p, r), 1.0f / 24.0f);
+  p = add(mul(p, r), 1.0f / 6.0f);
+  p = add(mul(p, r), 0.5f);
+  p = add(mul(p, r), 1.0f);
+  p = add(mul(p, r), 1.0f);
+  int ni = (int)n;
+  float scale = __int_as_float((ni + 127) << 23);
+  return mul(p, scale);
+}
+
+// Linear interpolation of one RGBA table at v in float32 (fixed order).
+// Entries sit at v = k/(L-1); v is clamped to [0, 1].
+struct TfPos {
+  int k;
+  float tau, one_m;
+};
+__device__ __forceinline__ TfPos tf_pos(float v, int L) {
+  float vc = fminf(fmaxf(v, 0.0f), 1.0f);
+  float p = mul(vc, (float)(L - 1));
+  float kf = fminf(floorf(p), (float)(L - 2));
+  TfPos r;
+  r.k = (int)kf;
+  r.tau = sub(p, kf);
+  r.one_m = sub(1.0f, r.tau);
+  return r;
+}
+__device__ __forceinline__ float lerp_rn(float lo, float hi, const TfPos& q) {
+  return add(mul(q.one_m, lo), mul(q.tau, hi));
+}
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;
+constexpr float kFrustumSlack = 1.3f;
+constexpr float kLambdaFloor = 0.1f;
+
+}  // namespace veg

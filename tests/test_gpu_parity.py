@@ -1,0 +1,360 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Bars: tile rectangles, instance keys, sort order and tile ranges bit-exact;
+images within 1e-4 max-abs per channel (pixels whose decisions straddle a
+threshold, flagged by the oracle, excluded and counted); gradients within a
+relative 1e-3 of the oracle's largest entry per tensor.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import veg_oracle as O
+from paper_2504_13339_gb300 import _lib, scenes as S
+from paper_2504_13339_gb300.render import SplatPipeline, VEGRender, lut_tensor
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def gpu_forward(g, cams, tfs, cull=True, capacity=None, bg=(0.0, 0.0, 0.0), tf_group=0,
+                stats=None):
+    p = SplatPipeline(g.n, cams, n_tf=len(tfs), capacity=capacity, tf_group=tf_group)
+    tens = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
+    luts = lut_tensor(tfs)
+    p.project(*tens, luts if cull else None)
+    p.bin_sort(want_keys=True)
+    st, m = p.status()
+    p.composite(luts, bg, stats=stats)
+    torch.cuda.synchronize()
+    return p, st, m, tens, luts
+
+
+def image_check(out_gpu, fwd):
+    ok = ~fwd["flag"]
+    err = np.abs(out_gpu - fwd["out"])
+    assert np.all(err[ok] <= IMG_TOL), float(err[ok].max())
+    assert fwd["flag"].mean() <= 1e-3
+    return float(err[ok].max())
+
+
+def grad_check(got, ref, name):
+    scale = np.abs(ref).max()
+    rel = np.abs(got - ref).max() / max(scale, 1e-30)
+    assert rel <= GRAD_TOL, (name, rel)
+    return rel
+
+
+def small_multiview():
+    g = S.uniform_gaussians(2000, 31, logscale_mean=-3.0, logscale_std=0.4)
+    g.logscale_w[:, 3] = np.random.default_rng(32).uniform(0.3, 1.0, g.n)
+    cams = S.orbit_cameras(3, 33, 100, 70)  # ragged: 7 x 5 tiles of which the last are partial
+    return g, cams
+
+
+# ----------------------------------------------------------------------------
+# projection and binning: bit-exact
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scene", ["plain", "multiview"])
+def test_projection_and_bins_bit_exact(scene):
+    if scene == "plain":
+        g, cams, tfs = S.plain_scene()
+    else:
+        g, cams = small_multiview()
+        tfs = S.bump_tfs(3, 34)
+    p, st, m, _, _ = gpu_forward(g, cams, tfs)
+    proj = [O.project32(c, g, tfs) for c in cams]
+    geo = p.geo.cpu().numpy().reshape(len(cams), g.n, 4)
+    aux = p.aux.cpu().numpy().reshape(len(cams), g.n, 4)
+    tiles = p.tiles.cpu().numpy().reshape(len(cams), g.n)
+    rect = p.rect.cpu().numpy().reshape(len(cams), g.n, 4)
+    for v, pr in enumerate(proj):
+        assert np.array_equal(tiles[v], pr["count"])
+        assert np.array_equal(rect[v], pr["rect"])
+        assert np.array_equal(geo[v].view(np.uint32), pr["geo"].view(np.uint32))
+        assert np.array_equal(aux[v].view(np.uint32), pr["aux"].view(np.uint32))
+    bins = O.bin_sort(proj, cams)
+    M = bins["keys"].size
+    assert st == _lib.VEG_OK and m == M
+    assert np.array_equal(p.keys[:M].cpu().numpy().view(np.uint64), bins["keys"])
+    assert np.array_equal(p.vals[:M].cpu().numpy().astype(np.uint32), bins["vals"])
+    rng = p.ranges.cpu().numpy().reshape(len(cams), -1, 2)
+    assert np.array_equal(rng, bins["ranges"])
+
+
+def test_capacity_overflow_keeps_front_instances():
+    g, cams, tfs = S.plain_scene()
+    proj = [O.project32(cams[0], g, tfs)]
+    M = int(proj[0]["count"].sum())
+    cap = M // 2
+    p, st, m, _, _ = gpu_forward(g, cams, tfs, capacity=cap)
+    assert st == _lib.VEG_ERR_CAPACITY
+    assert m == M
+    # expected: pairs emitted in (depth, index) order, first `cap` kept, stable by tile
+    pr = proj[0]
+    order = np.lexsort((np.arange(g.n), pr["geo"][:, 2]))
+    keys, vals = [], []
+    for i in order:
+        if pr["count"][i] == 0:
+            continue
+        x0, y0, x1, y1 = pr["rect"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                keys.append(ty * cams[0].tiles_x + tx)
+                vals.append(i)
+    keys, vals = np.array(keys[:cap]), np.array(vals[:cap])
+    srt = np.argsort(keys, kind="stable")
+    assert np.array_equal(p.vals[:cap].cpu().numpy(), vals[srt])
+
+
+def test_empty_and_fully_culled():
+    g, cams, tfs = S.plain_scene()
+    empty = g.subset(np.arange(0))
+    p, st, m, _, _ = gpu_forward(empty, cams, tfs, capacity=16, bg=(0.1, 0.2, 0.3))
+    out = p.out.cpu().numpy()
+    assert m == 0 and np.allclose(out[..., :3], [0.1, 0.2, 0.3]) and np.all(out[..., 3] == 1)
+    clear = S.constant_tf([1, 1, 1, 0])[None]
+    p, st, m, _, _ = gpu_forward(g, cams, clear)
+    assert m == 0 and np.all(p.ranges.cpu().numpy() == 0)
+    assert np.all(p.out.cpu().numpy()[..., 3] == 1) and np.all(p.n_contrib.cpu().numpy() == 0)
+
+
+def test_degenerate_gaussians():
+    """Behind the camera, on the near plane, zero quaternion, huge (covers
+    every tile), sub-pixel, off screen."""
+    cam = S.look_at_camera((0, 0, 3), 80, 48)
+    mv = np.array([[0, 0, 3.5, .5], [0, 0, 2.85, .5], [0.1, 0, 0, .5], [0, 0, 0, .6],
+                   [0.2, 0.1, 0.5, .7], [9.0, 0, 0, .5], [-0.3, 0.2, -0.5, .4]], np.float32)
+    ls = np.array([[-3, -3, -3, 1], [-3, -3, -3, 1], [-2, -2, -2, 1], [0.5, 0.5, 0.5, .5],
+                   [-9, -9, -9, 1], [-2, -2, -2, 1], [-2.5, -1.5, -3.5, .9]], np.float32)
+    q = np.array([[1, 0, 0, 0], [1, 0, 0, 0], [0, 0, 0, 0], [1, 0, 0, 0], [0.3, 0.2, 0.1, 0.9],
+                  [1, 0, 0, 0], [0.5, -0.5, 0.5, 0.5]], np.float32)
+    g = S.Gaussians(mv, ls, q)
+    tfs = np.stack([S.constant_tf([0.9, 0.5, 0.2, 0.8]), S.bump_tf(35)])
+    p, st, m, _, _ = gpu_forward(g, [cam], tfs)
+    proj, bins, fwd = O.render([cam], g, tfs)
+    assert np.array_equal(p.tiles.cpu().numpy(), proj[0]["count"])
+    assert proj[0]["count"][3] == cam.tiles_x * cam.tiles_y  # the huge one covers everything
+    assert np.all(proj[0]["count"][[0, 1, 2, 5]] == 0)
+    assert np.array_equal(p.vals[:m].cpu().numpy().astype(np.uint32), bins["vals"])
+    image_check(p.out.cpu().numpy(), fwd)
+
+
+# ----------------------------------------------------------------------------
+# compositing
+# ----------------------------------------------------------------------------
+
+def test_plain_render_matches_oracle():
+    g, cams, tfs = S.plain_scene()
+    stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+    p, st, m, _, _ = gpu_forward(g, cams, tfs, stats=stats)
+    proj, bins, fwd = O.render(cams, g, tfs)
+    image_check(p.out.cpu().numpy(), fwd)
+    nc_ok = ~fwd["flag"]
+    assert np.array_equal(p.n_contrib.cpu().numpy()[nc_ok], fwd["n_contrib"][nc_ok])
+    got = stats.cpu().numpy()
+    ref = np.array([fwd["stats"]["visited"], fwd["stats"]["alpha_evals"], fwd["stats"]["blended"]])
+    assert np.all(np.abs(got - ref) <= 1e-4 * ref + 2), (got, ref)
+
+
+def test_multiview_multitf_background_matches_oracle():
+    g, cams = small_multiview()
+    tfs = S.bump_tfs(3, 36)
+    bg = (0.2, 0.05, 0.4)
+    p, st, m, _, _ = gpu_forward(g, cams, tfs, bg=bg)
+    proj, bins, fwd = O.render(cams, g, tfs, bg=bg)
+    image_check(p.out.cpu().numpy(), fwd)
+
+
+def test_batched_tfs_equal_single_tf_renders_bit_exact():
+    g, cams, _ = S.plain_scene()
+    tfs = S.bump_tfs(8, 37)
+    ref = None
+    for grp in (1, 2, 4, 8):
+        p, *_ = gpu_forward(g, cams, tfs, tf_group=grp)
+        o = p.out.cpu().numpy()
+        ref = o if ref is None else ref
+        assert np.array_equal(o.view(np.uint32), ref.view(np.uint32)), grp
+    for t in range(8):
+        p, *_ = gpu_forward(g, cams, tfs[t:t + 1])
+        assert np.array_equal(p.out.cpu().numpy()[0, 0].view(np.uint32), ref[0, t].view(np.uint32))
+
+
+def test_tf_cull_is_lossless_bit_exact():
+    g, cams, _ = S.plain_scene()
+    tfs = S.bump_tfs(2, 38)
+    a, *_ = gpu_forward(g, cams, tfs, cull=True)
+    b, *_ = gpu_forward(g, cams, tfs, cull=False)
+    assert np.array_equal(a.out.cpu().numpy().view(np.uint32), b.out.cpu().numpy().view(np.uint32))
+
+
+def test_render_entry_point_equals_pipeline():
+    g, cams, tfs = S.plain_scene()
+    p, st, m, tens, luts = gpu_forward(g, cams, tfs)
+    ws = torch.empty(_lib.veg_render_workspace_size(g.n, 1, 4 * m, 128, 128), dtype=torch.uint8,
+                     device="cuda")
+    out = torch.empty_like(p.out)
+    nc = torch.empty_like(p.n_contrib)
+    _lib.veg_render(_lib.cameras(cams), _lib.gaussians(*tens), _lib.tf_desc(luts), (0, 0, 0),
+                    4 * m, ws, out, nc)
+    assert _lib.veg_sync_status(ws) == (_lib.VEG_OK, m)
+    assert torch.equal(out, p.out) and torch.equal(nc, p.n_contrib)
+
+
+# ----------------------------------------------------------------------------
+# backward
+# ----------------------------------------------------------------------------
+
+def test_backward_matches_oracle():
+    g, cams = small_multiview()
+    g = g.subset(np.arange(700))
+    tfs = S.bump_tfs(2, 39)
+    bg = (0.1, 0.0, 0.2)
+    p, st, m, tens, luts = gpu_forward(g, cams, tfs, bg=bg)
+    proj, bins, fwd = O.render(cams, g, tfs, bg=bg, record=True)
+    image_check(p.out.cpu().numpy(), fwd)
+    dout = np.random.default_rng(40).standard_normal(fwd["out"].shape)
+    grads = [torch.zeros_like(t) for t in tens]
+    p.backward(dev(dout.astype(np.float32)), *grads)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd(proj, cams, bins, tfs, bg, fwd, dout)
+    got2 = p.grad2d.cpu().numpy().reshape(len(cams), g.n, 8)
+    for k, name in enumerate(["du_x", "du_y", "da", "db", "dc", "dv", "dw"]):
+        grad_check(got2[..., k], g2[..., k], name)
+    gm, gl, gq = O.params_grad(cams, g, proj, g2)
+    grad_check(grads[0].cpu().numpy()[:, :3], gm[:, :3], "mean")
+    grad_check(grads[0].cpu().numpy()[:, 3], gm[:, 3], "v")
+    grad_check(grads[1].cpu().numpy()[:, :3], gl[:, :3], "logscale")
+    grad_check(grads[1].cpu().numpy()[:, 3], gl[:, 3], "w")
+    grad_check(grads[2].cpu().numpy(), gq, "quat")
+
+
+def test_autograd_function_and_sigmoid_chain():
+    g, cams, tfs = S.plain_scene()
+    g = g.subset(np.arange(1500))
+    luts = lut_tensor(tfs)
+    p = SplatPipeline(g.n, cams, n_tf=1)
+    mu = dev(g.mean_v[:, :3]).requires_grad_()
+    v_raw = dev(np.log(g.mean_v[:, 3:] + 1e-3) - np.log(1.001 - g.mean_v[:, 3:])).requires_grad_()
+    ls = dev(g.logscale_w).requires_grad_()
+    q = dev(g.quat).requires_grad_()
+    mean_v = torch.cat([mu, torch.sigmoid(v_raw)], 1)
+    out = VEGRender.apply(mean_v, ls, q, p, luts, (0.0, 0.0, 0.0))
+    w = torch.randn_like(out)
+    (out * w).sum().backward()
+    gm, gl, gq = (torch.zeros_like(t) for t in (mean_v, ls, q))
+    p.backward(w.contiguous(), gm, gl, gq)
+    # float atomics make the two backward runs differ in the last bits
+    close = lambda x, y: bool(((x - y).abs() <= 1e-5 * y.abs().max() + 1e-4 * y.abs()).all())
+    assert close(mu.grad, gm[:, :3]) and close(ls.grad, gl) and close(q.grad, gq)
+    s = torch.sigmoid(v_raw).detach()
+    assert close(v_raw.grad, gm[:, 3:] * s * (1 - s))
+
+
+def test_l1_loss_matches_oracle():
+    rng = np.random.default_rng(41)
+    out = rng.uniform(0, 1, (2, 3, 37, 29, 4)).astype(np.float32)
+    tgt = rng.uniform(0, 1, out.shape).astype(np.float32)
+    tgt[0, 0, 0, 0, :3] = out[0, 0, 0, 0, :3]  # sign(0) = 0
+    ref, gref = O.l1_loss(out, tgt)
+    grad = torch.empty(out.shape, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    ws = torch.empty(_lib.veg_l1_loss_workspace_size(), dtype=torch.uint8, device="cuda")
+    _lib.veg_l1_loss(dev(out), dev(tgt), out.size // 4, grad, loss, ws)
+    assert abs(loss.item() - ref) <= 1e-6 * max(1.0, ref)
+    assert np.allclose(grad.cpu().numpy(), gref, rtol=1e-6, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# the training-step workload at full size: 1M Gaussians, 1024^2, 4 TFs
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def train_full():
+    g, tgt_g, cams, tfs = S.train_scene()
+    p, st, m, tens, luts = gpu_forward(g, cams, tfs, capacity=16_000_000)
+    assert st == _lib.VEG_OK
+    return g, cams, tfs, p, m, tens, luts
+
+
+def test_full_size_projection_bit_exact(train_full):
+    g, cams, tfs, p, m, _, _ = train_full
+    pr = O.project32(cams[0], g, tfs)
+    assert np.array_equal(p.tiles.cpu().numpy(), pr["count"])
+    assert np.array_equal(p.rect.cpu().numpy(), pr["rect"])
+    assert np.array_equal(p.geo.cpu().numpy().view(np.uint32), pr["geo"].view(np.uint32))
+    assert m == int(pr["count"].sum())
+
+
+def _sample_tiles(p, k, seed):
+    lens = np.diff(p.ranges.cpu().numpy(), axis=1).ravel()
+    dense = list(np.argsort(lens)[-3:])
+    rng = np.random.default_rng(seed)
+    occupied = np.nonzero(lens)[0]
+    return sorted(set(dense) | set(rng.choice(occupied, k, replace=False).tolist()))
+
+
+def test_full_size_sampled_tiles_bit_exact_and_images(train_full):
+    g, cams, tfs, p, m, _, _ = train_full
+    pr = O.project32(cams[0], g, tfs)
+    tiles = _sample_tiles(p, 5, 42)
+    lists = O.tile_lists(pr, cams[0], tiles)
+    rng = p.ranges.cpu().numpy()
+    vals = p.vals.cpu().numpy()
+    for t in tiles:
+        lo, hi = rng[t]
+        assert np.array_equal(vals[lo:hi].astype(np.int64), lists[t]), t
+    bins = O.bins_from_lists([lists], 1, cams[0].tiles_x * cams[0].tiles_y)
+    fwd = O.composite_fwd([pr], cams, bins, tfs, tiles=tiles)
+    out = p.out.cpu().numpy()
+    for t in tiles:
+        px, py = O._tile_pixels(cams[0], t)
+        ok = ~fwd["flag"][0][:, py, px]
+        err = np.abs(out[0][:, py, px] - fwd["out"][0][:, py, px])
+        assert np.all(err[ok] <= IMG_TOL), (t, float(err[ok].max()))
+
+
+def test_full_size_crop_gradients(train_full):
+    """Gradients of a loss on a 64x64 crop, for the full 1M-Gaussian scene."""
+    g, cams, tfs, p, m, tens, luts = train_full
+    cam = cams[0]
+    x0 = y0 = 480
+    tiles = [(y0 // 16 + j) * cam.tiles_x + x0 // 16 + i for j in range(4) for i in range(4)]
+    pr = O.project32(cam, g, tfs)
+    lists = O.tile_lists(pr, cam, tiles)
+    bins = O.bins_from_lists([lists], 1, cam.tiles_x * cam.tiles_y)
+    fwd = O.composite_fwd([pr], cams, bins, tfs, tiles=tiles, record=True)
+    dout = np.zeros(fwd["out"].shape)
+    dout[..., y0:y0 + 64, x0:x0 + 64, :] = np.random.default_rng(43).standard_normal(
+        (1, len(tfs), 64, 64, 4))
+    grads = [torch.zeros_like(t) for t in tens]
+    p.backward(dev(dout.astype(np.float32)), *grads)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd([pr], cams, bins, tfs, (0, 0, 0), fwd, dout, tiles=tiles)
+    touched = np.nonzero(np.abs(g2[0]).sum(1))[0]
+    assert touched.size > 100
+    gs = g.subset(touched)
+    prs = {k: (v[touched] if isinstance(v, np.ndarray) and v.shape[:1] == (g.n,) else v)
+           for k, v in pr.items()}
+    gm, gl, gq = O.params_grad(cams, gs, [prs], g2[:, touched])
+    got = [t.cpu().numpy() for t in grads]
+    others = np.setdiff1d(np.arange(g.n), touched)
+    assert np.all(got[0][others] == 0) and np.all(got[2][others] == 0)
+    grad_check(got[0][touched, :3], gm[:, :3], "mean")
+    grad_check(got[0][touched, 3], gm[:, 3], "v")
+    grad_check(got[1][touched, :3], gl[:, :3], "logscale")
+    grad_check(got[1][touched, 3], gl[:, 3], "w")
+    grad_check(got[2][touched], gq, "quat")
