@@ -38,8 +38,15 @@ FP32_LANES_PER_SM = 128
 
 # FP32 operations per work unit (an FMA counts 2), taken from the kernels'
 # per-pair arithmetic; the instrumented kernels count the units.
-FWD_FLOPS = {"visited": 11, "alpha": 3, "blended": 10}
-BWD_FLOPS = {"replayed": 11, "alpha": 3, "blended": 21, "free": 7, "grad": 26}
+# The "visited"/"replayed" counts are the method's own pair counts; pairs
+# that the per-warp lists skip cost nothing and carry no flops.
+FWD_FLOPS = {"visited": 0, "iterated": 12, "evaluated": 2, "alpha": 3, "blended": 10}
+BWD_FLOPS = {"replayed": 0, "iterated": 12, "evaluated": 2, "alpha": 3, "blended": 21,
+             "free": 7, "grad": 26}
+
+
+def flops_of(model, counts):
+    return float(sum(model[k] * float(c) for k, c in zip(model, counts)))
 
 
 def parse():
@@ -252,19 +259,18 @@ def run_gpu(args):
     d2h = 4
 
     # ---- work counts for the roofline (instrumented launches, untimed) -----
-    fst = torch.zeros(3, dtype=torch.int64, device=device)
-    bst = torch.zeros(5, dtype=torch.int64, device=device)
+    fst = torch.zeros(len(FWD_FLOPS), dtype=torch.int64, device=device)
+    bst = torch.zeros(len(BWD_FLOPS), dtype=torch.int64, device=device)
     p.project(*tens, luts)
     p.bin_sort()
     p.composite(luts, stats=fst)
     p.l1(target)
     p.backward_2d(p.loss_grad, stats=bst)
     torch.cuda.synchronize()
-    f = fst.cpu().numpy().astype(float)
-    b = bst.cpu().numpy().astype(float)
-    fwd_flops = FWD_FLOPS["visited"] * f[0] + FWD_FLOPS["alpha"] * f[1] + FWD_FLOPS["blended"] * f[2]
-    bwd_flops = (BWD_FLOPS["replayed"] * b[0] + BWD_FLOPS["alpha"] * b[1] +
-                 BWD_FLOPS["blended"] * b[2] + BWD_FLOPS["free"] * b[3] + BWD_FLOPS["grad"] * b[4])
+    f = fst.cpu().numpy()
+    b = bst.cpu().numpy()
+    fwd_flops = flops_of(FWD_FLOPS, f)
+    bwd_flops = flops_of(BWD_FLOPS, b)
     props = torch.cuda.get_device_properties(device)
     peaks = {}
     try:
@@ -300,10 +306,10 @@ def run_gpu(args):
         "mpix_per_s": round(mpix, 2),
         "stages_ms": {"composite_fwd": round(fwd_avg, 4), "composite_bwd": round(bwd_avg, 4),
                       "other": round(total_ms / K - fwd_avg - bwd_avg, 4)},
-        "work": {"fwd": {"visited": int(f[0]), "alpha": int(f[1]), "blended": int(f[2])},
-                 "bwd": {"replayed": int(b[0]), "alpha": int(b[1]), "blended": int(b[2]),
-                         "free": int(b[3]), "grad": int(b[4])},
-                 "fwd_tflops": round(fwd_flops / (fwd_avg * 1e-3) / 1e12, 3)},
+        "work": {"fwd": dict(zip(FWD_FLOPS, (int(x) for x in f))),
+                 "bwd": dict(zip(BWD_FLOPS, (int(x) for x in b))),
+                 "fwd_tflops": round(fwd_flops / (fwd_avg * 1e-3) / 1e12, 3),
+                 "bwd_tflops": round(bwd_flops / (bwd_avg * 1e-3) / 1e12, 3)},
         "clocks": clk,
         "e2e": {"value": round(world * K / (e2e_ms * 1e-3), 3), "unit": "steps/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},

@@ -164,9 +164,11 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  * [V][n_tf][H][W] = 1 + list position of the last blended splat (0 if none).
  * The scene representation is TF-independent, so one sort serves every TF.
  * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default).
- * bg: host float[3].  stats: optional device uint64[3] accumulating
- * (visited pixel-splat pairs, alpha evaluations, blended pairs), NULL to skip
- * the instrumented kernel.  n is the per-view record count used by
+ * bg: host float[3].  stats: optional device uint64[5] accumulating
+ * (visited pixel-splat pairs -- every pair reached before the pixel stops --,
+ * pairs walked by the kernel after its culling, pairs above the exponent
+ * cutoff -- below it no TF of the group can reach alpha >= 1/255 --, alpha
+ * evaluations, blended pairs), NULL to skip the instrumented kernel.  n is the per-view record count used by
  * veg_project.
  */
 veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
@@ -191,10 +193,10 @@ veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
  * dw, 0) (overwritten).  workspace >= veg_composite_bwd_workspace_size.
  * If grad_mean_v, grad_logscale_w and grad_quat are all NULL, only grad2d
  * (then required) is computed; veg_project_bwd completes the chain.
- * stats: optional device uint64[5] accumulating (replayed pixel-splat pairs,
- * alpha evaluations, blended pairs, blended pairs below the 0.99 clamp,
- * pairs with a nonzero screen-space gradient); NULL skips the instrumented
- * kernel.
+ * stats: optional device uint64[7] accumulating (replayed pixel-splat pairs,
+ * pairs walked after culling, pairs above the exponent cutoff, alpha
+ * evaluations, blended pairs, blended pairs below the 0.99 clamp, pairs with
+ * a nonzero screen-space gradient); NULL skips the instrumented kernel.
  */
 veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views, size_t* bytes);
 veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,

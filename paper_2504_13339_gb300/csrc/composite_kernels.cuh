@@ -1,0 +1,584 @@
+// Compositing kernels: front-to-back blending (Eq. 1) of depth-sorted splats
+// per 16x16 tile for a group of transfer functions, and its backward pass.
+//
+// One CTA of 256 threads owns one (view, tile, TF group); each thread owns
+// one pixel and each warp an 8x4 pixel block.  The tile's list is staged in
+// batches of 256 splats through shared memory.  The stager evaluates every
+// splat's colour and opacity under each TF of the group once (linear
+// interpolation in TF tables held in shared memory), the exponent below which
+// no TF of the group can reach alpha = 1/255, and a conservative mask of the
+// warp blocks that the splat's visible ellipse can touch.  Each warp then
+// compacts the batch into its own list (ballots) and walks only that list,
+// so pairs that provably cannot blend cost nothing.  A pixel leaves once
+// every TF of the group has terminated (T (1 - alpha) < 1e-4); the block
+// stops staging once all its pixels have left.
+//
+// The per-pair arithmetic that decides skips, the 0.99 clamp and
+// termination uses explicitly rounded operations shared by the forward and
+// backward kernels, so the backward replays every forward decision bit for
+// bit.  Culling (cutoff, warp mask) only removes pairs whose alpha is
+// provably below 1/255, so it never changes a decision.
+#pragma once
+
+#include <algorithm>
+
+#include "veg_internal.cuh"
+
+namespace veg {
+
+namespace {
+
+constexpr int kBatch = 256;
+constexpr int kWarps = 8;
+
+// 2^x with the hardware approximation (ex2.approx.ftz), x = power * log2(e).
+__device__ __forceinline__ float gauss_of(float power) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(mul(power, 1.44269502162933349609375f)));
+  return fminf(y, 1.0f);
+}
+
+// power = -1/2 (a dx^2 + c dy^2) - b dx dy with (na, nb, nc) = (-a/2, -b, -c/2).
+__device__ __forceinline__ float power_of(float dx, float dy, float na, float nb, float nc) {
+  return __fmaf_rn(na, mul(dx, dx), __fmaf_rn(nc, mul(dy, dy), mul(nb, mul(dx, dy))));
+}
+
+// Lowest exponent at which some TF of the group can still reach alpha >=
+// 1/255: alpha = A w G <= max_t(A_t w) e^power, which stays below 1/255 for
+// power < ln(1/(255 max_t A_t w)).  The bound is lowered by 1e-3 to absorb
+// the float32 rounding of the exponent, the exp2 approximation and the log,
+// so every pair above it still meets the exact per-TF test and the skip
+// never changes a decision.  With max_t A_t w < 1/255 no pair can blend.
+__device__ __forceinline__ float power_cutoff(float max_aw) {
+  if (!(max_aw >= kAlphaMin)) return 1.0f;
+  return __logf(kAlphaMin / max_aw) - 1e-3f;
+}
+
+// Warp blocks (bit by*2+bx for the 8x4 block at tile-relative (8bx, 4by))
+// holding a pixel centre where the exponent can reach `cut`: the ellipse
+// d^T Q d <= -2 cut (Q = conic) has half extents sqrt(-2 cut Q^-1_xx) and
+// sqrt(-2 cut Q^-1_yy); they are widened by 0.2% + 0.02 px, far beyond the
+// float32 error of the per-pixel exponent.  An ill-conditioned conic keeps
+// every block (the exact per-pixel test then decides).
+__device__ __forceinline__ unsigned warp_block_mask(float rx, float ry, float a, float b, float c,
+                                                    float cut) {
+  if (!(cut < 0.0f)) return 0u;
+  const float det = a * c - b * b;
+  if (!(det > 1e-3f * a * c)) return 0xffu;
+  const float r2 = -2.0f * cut;
+  const float hx = sqrtf(r2 * c / det) * 1.002f + 0.02f;
+  const float hy = sqrtf(r2 * a / det) * 1.002f + 0.02f;
+  const float x0 = rx - hx, x1 = rx + hx, y0 = ry - hy, y1 = ry + hy;
+  unsigned m = 0u;
+#pragma unroll
+  for (int by = 0; by < 4; ++by) {
+    if (y1 < 4.0f * by || y0 > 4.0f * by + 3.0f) continue;
+#pragma unroll
+    for (int bx = 0; bx < 2; ++bx)
+      if (x1 >= 8.0f * bx && x0 <= 8.0f * bx + 7.0f) m |= 1u << (by * 2 + bx);
+  }
+  return m;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt_() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Compacts the batch positions whose mask has this warp's bit, in order.
+__device__ __forceinline__ int build_warp_list(const unsigned char* s_mask, unsigned char* list,
+                                               int cnt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt_();
+  int n = 0;
+  for (int c = 0; c < cnt; c += 32) {
+    const int j = c + lane;
+    const bool hit = j < cnt && ((s_mask[j] >> warp) & 1u);
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (hit) list[n + __popc(bal & lt)] = (unsigned char)j;
+    n += __popc(bal);
+  }
+  __syncwarp();
+  return n;
+}
+
+__device__ __forceinline__ void pixel_of(int tile, int tiles_x, int& px, int& py) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  px = (tile % tiles_x) * VEG_TILE + (w & 1) * 8 + (l & 7);
+  py = (tile / tiles_x) * VEG_TILE + (w >> 1) * 4 + (l >> 3);
+}
+
+struct CompArgs {
+  const float4* geo;
+  const float4* aux;
+  const uint32_t* vals;
+  const int2* ranges;
+  const float4* lut;
+  int lut_size, n_tf;
+  int width, height, tiles_x, tiles_per_view;
+  float bg0, bg1, bg2;
+};
+
+// Loads the TF tables of group [t0, t0+TG) into shared memory (missing
+// tables read as fully transparent).
+template <int TG>
+__device__ __forceinline__ void stage_luts(const CompArgs& A, int t0, float4* s_lut) {
+  const int L = A.lut_size;
+  for (int e = threadIdx.x; e < TG * L; e += blockDim.x) {
+    int t = e / L, k = e - t * L;
+    s_lut[e] = (t0 + t < A.n_tf) ? __ldg(&A.lut[(int64_t)(t0 + t) * L + k])
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Stages splat `i` of the tile list into batch slot threadIdx.x: geometry,
+// per-TF colour and A w (and, for the backward, slopes and A), the exponent
+// cutoff and the warp-block mask.  Returns the record index.
+template <int TG, bool BWD>
+__device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* s_lut,
+                                                float tx0, float ty0, float4* s_geo, float2* s_c,
+                                                float4* s_col, float4* s_slope, float* s_A,
+                                                unsigned char* s_mask) {
+  const int L = A.lut_size;
+  const int s = threadIdx.x;
+  const uint32_t g = A.vals[i];
+  const float4 ge = A.geo[g], au = A.aux[g];
+  s_geo[s] = make_float4(ge.x, ge.y, -0.5f * au.x, -au.y);
+  const TfPos q = tf_pos(au.w, L);
+  const float sl = (au.w >= 0.0f && au.w <= 1.0f) ? (float)(L - 1) : 0.0f;
+  float max_aw = 0.0f;
+#pragma unroll
+  for (int t = 0; t < TG; ++t) {
+    const float4 lo = s_lut[t * L + q.k], hi = s_lut[t * L + q.k + 1];
+    const float Aop = lerp_rn(lo.w, hi.w, q);
+    const float aw = mul(Aop, ge.w);
+    s_col[t * kBatch + s] =
+        make_float4(lerp_rn(lo.x, hi.x, q), lerp_rn(lo.y, hi.y, q), lerp_rn(lo.z, hi.z, q), aw);
+    if (BWD) {
+      s_slope[t * kBatch + s] = make_float4(sl * (hi.x - lo.x), sl * (hi.y - lo.y),
+                                            sl * (hi.z - lo.z), ge.w * sl * (hi.w - lo.w));
+      s_A[t * kBatch + s] = Aop;
+    }
+    max_aw = fmaxf(max_aw, aw);
+  }
+  const float cut = power_cutoff(max_aw);
+  s_c[s] = make_float2(-0.5f * au.z, cut);
+  s_mask[s] = (unsigned char)warp_block_mask(ge.x - tx0, ge.y - ty0, au.x, au.y, au.z, cut);
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+
+// stats (instrumented build): visited pairs (every pair reached before the
+// pixel's termination, the method's own count), iterated pairs (walked by
+// the warp lists), pairs above the cutoff, alpha evaluations, blended pairs.
+template <int TG, bool STATS>
+__global__ void __launch_bounds__(256)
+    composite_fwd_kernel(CompArgs A, float4* __restrict__ out, int32_t* __restrict__ n_contrib,
+                         unsigned long long* __restrict__ stats) {
+  extern __shared__ float4 s_lut[];  // [TG][L]
+  __shared__ float4 s_geo[kBatch];   // u_x, u_y, -a/2, -b
+  __shared__ float2 s_c[kBatch];     // -c/2, exponent cutoff
+  __shared__ float4 s_col[TG * kBatch];
+  __shared__ unsigned char s_mask[kBatch];
+  __shared__ unsigned char s_list[kWarps][kBatch];
+  const int tile = blockIdx.x, view = blockIdx.y, t0 = blockIdx.z * TG;
+  const int ntg = min(TG, A.n_tf - t0);
+  const int warp = threadIdx.x >> 5;
+  stage_luts<TG>(A, t0, s_lut);
+  int px, py;
+  pixel_of(tile, A.tiles_x, px, py);
+  const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
+  const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
+  const bool inside = px < A.width && py < A.height;
+  const float fx = (float)px, fy = (float)py;
+  const int2 rg = A.ranges[(int64_t)view * A.tiles_per_view + tile];
+  float T[TG], Cr[TG], Cg[TG], Cb[TG];
+  int last[TG];
+#pragma unroll
+  for (int t = 0; t < TG; ++t) {
+    T[t] = 1.0f;
+    Cr[t] = Cg[t] = Cb[t] = 0.0f;
+    last[t] = 0;
+  }
+  unsigned act = inside ? ((1u << ntg) - 1u) : 0u;
+  unsigned long long n_vis = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0;
+
+  for (int start = rg.x; start < rg.y; start += kBatch) {
+    if (__syncthreads_count(act != 0u) == 0) break;
+    const int cnt = min(kBatch, rg.y - start);
+    if ((int)threadIdx.x < cnt)
+      stage_splat<TG, false>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col, nullptr,
+                             nullptr, s_mask);
+    __syncthreads();
+    const int nw = build_warp_list(s_mask, s_list[warp], cnt);
+    const bool act0 = act != 0u;
+    int jstop = cnt;  // 1 + batch position where this pixel terminated
+    for (int k = 0; k < nw && act; ++k) {
+      const int j = s_list[warp][k];
+      const float4 sg = s_geo[j];
+      const float2 sc = s_c[j];
+      const float power = power_of(sub(sg.x, fx), sub(sg.y, fy), sg.z, sg.w, sc.x);
+      if (STATS) ++n_it;
+      if (power < sc.y || power > 0.0f) continue;
+      if (STATS) ++n_eval;
+      const float G = gauss_of(power);
+#pragma unroll
+      for (int t = 0; t < TG; ++t) {
+        if (!(act & (1u << t))) continue;
+        if (STATS) ++n_alpha;
+        const float4 c = s_col[t * kBatch + j];
+        const float alpha = fminf(kAlphaMax, mul(c.w, G));
+        if (alpha < kAlphaMin) continue;
+        const float test = mul(T[t], sub(1.0f, alpha));
+        if (test < kTMin) {
+          act &= ~(1u << t);
+          continue;
+        }
+        const float wgt = mul(alpha, T[t]);
+        Cr[t] = __fmaf_rn(c.x, wgt, Cr[t]);
+        Cg[t] = __fmaf_rn(c.y, wgt, Cg[t]);
+        Cb[t] = __fmaf_rn(c.z, wgt, Cb[t]);
+        T[t] = test;
+        last[t] = start + j - rg.x + 1;
+        if (STATS) ++n_blend;
+      }
+      if (STATS && !act) jstop = j + 1;
+    }
+    if (STATS && act0) n_vis += (unsigned long long)jstop;
+  }
+  if (inside) {
+#pragma unroll
+    for (int t = 0; t < TG; ++t) {
+      if (t >= ntg) break;
+      const int64_t o = (((int64_t)view * A.n_tf + t0 + t) * A.height + py) * A.width + px;
+      out[o] = make_float4(add(Cr[t], mul(T[t], A.bg0)), add(Cg[t], mul(T[t], A.bg1)),
+                           add(Cb[t], mul(T[t], A.bg2)), T[t]);
+      n_contrib[o] = last[t];
+    }
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_vis += __shfl_down_sync(0xffffffffu, n_vis, o);
+      n_it += __shfl_down_sync(0xffffffffu, n_it, o);
+      n_eval += __shfl_down_sync(0xffffffffu, n_eval, o);
+      n_alpha += __shfl_down_sync(0xffffffffu, n_alpha, o);
+      n_blend += __shfl_down_sync(0xffffffffu, n_blend, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats[0], n_vis);
+      atomicAdd(&stats[1], n_it);
+      atomicAdd(&stats[2], n_eval);
+      atomicAdd(&stats[3], n_alpha);
+      atomicAdd(&stats[4], n_blend);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+// Replays each pixel's forward blend front to back.  With S_i the running
+// sum of (c_j . g) alpha_j T_j over blended j <= i and K = C_final . g +
+// T_final (bg . g + g_T), the gradient of the loss w.r.t. alpha_i is
+//   dL/dalpha_i = T_i (c_i . g) - (K - S_i) / (1 - alpha_i),
+// the prefix form of the suffix sum over later splats (no division chain to
+// recover T).  Per splat, the seven screen-space gradients are reduced over
+// the warp, summed over warps in shared memory and added to the per-record
+// gradient buffer once per tile.
+//
+// stats (instrumented build): replayed pairs (list positions below the
+// pixel's last contribution), iterated pairs, pairs above the cutoff, alpha
+// evaluations, blended pairs, blended pairs below the clamp, pairs with a
+// nonzero screen-space gradient.
+template <int TG, bool STATS>
+__global__ void __launch_bounds__(256)
+    composite_bwd_kernel(CompArgs A, const float4* __restrict__ out,
+                         const int32_t* __restrict__ n_contrib, const float4* __restrict__ dout,
+                         float4* __restrict__ grad2d, unsigned long long* __restrict__ stats) {
+  unsigned long long n_rep = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0, n_free = 0,
+                     n_grad = 0;
+  extern __shared__ float4 smem[];
+  float4* s_lut = smem;                                     // [TG][L]
+  float4* s_col = s_lut + TG * A.lut_size;                  // [TG][kBatch]: rgb, A w
+  float4* s_slope = s_col + TG * kBatch;                    // [TG][kBatch]: drgb/dv, w dA/dv
+  float4* s_geo = s_slope + TG * kBatch;                    // [kBatch]: u, -a/2, -b
+  float2* s_c = reinterpret_cast<float2*>(s_geo + kBatch);  // [kBatch]: -c/2, cutoff
+  float* s_A = reinterpret_cast<float*>(s_c + kBatch);      // [TG][kBatch]: A
+  float* s_acc = s_A + TG * kBatch;                         // [8][kBatch]
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + 8 * kBatch);
+  unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + kBatch);
+  unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
+  __shared__ int s_maxnc;
+
+  const int tile = blockIdx.x, view = blockIdx.y, t0 = blockIdx.z * TG;
+  const int ntg = min(TG, A.n_tf - t0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* my_list = s_lists + warp * kBatch;
+  stage_luts<TG>(A, t0, s_lut);
+  for (int e = threadIdx.x; e < 8 * kBatch; e += 256) s_acc[e] = 0.0f;
+  if (threadIdx.x == 0) s_maxnc = 0;
+  int px, py;
+  pixel_of(tile, A.tiles_x, px, py);
+  const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
+  const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
+  const bool inside = px < A.width && py < A.height;
+  const float fx = (float)px, fy = (float)py;
+  const int2 rg = A.ranges[(int64_t)view * A.tiles_per_view + tile];
+
+  float T[TG], S[TG], K[TG], gr[TG], gg[TG], gb[TG];
+  int nc[TG];
+  int my_max = 0;
+#pragma unroll
+  for (int t = 0; t < TG; ++t) {
+    T[t] = 1.0f;
+    S[t] = 0.0f;
+    K[t] = 0.0f;
+    gr[t] = gg[t] = gb[t] = 0.0f;
+    nc[t] = 0;
+    if (inside && t < ntg) {
+      const int64_t o = (((int64_t)view * A.n_tf + t0 + t) * A.height + py) * A.width + px;
+      const float4 ov = out[o], dv4 = dout[o];
+      nc[t] = n_contrib[o];
+      gr[t] = dv4.x;
+      gg[t] = dv4.y;
+      gb[t] = dv4.z;
+      const float Tn = ov.w;
+      const float cr = ov.x - Tn * A.bg0, cg = ov.y - Tn * A.bg1, cb = ov.z - Tn * A.bg2;
+      K[t] = cr * dv4.x + cg * dv4.y + cb * dv4.z +
+             Tn * (A.bg0 * dv4.x + A.bg1 * dv4.y + A.bg2 * dv4.z + dv4.w);
+      my_max = max(my_max, nc[t]);
+    }
+  }
+  if (STATS) n_rep = (unsigned long long)my_max;
+  // loop bounds: a warp walks until its last pixel is done (all lanes take
+  // part in the reductions); the block stages until its last warp is done
+  int warp_max = my_max;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    warp_max = max(warp_max, __shfl_xor_sync(0xffffffffu, warp_max, o));
+  __syncthreads();
+  if (lane == 0) atomicMax(&s_maxnc, warp_max);
+  __syncthreads();
+  const int block_max = s_maxnc;
+
+  for (int start = rg.x; start < rg.x + block_max; start += kBatch) {
+    const int i = start + threadIdx.x;
+    const int cnt = min(kBatch, rg.y - start);
+    if (i < rg.y)
+      s_idx[threadIdx.x] = stage_splat<TG, true>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col,
+                                                 s_slope, s_A, s_mask);
+    __syncthreads();
+    const int nw = build_warp_list(s_mask, my_list, cnt);
+    for (int k = 0; k < nw; ++k) {
+      const int j = my_list[k];
+      const int idx = start + j - rg.x;  // list position
+      if (idx >= warp_max) break;
+      if (STATS) ++n_it;
+      float dG = 0.f, dvv = 0.f, dww = 0.f;
+      const float4 sg = s_geo[j];
+      const float2 scc = s_c[j];
+      const float sc = scc.x;
+      const float dx = sub(sg.x, fx), dy = sub(sg.y, fy);
+      const float power = power_of(dx, dy, sg.z, sg.w, sc);
+      float G = 0.f;
+      if (idx < my_max && power <= 0.0f && power >= scc.y) {
+        if (STATS) ++n_eval;
+        G = gauss_of(power);
+#pragma unroll
+        for (int t = 0; t < TG; ++t) {
+          if (idx >= nc[t]) continue;
+          if (STATS) ++n_alpha;
+          const float4 c = s_col[t * kBatch + j];
+          const float raw = mul(c.w, G);
+          const float alpha = fminf(kAlphaMax, raw);
+          if (alpha < kAlphaMin) continue;
+          if (STATS) {
+            ++n_blend;
+            n_free += (raw <= kAlphaMax);
+          }
+          const float wgt = mul(alpha, T[t]);
+          const float cgd = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
+          S[t] += cgd * wgt;
+          const float one_m = sub(1.0f, alpha);
+          const float dalpha = T[t] * cgd - __fdividef(K[t] - S[t], one_m);
+          const float4 sl = s_slope[t * kBatch + j];
+          dvv += wgt * (gr[t] * sl.x + gg[t] * sl.y + gb[t] * sl.z);
+          if (raw <= kAlphaMax) {
+            const float daw = dalpha * G;
+            dvv += daw * sl.w;
+            dww += daw * s_A[t * kBatch + j];
+            dG += dalpha * c.w;
+          }
+          T[t] = mul(T[t], one_m);
+        }
+      }
+      const float dp = dG * G;
+      if (STATS) n_grad += (dG != 0.f);
+      const bool nz = (dp != 0.f) || (dvv != 0.f) || (dww != 0.f);
+      if (__any_sync(0xffffffffu, nz)) {
+        float v0 = dp * (2.0f * sg.z * dx + sg.w * dy);
+        float v1 = dp * (2.0f * sc * dy + sg.w * dx);
+        float v2 = dp * (-0.5f * dx * dx);
+        float v3 = dp * (-dx * dy);
+        float v4 = dp * (-0.5f * dy * dy);
+        float v5 = dvv, v6 = dww;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+          v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+          v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+          v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+          v4 += __shfl_xor_sync(0xffffffffu, v4, o);
+          v5 += __shfl_xor_sync(0xffffffffu, v5, o);
+          v6 += __shfl_xor_sync(0xffffffffu, v6, o);
+        }
+        if (lane == 0) {
+          atomicAdd(&s_acc[0 * kBatch + j], v0);
+          atomicAdd(&s_acc[1 * kBatch + j], v1);
+          atomicAdd(&s_acc[2 * kBatch + j], v2);
+          atomicAdd(&s_acc[3 * kBatch + j], v3);
+          atomicAdd(&s_acc[4 * kBatch + j], v4);
+          atomicAdd(&s_acc[5 * kBatch + j], v5);
+          atomicAdd(&s_acc[6 * kBatch + j], v6);
+        }
+      }
+    }
+    __syncthreads();
+    if (i < rg.y) {
+      float a[7];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        a[k] = s_acc[k * kBatch + threadIdx.x];
+        s_acc[k * kBatch + threadIdx.x] = 0.0f;
+        any |= (a[k] != 0.0f);
+      }
+      if (any) {
+        float4* dst = grad2d + 2 * (int64_t)s_idx[threadIdx.x];
+        red_add_v4(dst, a[0], a[1], a[2], a[3]);
+        red_add_v4(dst + 1, a[4], a[5], a[6], 0.0f);
+      }
+    }
+    __syncthreads();
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_rep += __shfl_down_sync(0xffffffffu, n_rep, o);
+      n_it += __shfl_down_sync(0xffffffffu, n_it, o);
+      n_eval += __shfl_down_sync(0xffffffffu, n_eval, o);
+      n_alpha += __shfl_down_sync(0xffffffffu, n_alpha, o);
+      n_blend += __shfl_down_sync(0xffffffffu, n_blend, o);
+      n_free += __shfl_down_sync(0xffffffffu, n_free, o);
+      n_grad += __shfl_down_sync(0xffffffffu, n_grad, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&stats[0], n_rep);
+      atomicAdd(&stats[1], n_it);
+      atomicAdd(&stats[2], n_eval);
+      atomicAdd(&stats[3], n_alpha);
+      atomicAdd(&stats[4], n_blend);
+      atomicAdd(&stats[5], n_free);
+      atomicAdd(&stats[6], n_grad);
+    }
+  }
+}
+
+size_t bwd_smem_bytes(int TG, int L) {
+  // lut, col + slope, geo, (c, cutoff), A, acc[8], idx, mask, warp lists
+  return (size_t)TG * L * 16 + (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
+         (size_t)kBatch * 8 + (size_t)TG * kBatch * 4 + (size_t)8 * kBatch * 4 +
+         (size_t)kBatch * 4 + (size_t)kBatch + (size_t)kWarps * kBatch;
+}
+
+int pick_group(int tf_group, int n_tf, bool bwd) {
+  int g = tf_group;
+  if (g <= 0) g = std::min(n_tf, 4);
+  if (g <= 1) return 1;
+  if (g <= 2) return 2;
+  if (g <= 4 || bwd) return 4;
+  return 8;
+}
+
+CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
+                   const uint32_t* vals, const int2* ranges, veg_tf tf, const float* bg) {
+  CompArgs A;
+  A.geo = geo;
+  A.aux = aux;
+  A.vals = vals;
+  A.ranges = ranges;
+  A.lut = reinterpret_cast<const float4*>(tf.lut);
+  A.lut_size = tf.lut_size;
+  A.n_tf = tf.n_tf;
+  A.width = cams[0].width;
+  A.height = cams[0].height;
+  A.tiles_x = tiles_x_of(A.width);
+  A.tiles_per_view = A.tiles_x * tiles_x_of(A.height);
+  A.bg0 = bg ? bg[0] : 0.f;
+  A.bg1 = bg ? bg[1] : 0.f;
+  A.bg2 = bg ? bg[2] : 0.f;
+  return A;
+}
+
+// Allows `dyn` bytes of dynamic shared memory for `kern` and prefers the
+// largest shared-memory carveout (once per size increase); refuses sizes
+// beyond the 227 KB a CTA may hold.
+template <typename K>
+veg_status prepare_smem(K kern, size_t dyn, size_t* configured) {
+  if (dyn <= *configured) return VEG_OK;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return VEG_ERR_CUDA;
+  if (fa.sharedSizeBytes + dyn > 227 * 1024) return VEG_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return VEG_ERR_UNSUPPORTED;
+  *configured = dyn;
+  return VEG_OK;
+}
+
+template <int TG, bool STATS>
+veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc,
+                        unsigned long long* stats, cudaStream_t stream) {
+  const size_t smem = (size_t)TG * A.lut_size * sizeof(float4);
+  auto kern = composite_fwd_kernel<TG, STATS>;
+  static size_t configured = 0;
+  veg_status st = prepare_smem(kern, smem, &configured);
+  if (st != VEG_OK) return st;
+  dim3 grid((unsigned)A.tiles_per_view, (unsigned)n_views, (unsigned)((A.n_tf + TG - 1) / TG));
+  kern<<<grid, 256, smem, stream>>>(A, out, nc, stats);
+  count_launch();
+  return launch_status();
+}
+
+template <int TG, bool STATS>
+veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const int32_t* nc,
+                        const float4* dout, float4* grad2d, unsigned long long* stats,
+                        cudaStream_t stream) {
+  const size_t smem = bwd_smem_bytes(TG, A.lut_size);
+  auto kern = composite_bwd_kernel<TG, STATS>;
+  static size_t configured = 0;
+  veg_status st = prepare_smem(kern, smem, &configured);
+  if (st != VEG_OK) return st;
+  dim3 grid((unsigned)A.tiles_per_view, (unsigned)n_views, (unsigned)((A.n_tf + TG - 1) / TG));
+  kern<<<grid, 256, smem, stream>>>(A, out, nc, dout, grad2d, stats);
+  count_launch();
+  return launch_status();
+}
+
+}  // namespace
+
+}  // namespace veg
