@@ -143,6 +143,41 @@ veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int64_t n,
                         int32_t* tile_ranges, cudaStream_t stream);
 
 /*
+ * veg_bin_sort_static -- veg_bin_sort without any memory from the caller
+ * beyond inputs and outputs.  The paper has no counterpart; this exists for
+ * callers that cannot allocate device memory: code that runs while another
+ * component holds a CUDA stream capture open (cudaMalloc is not allowed
+ * then), real-time render loops that must never enter the driver's
+ * allocator, and plug-ins whose host application owns every device
+ * allocation.  It runs the same kernels as veg_bin_sort with their scratch in
+ * one fixed 16 MiB device array compiled into the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   Size limit: the scratch needed is about 20 bytes per record (n_views * n)
+ *   plus 12 bytes per instance of `capacity` plus 1 KiB per 4096 items of the
+ *   larger of the two (e.g. 65,536 records with a capacity of 1,000,000 fit);
+ *   a request needing more than 16 MiB returns VEG_ERR_UNSUPPORTED before
+ *   anything is launched.  Nothing is allocated or freed, by this library or
+ *   any routine it calls.
+ *   Outputs: vals, keys (optional), tile_ranges exactly as veg_bin_sort;
+ *   n_instances (device int64, optional) receives the instance count M, and
+ *   M > capacity means the binning overflowed (only the first `capacity`
+ *   instances were binned).  There is no workspace header to pass to
+ *   veg_sync_status.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (with that device current); make that first call before any stream
+ *   capture begins.
+ *   Sharing: every call on a device uses the same array, which keeps the
+ *   previous call's contents; each call writes every scratch word before it
+ *   reads it, so no clearing is needed.  Calls whose work overlaps on the GPU
+ *   (other streams, other host threads) race on the array: serialise them.
+ */
+veg_status veg_bin_sort_static(const veg_camera* cams, int32_t n_views, int64_t n,
+                               const float* splat_geo, const int32_t* tiles_touched,
+                               const int16_t* rect, int64_t capacity, uint64_t* keys,
+                               uint32_t* vals, int32_t* tile_ranges, int64_t* n_instances,
+                               cudaStream_t stream);
+
+/*
  * veg_sync_status -- waits for `stream`, then reads the status header of a
  * bin_sort / render workspace.  Writes the instance count M (even when it
  * exceeded the capacity) to *n_instances (host, may be NULL).  Returns

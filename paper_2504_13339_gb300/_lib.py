@@ -55,6 +55,8 @@ _SIGS = {
     "veg_bin_sort_workspace_size": (ctypes.c_int, [_I64, _I32, _I64, _I32, _I32,
                                                    ctypes.POINTER(_SZ)]),
     "veg_bin_sort": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, _SZ, _I64, _P, _P, _P, _P]),
+    "veg_bin_sort_static": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _I64, _P, _P, _P, _P,
+                                           _P]),
     "veg_sync_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I64)]),
     "veg_composite_fwd": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, veg_tf, _P, _I32, _P,
                                          _P, _P, _P]),
@@ -158,6 +160,15 @@ def veg_bin_sort(cams, n, splat_geo, tiles_touched, rect, workspace, capacity, k
            load().veg_bin_sort(cams, len(cams), n, _ptr(splat_geo), _ptr(tiles_touched),
                                _ptr(rect), _ptr(workspace), workspace.numel(), capacity,
                                _ptr(keys), _ptr(vals), _ptr(tile_ranges), _stream(stream)))
+
+
+def veg_bin_sort_static(cams, n, splat_geo, tiles_touched, rect, capacity, keys, vals,
+                        tile_ranges, n_instances, stream=None):
+    """veg_bin_sort with the library's fixed device scratch (no workspace);
+    returns the raw status so callers can see VEG_ERR_UNSUPPORTED."""
+    return load().veg_bin_sort_static(cams, len(cams), n, _ptr(splat_geo), _ptr(tiles_touched),
+                                      _ptr(rect), capacity, _ptr(keys), _ptr(vals),
+                                      _ptr(tile_ranges), _ptr(n_instances), _stream(stream))
 
 
 def veg_sync_status(workspace, stream=None):

@@ -537,3 +537,76 @@ extern "C" veg_status veg_sync_status(const void* workspace, cudaStream_t stream
   if (n_instances) *n_instances = (int64_t)h.n_instances;
   return (h.flags & veg::FLAG_CAPACITY) ? VEG_ERR_CAPACITY : VEG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free binning: the same kernels with their scratch in a fixed
+// device array instead of a caller workspace.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace veg {
+namespace {
+
+// 16 MiB of scratch held by every GPU that loads the library, until exit.
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+constexpr int kMaxDevices = 64;
+
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+}  // namespace
+}  // namespace veg
+
+static __device__ __align__(256) unsigned char g_binsort_scratch[veg::kStaticScratchBytes];
+
+// The array's name is only a host-side handle: its device address has to be
+// looked up once per device, with that device current.
+static veg_status static_scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VEG_ERR_CUDA;
+  if (dev < 0 || dev >= veg::kMaxDevices) return VEG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(veg::g_static_mu);
+  if (veg::g_static_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_binsort_scratch) != cudaSuccess || p == nullptr)
+      return VEG_ERR_CUDA;
+    veg::g_static_ptr[dev] = p;
+  }
+  *out = veg::g_static_ptr[dev];
+  return VEG_OK;
+}
+
+extern "C" veg_status veg_bin_sort_static(const veg_camera* cams, int32_t n_views, int64_t n,
+                                          const float* splat_geo, const int32_t* tiles_touched,
+                                          const int16_t* rect, int64_t capacity, uint64_t* keys,
+                                          uint32_t* vals, int32_t* tile_ranges,
+                                          int64_t* n_instances, cudaStream_t stream) {
+  using namespace veg;
+  veg_status st = check_cameras(cams, n_views);
+  if (st != VEG_OK) return st;
+  if (n < 0 || capacity < 0 || capacity >= ((int64_t)1 << 31) || !tile_ranges ||
+      (capacity > 0 && !vals) || (n > 0 && (!splat_geo || !tiles_touched || !rect)))
+    return VEG_ERR_INVALID_ARGUMENT;
+  if (n * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
+  if (!aligned16(splat_geo) || (reinterpret_cast<uintptr_t>(rect) & 7) ||
+      (reinterpret_cast<uintptr_t>(tile_ranges) & 7) ||
+      (reinterpret_cast<uintptr_t>(n_instances) & 7))
+    return VEG_ERR_INVALID_ARGUMENT;
+  const int tpv = tiles_x_of(cams[0].width) * tiles_x_of(cams[0].height);
+  if ((int64_t)tpv * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
+  if (binsort_ws_bytes(n, n_views, capacity, tpv) > kStaticScratchBytes)
+    return VEG_ERR_UNSUPPORTED;
+  void* ws = nullptr;
+  st = static_scratch_address(&ws);
+  if (st != VEG_OK) return st;
+  st = binsort_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
+                      tiles_touched, reinterpret_cast<const short4*>(rect), ws, capacity, keys,
+                      vals, reinterpret_cast<int2*>(tile_ranges), stream);
+  if (st != VEG_OK) return st;
+  if (n_instances &&
+      cudaMemcpyAsync(n_instances, &static_cast<WsHeader*>(ws)->n_instances, sizeof(int64_t),
+                      cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+    return VEG_ERR_CUDA;
+  return VEG_OK;
+}

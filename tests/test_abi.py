@@ -74,4 +74,10 @@ def test_host_side_validation_needs_no_gpu(lib):
     assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, tf, None, 0, None, None,
                                  None, None) == 1
     assert lib.veg_sync_status(None, None, None) == 1
+    # the fixed-scratch binning refuses a request beyond its array on the host
+    fake = 1 << 20  # aligned placeholder addresses, never dereferenced
+    assert lib.veg_bin_sort_static(cams, 1, 4096, fake, fake, fake, 4_000_000, None, fake,
+                                   fake, None, None) == 5
+    assert lib.veg_bin_sort_static(cams, 1, -1, fake, fake, fake, 16, None, fake, fake, None,
+                                   None) == 1
     assert lib.veg_l1_loss(None, None, 4, None, None, None, 0, None) == 1
