@@ -283,6 +283,32 @@ __global__ void __launch_bounds__(256)
 // backward
 // ---------------------------------------------------------------------------
 
+// Sums eight per-lane values over the warp with 9 shuffles: three halving
+// exchanges (offsets 16, 8, 4; each lane keeps the half named by its offset
+// bit and receives the partner's sum of that half), then two full steps
+// (offsets 2, 1).  Lane l returns the warp total of slot l >> 2.
+__device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane) {
+  const bool b4 = lane & 16, b2 = lane & 8, b1 = lane & 4;
+  float w[4], x[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b4 ? v[i] : v[i + 4];
+    const float keep = b4 ? v[i + 4] : v[i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b2 ? w[i] : w[i + 2];
+    const float keep = b2 ? w[i + 2] : w[i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b1 ? x[0] : x[1];
+  float y = (b1 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  return y;
+}
+
 __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
                "f"(d)
@@ -316,7 +342,7 @@ __global__ void __launch_bounds__(256)
   float4* s_geo = s_slope + TG * kBatch;                    // [kBatch]: u, -a/2, -b
   float2* s_c = reinterpret_cast<float2*>(s_geo + kBatch);  // [kBatch]: -c/2, cutoff
   float* s_A = reinterpret_cast<float*>(s_c + kBatch);      // [TG][kBatch]: A
-  float* s_acc = s_A + TG * kBatch;                         // [8][kBatch]
+  float* s_acc = s_A + TG * kBatch;                         // [kBatch][8] gradient sums
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + 8 * kBatch);
   unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + kBatch);
   unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
@@ -428,47 +454,33 @@ __global__ void __launch_bounds__(256)
       if (STATS) n_grad += (dG != 0.f);
       const bool nz = (dp != 0.f) || (dvv != 0.f) || (dww != 0.f);
       if (__any_sync(0xffffffffu, nz)) {
-        float v0 = dp * (2.0f * sg.z * dx + sg.w * dy);
-        float v1 = dp * (2.0f * sc * dy + sg.w * dx);
-        float v2 = dp * (-0.5f * dx * dx);
-        float v3 = dp * (-dx * dy);
-        float v4 = dp * (-0.5f * dy * dy);
-        float v5 = dvv, v6 = dww;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-          v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-          v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-          v3 += __shfl_xor_sync(0xffffffffu, v3, o);
-          v4 += __shfl_xor_sync(0xffffffffu, v4, o);
-          v5 += __shfl_xor_sync(0xffffffffu, v5, o);
-          v6 += __shfl_xor_sync(0xffffffffu, v6, o);
-        }
-        if (lane == 0) {
-          atomicAdd(&s_acc[0 * kBatch + j], v0);
-          atomicAdd(&s_acc[1 * kBatch + j], v1);
-          atomicAdd(&s_acc[2 * kBatch + j], v2);
-          atomicAdd(&s_acc[3 * kBatch + j], v3);
-          atomicAdd(&s_acc[4 * kBatch + j], v4);
-          atomicAdd(&s_acc[5 * kBatch + j], v5);
-          atomicAdd(&s_acc[6 * kBatch + j], v6);
-        }
+        float v[8];
+        v[0] = dp * (2.0f * sg.z * dx + sg.w * dy);
+        v[1] = dp * (2.0f * sc * dy + sg.w * dx);
+        v[2] = dp * (-0.5f * dx * dx);
+        v[3] = dp * (-dx * dy);
+        v[4] = dp * (-0.5f * dy * dy);
+        v[5] = dvv;
+        v[6] = dww;
+        v[7] = 0.0f;
+        // reduce-scatter: lane l ends with slot l >> 2 summed over the warp
+        const float r = warp_reduce_scatter8(v, lane);
+        const int slot = lane >> 2;
+        if ((lane & 3) == 0 && slot < 7) atomicAdd(&s_acc[j * 8 + slot], r);
       }
     }
     __syncthreads();
     if (i < rg.y) {
-      float a[7];
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        a[k] = s_acc[k * kBatch + threadIdx.x];
-        s_acc[k * kBatch + threadIdx.x] = 0.0f;
-        any |= (a[k] != 0.0f);
-      }
+      const float4 a0 = reinterpret_cast<const float4*>(s_acc)[2 * threadIdx.x];
+      const float4 a1 = reinterpret_cast<const float4*>(s_acc)[2 * threadIdx.x + 1];
+      reinterpret_cast<float4*>(s_acc)[2 * threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(s_acc)[2 * threadIdx.x + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool any = a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f ||
+                       a1.x != 0.f || a1.y != 0.f || a1.z != 0.f;
       if (any) {
         float4* dst = grad2d + 2 * (int64_t)s_idx[threadIdx.x];
-        red_add_v4(dst, a[0], a[1], a[2], a[3]);
-        red_add_v4(dst + 1, a[4], a[5], a[6], 0.0f);
+        red_add_v4(dst, a0.x, a0.y, a0.z, a0.w);
+        red_add_v4(dst + 1, a1.x, a1.y, a1.z, 0.0f);
       }
     }
     __syncthreads();
