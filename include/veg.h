@@ -143,6 +143,18 @@ veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int64_t n,
                         int32_t* tile_ranges, cudaStream_t stream);
 
 /*
+ * veg_tile_order -- a processing order for the compositing kernels: the
+ * indices 0..count-1 of tile_ranges [count][2] (count = views * tiles), the
+ * tiles with the longest lists first (bucketed by floor(log2(length)), empty
+ * tiles last).  Passing it to veg_composite_fwd/bwd schedules the heaviest
+ * tiles first, which shortens the tail of the launch; results do not depend
+ * on it.  The order inside a bucket is unspecified (it may differ between
+ * calls).  tile_order: device int32 [count], overwritten.
+ */
+veg_status veg_tile_order(const int32_t* tile_ranges, int64_t count, int32_t* tile_order,
+                          cudaStream_t stream);
+
+/*
  * veg_bin_sort_static -- veg_bin_sort without any memory from the caller
  * beyond inputs and outputs.  The paper has no counterpart; this exists for
  * callers that cannot allocate device memory: code that runs while another
@@ -198,6 +210,9 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  * Writes out [V][n_tf][H][W][4] = (C + T bg, T_final) and n_contrib
  * [V][n_tf][H][W] = 1 + list position of the last blended splat (0 if none).
  * The scene representation is TF-independent, so one sort serves every TF.
+ * tile_order: optional device int32 [V * tiles] from veg_tile_order (the
+ * order in which tiles are scheduled; NULL = row-major; results do not
+ * depend on it).
  * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default).
  * bg: host float[3].  stats: optional device uint64[5] accumulating
  * (visited pixel-splat pairs -- every pair reached before the pixel stops --,
@@ -208,10 +223,10 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  */
 veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
                              const float* splat_geo, const float* splat_aux,
-                             const uint32_t* vals, const int32_t* tile_ranges, veg_tf tf,
-                             const float* bg, int32_t tf_group, float* out,
-                             int32_t* n_contrib, unsigned long long* stats,
-                             cudaStream_t stream);
+                             const uint32_t* vals, const int32_t* tile_ranges,
+                             const int32_t* tile_order, veg_tf tf, const float* bg,
+                             int32_t tf_group, float* out, int32_t* n_contrib,
+                             unsigned long long* stats, cudaStream_t stream);
 
 /*
  * veg_composite_bwd -- manual gradients of the render (Sec. 3.3, backward
@@ -237,8 +252,9 @@ veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views, size_t* 
 veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
                              const float* splat_geo, const float* splat_aux,
                              const int32_t* tiles_touched, const uint32_t* vals,
-                             const int32_t* tile_ranges, veg_tf tf, const float* bg,
-                             int32_t tf_group, const float* out, const int32_t* n_contrib,
+                             const int32_t* tile_ranges, const int32_t* tile_order, veg_tf tf,
+                             const float* bg, int32_t tf_group, const float* out,
+                             const int32_t* n_contrib,
                              const float* dL_dout, void* workspace, size_t workspace_bytes,
                              float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
                              float* grad2d, unsigned long long* stats, cudaStream_t stream);

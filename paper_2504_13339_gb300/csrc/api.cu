@@ -98,6 +98,7 @@ struct RenderLayout {
   short4* rect;
   uint32_t* vals;
   int2* ranges;
+  int32_t* order;
   size_t bytes;
 };
 
@@ -114,6 +115,7 @@ RenderLayout carve_render(void* ws, int64_t n, int n_views, int64_t capacity, in
   R.rect = c.take<short4>((size_t)n * n_views);
   R.vals = c.take<uint32_t>((size_t)capacity);
   R.ranges = c.take<int2>((size_t)tpv * n_views);
+  R.order = c.take<int32_t>((size_t)tpv * n_views);
   R.bytes = c.bytes();
   return R;
 }
@@ -196,6 +198,9 @@ extern "C" veg_status veg_render(const veg_camera* cams, int32_t n_views, veg_ga
   st = binsort_launch(cams, n_views, g.n, R.geo, R.tiles, R.rect, R.binsort_ws, capacity, nullptr,
                       R.vals, R.ranges, stream);
   if (st != VEG_OK) return st;
-  return composite_fwd_launch(cams, n_views, g.n, R.geo, R.aux, R.vals, R.ranges, tf, bg, 0,
-                              reinterpret_cast<float4*>(out), n_contrib, nullptr, stream);
+  const int count = tiles_x_of(cams[0].width) * tiles_x_of(cams[0].height) * n_views;
+  st = tile_order_launch(R.ranges, count, R.order, stream);
+  if (st != VEG_OK) return st;
+  return composite_fwd_launch(cams, n_views, g.n, R.geo, R.aux, R.vals, R.ranges, R.order, tf, bg,
+                              0, reinterpret_cast<float4*>(out), n_contrib, nullptr, stream);
 }

@@ -490,7 +490,58 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   return launch_status();
 }
 
+namespace {
+
+// Longest-first order of the tiles (one CTA): tiles are bucketed by
+// floor(log2(list length)) and the buckets emitted from the longest down,
+// empty tiles last.  Order inside a bucket is unspecified; it only steers
+// the CTA schedule, never a result.
+__global__ void __launch_bounds__(1024)
+    tile_order_kernel(const int2* __restrict__ ranges, int count, int32_t* __restrict__ order) {
+  __shared__ unsigned s_cnt[33];
+  __shared__ unsigned s_off[33];
+  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int2 r = ranges[i];
+    const unsigned len = (unsigned)(r.y - r.x);
+    atomicAdd(&s_cnt[len ? 32 - __clz(len) : 0], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned off = 0;
+    for (int b = 32; b >= 0; --b) {
+      s_off[b] = off;
+      off += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int2 r = ranges[i];
+    const unsigned len = (unsigned)(r.y - r.x);
+    order[atomicAdd(&s_off[len ? 32 - __clz(len) : 0], 1u)] = i;
+  }
+}
+
+}  // namespace
+
+veg_status tile_order_launch(const int2* ranges, int count, int32_t* order, cudaStream_t stream) {
+  if (count == 0) return VEG_OK;
+  tile_order_kernel<<<1, 1024, 0, stream>>>(ranges, count, order);
+  count_launch();
+  return launch_status();
+}
+
 }  // namespace veg
+
+extern "C" veg_status veg_tile_order(const int32_t* tile_ranges, int64_t count,
+                                     int32_t* tile_order, cudaStream_t stream) {
+  if (count < 0 || count >= ((int64_t)1 << 31) || (count > 0 && (!tile_ranges || !tile_order)) ||
+      (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+    return VEG_ERR_INVALID_ARGUMENT;
+  return veg::tile_order_launch(reinterpret_cast<const int2*>(tile_ranges), (int)count,
+                                tile_order, stream);
+}
 
 extern "C" veg_status veg_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t capacity,
                                                   int32_t width, int32_t height, size_t* bytes) {

@@ -11,10 +11,10 @@ veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
 
 veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float4* geo, const float4* aux, const uint32_t* vals,
-                                const int2* ranges, veg_tf tf, const float* bg, int tf_group,
-                                float4* out, int32_t* n_contrib, unsigned long long* stats,
-                                cudaStream_t stream) {
-  CompArgs A = make_args(cams, geo, aux, vals, ranges, tf, bg);
+                                const int2* ranges, const int32_t* order, veg_tf tf,
+                                const float* bg, int tf_group, float4* out, int32_t* n_contrib,
+                                unsigned long long* stats, cudaStream_t stream) {
+  CompArgs A = make_args(cams, geo, aux, vals, ranges, order, tf, bg);
   (void)n;
   const int TG = pick_group(tf_group, tf.n_tf, false);
   if (stats) {
@@ -61,9 +61,9 @@ static veg_status check_composite_common(const veg_camera* cams, int32_t n_views
 extern "C" veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
                                         const float* splat_geo, const float* splat_aux,
                                         const uint32_t* vals, const int32_t* tile_ranges,
-                                        veg_tf tf, const float* bg, int32_t tf_group, float* out,
-                                        int32_t* n_contrib, unsigned long long* stats,
-                                        cudaStream_t stream) {
+                                        const int32_t* tile_order, veg_tf tf, const float* bg,
+                                        int32_t tf_group, float* out, int32_t* n_contrib,
+                                        unsigned long long* stats, cudaStream_t stream) {
   veg_status st =
       check_composite_common(cams, n_views, n, splat_geo, splat_aux, vals, tile_ranges, tf);
   if (st != VEG_OK) return st;
@@ -71,8 +71,8 @@ extern "C" veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views,
     return VEG_ERR_INVALID_ARGUMENT;
   return composite_fwd_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
                               reinterpret_cast<const float4*>(splat_aux), vals,
-                              reinterpret_cast<const int2*>(tile_ranges), tf, bg, tf_group,
-                              reinterpret_cast<float4*>(out), n_contrib, stats, stream);
+                              reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
+                              tf_group, reinterpret_cast<float4*>(out), n_contrib, stats, stream);
 }
 
 extern "C" veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views,
@@ -85,8 +85,9 @@ extern "C" veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_view
 extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
                                         const float* splat_geo, const float* splat_aux,
                                         const int32_t* tiles_touched, const uint32_t* vals,
-                                        const int32_t* tile_ranges, veg_tf tf, const float* bg,
-                                        int32_t tf_group, const float* out,
+                                        const int32_t* tile_ranges, const int32_t* tile_order,
+                                        veg_tf tf, const float* bg, int32_t tf_group,
+                                        const float* out,
                                         const int32_t* n_contrib, const float* dL_dout,
                                         void* workspace, size_t workspace_bytes,
                                         float* grad_mean_v, float* grad_logscale_w,
@@ -120,7 +121,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
     return VEG_ERR_CUDA;
   CompArgs A = make_args(cams, reinterpret_cast<const float4*>(splat_geo),
                          reinterpret_cast<const float4*>(splat_aux), vals,
-                         reinterpret_cast<const int2*>(tile_ranges), tf, bg);
+                         reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg);
   const int TG = pick_group(tf_group, tf.n_tf, true);
   const float4* o4 = reinterpret_cast<const float4*>(out);
   const float4* d4 = reinterpret_cast<const float4*>(dL_dout);

@@ -114,6 +114,7 @@ struct CompArgs {
   const float4* aux;
   const uint32_t* vals;
   const int2* ranges;
+  const int32_t* order;  // work-item order (view * tiles + tile) or null
   const float4* lut;
   int lut_size, n_tf;
   int width, height, tiles_x, tiles_per_view;
@@ -176,7 +177,7 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
 // pixel's termination, the method's own count), iterated pairs (walked by
 // the warp lists), pairs above the cutoff, alpha evaluations, blended pairs.
 template <int TG, bool STATS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     composite_fwd_kernel(CompArgs A, float4* __restrict__ out, int32_t* __restrict__ n_contrib,
                          unsigned long long* __restrict__ stats) {
   extern __shared__ float4 s_lut[];  // [TG][L]
@@ -185,7 +186,9 @@ __global__ void __launch_bounds__(256)
   __shared__ float4 s_col[TG * kBatch];
   __shared__ unsigned char s_mask[kBatch];
   __shared__ unsigned char s_list[kWarps][kBatch];
-  const int tile = blockIdx.x, view = blockIdx.y, t0 = blockIdx.z * TG;
+  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
+  const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
+  const int t0 = blockIdx.z * TG;
   const int ntg = min(TG, A.n_tf - t0);
   const int warp = threadIdx.x >> 5;
   stage_luts<TG>(A, t0, s_lut);
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(256)
   const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
   const bool inside = px < A.width && py < A.height;
   const float fx = (float)px, fy = (float)py;
-  const int2 rg = A.ranges[(int64_t)view * A.tiles_per_view + tile];
+  const int2 rg = A.ranges[wi];
   float T[TG], Cr[TG], Cg[TG], Cb[TG];
   int last[TG];
 #pragma unroll
@@ -348,7 +351,9 @@ __global__ void __launch_bounds__(256)
   unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
   __shared__ int s_maxnc;
 
-  const int tile = blockIdx.x, view = blockIdx.y, t0 = blockIdx.z * TG;
+  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
+  const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
+  const int t0 = blockIdx.z * TG;
   const int ntg = min(TG, A.n_tf - t0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* my_list = s_lists + warp * kBatch;
@@ -361,7 +366,7 @@ __global__ void __launch_bounds__(256)
   const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
   const bool inside = px < A.width && py < A.height;
   const float fx = (float)px, fy = (float)py;
-  const int2 rg = A.ranges[(int64_t)view * A.tiles_per_view + tile];
+  const int2 rg = A.ranges[wi];
 
   float T[TG], S[TG], K[TG], gr[TG], gg[TG], gb[TG];
   int nc[TG];
@@ -525,12 +530,14 @@ int pick_group(int tf_group, int n_tf, bool bwd) {
 }
 
 CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
-                   const uint32_t* vals, const int2* ranges, veg_tf tf, const float* bg) {
+                   const uint32_t* vals, const int2* ranges, const int32_t* order, veg_tf tf,
+                   const float* bg) {
   CompArgs A;
   A.geo = geo;
   A.aux = aux;
   A.vals = vals;
   A.ranges = ranges;
+  A.order = order;
   A.lut = reinterpret_cast<const float4*>(tf.lut);
   A.lut_size = tf.lut_size;
   A.n_tf = tf.n_tf;
@@ -570,7 +577,7 @@ veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc
   static size_t configured = 0;
   veg_status st = prepare_smem(kern, smem, &configured);
   if (st != VEG_OK) return st;
-  dim3 grid((unsigned)A.tiles_per_view, (unsigned)n_views, (unsigned)((A.n_tf + TG - 1) / TG));
+  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, (unsigned)((A.n_tf + TG - 1) / TG));
   kern<<<grid, 256, smem, stream>>>(A, out, nc, stats);
   count_launch();
   return launch_status();
@@ -585,7 +592,7 @@ veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const
   static size_t configured = 0;
   veg_status st = prepare_smem(kern, smem, &configured);
   if (st != VEG_OK) return st;
-  dim3 grid((unsigned)A.tiles_per_view, (unsigned)n_views, (unsigned)((A.n_tf + TG - 1) / TG));
+  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, (unsigned)((A.n_tf + TG - 1) / TG));
   kern<<<grid, 256, smem, stream>>>(A, out, nc, dout, grad2d, stats);
   count_launch();
   return launch_status();

@@ -79,9 +79,10 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
                           uint64_t* keys, uint32_t* vals, int2* ranges, cudaStream_t stream);
 veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float4* geo, const float4* aux, const uint32_t* vals,
-                                const int2* ranges, veg_tf tf, const float* bg, int tf_group,
-                                float4* out, int32_t* n_contrib, unsigned long long* stats,
-                                cudaStream_t stream);
+                                const int2* ranges, const int32_t* order, veg_tf tf,
+                                const float* bg, int tf_group, float4* out, int32_t* n_contrib,
+                                unsigned long long* stats, cudaStream_t stream);
+veg_status tile_order_launch(const int2* ranges, int count, int32_t* order, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // device side: float32 operations in a fixed order (no contraction)

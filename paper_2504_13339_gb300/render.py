@@ -45,6 +45,7 @@ class SplatPipeline:
         self.tiles_x = (self.W + 15) // 16
         self.tiles_per_view = self.tiles_x * ((self.H + 15) // 16)
         self.ranges = torch.empty(self.V * self.tiles_per_view, 2, dtype=torch.int32, device=dev)
+        self.order = torch.empty(self.V * self.tiles_per_view, dtype=torch.int32, device=dev)
         self.out = torch.empty(self.V, self.n_tf, self.H, self.W, 4, device=dev)
         self.n_contrib = torch.empty(self.V, self.n_tf, self.H, self.W, dtype=torch.int32,
                                      device=dev)
@@ -79,6 +80,7 @@ class SplatPipeline:
             keys = self.keys
         _lib.veg_bin_sort(self.c_cams, self.n, self.geo, self.tiles, self.rect, self.ws,
                           self.capacity, keys, self.vals, self.ranges, stream)
+        _lib.veg_tile_order(self.ranges, self.order, stream)
 
     def status(self, stream=None):
         """(status, instance count) after waiting for the stream."""
@@ -89,7 +91,7 @@ class SplatPipeline:
         self._bg = tuple(float(b) for b in bg)
         _lib.veg_composite_fwd(self.c_cams, self.n, self.geo, self.aux, self.vals, self.ranges,
                                _lib.tf_desc(luts), self._bg, self.tf_group, self.out,
-                               self.n_contrib, stats, stream)
+                               self.n_contrib, stats, stream, tile_order=self.order)
         return self.out
 
     def l1(self, target, stream=None):
@@ -101,14 +103,15 @@ class SplatPipeline:
         _lib.veg_composite_bwd(self.c_cams, self._g, self.geo, self.aux, self.tiles, self.vals,
                                self.ranges, _lib.tf_desc(self._luts), self._bg, self.tf_group,
                                self.out, self.n_contrib, dL_dout, None, grad_mean_v,
-                               grad_logscale_w, grad_quat, self.grad2d, None, stream)
+                               grad_logscale_w, grad_quat, self.grad2d, None, stream,
+                               tile_order=self.order)
 
     def backward_2d(self, dL_dout, stats=None, stream=None):
         """Screen-space gradients only (into self.grad2d)."""
         _lib.veg_composite_bwd(self.c_cams, self._g, self.geo, self.aux, self.tiles, self.vals,
                                self.ranges, _lib.tf_desc(self._luts), self._bg, self.tf_group,
                                self.out, self.n_contrib, dL_dout, None, None, None, None,
-                               self.grad2d, stats, stream)
+                               self.grad2d, stats, stream, tile_order=self.order)
 
     def project_backward(self, grad_mean_v, grad_logscale_w, grad_quat, stream=None):
         _lib.veg_project_bwd(self.c_cams, self._g, self.tiles, self.grad2d, grad_mean_v,

@@ -71,8 +71,9 @@ def test_host_side_validation_needs_no_gpu(lib):
     # null Gaussian arrays with n > 0
     assert lib.veg_project(cams, 1, g, None, None, None, None, None, None) == 1
     tf = _lib.veg_tf(0, 1, 1)
-    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, tf, None, 0, None, None,
-                                 None, None) == 1
+    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, None, tf, None, 0, None,
+                                 None, None, None) == 1
+    assert lib.veg_tile_order(None, 5, None, None) == 1
     assert lib.veg_sync_status(None, None, None) == 1
     # the fixed-scratch binning refuses a request beyond its array on the host
     fake = 1 << 20  # aligned placeholder addresses, never dereferenced
