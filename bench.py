@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--cpu-tiles", type=int, default=6)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--width", type=int, default=1024)
+    ap.add_argument("--workload", default="train",
+                    choices=["train", "plain", "sweep", "batched", "serve"])
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -431,12 +435,228 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# other configurations (each prints its own JSON line; not the default line)
+# ----------------------------------------------------------------------------
+
+def _dev_tensors(g, device):
+    import torch
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=device)
+    return t(g.mean_v), t(g.logscale_w), t(g.quat)
+
+
+def _event_time(fn, reps, flush=None):
+    import torch
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def run_plain(args):
+    """4096 Gaussians, 128x128, one TF: render latency, eager and graph-replayed."""
+    import torch
+
+    import __graft_entry__
+    from paper_2504_13339_gb300 import scenes as S
+    from paper_2504_13339_gb300.graphs import CapturedStep
+    from paper_2504_13339_gb300.render import SplatPipeline, lut_tensor
+    __graft_entry__.build()
+    g, cams, tfs = S.plain_scene()
+    tens = _dev_tensors(g, "cuda")
+    luts = lut_tensor(tfs)
+    p = SplatPipeline(g.n, cams, n_tf=1)
+    p.render(*tens, luts)
+
+    def step():
+        p.project(*tens, luts)
+        p.bin_sort()
+        p.composite(luts)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    eager = _event_time(step, args.steps)
+    cs = CapturedStep(step)
+    graph = _event_time(cs.replay, args.steps)
+    px = 128 * 128
+    print(json.dumps({"workload": "plain render: 4096 Gaussians, 128x128, 1 TF",
+                      "us_per_render_eager": round(eager * 1e3, 2),
+                      "us_per_render_graph": round(graph * 1e3, 2),
+                      "mpix_per_s_graph": round(px / (graph * 1e-3) / 1e6, 2),
+                      "launches_per_render": cs.launches}))
+
+
+def run_sweep(args):
+    """10M Gaussians (32-blob field), 2048x2048, 64 TFs: one projection + sort
+    and TF-grouped compositing vs 64 independent plain renders."""
+    import torch
+
+    import __graft_entry__
+    from paper_2504_13339_gb300 import autotune, scenes as S
+    from paper_2504_13339_gb300.render import SplatPipeline, lut_tensor
+    __graft_entry__.build()
+    n = args.n if args.n != 1_000_000 else 10_000_000
+    width = args.width if args.width != 1024 else 2048
+    g, _ = S.field_gaussians(n, 32, 11)
+    cams = [S.orbit_camera(30.0, 20.0, 3.0, width, width)]
+    tfs = S.bump_tfs(64, 12)
+    tens = _dev_tensors(g, "cuda")
+    luts = lut_tensor(tfs)
+    p = SplatPipeline(g.n, cams, n_tf=64, capacity=12 * g.n)
+    p.render(*tens, luts)
+    _, m = p.status()
+    p.set_capacity(int(m * 1.1) + 4096)
+    p.project(*tens, luts)
+    p.bin_sort()
+    tuned = autotune.tune(p, luts)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def batched():
+        p.project(*tens, luts)
+        p.bin_sort()
+        p.composite(luts)
+    for _ in range(2):
+        batched()
+    t_batched = _event_time(batched, args.steps, flush)
+    ref = p.out.clone()
+    q = SplatPipeline(g.n, cams, n_tf=1, capacity=p.capacity)
+    single = [luts[t:t + 1].contiguous() for t in range(64)]
+    outs = torch.empty_like(p.out)
+
+    def plain():
+        for t in range(64):
+            q.project(*tens, single[t])
+            q.bin_sort()
+            q.composite(single[t])
+            outs[:, t:t + 1].copy_(q.out)
+    plain()
+    t_plain = _event_time(plain, max(1, args.steps // 2), flush)
+    same = bool(torch.equal(outs, ref))
+    pix = 64 * width * width
+    print(json.dumps({"workload": f"multi-TF sweep: {n} Gaussians (32 blobs), {width}x{width}, "
+                                  f"64 TFs", "tile_instances": int(m),
+                      "batched_ms": round(t_batched, 3), "plain_64_ms": round(t_plain, 3),
+                      "batched_mpix_per_s": round(pix / (t_batched * 1e-3) / 1e6, 1),
+                      "plain_mpix_per_s": round(pix / (t_plain * 1e-3) / 1e6, 1),
+                      "speedup": round(t_plain / t_batched, 2), "images_bit_identical": same,
+                      "tf_group": tuned["fwd"], "autotune_ms": tuned["times"]}))
+
+
+def run_batched(args):
+    """Batched training launch: 3M Gaussians (16 blobs), 8 orbit views x 4 TFs
+    at 1600x1600 in one projection/bin/sort over all views and one composite
+    forward/backward, graph-captured, autotuned TF group; vs the same work as
+    32 plain (view, TF) steps."""
+    import torch
+
+    import __graft_entry__
+    from paper_2504_13339_gb300 import autotune, scenes as S
+    from paper_2504_13339_gb300.graphs import CapturedStep
+    from paper_2504_13339_gb300.render import SplatPipeline, lut_tensor
+    __graft_entry__.build()
+    n = args.n if args.n != 1_000_000 else 3_000_000
+    width = args.width if args.width != 1024 else 1600
+    g, _ = S.field_gaussians(n, 16, 21)
+    tgt = S.perturbed(g, 22)
+    cams = S.orbit_cameras(8, 23, width, width)
+    tfs = S.bump_tfs(4, 24)
+    tens = _dev_tensors(g, "cuda")
+    luts = lut_tensor(tfs)
+    p = SplatPipeline(g.n, cams, n_tf=4, capacity=8 * g.n * len(cams))
+    target = p.render(*_dev_tensors(tgt, "cuda"), luts).clone()
+    p.render(*tens, luts)
+    _, m = p.status()
+    p.set_capacity(int(m * 1.15) + 4096)
+    grads = [torch.zeros_like(x) for x in tens]
+    p.project(*tens, luts)
+    p.bin_sort()
+    p.composite(luts)
+    p.l1(target)
+    tuned = autotune.tune(p, luts, dout=p.loss_grad)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        p.train_step(*tens, luts, target, grads)
+    eager = _event_time(step, args.steps, flush)
+    cs = CapturedStep(step)
+    graph = _event_time(cs.replay, args.steps, flush)
+    # the same work as 32 single-view single-TF steps
+    singles = []
+    for v in range(len(cams)):
+        for t in range(4):
+            q = SplatPipeline(g.n, [cams[v]], n_tf=1, capacity=p.capacity // len(cams) + 4096)
+            singles.append((q, luts[t:t + 1].contiguous(), target[v:v + 1, t:t + 1].contiguous()))
+    sgrads = [torch.zeros_like(x) for x in tens]
+
+    def plain():
+        for gb in sgrads:
+            gb.zero_()
+        for q, lt, tg in singles:
+            q.project(*tens, lt)
+            q.bin_sort()
+            q.composite(lt)
+            q.l1(tg)
+            q.backward(q.loss_grad, *sgrads)
+    plain()
+    t_plain = _event_time(plain, max(1, args.steps // 2), flush)
+    pix = len(cams) * 4 * width * width
+    print(json.dumps({"workload": f"batched training launch: {n} Gaussians (16 blobs), "
+                                  f"{len(cams)} views x 4 TFs at {width}x{width}",
+                      "tile_instances": int(m), "eager_ms": round(eager, 3),
+                      "graph_ms": round(graph, 3), "plain_32_ms": round(t_plain, 3),
+                      "steps_per_s_graph": round(1e3 / graph, 2),
+                      "mpix_per_s_graph": round(pix / (graph * 1e-3) / 1e6, 1),
+                      "speedup_vs_plain": round(t_plain / graph, 2),
+                      "launches_per_step": cs.launches, "tf_group": tuned}))
+
+
+def run_serve(args):
+    """Five resident models (200k, 500k, 1M, 3M, 6M Gaussians), Poisson
+    requests at `rate`/s with random model, orbit view, TF and resolution in
+    {256, 512, 1024, 2048}^2; continuous batching vs FIFO one at a time."""
+    import torch
+
+    import __graft_entry__
+    from paper_2504_13339_gb300 import scenes as S
+    from paper_2504_13339_gb300.serve import (RenderServer, fifo_serve, latency_stats,
+                                              poisson_requests)
+    __graft_entry__.build()
+    models = {}
+    for i, n in enumerate((200_000, 500_000, 1_000_000, 3_000_000, 6_000_000)):
+        g, _ = S.field_gaussians(n, 16, 31 + i)
+        models[f"{n // 1000}k"] = _dev_tensors(g, "cuda")
+    tfs = torch.as_tensor(S.bump_tfs(16, 32), device="cuda")
+    out = {"workload": "serving: 5 resident models, Poisson arrivals, random model/view/TF/"
+                       "resolution in {256,512,1024,2048}^2"}
+    for rate in (args.rate, args.rate * 10):
+        warm = poisson_requests(models, 16, rate, 5.0, 40)
+        meas = poisson_requests(models, 16, rate, args.duration, 41)
+        srv = RenderServer(models, tfs, n_slots=4, max_batch=8)
+        srv.run(warm)
+        res = latency_stats(srv.run(meas))
+        fsrv = RenderServer(models, tfs)
+        fifo_serve(fsrv, warm)
+        base = latency_stats(fifo_serve(fsrv, poisson_requests(models, 16, rate, args.duration,
+                                                               41)))
+        out[f"rate_{int(rate)}"] = {"continuous_batching": res, "fifo_plain": base}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "train":
         run_gpu(args)
+    else:
+        {"plain": run_plain, "sweep": run_sweep, "batched": run_batched,
+         "serve": run_serve}[args.workload](args)
 
 
 if __name__ == "__main__":

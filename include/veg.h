@@ -77,6 +77,11 @@ typedef struct veg_tf {
   const float* lut; /* device [n_tf][lut_size][4] RGBA, straight alpha */
   int32_t lut_size; /* >= 2 */
   int32_t n_tf;     /* >= 1 */
+  /* Optional device int32 [n_views]: view v is composited with table
+   * view_tf[v] only, giving one image per view (out [V][1][H][W]); NULL
+   * composites every view with every table.  An index outside [0, n_tf)
+   * reads as a fully transparent table. */
+  const int32_t* view_tf;
 } veg_tf;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -102,7 +107,8 @@ uint64_t veg_kernel_launches(void);
  * A culled Gaussian gets tiles_touched = 0 and all-zero records.  Culling:
  * camera z <= near_plane, zero quaternion, det(Sigma') <= 0, empty rectangle,
  * and -- only when cull_tf is non-NULL -- O_t(v) w < 1/255 for every table t
- * of cull_tf (lossless: such a Gaussian can never reach alpha >= 1/255).
+ * of cull_tf (lossless: such a Gaussian can never reach alpha >= 1/255); with
+ * cull_tf->view_tf set, view v is tested against table view_tf[v] only.
  * Depth, screen mean, radius, rectangle and the opacity test are evaluated in
  * IEEE float32 with a fixed operation order (no fused multiply-add) so that
  * tile lists are reproducible bit for bit.

@@ -41,7 +41,8 @@ class veg_gaussians(ctypes.Structure):
 
 
 class veg_tf(ctypes.Structure):
-    _fields_ = [("lut", ctypes.c_void_p), ("lut_size", ctypes.c_int32), ("n_tf", ctypes.c_int32)]
+    _fields_ = [("lut", ctypes.c_void_p), ("lut_size", ctypes.c_int32), ("n_tf", ctypes.c_int32),
+                ("view_tf", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -125,8 +126,11 @@ def gaussians(mean_v, logscale_w, quat):
                          mean_v.shape[0])
 
 
-def tf_desc(luts):
-    return veg_tf(luts.data_ptr(), luts.shape[-2], luts.shape[0])
+def tf_desc(luts, view_tf=None):
+    """Descriptor of TF tables luts [n_tf][L][4]; view_tf (device int32 [V])
+    selects one table per view."""
+    return veg_tf(luts.data_ptr(), luts.shape[-2], luts.shape[0],
+                  None if view_tf is None else view_tf.data_ptr())
 
 
 # ---------------------------------------------------------------------------

@@ -16,7 +16,7 @@ veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 unsigned long long* stats, cudaStream_t stream) {
   CompArgs A = make_args(cams, geo, aux, vals, ranges, order, tf, bg);
   (void)n;
-  const int TG = pick_group(tf_group, tf.n_tf, false);
+  const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, false);
   if (stats) {
     switch (TG) {
       case 1: return launch_fwd_t<1, true>(A, n_views, out, n_contrib, stats, stream);
@@ -122,7 +122,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
   CompArgs A = make_args(cams, reinterpret_cast<const float4*>(splat_geo),
                          reinterpret_cast<const float4*>(splat_aux), vals,
                          reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg);
-  const int TG = pick_group(tf_group, tf.n_tf, true);
+  const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, true);
   const float4* o4 = reinterpret_cast<const float4*>(out);
   const float4* d4 = reinterpret_cast<const float4*>(dL_dout);
   if (stats) {

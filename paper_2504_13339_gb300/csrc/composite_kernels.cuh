@@ -114,33 +114,36 @@ struct CompArgs {
   const float4* aux;
   const uint32_t* vals;
   const int2* ranges;
-  const int32_t* order;  // work-item order (view * tiles + tile) or null
+  const int32_t* order;    // work-item order (view * tiles + tile) or null
+  const int32_t* view_tf;  // per-view table index (one image per view) or null
   const float4* lut;
   int lut_size, n_tf;
   int width, height, tiles_x, tiles_per_view;
   float bg0, bg1, bg2;
 };
 
-// Loads the TF tables of group [t0, t0+TG) into shared memory (missing
-// tables read as fully transparent).
+// Loads tables [lut0, lut0 + ntg) into shared memory; slots past ntg and
+// table indices outside [0, n_tf) read as fully transparent.
 template <int TG>
-__device__ __forceinline__ void stage_luts(const CompArgs& A, int t0, float4* s_lut) {
+__device__ __forceinline__ void stage_luts(const CompArgs& A, int lut0, int ntg, float4* s_lut) {
   const int L = A.lut_size;
   for (int e = threadIdx.x; e < TG * L; e += blockDim.x) {
-    int t = e / L, k = e - t * L;
-    s_lut[e] = (t0 + t < A.n_tf) ? __ldg(&A.lut[(int64_t)(t0 + t) * L + k])
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int t = e / L, k = e - t * L, ti = lut0 + t;
+    s_lut[e] = (t < ntg && ti >= 0 && ti < A.n_tf) ? __ldg(&A.lut[(int64_t)ti * L + k])
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
 // Stages splat `i` of the tile list into batch slot threadIdx.x: geometry,
 // per-TF colour and A w (and, for the backward, slopes and A), the exponent
-// cutoff and the warp-block mask.  Returns the record index.
+// cutoff, the warp-block mask and the TF visibility mask (bit t set iff
+// A_t w >= 1/255; with the 2D Gaussian <= 1, a clear bit means alpha can
+// never reach 1/255 for that TF).  Returns the record index.
 template <int TG, bool BWD>
 __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* s_lut,
                                                 float tx0, float ty0, float4* s_geo, float2* s_c,
                                                 float4* s_col, float4* s_slope, float* s_A,
-                                                unsigned char* s_mask) {
+                                                unsigned char* s_mask, unsigned char* s_tfm) {
   const int L = A.lut_size;
   const int s = threadIdx.x;
   const uint32_t g = A.vals[i];
@@ -149,6 +152,7 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
   const TfPos q = tf_pos(au.w, L);
   const float sl = (au.w >= 0.0f && au.w <= 1.0f) ? (float)(L - 1) : 0.0f;
   float max_aw = 0.0f;
+  unsigned tfm = 0u;
 #pragma unroll
   for (int t = 0; t < TG; ++t) {
     const float4 lo = s_lut[t * L + q.k], hi = s_lut[t * L + q.k + 1];
@@ -162,10 +166,12 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
       s_A[t * kBatch + s] = Aop;
     }
     max_aw = fmaxf(max_aw, aw);
+    tfm |= (aw >= kAlphaMin ? 1u : 0u) << t;
   }
   const float cut = power_cutoff(max_aw);
   s_c[s] = make_float2(-0.5f * au.z, cut);
   s_mask[s] = (unsigned char)warp_block_mask(ge.x - tx0, ge.y - ty0, au.x, au.y, au.z, cut);
+  s_tfm[s] = (unsigned char)tfm;
   return g;
 }
 
@@ -185,13 +191,16 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
   __shared__ float2 s_c[kBatch];     // -c/2, exponent cutoff
   __shared__ float4 s_col[TG * kBatch];
   __shared__ unsigned char s_mask[kBatch];
+  __shared__ unsigned char s_tfm[kBatch];
   __shared__ unsigned char s_list[kWarps][kBatch];
   const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
   const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
-  const int t0 = blockIdx.z * TG;
-  const int ntg = min(TG, A.n_tf - t0);
+  const int t0 = blockIdx.z * TG;                     // first output image of the group
+  const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
+  const int ntg = A.view_tf ? 1 : min(TG, A.n_tf - t0);
+  const int n_out = A.view_tf ? 1 : A.n_tf;           // images per view
   const int warp = threadIdx.x >> 5;
-  stage_luts<TG>(A, t0, s_lut);
+  stage_luts<TG>(A, lut0, ntg, s_lut);
   int px, py;
   pixel_of(tile, A.tiles_x, px, py);
   const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     const int cnt = min(kBatch, rg.y - start);
     if ((int)threadIdx.x < cnt)
       stage_splat<TG, false>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col, nullptr,
-                             nullptr, s_mask);
+                             nullptr, s_mask, s_tfm);
     __syncthreads();
     const int nw = build_warp_list(s_mask, s_list[warp], cnt);
     const bool act0 = act != 0u;
@@ -229,9 +238,10 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
       if (power < sc.y || power > 0.0f) continue;
       if (STATS) ++n_eval;
       const float G = gauss_of(power);
+      const unsigned live = act & s_tfm[j];  // active TFs that can blend this splat
 #pragma unroll
       for (int t = 0; t < TG; ++t) {
-        if (!(act & (1u << t))) continue;
+        if (!(live & (1u << t))) continue;
         if (STATS) ++n_alpha;
         const float4 c = s_col[t * kBatch + j];
         const float alpha = fminf(kAlphaMax, mul(c.w, G));
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
 #pragma unroll
     for (int t = 0; t < TG; ++t) {
       if (t >= ntg) break;
-      const int64_t o = (((int64_t)view * A.n_tf + t0 + t) * A.height + py) * A.width + px;
+      const int64_t o = (((int64_t)view * n_out + t0 + t) * A.height + py) * A.width + px;
       out[o] = make_float4(add(Cr[t], mul(T[t], A.bg0)), add(Cg[t], mul(T[t], A.bg1)),
                            add(Cb[t], mul(T[t], A.bg2)), T[t]);
       n_contrib[o] = last[t];
@@ -349,15 +359,18 @@ __global__ void __launch_bounds__(256)
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + 8 * kBatch);
   unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + kBatch);
   unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
+  unsigned char* s_tfm = s_lists + kWarps * kBatch;
   __shared__ int s_maxnc;
 
   const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
   const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
-  const int t0 = blockIdx.z * TG;
-  const int ntg = min(TG, A.n_tf - t0);
+  const int t0 = blockIdx.z * TG;                     // first output image of the group
+  const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
+  const int ntg = A.view_tf ? 1 : min(TG, A.n_tf - t0);
+  const int n_out = A.view_tf ? 1 : A.n_tf;           // images per view
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* my_list = s_lists + warp * kBatch;
-  stage_luts<TG>(A, t0, s_lut);
+  stage_luts<TG>(A, lut0, ntg, s_lut);
   for (int e = threadIdx.x; e < 8 * kBatch; e += 256) s_acc[e] = 0.0f;
   if (threadIdx.x == 0) s_maxnc = 0;
   int px, py;
@@ -379,7 +392,7 @@ __global__ void __launch_bounds__(256)
     gr[t] = gg[t] = gb[t] = 0.0f;
     nc[t] = 0;
     if (inside && t < ntg) {
-      const int64_t o = (((int64_t)view * A.n_tf + t0 + t) * A.height + py) * A.width + px;
+      const int64_t o = (((int64_t)view * n_out + t0 + t) * A.height + py) * A.width + px;
       const float4 ov = out[o], dv4 = dout[o];
       nc[t] = n_contrib[o];
       gr[t] = dv4.x;
@@ -409,7 +422,7 @@ __global__ void __launch_bounds__(256)
     const int cnt = min(kBatch, rg.y - start);
     if (i < rg.y)
       s_idx[threadIdx.x] = stage_splat<TG, true>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col,
-                                                 s_slope, s_A, s_mask);
+                                                 s_slope, s_A, s_mask, s_tfm);
     __syncthreads();
     const int nw = build_warp_list(s_mask, my_list, cnt);
     for (int k = 0; k < nw; ++k) {
@@ -427,9 +440,10 @@ __global__ void __launch_bounds__(256)
       if (idx < my_max && power <= 0.0f && power >= scc.y) {
         if (STATS) ++n_eval;
         G = gauss_of(power);
+        const unsigned vis = s_tfm[j];
 #pragma unroll
         for (int t = 0; t < TG; ++t) {
-          if (idx >= nc[t]) continue;
+          if (idx >= nc[t] || !((vis >> t) & 1u)) continue;
           if (STATS) ++n_alpha;
           const float4 c = s_col[t * kBatch + j];
           const float raw = mul(c.w, G);
@@ -514,10 +528,10 @@ __global__ void __launch_bounds__(256)
 }
 
 size_t bwd_smem_bytes(int TG, int L) {
-  // lut, col + slope, geo, (c, cutoff), A, acc[8], idx, mask, warp lists
+  // lut, col + slope, geo, (c, cutoff), A, acc[8], idx, mask, warp lists, tf mask
   return (size_t)TG * L * 16 + (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
          (size_t)kBatch * 8 + (size_t)TG * kBatch * 4 + (size_t)8 * kBatch * 4 +
-         (size_t)kBatch * 4 + (size_t)kBatch + (size_t)kWarps * kBatch;
+         (size_t)kBatch * 4 + (size_t)kBatch + (size_t)kWarps * kBatch + (size_t)kBatch;
 }
 
 int pick_group(int tf_group, int n_tf, bool bwd) {
@@ -538,6 +552,7 @@ CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
   A.vals = vals;
   A.ranges = ranges;
   A.order = order;
+  A.view_tf = tf.view_tf;
   A.lut = reinterpret_cast<const float4*>(tf.lut);
   A.lut_size = tf.lut_size;
   A.n_tf = tf.n_tf;
@@ -577,7 +592,8 @@ veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc
   static size_t configured = 0;
   veg_status st = prepare_smem(kern, smem, &configured);
   if (st != VEG_OK) return st;
-  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, (unsigned)((A.n_tf + TG - 1) / TG));
+  const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
+  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
   kern<<<grid, 256, smem, stream>>>(A, out, nc, stats);
   count_launch();
   return launch_status();
@@ -592,7 +608,8 @@ veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const
   static size_t configured = 0;
   veg_status st = prepare_smem(kern, smem, &configured);
   if (st != VEG_OK) return st;
-  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, (unsigned)((A.n_tf + TG - 1) / TG));
+  const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
+  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
   kern<<<grid, 256, smem, stream>>>(A, out, nc, dout, grad2d, stats);
   count_launch();
   return launch_status();

@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(256)
     project_fwd_kernel(CamSet cams, const float4* __restrict__ mean_v,
                        const float4* __restrict__ logscale_w, const float4* __restrict__ quat,
                        int64_t n, const float4* __restrict__ cull_lut, int lut_size, int n_tf,
-                       float4* __restrict__ geo, float4* __restrict__ aux,
+                       const int32_t* __restrict__ view_tf, float4* __restrict__ geo,
+                       float4* __restrict__ aux,
                        int32_t* __restrict__ tiles, short4* __restrict__ rect) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -143,7 +144,13 @@ __global__ void __launch_bounds__(256)
   if (ok && cull_lut != nullptr) {
     TfPos tp = tf_pos(mv.w, lut_size);
     bool vis = false;
-    for (int t = 0; t < n_tf && !vis; ++t) {
+    int t_lo = 0, t_hi = n_tf;
+    if (view_tf != nullptr) {  // this view is composited with one table only
+      t_lo = view_tf[view];
+      t_hi = t_lo + 1;
+      if (t_lo < 0 || t_lo >= n_tf) t_lo = t_hi = 0;  // transparent table: cull
+    }
+    for (int t = t_lo; t < t_hi && !vis; ++t) {
       const float4* L = cull_lut + (int64_t)t * lut_size;
       float A = lerp_rn(__ldg(&L[tp.k].w), __ldg(&L[tp.k + 1].w), tp);
       vis = !(mul(A, lw.w) < kAlphaMin);
@@ -298,7 +305,7 @@ veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const 
   project_fwd_kernel<<<grid, 256, 0, stream>>>(
       cs, reinterpret_cast<const float4*>(g.mean_v), reinterpret_cast<const float4*>(g.logscale_w),
       reinterpret_cast<const float4*>(g.quat), g.n, lut, cull_tf ? cull_tf->lut_size : 0,
-      cull_tf ? cull_tf->n_tf : 0, geo, aux, tiles, rect);
+      cull_tf ? cull_tf->n_tf : 0, cull_tf ? cull_tf->view_tf : nullptr, geo, aux, tiles, rect);
   count_launch();
   return launch_status();
 }

@@ -33,7 +33,8 @@ class SplatPipeline:
         self.V = len(self.cams)
         self.W, self.H = self.cams[0].width, self.cams[0].height
         self.n_tf = int(n_tf)
-        self.tf_group = int(tf_group)
+        self.tf_group = int(tf_group)      # TFs per compositing pass (forward)
+        self.tf_group_bwd = int(tf_group)  # TFs per pass (backward)
         self.device = torch.device(device)
         self.c_cams = _lib.cameras(self.cams)
         nrec = self.V * self.n
@@ -101,7 +102,8 @@ class SplatPipeline:
 
     def backward(self, dL_dout, grad_mean_v, grad_logscale_w, grad_quat, stream=None):
         _lib.veg_composite_bwd(self.c_cams, self._g, self.geo, self.aux, self.tiles, self.vals,
-                               self.ranges, _lib.tf_desc(self._luts), self._bg, self.tf_group,
+                               self.ranges, _lib.tf_desc(self._luts), self._bg,
+                               self.tf_group_bwd,
                                self.out, self.n_contrib, dL_dout, None, grad_mean_v,
                                grad_logscale_w, grad_quat, self.grad2d, None, stream,
                                tile_order=self.order)
@@ -109,7 +111,8 @@ class SplatPipeline:
     def backward_2d(self, dL_dout, stats=None, stream=None):
         """Screen-space gradients only (into self.grad2d)."""
         _lib.veg_composite_bwd(self.c_cams, self._g, self.geo, self.aux, self.tiles, self.vals,
-                               self.ranges, _lib.tf_desc(self._luts), self._bg, self.tf_group,
+                               self.ranges, _lib.tf_desc(self._luts), self._bg,
+                               self.tf_group_bwd,
                                self.out, self.n_contrib, dL_dout, None, None, None, None,
                                self.grad2d, stats, stream, tile_order=self.order)
 
