@@ -174,7 +174,8 @@ def profiled_traffic(kernel_key):
         rec = json.load(open(path)).get(kernel_key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_sha") != source_hash("composite.cu", "veg_internal.cuh"):
+    if not rec or rec.get("source_sha") != source_hash("composite_kernels.cuh",
+                                                       "veg_internal.cuh"):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -634,13 +635,15 @@ def run_serve(args):
     tfs = torch.as_tensor(S.bump_tfs(16, 32), device="cuda")
     out = {"workload": "serving: 5 resident models, Poisson arrivals, random model/view/TF/"
                        "resolution in {256,512,1024,2048}^2"}
-    for rate in (args.rate, args.rate * 10):
+    srv = RenderServer(models, tfs, n_slots=4, max_batch=8)
+    fsrv = RenderServer(models, tfs, n_slots=1)
+    out["slot_bytes"] = srv.bytes
+    for rate in (args.rate, args.rate * 2, args.rate * 4):
         warm = poisson_requests(models, 16, rate, 5.0, 40)
-        meas = poisson_requests(models, 16, rate, args.duration, 41)
-        srv = RenderServer(models, tfs, n_slots=4, max_batch=8)
         srv.run(warm)
-        res = latency_stats(srv.run(meas))
-        fsrv = RenderServer(models, tfs)
+        srv.batch_sizes.clear()
+        res = latency_stats(srv.run(poisson_requests(models, 16, rate, args.duration, 41)))
+        res["mean_batch"] = float(np.mean(srv.batch_sizes))
         fifo_serve(fsrv, warm)
         base = latency_stats(fifo_serve(fsrv, poisson_requests(models, 16, rate, args.duration,
                                                                41)))

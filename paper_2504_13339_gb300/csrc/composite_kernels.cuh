@@ -136,14 +136,12 @@ __device__ __forceinline__ void stage_luts(const CompArgs& A, int lut0, int ntg,
 
 // Stages splat `i` of the tile list into batch slot threadIdx.x: geometry,
 // per-TF colour and A w (and, for the backward, slopes and A), the exponent
-// cutoff, the warp-block mask and the TF visibility mask (bit t set iff
-// A_t w >= 1/255; with the 2D Gaussian <= 1, a clear bit means alpha can
-// never reach 1/255 for that TF).  Returns the record index.
+// cutoff and the warp-block mask.  Returns the record index.
 template <int TG, bool BWD>
 __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* s_lut,
                                                 float tx0, float ty0, float4* s_geo, float2* s_c,
                                                 float4* s_col, float4* s_slope, float* s_A,
-                                                unsigned char* s_mask, unsigned char* s_tfm) {
+                                                unsigned char* s_mask) {
   const int L = A.lut_size;
   const int s = threadIdx.x;
   const uint32_t g = A.vals[i];
@@ -152,7 +150,6 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
   const TfPos q = tf_pos(au.w, L);
   const float sl = (au.w >= 0.0f && au.w <= 1.0f) ? (float)(L - 1) : 0.0f;
   float max_aw = 0.0f;
-  unsigned tfm = 0u;
 #pragma unroll
   for (int t = 0; t < TG; ++t) {
     const float4 lo = s_lut[t * L + q.k], hi = s_lut[t * L + q.k + 1];
@@ -166,12 +163,10 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
       s_A[t * kBatch + s] = Aop;
     }
     max_aw = fmaxf(max_aw, aw);
-    tfm |= (aw >= kAlphaMin ? 1u : 0u) << t;
   }
   const float cut = power_cutoff(max_aw);
   s_c[s] = make_float2(-0.5f * au.z, cut);
   s_mask[s] = (unsigned char)warp_block_mask(ge.x - tx0, ge.y - ty0, au.x, au.y, au.z, cut);
-  s_tfm[s] = (unsigned char)tfm;
   return g;
 }
 
@@ -191,7 +186,6 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
   __shared__ float2 s_c[kBatch];     // -c/2, exponent cutoff
   __shared__ float4 s_col[TG * kBatch];
   __shared__ unsigned char s_mask[kBatch];
-  __shared__ unsigned char s_tfm[kBatch];
   __shared__ unsigned char s_list[kWarps][kBatch];
   const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
   const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
@@ -224,7 +218,7 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     const int cnt = min(kBatch, rg.y - start);
     if ((int)threadIdx.x < cnt)
       stage_splat<TG, false>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col, nullptr,
-                             nullptr, s_mask, s_tfm);
+                             nullptr, s_mask);
     __syncthreads();
     const int nw = build_warp_list(s_mask, s_list[warp], cnt);
     const bool act0 = act != 0u;
@@ -238,10 +232,9 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
       if (power < sc.y || power > 0.0f) continue;
       if (STATS) ++n_eval;
       const float G = gauss_of(power);
-      const unsigned live = act & s_tfm[j];  // active TFs that can blend this splat
 #pragma unroll
       for (int t = 0; t < TG; ++t) {
-        if (!(live & (1u << t))) continue;
+        if (!(act & (1u << t))) continue;
         if (STATS) ++n_alpha;
         const float4 c = s_col[t * kBatch + j];
         const float alpha = fminf(kAlphaMax, mul(c.w, G));
@@ -359,7 +352,6 @@ __global__ void __launch_bounds__(256)
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + 8 * kBatch);
   unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + kBatch);
   unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
-  unsigned char* s_tfm = s_lists + kWarps * kBatch;
   __shared__ int s_maxnc;
 
   const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
@@ -422,7 +414,7 @@ __global__ void __launch_bounds__(256)
     const int cnt = min(kBatch, rg.y - start);
     if (i < rg.y)
       s_idx[threadIdx.x] = stage_splat<TG, true>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col,
-                                                 s_slope, s_A, s_mask, s_tfm);
+                                                 s_slope, s_A, s_mask);
     __syncthreads();
     const int nw = build_warp_list(s_mask, my_list, cnt);
     for (int k = 0; k < nw; ++k) {
@@ -440,10 +432,9 @@ __global__ void __launch_bounds__(256)
       if (idx < my_max && power <= 0.0f && power >= scc.y) {
         if (STATS) ++n_eval;
         G = gauss_of(power);
-        const unsigned vis = s_tfm[j];
 #pragma unroll
         for (int t = 0; t < TG; ++t) {
-          if (idx >= nc[t] || !((vis >> t) & 1u)) continue;
+          if (idx >= nc[t]) continue;
           if (STATS) ++n_alpha;
           const float4 c = s_col[t * kBatch + j];
           const float raw = mul(c.w, G);
@@ -528,10 +519,10 @@ __global__ void __launch_bounds__(256)
 }
 
 size_t bwd_smem_bytes(int TG, int L) {
-  // lut, col + slope, geo, (c, cutoff), A, acc[8], idx, mask, warp lists, tf mask
+  // lut, col + slope, geo, (c, cutoff), A, acc[8], idx, mask, warp lists
   return (size_t)TG * L * 16 + (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
          (size_t)kBatch * 8 + (size_t)TG * kBatch * 4 + (size_t)8 * kBatch * 4 +
-         (size_t)kBatch * 4 + (size_t)kBatch + (size_t)kWarps * kBatch + (size_t)kBatch;
+         (size_t)kBatch * 4 + (size_t)kBatch + (size_t)kWarps * kBatch;
 }
 
 int pick_group(int tf_group, int n_tf, bool bwd) {

@@ -5,20 +5,22 @@ colour and opacity come from the TF at render time), one resident copy of each
 model serves every (view, TF) request.  The server keeps several models on
 the device and admits render requests (model, camera, TF, resolution):
 
-* a request waits in a queue until a stream slot is free; a free slot takes
-  the oldest waiting request and every other waiting request for the same
-  model and resolution (up to `max_batch`), and renders them as one batch:
-  one projection + binning + sort over all the batch's views and one
-  compositing launch in which view v uses its own TF (`veg_tf.view_tf`);
-* requests that arrive while batches are on the GPU are admitted as soon as
-  a slot frees, and the slots run on separate CUDA streams, so their work
-  overlaps on the device (continuous batching, not a queue drained one batch
-  at a time);
-* device buffers are sized per (model, resolution, batch) and cached per
-  slot; a byte budget bounds them (least recently used idle buffers are
-  released first), which is the admission-by-memory rule;
-* latency = result ready (the batch's completion event observed on the host)
-  minus arrival time.
+* Memory: each stream slot owns one fixed set of device buffers, allocated
+  up front (records, tile instances, pixels, views).  The number of slots is
+  what the memory budget admits; nothing is allocated while serving.
+* Batching: a free slot takes the oldest waiting request and every other
+  waiting request for the same model and resolution that still fits its
+  buffers (records = views x Gaussians, pixels, estimated tile instances),
+  and renders them as one batch: one projection + binning + sort over all
+  the batch's views and one compositing launch in which view v uses its own
+  TF (`veg_tf.view_tf`).
+* Continuity: requests that arrive while batches run are admitted as soon as
+  a slot frees; slots run on separate CUDA streams, so their work overlaps
+  on the device.
+* Latency = result ready (the batch's completion event observed on the host)
+  minus arrival time.  The per-(model, resolution) instance estimate is
+  learned from completed batches; a batch that overflowed its instance
+  buffer is rendered again one request at a time.
 
 `fifo_serve` is the comparison path: one request at a time, in arrival order,
 each as a plain single-view render.
@@ -27,7 +29,7 @@ from __future__ import annotations
 
 import math
 import time
-from collections import OrderedDict, deque
+from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -51,32 +53,38 @@ class Request:
         return self.done - self.arrival
 
 
-class _Buffers:
-    """Device buffers for batches of up to `vmax` views of one model at one
-    resolution, one image per view."""
+@dataclass
+class SlotLimits:
+    records: int = 12_000_000    # views x Gaussians per batch
+    instances: int = 160_000_000
+    pixels: int = 16 << 20       # views x width x height per batch
+    views: int = 8
+    max_side: int = 2048
 
-    def __init__(self, n, vmax, width, height, capacity, device):
-        self.n, self.vmax, self.W, self.H = n, vmax, width, height
-        self.tiles = ((width + 15) // 16) * ((height + 15) // 16)
-        nrec = n * vmax
+
+class _SlotBuffers:
+    """One slot's device memory, reused by every batch it renders."""
+
+    def __init__(self, lim: SlotLimits, device):
         d = device
-        self.geo = torch.empty(nrec, 4, device=d)
-        self.aux = torch.empty(nrec, 4, device=d)
-        self.count = torch.empty(nrec, dtype=torch.int32, device=d)
-        self.rect = torch.empty(nrec, 4, dtype=torch.int16, device=d)
-        self.ranges = torch.empty(vmax * self.tiles, 2, dtype=torch.int32, device=d)
-        self.order = torch.empty(vmax * self.tiles, dtype=torch.int32, device=d)
-        self.out = torch.empty(vmax, 1, height, width, 4, device=d)
-        self.nc = torch.empty(vmax, 1, height, width, dtype=torch.int32, device=d)
-        self.view_tf = torch.zeros(vmax, dtype=torch.int32, device=d)
-        self.view_tf_host = torch.zeros(vmax, dtype=torch.int32).pin_memory()
-        self.set_capacity(capacity, device)
-
-    def set_capacity(self, capacity, device):
-        self.capacity = int(capacity)
-        ws = _lib.veg_bin_sort_workspace_size(self.n, self.vmax, self.capacity, self.W, self.H)
-        self.ws = torch.empty(ws, dtype=torch.uint8, device=device)
-        self.vals = torch.empty(max(1, self.capacity), dtype=torch.int32, device=device)
+        self.lim = lim
+        R, P, V = lim.records, lim.pixels, lim.views
+        tiles = V * ((lim.max_side + 15) // 16) ** 2
+        self.geo = torch.empty(R, 4, device=d)
+        self.aux = torch.empty(R, 4, device=d)
+        self.count = torch.empty(R, dtype=torch.int32, device=d)
+        self.rect = torch.empty(R, 4, dtype=torch.int16, device=d)
+        self.ranges = torch.empty(tiles, 2, dtype=torch.int32, device=d)
+        self.order = torch.empty(tiles, dtype=torch.int32, device=d)
+        self.out = torch.empty(P * 4, device=d)
+        self.nc = torch.empty(P, dtype=torch.int32, device=d)
+        self.view_tf = torch.zeros(V, dtype=torch.int32, device=d)
+        self.view_tf_host = torch.zeros(V, dtype=torch.int32).pin_memory()
+        self.n_inst = torch.zeros(1, dtype=torch.int64, device=d)
+        # the workspace layout depends only on records and capacity
+        ws = _lib.veg_bin_sort_workspace_size(R, 1, lim.instances, lim.max_side, lim.max_side)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=d)
+        self.vals = torch.empty(lim.instances, dtype=torch.int32, device=d)
 
     def nbytes(self):
         return sum(t.numel() * t.element_size() for t in (
@@ -87,144 +95,142 @@ class _Buffers:
 @dataclass
 class _Slot:
     stream: torch.cuda.Stream
+    bufs: _SlotBuffers
     event: torch.cuda.Event | None = None
     batch: list = field(default_factory=list)
-    key: tuple | None = None
-    bufs: "OrderedDict[tuple, _Buffers]" = field(default_factory=OrderedDict)
 
 
 class RenderServer:
     """Continuous-batching render server (see module docstring)."""
 
-    def __init__(self, models, tf_bank, n_slots=4, max_batch=8, mem_budget=64 << 30,
-                 bg=(0.0, 0.0, 0.0), instances_per_view=None, keep_images=False,
-                 device="cuda"):
+    def __init__(self, models, tf_bank, n_slots=4, max_batch=8, limits=None,
+                 mem_budget=None, bg=(0.0, 0.0, 0.0), keep_images=False, device="cuda"):
         _lib.load()
         self.device = torch.device(device)
         self.models = {k: tuple(t.contiguous() for t in v) for k, v in models.items()}
         self.tf_bank = tf_bank.contiguous()
-        self.max_batch = int(max_batch)
-        self.budget = int(mem_budget)
+        self.lim = limits or SlotLimits()
+        self.lim.views = min(self.lim.views, int(max_batch))
         self.bg = tuple(float(b) for b in bg)
         self.keep = keep_images
-        self.slots = [_Slot(torch.cuda.Stream(self.device)) for _ in range(n_slots)]
-        # instance estimate per (model, width, height): grows on overflow
-        self.inst = dict(instances_per_view or {})
-        self.allocated = 0
+        self.slots = []
+        used = 0
+        for _ in range(n_slots):
+            b = _SlotBuffers(self.lim, self.device)
+            used += b.nbytes()
+            self.slots.append(_Slot(torch.cuda.Stream(self.device), b))
+            if mem_budget is not None and used > mem_budget and len(self.slots) > 1:
+                self.slots.pop()  # admission by memory: no more slots than fit
+                break
+        self.bytes = used
+        self.inst = {}  # (model, W, H) -> tile instances per view (largest seen)
+        self.batch_sizes = []
 
-    # -- buffers -------------------------------------------------------------
-    def _capacity_for(self, model, W, H, k):
+    def _est(self, model, W, H):
         n = self.models[model][0].shape[0]
-        per_view = self.inst.get((model, W, H), 12 * n)
-        return int(per_view * k * 1.25) + 4096
+        return self.inst.get((model, W, H), min(16 * n, self.lim.instances))
 
-    def _buffers(self, slot, model, W, H):
-        key = (model, W, H)
-        if key in slot.bufs:
-            slot.bufs.move_to_end(key)
-            return slot.bufs[key]
+    def _fits(self, model, W, H, k):
         n = self.models[model][0].shape[0]
-        cap = self._capacity_for(model, W, H, self.max_batch)
-        # admission by memory: release least recently used idle buffers
-        need = n * self.max_batch * 56 + cap * 16 + self.max_batch * W * H * 20
-        while self.allocated + need > self.budget and self._evict_one(slot):
-            pass
-        b = _Buffers(n, self.max_batch, W, H, cap, self.device)
-        self.allocated += b.nbytes()
-        slot.bufs[key] = b
-        return b
-
-    def _evict_one(self, current):
-        for s in self.slots:
-            if s is not current and s.event is not None:
-                continue  # busy
-            for key in list(s.bufs):
-                if s is current and len(s.bufs) == 1:
-                    break
-                b = s.bufs.pop(key)
-                self.allocated -= b.nbytes()
-                return True
-        return False
+        return (k <= self.lim.views and k * n <= self.lim.records
+                and k * W * H <= self.lim.pixels
+                and k * self._est(model, W, H) <= self.lim.instances)
 
     # -- one batch -------------------------------------------------------------
     def _launch(self, slot, batch):
         r0 = batch[0]
         W, H = r0.camera.width, r0.camera.height
-        b = self._buffers(slot, r0.model, W, H)
+        b = slot.bufs
         k = len(batch)
+        n = self.models[r0.model][0].shape[0]
         g = _lib.gaussians(*self.models[r0.model])
         cams = _lib.cameras([r.camera for r in batch])
+        tiles = ((W + 15) // 16) * ((H + 15) // 16)
         for i, r in enumerate(batch):
             b.view_tf_host[i] = r.tf
-        with torch.cuda.stream(slot.stream):
+        s = slot.stream
+        with torch.cuda.stream(s):
             b.view_tf[:k].copy_(b.view_tf_host[:k], non_blocking=True)
             tf = _lib.tf_desc(self.tf_bank, b.view_tf)
-            s = slot.stream
+            out = b.out[:k * H * W * 4].view(k, 1, H, W, 4)
+            nc = b.nc[:k * H * W].view(k, 1, H, W)
             _lib.veg_project(cams, g, tf, b.geo, b.aux, b.count, b.rect, s)
-            _lib.veg_bin_sort(cams, b.n, b.geo, b.count, b.rect, b.ws, b.capacity, None, b.vals,
-                              b.ranges, s)
-            _lib.veg_tile_order(b.ranges[:k * b.tiles], b.order, s)
-            _lib.veg_composite_fwd(cams, b.n, b.geo, b.aux, b.vals, b.ranges, tf, self.bg, 1,
-                                   b.out, b.nc, None, s, tile_order=b.order)
+            _lib.veg_bin_sort(cams, n, b.geo, b.count, b.rect, b.ws, self.lim.instances, None,
+                              b.vals, b.ranges, s)
+            _lib.veg_tile_order(b.ranges[:k * tiles], b.order, s)
+            _lib.veg_composite_fwd(cams, n, b.geo, b.aux, b.vals, b.ranges, tf, self.bg, 1, out,
+                                   nc, None, s, tile_order=b.order)
             ev = torch.cuda.Event()
             ev.record(s)
-        slot.event, slot.batch, slot.key = ev, batch, (r0.model, W, H)
+        slot.event, slot.batch = ev, batch
+        self.batch_sizes.append(k)
+        return out
 
-    def _finish(self, slot, now):
-        b = slot.bufs[slot.key]
-        st, m = _lib.veg_sync_status(b.ws, slot.stream)
-        k = len(slot.batch)
-        model, W, H = slot.key
-        self.inst[(model, W, H)] = max(self.inst.get((model, W, H), 0), m // k + 1)
-        if st != _lib.VEG_OK:  # capacity overflow: grow and render the batch again
-            self.allocated -= b.nbytes()
-            b.set_capacity(int(m * 1.25) + 4096, self.device)
-            self.allocated += b.nbytes()
-            batch = slot.batch
-            self._launch(slot, batch)
-            slot.event.synchronize()
-            now = self.clock()
-        for i, r in enumerate(slot.batch):
+    def _finish(self, slot):
+        b = slot.bufs
+        st, m = _lib.veg_sync_status(b.ws, slot.stream)  # the stream is already done
+        batch = slot.batch
+        r0 = batch[0]
+        key = (r0.model, r0.camera.width, r0.camera.height)
+        self.inst[key] = max(self.inst.get(key, 0), int(m / len(batch) * 1.2) + 1)
+        if st != _lib.VEG_OK:  # overflow: render the batch again one request at a time
+            for r in batch:
+                out = self._launch(slot, [r])
+                slot.event.synchronize()
+                self._complete(slot, [r], out)
+        else:
+            H, W = r0.camera.height, r0.camera.width
+            self._complete(slot, batch, b.out[:len(batch) * H * W * 4].view(len(batch), 1, H, W,
+                                                                            4))
+        slot.event, slot.batch = None, []
+        return batch
+
+    def _complete(self, slot, batch, out):
+        now = self.clock()
+        for i, r in enumerate(batch):
             r.done = now
             if self.keep:
-                r.image = b.out[i, 0].clone()
-        done = slot.batch
-        slot.event, slot.batch, slot.key = None, [], None
-        return done
+                r.image = out[i, 0].clone()
 
     # -- the loop --------------------------------------------------------------
     def clock(self):
         return time.perf_counter() - self.t0
 
+    def _take_batch(self, pending):
+        head = pending[0]
+        key = (head.model, head.camera.width, head.camera.height)
+        batch = [head]
+        for r in list(pending)[1:]:
+            if (r.model, r.camera.width, r.camera.height) == key and \
+                    self._fits(head.model, key[1], key[2], len(batch) + 1):
+                batch.append(r)
+        for r in batch:
+            pending.remove(r)
+        return batch
+
     def run(self, requests, poll_s=20e-6):
-        """Serves `requests` (sorted by arrival, arrival times relative to the
-        start); returns them completed.  Arrivals are released in real time."""
+        """Serves `requests` (arrival times relative to the start, released in
+        real time); returns them completed."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = deque()
-        done = []
+        n_done = 0
         nxt = 0
         self.t0 = time.perf_counter()
-        while len(done) < len(reqs):
+        while n_done < len(reqs):
             now = self.clock()
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
                 pending.append(reqs[nxt])
                 nxt += 1
             for s in self.slots:
                 if s.event is not None and s.event.query():
-                    done.extend(self._finish(s, self.clock()))
+                    n_done += len(self._finish(s))
             for s in self.slots:
                 if s.event is None and pending:
-                    head = pending[0]
-                    key = (head.model, head.camera.width, head.camera.height)
-                    batch = [r for r in pending
-                             if (r.model, r.camera.width, r.camera.height) == key][:self.max_batch]
-                    for r in batch:
-                        pending.remove(r)
-                    self._launch(s, batch)
-            if not pending and nxt < len(reqs):
+                    self._launch(s, self._take_batch(pending))
+            if not pending and nxt < len(reqs) and all(s.event is None for s in self.slots):
                 wait = reqs[nxt].arrival - self.clock()
-                if wait > 1e-3:
-                    time.sleep(min(wait, 1e-3) * 0.5)
+                if wait > 2e-4:
+                    time.sleep(wait * 0.5)
             elif poll_s:
                 time.sleep(poll_s)
         return reqs
@@ -232,13 +238,13 @@ class RenderServer:
 
 def fifo_serve(server: RenderServer, requests, poll_s=20e-6):
     """One request at a time in arrival order on one stream (the plain path)."""
-    saved = (server.max_batch, server.slots)
+    saved = (server.lim.views, server.slots)
     server.slots = server.slots[:1]
-    server.max_batch = 1
+    server.lim.views = 1
     try:
         return server.run(requests, poll_s)
     finally:
-        server.max_batch, server.slots = saved
+        server.lim.views, server.slots = saved
 
 
 def latency_stats(reqs):

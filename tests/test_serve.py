@@ -5,8 +5,8 @@ import pytest
 import torch
 
 from paper_2504_13339_gb300 import _lib, scenes as S
-from paper_2504_13339_gb300.serve import (Request, RenderServer, fifo_serve, latency_stats,
-                                          poisson_requests)
+from paper_2504_13339_gb300.serve import (Request, RenderServer, SlotLimits, fifo_serve,
+                                          latency_stats, poisson_requests)
 
 
 def test_poisson_requests_are_seeded_and_in_range():
@@ -42,24 +42,25 @@ def test_results_same_alone_and_in_the_mix():
     reqs = poisson_requests(models, 6, rate=400.0, duration=0.15, seed=9,
                             resolutions=(64, 96, 128))
     assert len(reqs) >= 20
-    mixed = RenderServer(models, tfs, n_slots=3, max_batch=6, keep_images=True)
+    lim = lambda: SlotLimits(records=200_000, instances=4_000_000, pixels=1 << 20, views=6,
+                             max_side=128)
+    mixed = RenderServer(models, tfs, n_slots=3, max_batch=6, limits=lim(), keep_images=True)
     out_mix = mixed.run(reqs)
     assert all(r.image is not None for r in out_mix)
+    assert max(mixed.batch_sizes) > 1  # requests were really batched together
     # each request alone: fresh copies of the requests, one at a time
     alone = [Request(r.rid, r.model, r.camera, r.tf, 0.0) for r in reqs]
-    single = RenderServer(models, tfs, n_slots=1, max_batch=1, keep_images=True)
+    single = RenderServer(models, tfs, n_slots=1, max_batch=1, limits=lim(), keep_images=True)
     for a in alone:
         single.run([a])
     by_id = {r.rid: r for r in out_mix}
-    batched = 0
     for a in alone:
         m = by_id[a.rid]
         assert torch.equal(a.image, m.image), a.rid
     st = latency_stats(out_mix)
     assert st["p99_ms"] >= st["p50_ms"] > 0
     # the FIFO comparison path renders the same pixels
-    fifo = fifo_serve(RenderServer(models, tfs, keep_images=True),
+    fifo = fifo_serve(RenderServer(models, tfs, limits=lim(), keep_images=True),
                       [Request(r.rid, r.model, r.camera, r.tf, r.arrival) for r in reqs])
     for f in fifo:
         assert torch.equal(f.image, by_id[f.rid].image)
-    assert batched == 0
