@@ -180,6 +180,22 @@ def profiled_traffic(kernel_key):
     return rec.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(value_ms, world, device=None):
+    """The job's time: the largest of the ranks' times (every rank calls)."""
+    if world <= 1:
+        return float(value_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, time_ms):
+    """Units processed by all ranks divided by the job's time (per second)."""
+    return world * units_per_rank / (time_ms * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -233,11 +249,7 @@ def run_gpu(args):
     step_ms = [e[4].elapsed_time(e[5]) for e in evs]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, device)
 
     # ---- end to end through the public API with host buffers ---------------
     tgt_host = target.cpu().pin_memory()
@@ -255,11 +267,7 @@ def run_gpu(args):
         loss_host.copy_(p.loss, non_blocking=True)
         ev2[k][1].record(stream)
     barrier()
-    e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in ev2]))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev2])), world, device)
     h2d = tgt_host.numel() * 4 + lut_host.numel() * 4
     d2h = 4
 
@@ -297,7 +305,7 @@ def run_gpu(args):
                               f"x 2 (FMA) x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
                 "avg_launch_ms": round(dom_ms, 4), "flops_per_launch": dom_flops}
 
-    steps_per_s = world * K / (total_ms * 1e-3)
+    steps_per_s = whole_job_rate(K, world, total_ms)
     mpix = world * K * p.out.numel() // 4 / (total_ms * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": round(steps_per_s, 3), "unit": "steps/s",
@@ -316,7 +324,7 @@ def run_gpu(args):
                  "fwd_tflops": round(fwd_flops / (fwd_avg * 1e-3) / 1e12, 3),
                  "bwd_tflops": round(bwd_flops / (bwd_avg * 1e-3) / 1e12, 3)},
         "clocks": clk,
-        "e2e": {"value": round(world * K / (e2e_ms * 1e-3), 3), "unit": "steps/s",
+        "e2e": {"value": round(whole_job_rate(K, world, e2e_ms), 3), "unit": "steps/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roofline,

@@ -39,7 +39,8 @@ def test_results_same_alone_and_in_the_mix():
         g, _ = S.field_gaussians(n, 4, seed)
         models[name] = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
     tfs = torch.as_tensor(S.bump_tfs(6, 5), device="cuda")
-    reqs = poisson_requests(models, 6, rate=400.0, duration=0.15, seed=9,
+    # a burst (~40 requests within 2 ms) so that requests queue and batch
+    reqs = poisson_requests(models, 6, rate=20000.0, duration=0.002, seed=9,
                             resolutions=(64, 96, 128))
     assert len(reqs) >= 20
     lim = lambda: SlotLimits(records=200_000, instances=4_000_000, pixels=1 << 20, views=6,
