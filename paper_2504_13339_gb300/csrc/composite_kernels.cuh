@@ -223,15 +223,8 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     const int nw = build_warp_list(s_mask, s_list[warp], cnt);
     const bool act0 = act != 0u;
     int jstop = cnt;  // 1 + batch position where this pixel terminated
-    for (int k = 0; k < nw && act; ++k) {
-      const int j = s_list[warp][k];
-      const float4 sg = s_geo[j];
-      const float2 sc = s_c[j];
-      const float power = power_of(sub(sg.x, fx), sub(sg.y, fy), sg.z, sg.w, sc.x);
-      if (STATS) ++n_it;
-      if (power < sc.y || power > 0.0f) continue;
-      if (STATS) ++n_eval;
-      const float G = gauss_of(power);
+    // Eq. 1 update of every live TF of the group with splat j (exponent G).
+    auto blend = [&](int j, float G) {
 #pragma unroll
       for (int t = 0; t < TG; ++t) {
         if (!(act & (1u << t))) continue;
@@ -253,6 +246,34 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
         if (STATS) ++n_blend;
       }
       if (STATS && !act) jstop = j + 1;
+    };
+    // two splats per step: their exponents are independent and overlap,
+    // the blends stay in list order
+    int k = 0;
+    for (; k + 1 < nw && act; k += 2) {
+      const int j0 = s_list[warp][k], j1 = s_list[warp][k + 1];
+      const float4 g0 = s_geo[j0], g1 = s_geo[j1];
+      const float2 c0 = s_c[j0], c1 = s_c[j1];
+      const float p0 = power_of(sub(g0.x, fx), sub(g0.y, fy), g0.z, g0.w, c0.x);
+      const float p1 = power_of(sub(g1.x, fx), sub(g1.y, fy), g1.z, g1.w, c1.x);
+      const bool e0 = !(p0 < c0.y || p0 > 0.0f), e1 = !(p1 < c1.y || p1 > 0.0f);
+      if (STATS) {
+        n_it += 2;
+        n_eval += (unsigned)e0 + (unsigned)e1;
+      }
+      if (e0) blend(j0, gauss_of(p0));
+      if (e1 && act) blend(j1, gauss_of(p1));
+    }
+    if (k < nw && act) {
+      const int j = s_list[warp][k];
+      const float4 sg = s_geo[j];
+      const float2 sc = s_c[j];
+      const float power = power_of(sub(sg.x, fx), sub(sg.y, fy), sg.z, sg.w, sc.x);
+      if (STATS) ++n_it;
+      if (!(power < sc.y || power > 0.0f)) {
+        if (STATS) ++n_eval;
+        blend(j, gauss_of(power));
+      }
     }
     if (STATS && act0) n_vis += (unsigned long long)jstop;
   }
