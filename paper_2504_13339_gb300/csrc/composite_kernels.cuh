@@ -336,6 +336,36 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane
   return y;
 }
 
+// The same for sixteen values with 16 shuffles (halving at offsets 16, 8, 4,
+// 2, then one full step at offset 1).  Lane l returns the warp total of
+// slot l >> 1.
+__device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int lane) {
+  const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2;
+  float w[8], x[4], y[2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float send = b16 ? v[i] : v[i + 8];
+    const float keep = b16 ? v[i + 8] : v[i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b8 ? w[i] : w[i + 4];
+    const float keep = b8 ? w[i + 4] : w[i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b4 ? x[i] : x[i + 2];
+    const float keep = b4 ? x[i + 2] : x[i];
+    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const float send = b2 ? y[0] : y[1];
+  float z = (b2 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  return z;
+}
+
 __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
                "f"(d)
@@ -438,66 +468,87 @@ __global__ void __launch_bounds__(256)
                                                  s_slope, s_A, s_mask);
     __syncthreads();
     const int nw = build_warp_list(s_mask, my_list, cnt);
-    for (int k = 0; k < nw; ++k) {
-      const int j = my_list[k];
-      const int idx = start + j - rg.x;  // list position
-      if (idx >= warp_max) break;
-      if (STATS) ++n_it;
-      float dG = 0.f, dvv = 0.f, dww = 0.f;
-      const float4 sg = s_geo[j];
-      const float2 scc = s_c[j];
-      const float sc = scc.x;
-      const float dx = sub(sg.x, fx), dy = sub(sg.y, fy);
-      const float power = power_of(dx, dy, sg.z, sg.w, sc);
-      float G = 0.f;
-      if (idx < my_max && power <= 0.0f && power >= scc.y) {
-        if (STATS) ++n_eval;
-        G = gauss_of(power);
+    // replayed blend of splat j at list position idx for every TF of the
+    // group: accumulates dL/dG, dL/dv, dL/dw of this pixel
+    auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dww) {
 #pragma unroll
-        for (int t = 0; t < TG; ++t) {
-          if (idx >= nc[t]) continue;
-          if (STATS) ++n_alpha;
-          const float4 c = s_col[t * kBatch + j];
-          const float raw = mul(c.w, G);
-          const float alpha = fminf(kAlphaMax, raw);
-          if (alpha < kAlphaMin) continue;
-          if (STATS) {
-            ++n_blend;
-            n_free += (raw <= kAlphaMax);
-          }
-          const float wgt = mul(alpha, T[t]);
-          const float cgd = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
-          S[t] += cgd * wgt;
-          const float one_m = sub(1.0f, alpha);
-          const float dalpha = T[t] * cgd - __fdividef(K[t] - S[t], one_m);
-          const float4 sl = s_slope[t * kBatch + j];
-          dvv += wgt * (gr[t] * sl.x + gg[t] * sl.y + gb[t] * sl.z);
-          if (raw <= kAlphaMax) {
-            const float daw = dalpha * G;
-            dvv += daw * sl.w;
-            dww += daw * s_A[t * kBatch + j];
-            dG += dalpha * c.w;
-          }
-          T[t] = mul(T[t], one_m);
+      for (int t = 0; t < TG; ++t) {
+        if (idx >= nc[t]) continue;
+        if (STATS) ++n_alpha;
+        const float4 c = s_col[t * kBatch + j];
+        const float raw = mul(c.w, G);
+        const float alpha = fminf(kAlphaMax, raw);
+        if (alpha < kAlphaMin) continue;
+        if (STATS) {
+          ++n_blend;
+          n_free += (raw <= kAlphaMax);
         }
+        const float wgt = mul(alpha, T[t]);
+        const float cgd = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
+        S[t] += cgd * wgt;
+        const float one_m = sub(1.0f, alpha);
+        const float dalpha = T[t] * cgd - __fdividef(K[t] - S[t], one_m);
+        const float4 sl = s_slope[t * kBatch + j];
+        dvv += wgt * (gr[t] * sl.x + gg[t] * sl.y + gb[t] * sl.z);
+        if (raw <= kAlphaMax) {
+          const float daw = dalpha * G;
+          dvv += daw * sl.w;
+          dww += daw * s_A[t * kBatch + j];
+          dG += dalpha * c.w;
+        }
+        T[t] = mul(T[t], one_m);
       }
-      const float dp = dG * G;
-      if (STATS) n_grad += (dG != 0.f);
-      const bool nz = (dp != 0.f) || (dvv != 0.f) || (dww != 0.f);
+    };
+    // screen-space gradient parts of one pair: u_x, u_y, conic a, b, c, v, w
+    auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float dx, float dy, float dvv,
+                          float dww) {
+      v[0] = dp * (2.0f * sg.z * dx + sg.w * dy);
+      v[1] = dp * (2.0f * sc * dy + sg.w * dx);
+      v[2] = dp * (-0.5f * dx * dx);
+      v[3] = dp * (-dx * dy);
+      v[4] = dp * (-0.5f * dy * dy);
+      v[5] = dvv;
+      v[6] = dww;
+      v[7] = 0.0f;
+    };
+    // two splats per step: independent geometry and exponentials overlap,
+    // the replay stays in list order, and one 16-slot reduce-scatter sums
+    // both splats' gradients over the warp
+    for (int k = 0; k < nw; k += 2) {
+      const int j0 = my_list[k];
+      const int idx0 = start + j0 - rg.x;  // list position
+      if (idx0 >= warp_max) break;
+      const bool has1 = (k + 1 < nw) && (start + my_list[k + 1] - rg.x < warp_max);
+      const int j1 = has1 ? my_list[k + 1] : j0;
+      const int idx1 = start + j1 - rg.x;
+      if (STATS) n_it += 1 + (unsigned)has1;
+      const float4 sg0 = s_geo[j0], sg1 = s_geo[j1];
+      const float2 sc0 = s_c[j0], sc1 = s_c[j1];
+      const float dx0 = sub(sg0.x, fx), dy0 = sub(sg0.y, fy);
+      const float dx1 = sub(sg1.x, fx), dy1 = sub(sg1.y, fy);
+      const float p0 = power_of(dx0, dy0, sg0.z, sg0.w, sc0.x);
+      const float p1 = power_of(dx1, dy1, sg1.z, sg1.w, sc1.x);
+      const bool ev0 = idx0 < my_max && p0 <= 0.0f && p0 >= sc0.y;
+      const bool ev1 = has1 && idx1 < my_max && p1 <= 0.0f && p1 >= sc1.y;
+      const float G0 = ev0 ? gauss_of(p0) : 0.f;
+      const float G1 = ev1 ? gauss_of(p1) : 0.f;
+      float dG0 = 0.f, dv0 = 0.f, dw0 = 0.f, dG1 = 0.f, dv1 = 0.f, dw1 = 0.f;
+      if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dw0);
+      if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dw1);
+      if (STATS) n_eval += (unsigned)ev0 + (unsigned)ev1;
+      if (STATS) n_grad += (unsigned)(dG0 != 0.f) + (unsigned)(dG1 != 0.f);
+      const float dp0 = dG0 * G0, dp1 = dG1 * G1;
+      const bool nz = dp0 != 0.f || dv0 != 0.f || dw0 != 0.f || dp1 != 0.f || dv1 != 0.f ||
+                      dw1 != 0.f;
       if (__any_sync(0xffffffffu, nz)) {
-        float v[8];
-        v[0] = dp * (2.0f * sg.z * dx + sg.w * dy);
-        v[1] = dp * (2.0f * sc * dy + sg.w * dx);
-        v[2] = dp * (-0.5f * dx * dx);
-        v[3] = dp * (-dx * dy);
-        v[4] = dp * (-0.5f * dy * dy);
-        v[5] = dvv;
-        v[6] = dww;
-        v[7] = 0.0f;
-        // reduce-scatter: lane l ends with slot l >> 2 summed over the warp
-        const float r = warp_reduce_scatter8(v, lane);
-        const int slot = lane >> 2;
-        if ((lane & 3) == 0 && slot < 7) atomicAdd(&s_acc[j * 8 + slot], r);
+        float v[16];
+        pair_parts(v, dp0, sg0, sc0.x, dx0, dy0, dv0, dw0);
+        pair_parts(v + 8, dp1, sg1, sc1.x, dx1, dy1, dv1, dw1);
+        // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
+        const float r = warp_reduce_scatter16(v, lane);
+        const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
+        if ((lane & 1) == 0 && comp < 7 && (which == 0 || has1))
+          atomicAdd(&s_acc[(which ? j1 : j0) * 8 + comp], r);
       }
     }
     __syncthreads();
