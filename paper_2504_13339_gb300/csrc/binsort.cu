@@ -319,28 +319,56 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// One thread per record in depth order: write its (view*tiles + tile, record)
-// pairs, tiles row-major, while below capacity.
-__global__ void emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
-                            const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                            int64_t nrec, int64_t n_per_view, int tiles_x, int tiles_per_view,
-                            int64_t capacity, uint32_t* __restrict__ ikeys,
-                            uint32_t* __restrict__ ivals) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrec) return;
-  uint32_t g = order[i];
-  if (tiles[g] == 0) return;
-  int64_t off = offsets[i];
-  if (off >= capacity) return;
-  short4 rc = rect[g];
-  uint32_t kb = (uint32_t)(g / n_per_view) * (uint32_t)tiles_per_view;
-  for (int ty = rc.y; ty < rc.w; ++ty)
-    for (int tx = rc.x; tx < rc.z; ++tx) {
-      if (off >= capacity) return;
-      ikeys[off] = kb + (uint32_t)(ty * tiles_x + tx);
-      ivals[off] = g;
-      ++off;
+// Writes the (view*tiles + tile, record) pairs of 32 consecutive records (in
+// depth order) per warp, tiles of a record row-major, below capacity.  The
+// warp's instances form one contiguous run; lanes write consecutive
+// positions of it, each finding the record that owns its position by a
+// binary search over the lanes' offsets (offsets increase with the lane).
+__global__ void __launch_bounds__(256)
+    emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
+                const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+                int64_t nrec, int64_t n_per_view, int tiles_x, int tiles_per_view,
+                int64_t capacity, uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t g = 0, cnt = 0, off = 0xffffffffu;
+  short4 rc = make_short4(0, 0, 0, 0);
+  if (i < nrec) {
+    g = order[i];
+    cnt = (uint32_t)tiles[g];
+    off = offsets[i];  // saturated at 0xffffffff beyond 2^32 instances
+    if (cnt) rc = rect[g];
+  }
+  const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
+  unsigned long long end = off == 0xffffffffu ? 0ull : (unsigned long long)off + cnt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) end = max(end, __shfl_xor_sync(0xffffffffu, end, o));
+  if (first == 0xffffffffu || first >= (uint64_t)capacity) return;  // warp-uniform
+  const uint32_t stop = (uint32_t)min(end, (unsigned long long)capacity);
+  const int wx = rc.z - rc.x;
+  const uint32_t kb = (uint32_t)(g / (uint32_t)n_per_view) * (uint32_t)tiles_per_view;
+  for (uint32_t base = first; base < stop; base += 32) {
+    const uint32_t p = base + lane;
+    // owner: the largest lane whose offset is <= p
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t o = __shfl_sync(0xffffffffu, off, lo + step);
+      if (o <= p) lo += step;
     }
+    const uint32_t o_off = __shfl_sync(0xffffffffu, off, lo);
+    const int o_wx = __shfl_sync(0xffffffffu, wx, lo);
+    const int o_x0 = __shfl_sync(0xffffffffu, (int)rc.x, lo);
+    const int o_y0 = __shfl_sync(0xffffffffu, (int)rc.y, lo);
+    const uint32_t o_kb = __shfl_sync(0xffffffffu, kb, lo);
+    const uint32_t o_g = __shfl_sync(0xffffffffu, g, lo);
+    if (p < stop) {
+      const int local = (int)(p - o_off);
+      const int ry = local / o_wx, rx = local - ry * o_wx;
+      ikeys[p] = o_kb + (uint32_t)((o_y0 + ry) * tiles_x + o_x0 + rx);
+      ivals[p] = o_g;
+    }
+  }
 }
 
 __global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count) {
@@ -348,14 +376,36 @@ __global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count) {
   if (i < count) ranges[i] = make_int2(0, 0);
 }
 
+// Four sorted keys per thread (one 16-byte load; the key array is 256-byte
+// aligned): a run starts where the key differs from its predecessor and
+// ends where it differs from its successor.  Keys are < 2^31, so 0xffffffff
+// marks "no neighbour".
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
                               int2* __restrict__ ranges) {
   const int64_t n = cnt.get();
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t k = keys[i];
-  if (i == 0 || keys[i - 1] != k) ranges[k].x = (int)i;
-  if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (int)(i + 1);
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 >= n) return;
+  uint32_t k[6];
+  k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+  if (i0 + 4 <= n) {
+    const uint4 q = *reinterpret_cast<const uint4*>(keys + i0);
+    k[1] = q.x;
+    k[2] = q.y;
+    k[3] = q.z;
+    k[4] = q.w;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) k[1 + t] = i0 + t < n ? keys[i0 + t] : 0xffffffffu;
+  }
+  k[5] = i0 + 4 < n ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int64_t i = i0 + t;
+    if (i >= n) break;
+    const uint32_t kk = k[1 + t];
+    if (kk != k[t]) ranges[kk].x = (int)i;
+    if (kk != k[2 + t]) ranges[kk].y = (int)(i + 1);
+  }
 }
 
 __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
@@ -480,7 +530,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   }
   const uint32_t* fkeys = kbuf[passes & 1];
   // 4. per-tile ranges and optional 64-bit keys
-  ranges_kernel<<<grid_for(capacity, 256), 256, 0, stream>>>(fkeys, ci, ranges);
+  ranges_kernel<<<grid_for(capacity, 1024), 256, 0, stream>>>(fkeys, ci, ranges);
   count_launch();
   if (keys) {
     keys64_kernel<<<grid_for(capacity, 256), 256, 0, stream>>>(
