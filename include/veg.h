@@ -171,7 +171,7 @@ veg_status veg_tile_order(const int32_t* tile_ranges, int64_t count, int32_t* ti
  * one fixed 16 MiB device array compiled into the library, which every GPU
  * that loads the library holds until the process exits.
  *   Size limit: the scratch needed is about 20 bytes per record (n_views * n)
- *   plus 12 bytes per instance of `capacity` plus 1 KiB per 4096 items of the
+ *   plus 12 bytes per instance of `capacity` plus 1 KiB per 2048 items of the
  *   larger of the two (e.g. 65,536 records with a capacity of 1,000,000 fit);
  *   a request needing more than 16 MiB returns VEG_ERR_UNSUPPORTED before
  *   anything is launched.  Nothing is allocated or freed, by this library or

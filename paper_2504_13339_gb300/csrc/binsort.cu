@@ -10,7 +10,7 @@
 //      stable-sort them by that key alone -- ceil(bits/8) passes over M.
 // A stable sort by tile of a sequence already ordered by (depth, index)
 // yields (view, tile, depth, index) order.  Both stages use one hand-written
-// LSD radix sort (reduce / scan / stable scatter, 8-bit digits, 4096 items
+// LSD radix sort (reduce / scan / stable scatter, 8-bit digits, 2048 items
 // per block).  The instance count M lives only on the device; later kernels
 // read it from the workspace header, so no host round trip is needed.
 #include <algorithm>
@@ -22,8 +22,8 @@ namespace veg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTileItems = kThreads * kItems;  // 4096 items per radix block
+constexpr int kItems = 8;
+constexpr int kTileItems = kThreads * kItems;  // 2048 items per radix block
 
 // Number of items to process: a fixed count, or min(*dev, cap).
 struct Count {
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(1024)
 // Stable scatter: rank every item among equal digits of its block (warp
 // order, then lane order = item order), stage the block in digit order in
 // shared memory, then write each digit run out contiguously.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, Count cnt,
                          int shift, int nbits, const uint32_t* __restrict__ hist,
