@@ -54,12 +54,34 @@ __device__ __forceinline__ float power_cutoff(float max_aw) {
   return __logf(kAlphaMin / max_aw) - 1e-3f;
 }
 
+// Minimum of q(d) = a dx^2 + 2 b dx dy + c dy^2 (a, c > 0, positive
+// definite) over the rectangle [x0, x1] x [y0, y1]: zero when the rectangle
+// holds the origin, else the least of the four edge minima (on an edge q is
+// a 1-D convex quadratic, minimised at its vertex clamped to the edge).
+__device__ __forceinline__ float conic_min_over_rect(float a, float b, float c, float x0,
+                                                     float x1, float y0, float y1) {
+  if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) return 0.0f;
+  auto qf = [&](float x, float y) { return a * x * x + 2.0f * b * x * y + c * y * y; };
+  const float ia = 1.0f / a, ic = 1.0f / c;
+  float m = qf(x0, fminf(fmaxf(-b * x0 * ic, y0), y1));
+  m = fminf(m, qf(x1, fminf(fmaxf(-b * x1 * ic, y0), y1)));
+  m = fminf(m, qf(fminf(fmaxf(-b * y0 * ia, x0), x1), y0));
+  m = fminf(m, qf(fminf(fmaxf(-b * y1 * ia, x0), x1), y1));
+  return m;
+}
+
 // Warp blocks (bit by*2+bx for the 8x4 block at tile-relative (8bx, 4by))
-// holding a pixel centre where the exponent can reach `cut`: the ellipse
-// d^T Q d <= -2 cut (Q = conic) has half extents sqrt(-2 cut Q^-1_xx) and
-// sqrt(-2 cut Q^-1_yy); they are widened by 0.2% + 0.02 px, far beyond the
-// float32 error of the per-pixel exponent.  An ill-conditioned conic keeps
-// every block (the exact per-pixel test then decides).
+// holding a pixel centre where the exponent can reach `cut`, i.e. a centre d
+// (relative to the splat centre) with d^T Q d <= -2 cut (Q = conic).  A
+// block's bounding-box test rejects far blocks; the rest are kept when the
+// quadratic's minimum over the block's rectangle of pixel centres is within
+// the radius.  Box half extents are widened by 0.2% + 0.02 px and the
+// squared radius by 0.2% + 1e-4, far beyond the float32 error of the
+// per-pixel exponent, so the mask never drops a pixel the exact test keeps.
+// An ill-conditioned conic keeps every block (the per-pixel test decides).
+// EXACT = false keeps every block passing the box test (cheaper to stage;
+// the forward pass, whose iterations are cheap, prefers it).
+template <bool EXACT>
 __device__ __forceinline__ unsigned warp_block_mask(float rx, float ry, float a, float b, float c,
                                                     float cut) {
   if (!(cut < 0.0f)) return 0u;
@@ -68,14 +90,24 @@ __device__ __forceinline__ unsigned warp_block_mask(float rx, float ry, float a,
   const float r2 = -2.0f * cut;
   const float hx = sqrtf(r2 * c / det) * 1.002f + 0.02f;
   const float hy = sqrtf(r2 * a / det) * 1.002f + 0.02f;
+  const float r2m = r2 * 1.002f + 1e-4f;
   const float x0 = rx - hx, x1 = rx + hx, y0 = ry - hy, y1 = ry + hy;
   unsigned m = 0u;
 #pragma unroll
   for (int by = 0; by < 4; ++by) {
     if (y1 < 4.0f * by || y0 > 4.0f * by + 3.0f) continue;
 #pragma unroll
-    for (int bx = 0; bx < 2; ++bx)
-      if (x1 >= 8.0f * bx && x0 <= 8.0f * bx + 7.0f) m |= 1u << (by * 2 + bx);
+    for (int bx = 0; bx < 2; ++bx) {
+      if (x1 < 8.0f * bx || x0 > 8.0f * bx + 7.0f) continue;
+      if (!EXACT) {
+        m |= 1u << (by * 2 + bx);
+        continue;
+      }
+      const float q = conic_min_over_rect(a, b, c, 8.0f * bx - rx - 0.01f,
+                                          8.0f * bx + 7.0f - rx + 0.01f,
+                                          4.0f * by - ry - 0.01f, 4.0f * by + 3.0f - ry + 0.01f);
+      if (q <= r2m) m |= 1u << (by * 2 + bx);
+    }
   }
   return m;
 }
@@ -166,7 +198,7 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
   }
   const float cut = power_cutoff(max_aw);
   s_c[s] = make_float2(-0.5f * au.z, cut);
-  s_mask[s] = (unsigned char)warp_block_mask(ge.x - tx0, ge.y - ty0, au.x, au.y, au.z, cut);
+  s_mask[s] = (unsigned char)warp_block_mask<BWD>(ge.x - tx0, ge.y - ty0, au.x, au.y, au.z, cut);
   return g;
 }
 
