@@ -315,11 +315,12 @@ def _flag_near(x, ref, rel):
     return np.abs(x / ref - 1.0) < rel
 
 
-def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False):
+def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False, shade=None):
     """Front-to-back blending (Eq. 1) of one tile's depth-sorted splats for
     the pixel centres (px, py) and every transfer function in `luts`.
 
-    u (n,2), conic (n,3), v (n,), w (n,) are the tile's splats in list order.
+    u (n,2), conic (n,3), v (n,), w (n,) are the tile's splats in list order;
+    shade (n,2) optional Blinn-Phong factors (s_d, s_s): colour s_d C(v) + s_s.
     Returns dict(out (P,T,4), n_contrib (P,T), flag (P,T), stats, rec): rec
     holds per-splat (blend, clamped) masks when `record`.  With `frozen` (a
     previous rec) the threshold decisions are taken from it instead, which
@@ -350,6 +351,8 @@ def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False):
         G = np.exp(power)
         vals = np.stack([tf_eval64(luts[t], v[i])[0] for t in range(nT)])  # (T,4)
         rgb = vals[:, :3]
+        if shade is not None:
+            rgb = shade[i, 0] * rgb + shade[i, 1]
         aw = vals[:, 3] * w[i]
         raw = G[:, None] * aw[None, :]
         alpha = np.minimum(ALPHA_MAX, raw)
@@ -391,6 +394,11 @@ def _tile_splats(proj, vals, lo, hi, n):
     return idx, geo[:, :2], aux[:, :3], aux[:, 3], geo[:, 3]
 
 
+def _tile_shade(proj, idx):
+    sh = proj.get("shade")
+    return None if sh is None else np.asarray(sh, np.float64)[idx]
+
+
 def composite_fwd(proj_views, cams, bins, luts, bg=(0.0, 0.0, 0.0), tiles=None,
                   record=False):
     """Render every view x transfer function.  Returns out (V,T,H,W,4),
@@ -412,8 +420,9 @@ def composite_fwd(proj_views, cams, bins, luts, bg=(0.0, 0.0, 0.0), tiles=None,
         for tile in (range(ntiles) if tiles is None else tiles):
             lo, hi = bins["ranges"][vi, tile]
             px, py = _tile_pixels(cam, tile)
-            _, u, conic, v, w = _tile_splats(proj, bins["vals"], lo, hi, n)
-            r = composite_tile(px, py, u, conic, v, w, luts, bg, record=record)
+            idx, u, conic, v, w = _tile_splats(proj, bins["vals"], lo, hi, n)
+            r = composite_tile(px, py, u, conic, v, w, luts, bg, record=record,
+                               shade=_tile_shade(proj, idx))
             out[vi, :, py, px] = r["out"]
             nc[vi, :, py, px] = r["n_contrib"]
             flag[vi, :, py, px] = r["flag"]
@@ -424,13 +433,14 @@ def composite_fwd(proj_views, cams, bins, luts, bg=(0.0, 0.0, 0.0), tiles=None,
     return {"out": out, "n_contrib": nc, "flag": flag, "stats": stats, "rec": recs}
 
 
-def composite_bwd_tile(px, py, u, conic, v, w, luts, bg, rec, dout):
+def composite_bwd_tile(px, py, u, conic, v, w, luts, bg, rec, dout, shade=None):
     """Gradients of one tile's blend w.r.t. each splat's screen mean, conic,
-    scalar and weight, given the forward decisions `rec` and dL/d(out)
-    `dout` (P,T,4).  Returns (n,7): du_x, du_y, da, db, dc, dv, dw."""
+    scalar and weight (and shading factors), given the forward decisions
+    `rec` and dL/d(out) `dout` (P,T,4).  Returns (n,9): du_x, du_y, da, db,
+    dc, dv, dw, ds_d, ds_s (the last two zero without `shade`)."""
     P, nT = px.shape[0], luts.shape[0]
     n = len(rec)
-    grad = np.zeros((u.shape[0], 7))
+    grad = np.zeros((u.shape[0], 9))
     if n == 0:
         return grad
     px = px.astype(np.float64)
@@ -453,25 +463,30 @@ def composite_bwd_tile(px, py, u, conic, v, w, luts, bg, rec, dout):
         aw = vals[:, 3] * w[i]
         raw = G[:, None] * aw[None]
         alpha = np.where(clamped, ALPHA_MAX, np.minimum(ALPHA_MAX, raw))
-        cg = (g * vals[None, :, :3]).sum(-1)  # (P,T)
-        steps.append((blend, clamped, dx, dy, power, G, vals, slopes, alpha, Tr.copy(), cg))
+        sd, ss = (1.0, 0.0) if shade is None else (shade[i, 0], shade[i, 1])
+        rgb = sd * vals[:, :3] + ss  # the blended colour
+        cg = (g * rgb[None]).sum(-1)  # (P,T)
+        steps.append((blend, clamped, dx, dy, power, G, vals, slopes, alpha, Tr.copy(), cg, sd))
         Tr = np.where(blend, Tr * (1.0 - alpha), Tr)
     T_final = Tr
     contrib = np.stack([np.where(s[0], s[10] * s[8] * s[9], 0.0) for s in steps])
     suffix = np.cumsum(contrib[::-1], 0)[::-1] - contrib
     K_end = T_final * ((g * bgv).sum(-1) + gT)
-    for i, (blend, clamped, dx, dy, power, G, vals, slopes, alpha, Ti, cg) in enumerate(steps):
+    for i, (blend, clamped, dx, dy, power, G, vals, slopes, alpha, Ti, cg, sd) in \
+            enumerate(steps):
         if not blend.any():
             continue
         dalpha = np.where(blend, Ti * cg - (suffix[i] + K_end) / (1.0 - alpha), 0.0)
-        wgt = np.where(blend, alpha * Ti, 0.0)  # dL/drgb = wgt * g
+        wgt = np.where(blend, alpha * Ti, 0.0)  # dL/d(colour) = wgt * g
         free = blend & ~clamped
         A = vals[:, 3]
         daw = np.where(free, dalpha * G[:, None], 0.0)  # dL/d(A w)
         dG = np.where(free, dalpha * (A * w[i])[None], 0.0).sum(1)
-        dv = ((wgt[..., None] * g) * slopes[None, :, :3]).sum((1, 2)) \
+        dv = ((sd * wgt[..., None] * g) * slopes[None, :, :3]).sum((1, 2)) \
             + (daw * w[i] * slopes[None, :, 3]).sum(1)
         dw = (daw * A[None]).sum(1)
+        grad[i, 7] = (wgt[..., None] * g * vals[None, :, :3]).sum()
+        grad[i, 8] = (wgt[..., None] * g).sum()
         dpow = dG * G
         a, b, c = conic[i]
         grad[i, 0] = (dpow * (-a * dx - b * dy)).sum()
@@ -490,7 +505,7 @@ def composite_bwd(proj_views, cams, bins, luts, bg, fwd, dout, tiles=None):
     luts = np.asarray(luts, np.float64)
     V = len(cams)
     n = proj_views[0]["geo"].shape[0]
-    grad2d = np.zeros((V, n, 7))
+    grad2d = np.zeros((V, n, 9))
     ntiles = cams[0].tiles_x * cams[0].tiles_y
     for vi, (proj, cam) in enumerate(zip(proj_views, cams)):
         for tile in (range(ntiles) if tiles is None else tiles):
@@ -500,7 +515,8 @@ def composite_bwd(proj_views, cams, bins, luts, bg, fwd, dout, tiles=None):
             px, py = _tile_pixels(cam, tile)
             idx, u, conic, v, w = _tile_splats(proj, bins["vals"], lo, hi, n)
             d = np.transpose(dout[vi][:, py, px], (1, 0, 2))
-            gt = composite_bwd_tile(px, py, u, conic, v, w, luts, bg, fwd["rec"][vi, tile], d)
+            gt = composite_bwd_tile(px, py, u, conic, v, w, luts, bg, fwd["rec"][vi, tile], d,
+                                    shade=_tile_shade(proj, idx))
             np.add.at(grad2d[vi], idx, gt)
     return grad2d
 
@@ -661,9 +677,45 @@ def l1_loss(out, target):
 # whole path
 # ============================================================================
 
-def render(cams, gs, luts, bg=(0.0, 0.0, 0.0), cull=True, tiles=None, record=False):
-    """Project (per view), bin and sort, composite.  Returns (proj_views, bins, fwd)."""
+def attach_shading(proj_views, cams, gs, lighting):
+    """Adds the Blinn-Phong factors (s_d, s_s) of every view to its
+    projection.  lighting: dict normal (N,3), ka, kd, ks, beta (N,), lights
+    (V,3) unit world directions toward the light."""
+    mean = gs.mean_v[:, :3].astype(np.float64)
+    for vi, (p, cam) in enumerate(zip(proj_views, cams)):
+        f = shade64(cam, lighting["lights"][vi], mean, np.asarray(lighting["normal"], np.float64),
+                    *(np.asarray(lighting[k], np.float64) for k in ("ka", "kd", "ks", "beta")))
+        p["shade"] = np.stack([f["s_d"], f["s_s"]], 1)
+    return proj_views
+
+
+def lighting_grad(cams, gs, lighting, proj_views, grad2d):
+    """Chains the shading columns of grad2d (ds_d, ds_s) to the lighting
+    parameters and the means, summed over views: returns dnormal (N,3),
+    dka, dkd, dks, dbeta (N,), dmean (N,3)."""
+    n = gs.n
+    mean = gs.mean_v[:, :3].astype(np.float64)
+    normal = np.asarray(lighting["normal"], np.float64)
+    ka, kd, ks, beta = (np.asarray(lighting[k], np.float64) for k in ("ka", "kd", "ks", "beta"))
+    acc = [np.zeros((n, 3)), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros((n, 3))]
+    for vi, (cam, proj) in enumerate(zip(cams, proj_views)):
+        ok = proj["valid"]
+        f = shade64(cam, lighting["lights"][vi], mean[ok], normal[ok], ka[ok], kd[ok], ks[ok],
+                    beta[ok])
+        parts = shade_bwd64(f, lighting["lights"][vi], ka[ok], kd[ok], ks[ok], beta[ok],
+                            grad2d[vi][ok, 7], grad2d[vi][ok, 8])
+        for a, p in zip(acc, parts):
+            a[ok] += p
+    return tuple(acc)
+
+
+def render(cams, gs, luts, bg=(0.0, 0.0, 0.0), cull=True, tiles=None, record=False,
+           lighting=None):
+    """Project (per view), bin and sort, composite (Blinn-Phong shaded when
+    `lighting` is given).  Returns (proj_views, bins, fwd)."""
     proj = [project32(c, gs, luts if cull else None) for c in cams]
+    if lighting is not None:
+        attach_shading(proj, cams, gs, lighting)
     bins = bin_sort(proj, cams)
     fwd = composite_fwd(proj, cams, bins, luts, bg, tiles=tiles, record=record)
     return proj, bins, fwd
@@ -714,10 +766,11 @@ def bruteforce_pixel(cam, proj, luts, bg, x, y):
     return np.array(res), ncs
 
 
-def render_frozen(cams, mean, logscale, quat, v, w, luts, bg, bins, recs, tiles):
-    """The forward image as a smooth float64 function of the 3D parameters:
-    tile lists and every threshold decision are taken from an earlier
-    recorded pass (`bins`, `recs`).  Used by the finite-difference pins."""
+def render_frozen(cams, mean, logscale, quat, v, w, luts, bg, bins, recs, tiles, lighting=None):
+    """The forward image as a smooth float64 function of the 3D parameters
+    (and the lighting parameters): tile lists and every threshold decision
+    are taken from an earlier recorded pass (`bins`, `recs`).  Used by the
+    finite-difference pins."""
     luts = np.asarray(luts, np.float64)
     V, nT = len(cams), luts.shape[0]
     H, W = cams[0].height, cams[0].width
@@ -727,12 +780,17 @@ def render_frozen(cams, mean, logscale, quat, v, w, luts, bg, bins, recs, tiles)
     out[..., 3] = 1.0
     for vi, cam in enumerate(cams):
         f = project64(cam, mean, logscale, quat)
+        shade = None
+        if lighting is not None:
+            s = shade64(cam, lighting["lights"][vi], mean, lighting["normal"], lighting["ka"],
+                        lighting["kd"], lighting["ks"], lighting["beta"])
+            shade = np.stack([s["s_d"], s["s_s"]], 1)
         for tile in tiles:
             lo, hi = bins["ranges"][vi, tile]
             px, py = _tile_pixels(cam, tile)
             idx = bins["vals"][lo:hi].astype(np.int64) % n
             r = composite_tile(px, py, f["u"][idx], f["conic"][idx], v[idx], w[idx], luts, bg,
-                               frozen=recs[vi, tile])
+                               frozen=recs[vi, tile], shade=None if shade is None else shade[idx])
             out[vi, :, py, px] = r["out"]
     return out
 
@@ -765,3 +823,78 @@ def bins_from_lists(lists_per_view, n_views, n_tiles):
             pos += len(lst)
     vals = np.concatenate(vals) if vals else np.zeros(0, np.uint32)
     return {"vals": vals, "ranges": ranges}
+
+
+# ============================================================================
+# Blinn-Phong shading (Eq. 2-3), float64
+# ============================================================================
+#
+# Reading R16: the light is directional per view, `light` a unit world-space
+# vector from the scene toward the light (the headlight of Sec. 4.2 / 5.1 is
+# the camera's backward optical axis); v_i is the unit vector from the
+# Gaussian's mean toward the camera centre; n_i is normalised.  Eq. 2-3 then
+# read c_i = s_d C(v_i) + s_s white with
+#     s_d = k^a + k^d |n.l|,  s_s = k^s |n.h|^beta if |n.l| > 0 else 0,
+#     h = (v + l) / |v + l|.
+
+def camera_centre(cam):
+    w2c = np.asarray(cam.world_to_cam, np.float64)
+    return -w2c[:, :3].T @ w2c[:, 3]
+
+
+def headlight(cam):
+    """Unit world direction toward a light on the camera's optical axis."""
+    return -np.asarray(cam.world_to_cam, np.float64)[2, :3]
+
+
+def shade64(cam, light, mean, normal, ka, kd, ks, beta):
+    """(s_d, s_s) per Gaussian for one view, and the intermediates."""
+    eye = camera_centre(cam)
+    l = np.asarray(light, np.float64)
+    vd = eye[None] - mean
+    vlen = np.linalg.norm(vd, axis=1, keepdims=True)
+    vh = vd / vlen
+    nlen = np.linalg.norm(normal, axis=1, keepdims=True)
+    nh_ = normal / nlen
+    nl = nh_ @ l
+    hv = vh + l[None]
+    hlen = np.linalg.norm(hv, axis=1, keepdims=True)
+    h = hv / hlen
+    ndh = (nh_ * h).sum(1)
+    s_d = ka + kd * np.abs(nl)
+    lit = np.abs(nl) > 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s_s = np.where(lit, ks * np.abs(ndh) ** beta, 0.0)
+    return {"s_d": s_d, "s_s": s_s, "nl": nl, "ndh": ndh, "n_hat": nh_, "nlen": nlen[:, 0],
+            "v_hat": vh, "vlen": vlen[:, 0], "h": h, "hlen": hlen[:, 0], "lit": lit}
+
+
+def shade_bwd64(f, light, ka, kd, ks, beta, d_sd, d_ss):
+    """Chains dL/ds_d and dL/ds_s to (dnormal (N,3), dka, dkd, dks, dbeta,
+    dmean (N,3)); derivatives of |.| use sign (0 at 0)."""
+    l = np.asarray(light, np.float64)
+    nl, ndh = f["nl"], f["ndh"]
+    sgn_l = np.sign(nl)
+    sgn_h = np.sign(ndh)
+    a = np.abs(ndh)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        pw = np.where(f["lit"] & (a > 0), a ** beta, 0.0)
+        dpw_da = np.where(f["lit"] & (a > 0), beta * a ** (beta - 1.0), 0.0)
+        dpw_db = np.where(f["lit"] & (a > 0), pw * np.log(np.where(a > 0, a, 1.0)), 0.0)
+    dka = d_sd
+    dkd = d_sd * np.abs(nl)
+    dks = d_ss * pw
+    dbeta = d_ss * ks * dpw_db
+    g_nl = d_sd * kd * sgn_l                       # dL/d(n_hat . l)
+    g_ndh = d_ss * ks * dpw_da * sgn_h             # dL/d(n_hat . h)
+    g_nhat = g_nl[:, None] * l[None] + g_ndh[:, None] * f["h"]
+    nh_ = f["n_hat"]
+    dnormal = (g_nhat - nh_ * (nh_ * g_nhat).sum(1, keepdims=True)) / f["nlen"][:, None]
+    # h = (v_hat + l) / |v_hat + l|, v_hat = (eye - mean) / |eye - mean|
+    g_h = g_ndh[:, None] * nh_
+    h = f["h"]
+    g_hv = (g_h - h * (h * g_h).sum(1, keepdims=True)) / f["hlen"][:, None]
+    vh = f["v_hat"]
+    g_vd = (g_hv - vh * (vh * g_hv).sum(1, keepdims=True)) / f["vlen"][:, None]
+    dmean = -g_vd
+    return dnormal, dka, dkd, dks, dbeta, dmean

@@ -388,32 +388,35 @@ def _random_tile_splats(rng, n):
     return u, np.array(conic), rng.uniform(0.05, 0.95, n), rng.uniform(0.3, 1.0, n)
 
 
-def test_composite_bwd_matches_finite_differences():
+@pytest.mark.parametrize("lit", [False, True])
+def test_composite_bwd_matches_finite_differences(lit):
     rng = np.random.default_rng(20)
     n = 24
     u, conic, v, w = _random_tile_splats(rng, n)
     w[:8] = 1.0  # with the opaque table these splats clamp at 0.99 near their centres
+    shade = np.stack([rng.uniform(0.3, 1.2, n), rng.uniform(0.0, 0.4, n)], 1) if lit else None
     tfs = np.asarray(np.stack([S.bump_tf(21, peak=0.95), S.bump_tf(22, peak=0.9),
                                S.constant_tf([0.3, 0.6, 0.9, 1.0])]), float)
     ys, xs = np.mgrid[0:16, 0:16]
     px, py = xs.ravel(), ys.ravel()
     bg = (0.2, 0.1, 0.3)
-    r = O.composite_tile(px, py, u, conic, v, w, tfs, bg, record=True)
+    r = O.composite_tile(px, py, u, conic, v, w, tfs, bg, record=True, shade=shade)
     assert sum(int(b.sum()) for b, _ in r["rec"]) > 200
     assert sum(int(c.sum()) for _, c in r["rec"]) >= 3
     dout = rng.standard_normal(r["out"].shape)
-    grad = O.composite_bwd_tile(px, py, u, conic, v, w, tfs, bg, r["rec"], dout)
+    grad = O.composite_bwd_tile(px, py, u, conic, v, w, tfs, bg, r["rec"], dout, shade=shade)
+    sh0 = shade if lit else np.tile([1.0, 0.0], (n, 1))
 
-    def loss(u_, c_, v_, w_):
-        rr = O.composite_tile(px, py, u_, c_, v_, w_, tfs, bg, frozen=r["rec"])
+    def loss(u_, c_, v_, w_, s_):
+        rr = O.composite_tile(px, py, u_, c_, v_, w_, tfs, bg, frozen=r["rec"], shade=s_)
         return float((rr["out"] * dout).sum())
 
     fd = np.zeros_like(grad)
     for i in range(n):
-        for k in range(7):
+        for k in range(9):
             vals = []
             for sgn in (1, -1):
-                uu, cc, vv, ww = u.copy(), conic.copy(), v.copy(), w.copy()
+                uu, cc, vv, ww, ss = u.copy(), conic.copy(), v.copy(), w.copy(), sh0.copy()
                 if k < 2:
                     h = 1e-6
                     uu[i, k] += sgn * h
@@ -423,10 +426,13 @@ def test_composite_bwd_matches_finite_differences():
                 elif k == 5:
                     h = 1e-8
                     vv[i] += sgn * h
-                else:
+                elif k == 6:
                     h = 1e-7
                     ww[i] += sgn * h
-                vals.append(loss(uu, cc, vv, ww))
+                else:
+                    h = 1e-7
+                    ss[i, k - 7] += sgn * h
+                vals.append(loss(uu, cc, vv, ww, ss))
             fd[i, k] = (vals[0] - vals[1]) / (2 * h)
     scale = np.abs(fd).max(0) + 1e-12
     assert np.all(np.abs(grad - fd) <= 1e-5 * scale + 1e-6 * np.abs(fd))
@@ -518,3 +524,111 @@ def test_l1_loss_value_and_gradient():
         fd = (O.l1_loss(op, tgt)[0] - O.l1_loss(om, tgt)[0]) / (2 * h)
         assert abs(fd - grad[idx]) < 1e-6
     assert np.all(grad[..., 3] == 0)
+
+
+# ----------------------------------------------------------------------------
+# Blinn-Phong shading (Eq. 2-3)
+# ----------------------------------------------------------------------------
+
+def _lighting(rng, n, lights):
+    return {"normal": rng.standard_normal((n, 3)), "ka": rng.uniform(0.1, 0.6, n),
+            "kd": rng.uniform(0.2, 0.9, n), "ks": rng.uniform(0.0, 0.8, n),
+            "beta": rng.uniform(1.0, 30.0, n), "lights": lights}
+
+
+def test_shading_closed_forms():
+    cam = S.look_at_camera((0, 0, 3), 33, 33)
+    l = O.headlight(cam)
+    np.testing.assert_allclose(l, [0, 0, 1], atol=1e-7)  # toward the camera at +z
+    mean = np.zeros((3, 3))
+    normal = np.array([[0, 0, 2.0], [1.0, 0, 0], [0, 0, -0.5]])  # along l, across l, against l
+    ka, kd, ks, beta = np.array([0.2] * 3), np.array([0.5] * 3), np.array([0.7] * 3), np.array([9.0] * 3)
+    f = O.shade64(cam, l, mean, normal, ka, kd, ks, beta)
+    # on the axis the view direction equals the headlight: h = l, |n.h| = |n.l|
+    np.testing.assert_allclose(f["s_d"], [0.7, 0.2, 0.7], atol=1e-12)
+    np.testing.assert_allclose(f["s_s"], [0.7, 0.0, 0.7], atol=1e-12)
+    # a lit single splat at the centre pixel: (s_d C + s_s) alpha, Eq. 1-3
+    g = make_gs(np.zeros((1, 3)), math.log(0.05))
+    tf = S.constant_tf([0.25, 0.5, 0.75, 0.5])[None]
+    lighting = {"normal": normal[:1], "ka": ka[:1], "kd": kd[:1], "ks": ks[:1], "beta": beta[:1],
+                "lights": [l]}
+    _, _, fwd = O.render([cam], g, tf, lighting=lighting)
+    np.testing.assert_allclose(fwd["out"][0, 0, 16, 16, :3],
+                               (0.7 * np.array([0.25, 0.5, 0.75]) + 0.7) * 0.5, rtol=1e-12)
+
+
+def test_shading_backward_matches_finite_differences():
+    rng = np.random.default_rng(50)
+    cam = S.orbit_camera(40.0, 25.0, 3.0, 64, 64)
+    n = 30
+    mean = rng.uniform(-0.8, 0.8, (n, 3))
+    lt = _lighting(rng, n, [O.headlight(cam)])
+    l = lt["lights"][0]
+    f = O.shade64(cam, l, mean, lt["normal"], lt["ka"], lt["kd"], lt["ks"], lt["beta"])
+    assert np.all(np.abs(f["nl"]) > 1e-3)
+    d_sd, d_ss = rng.standard_normal(n), rng.standard_normal(n)
+    dn, dka, dkd, dks, db, dm = O.shade_bwd64(f, l, lt["ka"], lt["kd"], lt["ks"], lt["beta"],
+                                              d_sd, d_ss)
+
+    def L(mean_, normal_, ka_, kd_, ks_, beta_):
+        g = O.shade64(cam, l, mean_, normal_, ka_, kd_, ks_, beta_)
+        return d_sd * g["s_d"] + d_ss * g["s_s"]
+
+    base = [mean, lt["normal"], lt["ka"], lt["kd"], lt["ks"], lt["beta"]]
+    for which, got in ((0, dm), (1, dn), (2, dka), (3, dkd), (4, dks), (5, db)):
+        arr = base[which]
+        fd = np.zeros_like(got)
+        for idx in np.ndindex(*arr.shape[1:]) if arr.ndim > 1 else [()]:
+            h = 1e-6
+            ap, am = arr.copy(), arr.copy()
+            ap[(slice(None),) + idx] += h
+            am[(slice(None),) + idx] -= h
+            args_p, args_m = list(base), list(base)
+            args_p[which], args_m[which] = ap, am
+            fd[(slice(None),) + idx] = (L(*args_p) - L(*args_m)) / (2 * h)
+        np.testing.assert_allclose(got, fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max() + 1e-12)
+
+
+def test_lit_full_chain_matches_finite_differences():
+    rng = np.random.default_rng(51)
+    g = S.uniform_gaussians(10, 52, logscale_mean=-2.2, logscale_std=0.3)
+    g.mean_v[:, :3] *= 0.6
+    g.mean_v[:, 3] = rng.uniform(0.2, 0.8, g.n)
+    cams = [S.orbit_camera(10.0, 5.0, 3.0, 32, 32), S.orbit_camera(70.0, -15.0, 3.0, 32, 32)]
+    lt = _lighting(rng, g.n, [O.headlight(c) for c in cams])
+    tfs = np.asarray(S.bump_tfs(2, 53, peak=0.9), float)
+    bg = (0.0, 0.0, 0.0)
+    proj, bins, fwd = O.render(cams, g, tfs, bg=bg, record=True, lighting=lt)
+    dout = rng.standard_normal(fwd["out"].shape)
+    grad2d = O.composite_bwd(proj, cams, bins, tfs, bg, fwd, dout)
+    dn, dka, dkd, dks, db, dm_shade = O.lighting_grad(cams, g, lt, proj, grad2d)
+    gm, gl, gq = O.params_grad(cams, g, proj, grad2d)
+    tiles = range(cams[0].tiles_x * cams[0].tiles_y)
+    mean = g.mean_v[:, :3].astype(float)
+    ls, q = g.logscale_w[:, :3].astype(float), g.quat.astype(float)
+    v, w = g.mean_v[:, 3].astype(float), g.logscale_w[:, 3].astype(float)
+
+    def L(mean_, lt_):
+        out = O.render_frozen(cams, mean_, ls, q, v, w, tfs, bg, bins, fwd["rec"], tiles,
+                              lighting=lt_)
+        return float((out * dout).sum())
+
+    h = 1e-6
+    for key, got in (("normal", dn), ("ka", dka), ("kd", dkd), ("ks", dks), ("beta", db)):
+        fd = np.zeros_like(got)
+        for idx in np.ndindex(*got.shape):
+            lp, lm = dict(lt), dict(lt)
+            lp[key], lm[key] = lt[key].copy(), lt[key].copy()
+            lp[key][idx] += h
+            lm[key][idx] -= h
+            fd[idx] = (L(mean, lp) - L(mean, lm)) / (2 * h)
+        assert np.max(np.abs(got - fd)) <= 2e-5 * (np.abs(fd).max() + 1e-12), key
+    # the mean's gradient now has a shading part on top of the projection part
+    fd = np.zeros((g.n, 3))
+    for idx in np.ndindex(g.n, 3):
+        mp, mm = mean.copy(), mean.copy()
+        mp[idx] += h
+        mm[idx] -= h
+        fd[idx] = (L(mp, lt) - L(mm, lt)) / (2 * h)
+    tot = gm[:, :3] + dm_shade
+    assert np.max(np.abs(tot - fd)) <= 2e-5 * np.abs(fd).max()
