@@ -43,6 +43,9 @@ FP32_LANES_PER_SM = 128
 FWD_FLOPS = {"visited": 0, "iterated": 12, "evaluated": 2, "alpha": 3, "blended": 10}
 BWD_FLOPS = {"replayed": 0, "iterated": 12, "evaluated": 2, "alpha": 3, "blended": 21,
              "free": 7, "grad": 26}
+# shaded backward: per blended pair c.g = s_d (C.g) + s_s (g_r + g_g + g_b)
+# (+3) and the two shading sums (+4)
+BWD_FLOPS_LIT = dict(BWD_FLOPS, blended=28)
 
 
 def flops_of(model, counts):
@@ -61,6 +64,8 @@ def parse():
     ap.add_argument("--width", type=int, default=1024)
     ap.add_argument("--workload", default="train",
                     choices=["train", "plain", "sweep", "batched", "serve"])
+    ap.add_argument("--lighting", action="store_true",
+                    help="train step with Blinn-Phong shading (headlight, Eq. 2-3)")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=20.0)
     return ap.parse_args()
@@ -136,13 +141,21 @@ def setup_train(args, device):
     _, m = p.status()
     p.set_capacity(int(m * 1.15) + 4096)
     grads = [torch.zeros_like(x) for x in tens]
-    return p, tens, luts, target, grads, cams, tfs, g, m
+    lighting = None
+    if getattr(args, "lighting", False):
+        from paper_2504_13339_gb300.render import headlight_dirs
+        lt = S.random_lighting(g.n, 3)
+        lighting = (t(lt.normal_beta), t(lt.k_ads), headlight_dirs(cams))
+        grads += [torch.zeros_like(lighting[0]), torch.zeros_like(lighting[1])]
+    return p, tens, luts, target, grads, cams, tfs, g, m, lighting
 
 
-def gpu_step(p, tens, luts, target, grads, ev=None):
+def gpu_step(p, tens, luts, target, grads, ev=None, lighting=None):
     for gb in grads:
         gb.zero_()
     p.project(*tens, luts)
+    if lighting is not None:
+        p.shade(tens[0], *lighting)
     p.bin_sort()
     if ev is not None:
         ev[0].record()
@@ -155,7 +168,9 @@ def gpu_step(p, tens, luts, target, grads, ev=None):
     p.backward_2d(p.loss_grad)
     if ev is not None:
         ev[3].record()
-    p.project_backward(*grads)
+    p.project_backward(*grads[:3])
+    if lighting is not None:
+        p.shade_backward(grads[0], grads[3], grads[4])
 
 
 def source_hash(*names):
@@ -216,7 +231,7 @@ def run_gpu(args):
         dist.barrier()
     _lib.load()
 
-    p, tens, luts, target, grads, cams, tfs, g, m = setup_train(args, device)
+    p, tens, luts, target, grads, cams, tfs, g, m, lighting = setup_train(args, device)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
 
@@ -226,7 +241,7 @@ def run_gpu(args):
             dist.barrier()
 
     for _ in range(max(args.warmup, 3)):
-        gpu_step(p, tens, luts, target, grads)
+        gpu_step(p, tens, luts, target, grads, lighting=lighting)
     st, m2 = p.status()
     assert st == _lib.VEG_OK, "instance capacity overflow during warm-up"
 
@@ -241,7 +256,7 @@ def run_gpu(args):
         flush.zero_()
         e = evs[k]
         e[4].record(stream)
-        gpu_step(p, tens, luts, target, grads, ev=e[:4])
+        gpu_step(p, tens, luts, target, grads, ev=e[:4], lighting=lighting)
         e[5].record(stream)
     barrier()
     launches = _lib.veg_kernel_launches() - launches0
@@ -263,7 +278,7 @@ def run_gpu(args):
         ev2[k][0].record(stream)
         target.copy_(tgt_host, non_blocking=True)
         luts.copy_(lut_host, non_blocking=True)
-        gpu_step(p, tens, luts, target, grads)
+        gpu_step(p, tens, luts, target, grads, lighting=lighting)
         loss_host.copy_(p.loss, non_blocking=True)
         ev2[k][1].record(stream)
     barrier()
@@ -272,8 +287,11 @@ def run_gpu(args):
     d2h = 4
 
     # ---- work counts for the roofline (instrumented launches, untimed) -----
+    # The instrumented kernels are unshaded; shading changes no decision, so
+    # the pair counts are those of the shaded step.
     fst = torch.zeros(len(FWD_FLOPS), dtype=torch.int64, device=device)
     bst = torch.zeros(len(BWD_FLOPS), dtype=torch.int64, device=device)
+    p.unshade()
     p.project(*tens, luts)
     p.bin_sort()
     p.composite(luts, stats=fst)
@@ -283,7 +301,7 @@ def run_gpu(args):
     f = fst.cpu().numpy()
     b = bst.cpu().numpy()
     fwd_flops = flops_of(FWD_FLOPS, f)
-    bwd_flops = flops_of(BWD_FLOPS, b)
+    bwd_flops = flops_of(BWD_FLOPS_LIT if lighting is not None else BWD_FLOPS, b)
     props = torch.cuda.get_device_properties(device)
     peaks = {}
     try:
@@ -297,6 +315,8 @@ def run_gpu(args):
         dom, dom_ms, dom_flops, key = "composite_bwd_kernel", bwd_avg, bwd_flops, "composite_bwd"
     else:
         dom, dom_ms, dom_flops, key = "composite_fwd_kernel", fwd_avg, fwd_flops, "composite_fwd"
+    if lighting is not None:
+        key += "_lit"
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                 "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
@@ -312,7 +332,9 @@ def run_gpu(args):
         "n_gpus": world, "steps": K, "warmup": max(args.warmup, 3),
         "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_gaussians": g.n, "width": cams[0].width,
+        "config": {"workload": WORKLOAD + (", Blinn-Phong headlight shading (Eq. 2-3) with "
+                                           "its backward" if lighting is not None else ""),
+                   "n_gaussians": g.n, "width": cams[0].width,
                    "height": cams[0].height, "n_tf": len(tfs), "views": len(cams),
                    "tile_instances": int(m), "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

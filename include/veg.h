@@ -220,6 +220,11 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  * order in which tiles are scheduled; NULL = row-major; results do not
  * depend on it).
  * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default).
+ * splat_shade: optional device float [V][n][2] of Blinn-Phong factors
+ * (s_d, s_s) from veg_shade (8-byte aligned); when given, each splat is
+ * blended with the colour s_d rgb + s_s of Eq. 2 instead of rgb.  Opacity,
+ * skips and termination do not depend on it.  NULL = unshaded.  Shading
+ * with stats returns VEG_ERR_UNSUPPORTED.
  * bg: host float[3].  stats: optional device uint64[5] accumulating
  * (visited pixel-splat pairs -- every pair reached before the pixel stops --,
  * pairs walked by the kernel after its culling, pairs above the exponent
@@ -229,7 +234,8 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  */
 veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
                              const float* splat_geo, const float* splat_aux,
-                             const uint32_t* vals, const int32_t* tile_ranges,
+                             const float* splat_shade, const uint32_t* vals,
+                             const int32_t* tile_ranges,
                              const int32_t* tile_order, veg_tf tf, const float* bg,
                              int32_t tf_group, float* out, int32_t* n_contrib,
                              unsigned long long* stats, cudaStream_t stream);
@@ -249,6 +255,11 @@ veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
  * dw, 0) (overwritten).  workspace >= veg_composite_bwd_workspace_size.
  * If grad_mean_v, grad_logscale_w and grad_quat are all NULL, only grad2d
  * (then required) is computed; veg_project_bwd completes the chain.
+ * splat_shade: the forward's shading factors or NULL.  When given,
+ * grad_shade (device float [V][n][2], 8-byte aligned, overwritten) receives
+ * dL/ds_d and dL/ds_s per record, and veg_shade_bwd chains them to the
+ * normals, the material coefficients and the means; the colour slopes in dv
+ * are scaled by s_d.  Shading with stats returns VEG_ERR_UNSUPPORTED.
  * stats: optional device uint64[7] accumulating (replayed pixel-splat pairs,
  * pairs walked after culling, pairs above the exponent cutoff, alpha
  * evaluations, blended pairs, blended pairs below the 0.99 clamp, pairs with
@@ -257,13 +268,15 @@ veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
 veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views, size_t* bytes);
 veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
                              const float* splat_geo, const float* splat_aux,
-                             const int32_t* tiles_touched, const uint32_t* vals,
+                             const float* splat_shade, const int32_t* tiles_touched,
+                             const uint32_t* vals,
                              const int32_t* tile_ranges, const int32_t* tile_order, veg_tf tf,
                              const float* bg, int32_t tf_group, const float* out,
                              const int32_t* n_contrib,
                              const float* dL_dout, void* workspace, size_t workspace_bytes,
                              float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
-                             float* grad2d, unsigned long long* stats, cudaStream_t stream);
+                             float* grad2d, float* grad_shade, unsigned long long* stats,
+                             cudaStream_t stream);
 
 /*
  * veg_project_bwd -- the projection part of the backward pass (Sec. 3.3):
@@ -279,6 +292,40 @@ veg_status veg_project_bwd(const veg_camera* cams, int32_t n_views, veg_gaussian
                            const int32_t* tiles_touched, const float* grad2d,
                            float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
                            cudaStream_t stream);
+
+/*
+ * veg_shade -- Blinn-Phong factors of Eq. 2-3 per view and Gaussian (Sec. 3.3,
+ * "Phong shading").  For view v and Gaussian i, with n = normal / |normal|,
+ * l the unit light direction of the view (world space, toward the light; a
+ * headlight is the camera's backward optical axis), e the unit vector from
+ * the mean toward the camera centre and h = (e + l) / |e + l|:
+ *   s_d = k_a + k_d |n.l|,   s_s = k_s |n.h|^beta if |n.l| > 0 else 0,
+ * so that the shaded colour of Eq. 2 is s_d C(v) + s_s (white specular).
+ * mean_v [n][4] (mu, v) as for veg_project; normal_beta [n][4] = (normal,
+ * beta); k_ads [n][4] = (k_a, k_d, k_s, unused): device, 16-byte aligned.
+ * light_dirs: host float [n_views][3], normalised here (zero length is
+ * VEG_ERR_INVALID_ARGUMENT).  splat_shade: device float [n_views][n][2]
+ * (s_d, s_s), overwritten, 8-byte aligned.  One launch, no atomics.
+ */
+veg_status veg_shade(const veg_camera* cams, int32_t n_views, const float* mean_v, int64_t n,
+                     const float* normal_beta, const float* k_ads, const float* light_dirs,
+                     float* splat_shade, cudaStream_t stream);
+
+/*
+ * veg_shade_bwd -- chains grad_shade [n_views][n][2] = (dL/ds_d, dL/ds_s), as
+ * written by veg_composite_bwd, through veg_shade and ACCUMULATES (+=) the sum
+ * over views into grad_mean_v [n][4] (dL/dmu in xyz; w untouched),
+ * grad_normal_beta [n][4] = (dL/dnormal, dL/dbeta) and grad_k_ads [n][4] =
+ * (dL/dk_a, dL/dk_d, dL/dk_s, untouched).  Derivatives of |.| use its sign
+ * (0 at 0).  Records with tiles_touched == 0 contribute nothing.  One thread
+ * per Gaussian, no atomics: deterministic.  Same layouts and alignment as
+ * veg_shade.
+ */
+veg_status veg_shade_bwd(const veg_camera* cams, int32_t n_views, const float* mean_v, int64_t n,
+                         const float* normal_beta, const float* k_ads, const float* light_dirs,
+                         const int32_t* tiles_touched, const float* grad_shade,
+                         float* grad_mean_v, float* grad_normal_beta, float* grad_k_ads,
+                         cudaStream_t stream);
 
 /*
  * veg_l1_loss -- the L1 part of the training loss (Sec. 4.2:

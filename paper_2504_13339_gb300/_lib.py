@@ -59,12 +59,12 @@ _SIGS = {
     "veg_bin_sort_static": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _I64, _P, _P, _P, _P,
                                            _P]),
     "veg_sync_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I64)]),
-    "veg_composite_fwd": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, _P, veg_tf, _P, _I32,
-                                         _P, _P, _P, _P]),
+    "veg_composite_fwd": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, _P, _P, veg_tf, _P,
+                                         _I32, _P, _P, _P, _P]),
     "veg_composite_bwd_workspace_size": (ctypes.c_int, [_I64, _I32, ctypes.POINTER(_SZ)]),
-    "veg_composite_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P,
+    "veg_composite_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P, _P,
                                          veg_tf, _P, _I32, _P, _P, _P, _P, _SZ, _P, _P, _P, _P,
-                                         _P, _P]),
+                                         _P, _P, _P]),
     "veg_tile_order": (ctypes.c_int, [_P, _I64, _P, _P]),
     "veg_project_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P]),
     "veg_l1_loss_workspace_size": (ctypes.c_int, [ctypes.POINTER(_SZ)]),
@@ -73,6 +73,8 @@ _SIGS = {
                                                  ctypes.POINTER(_SZ)]),
     "veg_render": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, veg_tf, _P, _I64, _P, _SZ, _P, _P,
                                   _P]),
+    "veg_shade": (ctypes.c_int, [_CAMS, _I32, _P, _I64, _P, _P, _P, _P, _P]),
+    "veg_shade_bwd": (ctypes.c_int, [_CAMS, _I32, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -192,11 +194,11 @@ def veg_tile_order(tile_ranges, tile_order, stream=None):
 
 
 def veg_composite_fwd(cams, n, splat_geo, splat_aux, vals, tile_ranges, tf, bg, tf_group, out,
-                      n_contrib, stats=None, stream=None, tile_order=None):
+                      n_contrib, stats=None, stream=None, tile_order=None, splat_shade=None):
     bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
     _check("veg_composite_fwd",
            load().veg_composite_fwd(cams, len(cams), n, _ptr(splat_geo), _ptr(splat_aux),
-                                    _ptr(vals), _ptr(tile_ranges), _ptr(tile_order), tf,
+                                    _ptr(splat_shade), _ptr(vals), _ptr(tile_ranges), _ptr(tile_order), tf,
                                     ctypes.cast(bgc, ctypes.c_void_p), tf_group, _ptr(out),
                                     _ptr(n_contrib), _ptr(stats), _stream(stream)))
 
@@ -210,17 +212,45 @@ def veg_composite_bwd_workspace_size(n, n_views) -> int:
 
 def veg_composite_bwd(cams, g, splat_geo, splat_aux, tiles_touched, vals, tile_ranges, tf, bg,
                       tf_group, out, n_contrib, dL_dout, workspace, grad_mean_v, grad_logscale_w,
-                      grad_quat, grad2d=None, stats=None, stream=None, tile_order=None):
+                      grad_quat, grad2d=None, stats=None, stream=None, tile_order=None,
+                      splat_shade=None, grad_shade=None):
     bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check("veg_composite_bwd",
            load().veg_composite_bwd(cams, len(cams), g, _ptr(splat_geo), _ptr(splat_aux),
-                                    _ptr(tiles_touched), _ptr(vals), _ptr(tile_ranges),
+                                    _ptr(splat_shade), _ptr(tiles_touched), _ptr(vals), _ptr(tile_ranges),
                                     _ptr(tile_order), tf,
                                     ctypes.cast(bgc, ctypes.c_void_p), tf_group, _ptr(out),
                                     _ptr(n_contrib), _ptr(dL_dout), _ptr(workspace), ws_bytes,
                                     _ptr(grad_mean_v), _ptr(grad_logscale_w), _ptr(grad_quat),
-                                    _ptr(grad2d), _ptr(stats), _stream(stream)))
+                                    _ptr(grad2d), _ptr(grad_shade), _ptr(stats),
+                                    _stream(stream)))
+
+
+def _lights(light_dirs):
+    l = np.ascontiguousarray(np.asarray(light_dirs, np.float32).reshape(-1, 3))
+    return l, ctypes.c_void_p(l.ctypes.data)
+
+
+def veg_shade(cams, mean_v, normal_beta, k_ads, light_dirs, splat_shade, stream=None):
+    """Blinn-Phong factors (s_d, s_s) per view and Gaussian; light_dirs is a
+    host array [V][3]."""
+    keep, lp = _lights(light_dirs)
+    _check("veg_shade",
+           load().veg_shade(cams, len(cams), _ptr(mean_v), mean_v.shape[0], _ptr(normal_beta),
+                            _ptr(k_ads), lp, _ptr(splat_shade), _stream(stream)))
+    del keep
+
+
+def veg_shade_bwd(cams, mean_v, normal_beta, k_ads, light_dirs, tiles_touched, grad_shade,
+                  grad_mean_v, grad_normal_beta, grad_k_ads, stream=None):
+    keep, lp = _lights(light_dirs)
+    _check("veg_shade_bwd",
+           load().veg_shade_bwd(cams, len(cams), _ptr(mean_v), mean_v.shape[0],
+                                _ptr(normal_beta), _ptr(k_ads), lp, _ptr(tiles_touched),
+                                _ptr(grad_shade), _ptr(grad_mean_v), _ptr(grad_normal_beta),
+                                _ptr(grad_k_ads), _stream(stream)))
+    del keep
 
 
 def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,

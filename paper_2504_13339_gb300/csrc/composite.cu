@@ -12,24 +12,34 @@ veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
 veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float4* geo, const float4* aux, const uint32_t* vals,
                                 const int2* ranges, const int32_t* order, veg_tf tf,
-                                const float* bg, int tf_group, float4* out, int32_t* n_contrib,
-                                unsigned long long* stats, cudaStream_t stream) {
-  CompArgs A = make_args(cams, geo, aux, vals, ranges, order, tf, bg);
+                                const float* bg, const float* shade, int tf_group, float4* out,
+                                int32_t* n_contrib, unsigned long long* stats,
+                                cudaStream_t stream) {
+  CompArgs A = make_args(cams, geo, aux, vals, ranges, order, tf, bg, shade);
   (void)n;
   const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, false);
+  if (shade) {
+    if (stats) return VEG_ERR_UNSUPPORTED;
+    switch (TG) {
+      case 1: return launch_fwd_t<1, false, true>(A, n_views, out, n_contrib, nullptr, stream);
+      case 2: return launch_fwd_t<2, false, true>(A, n_views, out, n_contrib, nullptr, stream);
+      case 4: return launch_fwd_t<4, false, true>(A, n_views, out, n_contrib, nullptr, stream);
+      default: return launch_fwd_t<8, false, true>(A, n_views, out, n_contrib, nullptr, stream);
+    }
+  }
   if (stats) {
     switch (TG) {
-      case 1: return launch_fwd_t<1, true>(A, n_views, out, n_contrib, stats, stream);
-      case 2: return launch_fwd_t<2, true>(A, n_views, out, n_contrib, stats, stream);
-      case 4: return launch_fwd_t<4, true>(A, n_views, out, n_contrib, stats, stream);
-      default: return launch_fwd_t<8, true>(A, n_views, out, n_contrib, stats, stream);
+      case 1: return launch_fwd_t<1, true, false>(A, n_views, out, n_contrib, stats, stream);
+      case 2: return launch_fwd_t<2, true, false>(A, n_views, out, n_contrib, stats, stream);
+      case 4: return launch_fwd_t<4, true, false>(A, n_views, out, n_contrib, stats, stream);
+      default: return launch_fwd_t<8, true, false>(A, n_views, out, n_contrib, stats, stream);
     }
   }
   switch (TG) {
-    case 1: return launch_fwd_t<1, false>(A, n_views, out, n_contrib, nullptr, stream);
-    case 2: return launch_fwd_t<2, false>(A, n_views, out, n_contrib, nullptr, stream);
-    case 4: return launch_fwd_t<4, false>(A, n_views, out, n_contrib, nullptr, stream);
-    default: return launch_fwd_t<8, false>(A, n_views, out, n_contrib, nullptr, stream);
+    case 1: return launch_fwd_t<1, false, false>(A, n_views, out, n_contrib, nullptr, stream);
+    case 2: return launch_fwd_t<2, false, false>(A, n_views, out, n_contrib, nullptr, stream);
+    case 4: return launch_fwd_t<4, false, false>(A, n_views, out, n_contrib, nullptr, stream);
+    default: return launch_fwd_t<8, false, false>(A, n_views, out, n_contrib, nullptr, stream);
   }
 }
 
@@ -60,19 +70,22 @@ static veg_status check_composite_common(const veg_camera* cams, int32_t n_views
 
 extern "C" veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
                                         const float* splat_geo, const float* splat_aux,
-                                        const uint32_t* vals, const int32_t* tile_ranges,
-                                        const int32_t* tile_order, veg_tf tf, const float* bg,
-                                        int32_t tf_group, float* out, int32_t* n_contrib,
-                                        unsigned long long* stats, cudaStream_t stream) {
+                                        const float* splat_shade, const uint32_t* vals,
+                                        const int32_t* tile_ranges, const int32_t* tile_order,
+                                        veg_tf tf, const float* bg, int32_t tf_group, float* out,
+                                        int32_t* n_contrib, unsigned long long* stats,
+                                        cudaStream_t stream) {
   veg_status st =
       check_composite_common(cams, n_views, n, splat_geo, splat_aux, vals, tile_ranges, tf);
   if (st != VEG_OK) return st;
-  if (!out || !n_contrib || !aligned16(out) || tf_group < 0 || tf_group > 8)
+  if (!out || !n_contrib || !aligned16(out) || tf_group < 0 || tf_group > 8 ||
+      (reinterpret_cast<uintptr_t>(splat_shade) & 7))
     return VEG_ERR_INVALID_ARGUMENT;
   return composite_fwd_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
                               reinterpret_cast<const float4*>(splat_aux), vals,
                               reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
-                              tf_group, reinterpret_cast<float4*>(out), n_contrib, stats, stream);
+                              splat_shade, tf_group, reinterpret_cast<float4*>(out), n_contrib,
+                              stats, stream);
 }
 
 extern "C" veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views,
@@ -84,6 +97,7 @@ extern "C" veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_view
 
 extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
                                         const float* splat_geo, const float* splat_aux,
+                                        const float* splat_shade,
                                         const int32_t* tiles_touched, const uint32_t* vals,
                                         const int32_t* tile_ranges, const int32_t* tile_order,
                                         veg_tf tf, const float* bg, int32_t tf_group,
@@ -91,7 +105,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
                                         const int32_t* n_contrib, const float* dL_dout,
                                         void* workspace, size_t workspace_bytes,
                                         float* grad_mean_v, float* grad_logscale_w,
-                                        float* grad_quat, float* grad2d,
+                                        float* grad_quat, float* grad2d, float* grad_shade,
                                         unsigned long long* stats, cudaStream_t stream) {
   veg_status st =
       check_composite_common(cams, n_views, g.n, splat_geo, splat_aux, vals, tile_ranges, tf);
@@ -109,6 +123,11 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
       !aligned16(grad2d) || !aligned16(g.mean_v) || !aligned16(g.logscale_w) ||
       !aligned16(g.quat))
     return VEG_ERR_INVALID_ARGUMENT;
+  const bool lit = splat_shade != nullptr;
+  if (lit && (!grad_shade || (reinterpret_cast<uintptr_t>(splat_shade) & 7) ||
+              (reinterpret_cast<uintptr_t>(grad_shade) & 7)))
+    return VEG_ERR_INVALID_ARGUMENT;
+  if (lit && stats) return VEG_ERR_UNSUPPORTED;
   float4* g2 = reinterpret_cast<float4*>(grad2d);
   if (!g2) {
     if (!workspace || workspace_bytes < composite_bwd_ws_bytes(g.n, n_views) ||
@@ -119,23 +138,34 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
   const int64_t nrec2 = 2 * g.n * n_views;
   if (nrec2 > 0 && cudaMemsetAsync(g2, 0, (size_t)nrec2 * sizeof(float4), stream) != cudaSuccess)
     return VEG_ERR_CUDA;
+  float2* gsh = reinterpret_cast<float2*>(grad_shade);
+  if (lit && nrec2 > 0 &&
+      cudaMemsetAsync(gsh, 0, (size_t)(nrec2 / 2) * sizeof(float2), stream) != cudaSuccess)
+    return VEG_ERR_CUDA;
   CompArgs A = make_args(cams, reinterpret_cast<const float4*>(splat_geo),
                          reinterpret_cast<const float4*>(splat_aux), vals,
-                         reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg);
+                         reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
+                         splat_shade);
   const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, true);
   const float4* o4 = reinterpret_cast<const float4*>(out);
   const float4* d4 = reinterpret_cast<const float4*>(dL_dout);
-  if (stats) {
+  if (lit) {
     switch (TG) {
-      case 1: st = launch_bwd_t<1, true>(A, n_views, o4, n_contrib, d4, g2, stats, stream); break;
-      case 2: st = launch_bwd_t<2, true>(A, n_views, o4, n_contrib, d4, g2, stats, stream); break;
-      default: st = launch_bwd_t<4, true>(A, n_views, o4, n_contrib, d4, g2, stats, stream); break;
+      case 1: st = launch_bwd_t<1, false, true>(A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
+      case 2: st = launch_bwd_t<2, false, true>(A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
+      default: st = launch_bwd_t<4, false, true>(A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
+    }
+  } else if (stats) {
+    switch (TG) {
+      case 1: st = launch_bwd_t<1, true, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
+      case 2: st = launch_bwd_t<2, true, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
+      default: st = launch_bwd_t<4, true, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
     }
   } else {
     switch (TG) {
-      case 1: st = launch_bwd_t<1, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stream); break;
-      case 2: st = launch_bwd_t<2, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stream); break;
-      default: st = launch_bwd_t<4, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stream); break;
+      case 1: st = launch_bwd_t<1, false, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
+      case 2: st = launch_bwd_t<2, false, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
+      default: st = launch_bwd_t<4, false, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
     }
   }
   if (st != VEG_OK || only_2d) return st;

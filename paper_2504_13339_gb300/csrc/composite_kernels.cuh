@@ -149,6 +149,7 @@ struct CompArgs {
   const int32_t* order;    // work-item order (view * tiles + tile) or null
   const int32_t* view_tf;  // per-view table index (one image per view) or null
   const float4* lut;
+  const float2* shade;     // per-record Blinn-Phong factors (s_d, s_s) or null
   int lut_size, n_tf;
   int width, height, tiles_x, tiles_per_view;
   float bg0, bg1, bg2;
@@ -169,11 +170,15 @@ __device__ __forceinline__ void stage_luts(const CompArgs& A, int lut0, int ntg,
 // Stages splat `i` of the tile list into batch slot threadIdx.x: geometry,
 // per-TF colour and A w (and, for the backward, slopes and A), the exponent
 // cutoff and the warp-block mask.  Returns the record index.
-template <int TG, bool BWD>
+//
+// Shading (Eq. 2, LIT): the forward stages the shaded colour s_d C(v) + s_s;
+// the backward stages the unshaded C(v) and (s_d, s_s) in s_sh, with the
+// colour slopes already scaled by s_d.  Without shading s_sh is unused.
+template <int TG, bool BWD, bool LIT>
 __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* s_lut,
                                                 float tx0, float ty0, float4* s_geo, float2* s_c,
                                                 float4* s_col, float4* s_slope, float* s_A,
-                                                unsigned char* s_mask) {
+                                                float2* s_sh, unsigned char* s_mask) {
   const int L = A.lut_size;
   const int s = threadIdx.x;
   const uint32_t g = A.vals[i];
@@ -181,17 +186,26 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
   s_geo[s] = make_float4(ge.x, ge.y, -0.5f * au.x, -au.y);
   const TfPos q = tf_pos(au.w, L);
   const float sl = (au.w >= 0.0f && au.w <= 1.0f) ? (float)(L - 1) : 0.0f;
+  float2 sh = make_float2(1.0f, 0.0f);
+  if (LIT) sh = A.shade[g];
+  if (LIT && BWD) s_sh[s] = sh;
+  const float slc = LIT ? sl * sh.x : sl;  // colour slope scale
   float max_aw = 0.0f;
 #pragma unroll
   for (int t = 0; t < TG; ++t) {
     const float4 lo = s_lut[t * L + q.k], hi = s_lut[t * L + q.k + 1];
     const float Aop = lerp_rn(lo.w, hi.w, q);
     const float aw = mul(Aop, ge.w);
-    s_col[t * kBatch + s] =
-        make_float4(lerp_rn(lo.x, hi.x, q), lerp_rn(lo.y, hi.y, q), lerp_rn(lo.z, hi.z, q), aw);
+    float r = lerp_rn(lo.x, hi.x, q), gc = lerp_rn(lo.y, hi.y, q), b = lerp_rn(lo.z, hi.z, q);
+    if (LIT && !BWD) {
+      r = __fmaf_rn(sh.x, r, sh.y);
+      gc = __fmaf_rn(sh.x, gc, sh.y);
+      b = __fmaf_rn(sh.x, b, sh.y);
+    }
+    s_col[t * kBatch + s] = make_float4(r, gc, b, aw);
     if (BWD) {
-      s_slope[t * kBatch + s] = make_float4(sl * (hi.x - lo.x), sl * (hi.y - lo.y),
-                                            sl * (hi.z - lo.z), ge.w * sl * (hi.w - lo.w));
+      s_slope[t * kBatch + s] = make_float4(slc * (hi.x - lo.x), slc * (hi.y - lo.y),
+                                            slc * (hi.z - lo.z), ge.w * sl * (hi.w - lo.w));
       s_A[t * kBatch + s] = Aop;
     }
     max_aw = fmaxf(max_aw, aw);
@@ -209,7 +223,7 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
 // stats (instrumented build): visited pairs (every pair reached before the
 // pixel's termination, the method's own count), iterated pairs (walked by
 // the warp lists), pairs above the cutoff, alpha evaluations, blended pairs.
-template <int TG, bool STATS>
+template <int TG, bool STATS, bool LIT>
 __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     composite_fwd_kernel(CompArgs A, float4* __restrict__ out, int32_t* __restrict__ n_contrib,
                          unsigned long long* __restrict__ stats) {
@@ -249,8 +263,8 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     if (__syncthreads_count(act != 0u) == 0) break;
     const int cnt = min(kBatch, rg.y - start);
     if ((int)threadIdx.x < cnt)
-      stage_splat<TG, false>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col, nullptr,
-                             nullptr, s_mask);
+      stage_splat<TG, false, LIT>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col,
+                                    nullptr, nullptr, nullptr, s_mask);
     __syncthreads();
     const int nw = build_warp_list(s_mask, s_list[warp], cnt);
     const bool act0 = act != 0u;
@@ -398,6 +412,21 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int la
   return z;
 }
 
+// Sums one value per splat for two splats (a, b) over the warp with 5
+// shuffles (one halving exchange at offset 16, then full steps at 8, 4, 2,
+// 1).  Lanes 0-15 return the total of a, lanes 16-31 that of b.
+__device__ __forceinline__ float warp_reduce_pair(float a, float b, int lane) {
+  const bool hi = lane & 16;
+  float x = (hi ? b : a) + __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ void red_add_v2(float2* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
 __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
                "f"(d)
@@ -413,15 +442,23 @@ __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c,
 // the warp, summed over warps in shared memory and added to the per-record
 // gradient buffer once per tile.
 //
+// Shaded (LIT): the blended colour is s_d C + s_s, so c.g = s_d (C.g) + s_s
+// (g_r + g_g + g_b), dL/dC = s_d alpha T g, and the pair adds alpha T (C.g)
+// to dL/ds_d and alpha T (g_r + g_g + g_b) to dL/ds_s.  dL/ds_d takes the
+// eighth slot of the 16-slot reduce-scatter and dL/ds_s a separate pair
+// reduction; the two shading sums go to grad_shade.
+//
 // stats (instrumented build): replayed pairs (list positions below the
 // pixel's last contribution), iterated pairs, pairs above the cutoff, alpha
 // evaluations, blended pairs, blended pairs below the clamp, pairs with a
 // nonzero screen-space gradient.
-template <int TG, bool STATS>
-__global__ void __launch_bounds__(256)
+template <int TG, bool STATS, bool LIT>
+__global__ void __launch_bounds__(256, 3)
     composite_bwd_kernel(CompArgs A, const float4* __restrict__ out,
                          const int32_t* __restrict__ n_contrib, const float4* __restrict__ dout,
-                         float4* __restrict__ grad2d, unsigned long long* __restrict__ stats) {
+                         float4* __restrict__ grad2d, float2* __restrict__ grad_shade,
+                         unsigned long long* __restrict__ stats) {
+  constexpr int kAcc = LIT ? 12 : 8;  // accumulator slots per splat
   unsigned long long n_rep = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0, n_free = 0,
                      n_grad = 0;
   extern __shared__ float4 smem[];
@@ -430,10 +467,12 @@ __global__ void __launch_bounds__(256)
   float4* s_slope = s_col + TG * kBatch;                    // [TG][kBatch]: drgb/dv, w dA/dv
   float4* s_geo = s_slope + TG * kBatch;                    // [kBatch]: u, -a/2, -b
   float2* s_c = reinterpret_cast<float2*>(s_geo + kBatch);  // [kBatch]: -c/2, cutoff
-  float* s_A = reinterpret_cast<float*>(s_c + kBatch);      // [TG][kBatch]: A
-  float* s_acc = s_A + TG * kBatch;                         // [kBatch][8] gradient sums
-  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + 8 * kBatch);
-  unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + kBatch);
+  float2* s_sh = s_c + kBatch;                              // [kBatch]: s_d, s_s (LIT)
+  float* s_A = reinterpret_cast<float*>(s_sh + (LIT ? kBatch : 0));  // [TG][kBatch]: A
+  float* s_acc = s_A + TG * kBatch;                         // [kBatch][kAcc] gradient sums
+  // record index of each staged splat (LIT keeps it in the staging thread)
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + kAcc * kBatch);
+  unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + (LIT ? 0 : kBatch));
   unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
   __shared__ int s_maxnc;
 
@@ -446,7 +485,7 @@ __global__ void __launch_bounds__(256)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* my_list = s_lists + warp * kBatch;
   stage_luts<TG>(A, lut0, ntg, s_lut);
-  for (int e = threadIdx.x; e < 8 * kBatch; e += 256) s_acc[e] = 0.0f;
+  for (int e = threadIdx.x; e < kAcc * kBatch; e += 256) s_acc[e] = 0.0f;
   if (threadIdx.x == 0) s_maxnc = 0;
   int px, py;
   pixel_of(tile, A.tiles_x, px, py);
@@ -456,7 +495,7 @@ __global__ void __launch_bounds__(256)
   const float fx = (float)px, fy = (float)py;
   const int2 rg = A.ranges[wi];
 
-  float T[TG], S[TG], K[TG], gr[TG], gg[TG], gb[TG];
+  float T[TG], S[TG], K[TG], gr[TG], gg[TG], gb[TG], gs[TG];
   int nc[TG];
   int my_max = 0;
 #pragma unroll
@@ -464,7 +503,7 @@ __global__ void __launch_bounds__(256)
     T[t] = 1.0f;
     S[t] = 0.0f;
     K[t] = 0.0f;
-    gr[t] = gg[t] = gb[t] = 0.0f;
+    gr[t] = gg[t] = gb[t] = gs[t] = 0.0f;
     nc[t] = 0;
     if (inside && t < ntg) {
       const int64_t o = (((int64_t)view * n_out + t0 + t) * A.height + py) * A.width + px;
@@ -473,6 +512,7 @@ __global__ void __launch_bounds__(256)
       gr[t] = dv4.x;
       gg[t] = dv4.y;
       gb[t] = dv4.z;
+      gs[t] = dv4.x + dv4.y + dv4.z;
       const float Tn = ov.w;
       const float cr = ov.x - Tn * A.bg0, cg = ov.y - Tn * A.bg1, cb = ov.z - Tn * A.bg2;
       K[t] = cr * dv4.x + cg * dv4.y + cb * dv4.z +
@@ -495,14 +535,21 @@ __global__ void __launch_bounds__(256)
   for (int start = rg.x; start < rg.x + block_max; start += kBatch) {
     const int i = start + threadIdx.x;
     const int cnt = min(kBatch, rg.y - start);
-    if (i < rg.y)
-      s_idx[threadIdx.x] = stage_splat<TG, true>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col,
-                                                 s_slope, s_A, s_mask);
+    uint32_t my_rec = 0;
+    if (i < rg.y) {
+      my_rec = stage_splat<TG, true, LIT>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col, s_slope, s_A,
+                                          s_sh, s_mask);
+      if (!LIT) s_idx[threadIdx.x] = my_rec;
+    }
     __syncthreads();
     const int nw = build_warp_list(s_mask, my_list, cnt);
     // replayed blend of splat j at list position idx for every TF of the
-    // group: accumulates dL/dG, dL/dv, dL/dw of this pixel
-    auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dww) {
+    // group: accumulates dL/dG, dL/dv, dL/dw (and dL/ds_d, dL/ds_s) of this
+    // pixel
+    auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dww, float& dsd,
+                        float& dss) {
+      float2 sh = make_float2(1.0f, 0.0f);
+      if (LIT) sh = s_sh[j];
 #pragma unroll
       for (int t = 0; t < TG; ++t) {
         if (idx >= nc[t]) continue;
@@ -516,7 +563,12 @@ __global__ void __launch_bounds__(256)
           n_free += (raw <= kAlphaMax);
         }
         const float wgt = mul(alpha, T[t]);
-        const float cgd = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
+        const float cgu = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
+        const float cgd = LIT ? sh.x * cgu + sh.y * gs[t] : cgu;
+        if (LIT) {
+          dsd += wgt * cgu;
+          dss += wgt * gs[t];
+        }
         S[t] += cgd * wgt;
         const float one_m = sub(1.0f, alpha);
         const float dalpha = T[t] * cgd - __fdividef(K[t] - S[t], one_m);
@@ -531,9 +583,9 @@ __global__ void __launch_bounds__(256)
         T[t] = mul(T[t], one_m);
       }
     };
-    // screen-space gradient parts of one pair: u_x, u_y, conic a, b, c, v, w
+    // gradient parts of one pair: u_x, u_y, conic a, b, c, v, w (and s_d)
     auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float dx, float dy, float dvv,
-                          float dww) {
+                          float dww, float dsd) {
       v[0] = dp * (2.0f * sg.z * dx + sg.w * dy);
       v[1] = dp * (2.0f * sc * dy + sg.w * dx);
       v[2] = dp * (-0.5f * dx * dx);
@@ -541,7 +593,7 @@ __global__ void __launch_bounds__(256)
       v[4] = dp * (-0.5f * dy * dy);
       v[5] = dvv;
       v[6] = dww;
-      v[7] = 0.0f;
+      v[7] = LIT ? dsd : 0.0f;
     };
     // two splats per step: independent geometry and exponentials overlap,
     // the replay stays in list order, and one 16-slot reduce-scatter sums
@@ -565,37 +617,47 @@ __global__ void __launch_bounds__(256)
       const float G0 = ev0 ? gauss_of(p0) : 0.f;
       const float G1 = ev1 ? gauss_of(p1) : 0.f;
       float dG0 = 0.f, dv0 = 0.f, dw0 = 0.f, dG1 = 0.f, dv1 = 0.f, dw1 = 0.f;
-      if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dw0);
-      if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dw1);
+      float dd0 = 0.f, ds0 = 0.f, dd1 = 0.f, ds1 = 0.f;
+      if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dw0, dd0, ds0);
+      if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dw1, dd1, ds1);
       if (STATS) n_eval += (unsigned)ev0 + (unsigned)ev1;
       if (STATS) n_grad += (unsigned)(dG0 != 0.f) + (unsigned)(dG1 != 0.f);
       const float dp0 = dG0 * G0, dp1 = dG1 * G1;
-      const bool nz = dp0 != 0.f || dv0 != 0.f || dw0 != 0.f || dp1 != 0.f || dv1 != 0.f ||
-                      dw1 != 0.f;
+      bool nz = dp0 != 0.f || dv0 != 0.f || dw0 != 0.f || dp1 != 0.f || dv1 != 0.f || dw1 != 0.f;
+      if (LIT) nz = nz || dd0 != 0.f || ds0 != 0.f || dd1 != 0.f || ds1 != 0.f;
       if (__any_sync(0xffffffffu, nz)) {
         float v[16];
-        pair_parts(v, dp0, sg0, sc0.x, dx0, dy0, dv0, dw0);
-        pair_parts(v + 8, dp1, sg1, sc1.x, dx1, dy1, dv1, dw1);
+        pair_parts(v, dp0, sg0, sc0.x, dx0, dy0, dv0, dw0, dd0);
+        pair_parts(v + 8, dp1, sg1, sc1.x, dx1, dy1, dv1, dw1, dd1);
         // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
         const float r = warp_reduce_scatter16(v, lane);
         const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
-        if ((lane & 1) == 0 && comp < 7 && (which == 0 || has1))
-          atomicAdd(&s_acc[(which ? j1 : j0) * 8 + comp], r);
+        if ((lane & 1) == 0 && comp < (LIT ? 8 : 7) && (which == 0 || has1))
+          atomicAdd(&s_acc[(which ? j1 : j0) * kAcc + comp], r);
+        if (LIT) {
+          const float rs = warp_reduce_pair(ds0, ds1, lane);
+          if ((lane & 15) == 1 && (lane < 16 || has1))
+            atomicAdd(&s_acc[(lane < 16 ? j0 : j1) * kAcc + 8], rs);
+        }
       }
     }
     __syncthreads();
     if (i < rg.y) {
-      const float4 a0 = reinterpret_cast<const float4*>(s_acc)[2 * threadIdx.x];
-      const float4 a1 = reinterpret_cast<const float4*>(s_acc)[2 * threadIdx.x + 1];
-      reinterpret_cast<float4*>(s_acc)[2 * threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-      reinterpret_cast<float4*>(s_acc)[2 * threadIdx.x + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* acc = reinterpret_cast<float4*>(s_acc) + (kAcc / 4) * threadIdx.x;
+      const float4 a0 = acc[0], a1 = acc[1];
+      const float4 a2 = LIT ? acc[2] : make_float4(0.f, 0.f, 0.f, 0.f);
+      acc[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      acc[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (LIT) acc[2] = make_float4(0.f, 0.f, 0.f, 0.f);
       const bool any = a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f ||
                        a1.x != 0.f || a1.y != 0.f || a1.z != 0.f;
+      const uint32_t rec = LIT ? my_rec : s_idx[threadIdx.x];
       if (any) {
-        float4* dst = grad2d + 2 * (int64_t)s_idx[threadIdx.x];
+        float4* dst = grad2d + 2 * (int64_t)rec;
         red_add_v4(dst, a0.x, a0.y, a0.z, a0.w);
         red_add_v4(dst + 1, a1.x, a1.y, a1.z, 0.0f);
       }
+      if (LIT && (a1.w != 0.f || a2.x != 0.f)) red_add_v2(grad_shade + rec, a1.w, a2.x);
     }
     __syncthreads();
   }
@@ -622,11 +684,12 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-size_t bwd_smem_bytes(int TG, int L) {
-  // lut, col + slope, geo, (c, cutoff), A, acc[8], idx, mask, warp lists
+size_t bwd_smem_bytes(int TG, int L, bool lit) {
+  // lut, col + slope, geo, (c, cutoff), (s_d, s_s), A, acc, idx, mask, warp lists
   return (size_t)TG * L * 16 + (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
-         (size_t)kBatch * 8 + (size_t)TG * kBatch * 4 + (size_t)8 * kBatch * 4 +
-         (size_t)kBatch * 4 + (size_t)kBatch + (size_t)kWarps * kBatch;
+         (size_t)kBatch * 8 + (lit ? (size_t)kBatch * 8 : 0) + (size_t)TG * kBatch * 4 +
+         (size_t)(lit ? 12 : 8) * kBatch * 4 + (lit ? 0 : (size_t)kBatch * 4) + (size_t)kBatch +
+         (size_t)kWarps * kBatch;
 }
 
 int pick_group(int tf_group, int n_tf, bool bwd) {
@@ -640,8 +703,9 @@ int pick_group(int tf_group, int n_tf, bool bwd) {
 
 CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
                    const uint32_t* vals, const int2* ranges, const int32_t* order, veg_tf tf,
-                   const float* bg) {
+                   const float* bg, const float* shade) {
   CompArgs A;
+  A.shade = reinterpret_cast<const float2*>(shade);
   A.geo = geo;
   A.aux = aux;
   A.vals = vals;
@@ -679,11 +743,11 @@ veg_status prepare_smem(K kern, size_t dyn, size_t* configured) {
   return VEG_OK;
 }
 
-template <int TG, bool STATS>
+template <int TG, bool STATS, bool LIT>
 veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc,
                         unsigned long long* stats, cudaStream_t stream) {
   const size_t smem = (size_t)TG * A.lut_size * sizeof(float4);
-  auto kern = composite_fwd_kernel<TG, STATS>;
+  auto kern = composite_fwd_kernel<TG, STATS, LIT>;
   static size_t configured = 0;
   veg_status st = prepare_smem(kern, smem, &configured);
   if (st != VEG_OK) return st;
@@ -694,18 +758,18 @@ veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc
   return launch_status();
 }
 
-template <int TG, bool STATS>
+template <int TG, bool STATS, bool LIT>
 veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const int32_t* nc,
-                        const float4* dout, float4* grad2d, unsigned long long* stats,
-                        cudaStream_t stream) {
-  const size_t smem = bwd_smem_bytes(TG, A.lut_size);
-  auto kern = composite_bwd_kernel<TG, STATS>;
+                        const float4* dout, float4* grad2d, float2* grad_shade,
+                        unsigned long long* stats, cudaStream_t stream) {
+  const size_t smem = bwd_smem_bytes(TG, A.lut_size, LIT);
+  auto kern = composite_bwd_kernel<TG, STATS, LIT>;
   static size_t configured = 0;
   veg_status st = prepare_smem(kern, smem, &configured);
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
-  kern<<<grid, 256, smem, stream>>>(A, out, nc, dout, grad2d, stats);
+  kern<<<grid, 256, smem, stream>>>(A, out, nc, dout, grad2d, grad_shade, stats);
   count_launch();
   return launch_status();
 }

@@ -6,6 +6,11 @@ entry points: veg_project -> veg_bin_sort -> veg_composite_fwd, then
 veg_l1_loss and veg_composite_bwd for training.  PyTorch only provides the
 memory and the stream; every stage runs in libveg.so.
 
+With Blinn-Phong lighting (Eq. 2-3) `shade` runs veg_shade first; the
+compositor then blends s_d C(v) + s_s, and the backward chains the shading
+gradients through veg_shade_bwd to the normals, the shininess, the material
+coefficients and the means.
+
 `VEGRender` wraps forward/backward as a torch.autograd.Function so that the
 sigmoid activations of the stored scalar and weight (Sec. 3.3) and the
 optimiser stay in torch.
@@ -21,6 +26,12 @@ from . import _lib
 def lut_tensor(luts, device="cuda") -> torch.Tensor:
     t = torch.as_tensor(np.asarray(luts, np.float32), device=device)
     return t.reshape(-1, t.shape[-2], 4).contiguous()
+
+
+def headlight_dirs(cams) -> np.ndarray:
+    """[V][3] world directions toward a light on each camera's optical axis,
+    behind the camera (the headlight of the paper's reference renders)."""
+    return np.stack([-np.asarray(c.world_to_cam, np.float64)[2, :3] for c in cams])
 
 
 class SplatPipeline:
@@ -56,6 +67,9 @@ class SplatPipeline:
                                    device=dev)
         self.grad2d = torch.empty(nrec * 2, 4, device=dev)
         self.keys = None
+        self._lit = None  # (mean_v, normal_beta, k_ads, light_dirs) when shaded
+        self.splat_shade = None
+        self.grad_shade = None
         self.set_capacity(capacity if capacity is not None else max(1 << 16, 8 * nrec))
 
     def set_capacity(self, capacity):
@@ -71,6 +85,20 @@ class SplatPipeline:
         tf = _lib.tf_desc(cull_luts) if cull_luts is not None else None
         _lib.veg_project(self.c_cams, self._g, tf, self.geo, self.aux, self.tiles, self.rect,
                          stream)
+
+    def shade(self, mean_v, normal_beta, k_ads, light_dirs, stream=None):
+        """Blinn-Phong factors of every view (veg_shade); later composites and
+        backward passes are shaded until `unshade`."""
+        if self.splat_shade is None:
+            self.splat_shade = torch.empty(self.V * self.n, 2, device=self.device)
+            self.grad_shade = torch.empty(self.V * self.n, 2, device=self.device)
+        light_dirs = np.asarray(light_dirs, np.float32).reshape(self.V, 3)
+        self._lit = (mean_v, normal_beta, k_ads, light_dirs)
+        _lib.veg_shade(self.c_cams, mean_v, normal_beta, k_ads, light_dirs, self.splat_shade,
+                       stream)
+
+    def unshade(self):
+        self._lit = None
 
     def bin_sort(self, want_keys=False, stream=None):
         keys = None
@@ -92,33 +120,55 @@ class SplatPipeline:
         self._bg = tuple(float(b) for b in bg)
         _lib.veg_composite_fwd(self.c_cams, self.n, self.geo, self.aux, self.vals, self.ranges,
                                _lib.tf_desc(luts), self._bg, self.tf_group, self.out,
-                               self.n_contrib, stats, stream, tile_order=self.order)
+                               self.n_contrib, stats, stream, tile_order=self.order,
+                               splat_shade=self._shade_buf())
         return self.out
+
+    def _shade_buf(self):
+        return self.splat_shade if self._lit is not None else None
+
+    def _grad_shade_buf(self):
+        return self.grad_shade if self._lit is not None else None
 
     def l1(self, target, stream=None):
         _lib.veg_l1_loss(self.out, target, self.out.numel() // 4, self.loss_grad, self.loss,
                          self.loss_ws, stream)
         return self.loss
 
-    def backward(self, dL_dout, grad_mean_v, grad_logscale_w, grad_quat, stream=None):
+    def backward(self, dL_dout, grad_mean_v, grad_logscale_w, grad_quat, grad_normal_beta=None,
+                 grad_k_ads=None, stream=None):
+        """Accumulates the gradients of every parameter; when shaded, also
+        those of the lighting parameters (grad_normal_beta, grad_k_ads)."""
         _lib.veg_composite_bwd(self.c_cams, self._g, self.geo, self.aux, self.tiles, self.vals,
                                self.ranges, _lib.tf_desc(self._luts), self._bg,
                                self.tf_group_bwd,
                                self.out, self.n_contrib, dL_dout, None, grad_mean_v,
                                grad_logscale_w, grad_quat, self.grad2d, None, stream,
-                               tile_order=self.order)
+                               tile_order=self.order, splat_shade=self._shade_buf(),
+                               grad_shade=self._grad_shade_buf())
+        if self._lit is not None:
+            self.shade_backward(grad_mean_v, grad_normal_beta, grad_k_ads, stream)
 
     def backward_2d(self, dL_dout, stats=None, stream=None):
-        """Screen-space gradients only (into self.grad2d)."""
+        """Screen-space gradients only (into self.grad2d, and self.grad_shade
+        when shaded)."""
         _lib.veg_composite_bwd(self.c_cams, self._g, self.geo, self.aux, self.tiles, self.vals,
                                self.ranges, _lib.tf_desc(self._luts), self._bg,
                                self.tf_group_bwd,
                                self.out, self.n_contrib, dL_dout, None, None, None, None,
-                               self.grad2d, stats, stream, tile_order=self.order)
+                               self.grad2d, stats, stream, tile_order=self.order,
+                               splat_shade=self._shade_buf(), grad_shade=self._grad_shade_buf())
 
     def project_backward(self, grad_mean_v, grad_logscale_w, grad_quat, stream=None):
         _lib.veg_project_bwd(self.c_cams, self._g, self.tiles, self.grad2d, grad_mean_v,
                              grad_logscale_w, grad_quat, stream)
+
+    def shade_backward(self, grad_mean_v, grad_normal_beta, grad_k_ads, stream=None):
+        if grad_normal_beta is None or grad_k_ads is None:
+            raise ValueError("a shaded backward needs grad_normal_beta and grad_k_ads")
+        mean_v, normal_beta, k_ads, light_dirs = self._lit
+        _lib.veg_shade_bwd(self.c_cams, mean_v, normal_beta, k_ads, light_dirs, self.tiles,
+                           self.grad_shade, grad_mean_v, grad_normal_beta, grad_k_ads, stream)
 
     # -- whole passes --------------------------------------------------------
     def render(self, mean_v, logscale_w, quat, luts, bg=(0.0, 0.0, 0.0), cull=True,
@@ -134,12 +184,18 @@ class SplatPipeline:
         return self.composite(luts, bg, stream=stream)
 
     def train_step(self, mean_v, logscale_w, quat, luts, target, grads, bg=(0.0, 0.0, 0.0),
-                   stream=None):
-        """One pass of the hot path: project, bin, sort, composite, L1 loss,
-        composite backward, projection backward (grads are zeroed first)."""
+                   lighting=None, stream=None):
+        """One pass of the hot path: project, bin, sort, (shade,) composite,
+        L1 loss, composite backward, projection (and shading) backward.
+        grads = (mean_v, logscale_w, quat[, normal_beta, k_ads]) gradient
+        buffers, zeroed first; lighting = (normal_beta, k_ads, light_dirs)."""
         for gbuf in grads:
             gbuf.zero_()
         self.project(mean_v, logscale_w, quat, luts, stream)
+        if lighting is not None:
+            self.shade(mean_v, *lighting, stream=stream)
+        else:
+            self.unshade()
         self.bin_sort(stream=stream)
         self.composite(luts, bg, stream=stream)
         self.l1(target, stream)
@@ -148,27 +204,53 @@ class SplatPipeline:
 
 
 class VEGRender(torch.autograd.Function):
-    """out[V,T,H,W,4] = render(mean_v, logscale_w, quat) for fixed cameras,
-    transfer functions and background; gradients from veg_composite_bwd."""
+    """out[V,T,H,W,4] = render(mean_v, logscale_w, quat[, normal_beta, k_ads])
+    for fixed cameras, transfer functions, background (and light
+    directions); gradients from veg_composite_bwd (and veg_shade_bwd)."""
 
     @staticmethod
-    def forward(ctx, mean_v, logscale_w, quat, pipeline: SplatPipeline, luts, bg):
+    def forward(ctx, mean_v, logscale_w, quat, normal_beta, k_ads, pipeline: SplatPipeline, luts,
+                bg, light_dirs):
         mean_v, logscale_w, quat = (t.contiguous() for t in (mean_v, logscale_w, quat))
-        out = pipeline.render(mean_v, logscale_w, quat, luts, bg)
+        lit = normal_beta is not None
+        pipeline.project(mean_v, logscale_w, quat, luts)
+        if lit:
+            normal_beta, k_ads = normal_beta.contiguous(), k_ads.contiguous()
+            pipeline.shade(mean_v, normal_beta, k_ads, light_dirs)
+        else:
+            pipeline.unshade()
+        pipeline.bin_sort()
+        st, m = pipeline.status()
+        if st != _lib.VEG_OK:
+            pipeline.set_capacity(int(m * 1.25) + 1024)
+            pipeline.bin_sort()
+        out = pipeline.composite(luts, bg)
         ctx.pipeline = pipeline
-        ctx.save_for_backward(mean_v, logscale_w, quat)
+        ctx.lit = lit
+        if lit:
+            ctx.save_for_backward(mean_v, logscale_w, quat, normal_beta, k_ads)
+        else:
+            ctx.save_for_backward(mean_v, logscale_w, quat)
         return out.clone()
 
     @staticmethod
     def backward(ctx, dout):
-        mean_v, logscale_w, quat = ctx.saved_tensors
+        saved = ctx.saved_tensors
         p = ctx.pipeline
-        gm = torch.zeros_like(mean_v)
-        gl = torch.zeros_like(logscale_w)
-        gq = torch.zeros_like(quat)
+        gm, gl, gq = (torch.zeros_like(t) for t in saved[:3])
+        if ctx.lit:
+            gn = torch.zeros_like(saved[3])
+            gk = torch.zeros_like(saved[4])
+            p.backward(dout.contiguous(), gm, gl, gq, gn, gk)
+            return gm, gl, gq, gn, gk, None, None, None, None
         p.backward(dout.contiguous(), gm, gl, gq)
-        return gm, gl, gq, None, None, None
+        return gm, gl, gq, None, None, None, None, None, None
 
 
-def render(mean_v, logscale_w, quat, pipeline, luts, bg=(0.0, 0.0, 0.0)):
-    return VEGRender.apply(mean_v, logscale_w, quat, pipeline, luts, bg)
+def render(mean_v, logscale_w, quat, pipeline, luts, bg=(0.0, 0.0, 0.0), normal_beta=None,
+           k_ads=None, light_dirs=None):
+    """Differentiable render; Blinn-Phong shaded when normal_beta [n][4]
+    (normal, beta), k_ads [n][4] (k_a, k_d, k_s, -) and light_dirs [V][3]
+    are given."""
+    return VEGRender.apply(mean_v, logscale_w, quat, normal_beta, k_ads, pipeline, luts, bg,
+                           light_dirs)

@@ -238,6 +238,37 @@ def constant_tf(rgba, size=LUT_SIZE) -> np.ndarray:
     return np.tile(np.asarray(rgba, np.float32)[None], (size, 1))
 
 
+@dataclass
+class Lighting:
+    """Per-Gaussian Blinn-Phong parameters (Eq. 2-3) in the library's packed
+    layouts: normal_beta (N, 4) = (normal, beta), k_ads (N, 4) = (k_a, k_d,
+    k_s, 0)."""
+    normal_beta: np.ndarray
+    k_ads: np.ndarray
+
+    def as_dict(self, lights) -> dict:
+        """The oracle's form: normal, ka, kd, ks, beta in float64 plus the
+        per-view light directions."""
+        nb = self.normal_beta.astype(np.float64)
+        k = self.k_ads.astype(np.float64)
+        return {"normal": nb[:, :3], "beta": nb[:, 3], "ka": k[:, 0], "kd": k[:, 1],
+                "ks": k[:, 2], "lights": np.asarray(lights, np.float64)}
+
+
+def random_lighting(n, seed, beta=(1.0, 30.0)) -> Lighting:
+    """Normals N(0, I) (not normalised), k_a U[0.1, 0.6], k_d U[0.2, 0.9],
+    k_s U[0, 0.8], shininess U[beta]."""
+    rng = np.random.default_rng(seed)
+    normal = rng.standard_normal((n, 3))
+    ka = rng.uniform(0.1, 0.6, n)
+    kd = rng.uniform(0.2, 0.9, n)
+    ks = rng.uniform(0.0, 0.8, n)
+    b = rng.uniform(beta[0], beta[1], n)
+    nb = np.concatenate([normal, b[:, None]], 1).astype(np.float32)
+    k = np.stack([ka, kd, ks, np.zeros(n)], 1).astype(np.float32)
+    return Lighting(nb, k)
+
+
 # ----------------------------------------------------------------------------
 # Named workloads
 # ----------------------------------------------------------------------------

@@ -31,7 +31,8 @@ def lib():
 def test_header_declares_the_boundary():
     syms = declared_symbols()
     for name in ("veg_project", "veg_bin_sort", "veg_composite_fwd", "veg_composite_bwd",
-                 "veg_render", "veg_sync_status", "veg_status_string", "veg_l1_loss"):
+                 "veg_render", "veg_sync_status", "veg_status_string", "veg_l1_loss",
+                 "veg_shade", "veg_shade_bwd"):
         assert name in syms
 
 
@@ -71,8 +72,8 @@ def test_host_side_validation_needs_no_gpu(lib):
     # null Gaussian arrays with n > 0
     assert lib.veg_project(cams, 1, g, None, None, None, None, None, None) == 1
     tf = _lib.veg_tf(0, 1, 1)
-    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, None, tf, None, 0, None,
-                                 None, None, None) == 1
+    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, None, None, tf, None, 0,
+                                 None, None, None, None) == 1
     assert lib.veg_tile_order(None, 5, None, None) == 1
     assert lib.veg_sync_status(None, None, None) == 1
     # the fixed-scratch binning refuses a request beyond its array on the host
@@ -82,3 +83,15 @@ def test_host_side_validation_needs_no_gpu(lib):
     assert lib.veg_bin_sort_static(cams, 1, -1, fake, fake, fake, 16, None, fake, fake, None,
                                    None) == 1
     assert lib.veg_l1_loss(None, None, 4, None, None, None, 0, None) == 1
+    # shading: light directions are checked on the host; n = 0 launches nothing
+    light = (ctypes.c_float * 3)(0.0, 0.0, 1.0)
+    zero = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+    assert lib.veg_shade(cams, 1, fake, 8, fake, fake, zero, fake, None) == 1
+    assert lib.veg_shade(cams, 1, fake, 8, fake, fake, None, fake, None) == 1
+    assert lib.veg_shade(cams, 1, fake, -1, fake, fake, light, fake, None) == 1
+    assert lib.veg_shade(cams, 1, fake + 4, 8, fake, fake, light, fake, None) == 1
+    assert lib.veg_shade(cams, 1, None, 0, None, None, light, None, None) == 0
+    assert lib.veg_shade_bwd(cams, 1, fake, 8, fake, fake, light, None, fake, fake, fake, fake,
+                             None) == 1
+    assert lib.veg_shade_bwd(cams, 1, fake, 8, fake, fake, light, fake, fake, fake + 8, fake,
+                             fake, None) == 1

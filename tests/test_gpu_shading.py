@@ -1,0 +1,194 @@
+"""Blinn-Phong shading (Eq. 2-3) on the GPU vs the CPU oracle, through the C ABI.
+
+Bars: shading factors within a bound derived from float32 rounding (the
+specular power amplifies the error of n.h by at most beta); shaded images
+within 1e-4 max-abs (flagged pixels excluded, as for unshaded renders);
+gradients within a relative 1e-3 of the oracle's largest entry per tensor,
+with the upstream gradient zeroed at flagged pixels (a decision that float32
+and float64 may take differently there changes that pixel's gradients).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import veg_oracle as O
+from paper_2504_13339_gb300 import scenes as S
+from paper_2504_13339_gb300.render import SplatPipeline, headlight_dirs, lut_tensor, render
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def lit_scene(n=2000):
+    g = S.uniform_gaussians(2000, 31, logscale_mean=-3.0, logscale_std=0.4)
+    g.logscale_w[:, 3] = np.random.default_rng(32).uniform(0.3, 1.0, g.n)
+    g = g.subset(np.arange(n))
+    cams = S.orbit_cameras(3, 33, 100, 70)  # ragged 7 x 5 tiles
+    lt = S.random_lighting(g.n, 50)
+    return g, cams, lt
+
+
+def lights_of(cams, kind):
+    if kind == "headlight":
+        return np.stack([O.headlight(c) for c in cams])
+    d = np.array([[0.3, 0.8, 0.5], [-0.6, 0.2, 0.77], [0.0, -1.0, 0.1]])
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def lit_forward(g, cams, tfs, lt, lights, bg=(0.0, 0.0, 0.0)):
+    p = SplatPipeline(g.n, cams, n_tf=len(tfs))
+    tens = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
+    lit = (dev(lt.normal_beta), dev(lt.k_ads))
+    luts = lut_tensor(tfs)
+    p.project(*tens, luts)
+    p.shade(tens[0], *lit, lights)
+    p.bin_sort()
+    p.composite(luts, bg)
+    torch.cuda.synchronize()
+    return p, tens, lit, luts
+
+
+def image_check(out_gpu, fwd):
+    ok = ~fwd["flag"]
+    err = np.abs(out_gpu - fwd["out"])
+    assert np.all(err[ok] <= IMG_TOL), float(err[ok].max())
+    assert fwd["flag"].mean() <= 1e-3
+    return float(err[ok].max())
+
+
+def grad_check(got, ref, name):
+    scale = np.abs(ref).max()
+    rel = np.abs(got - ref).max() / max(scale, 1e-30)
+    assert rel <= GRAD_TOL, (name, rel)
+    return rel
+
+
+def test_headlight_directions_agree_with_oracle():
+    cams = S.orbit_cameras(5, 60, 64, 64)
+    assert np.allclose(headlight_dirs(cams), lights_of(cams, "headlight"), atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["headlight", "fixed"])
+def test_shade_factors_match_oracle(kind):
+    g, cams, lt = lit_scene()
+    lights = lights_of(cams, kind)
+    p = SplatPipeline(g.n, cams, n_tf=1)
+    p.shade(dev(g.mean_v), dev(lt.normal_beta), dev(lt.k_ads), lights)
+    torch.cuda.synchronize()
+    got = p.splat_shade.cpu().numpy().reshape(len(cams), g.n, 2)
+    d = lt.as_dict(lights)
+    for v, cam in enumerate(cams):
+        f = O.shade64(cam, lights[v], g.mean_v[:, :3].astype(np.float64), d["normal"], d["ka"],
+                      d["kd"], d["ks"], d["beta"])
+        assert np.all(np.abs(got[v, :, 0] - f["s_d"]) <= 2e-6 * (1 + np.abs(f["s_d"])))
+        # float32 error of n.h (a few 1e-7) times the power's slope <= beta k_s
+        tol = 1e-6 + 4e-6 * d["beta"] * d["ks"]
+        assert np.all(np.abs(got[v, :, 1] - f["s_s"]) <= tol)
+
+
+@pytest.mark.parametrize("kind", ["headlight", "fixed"])
+def test_lit_render_matches_oracle(kind):
+    g, cams, lt = lit_scene()
+    tfs = S.bump_tfs(2, 51)
+    bg = (0.1, 0.2, 0.0)
+    lights = lights_of(cams, kind)
+    p, *_ = lit_forward(g, cams, tfs, lt, lights, bg)
+    _, _, fwd = O.render(cams, g, tfs, bg=bg, lighting=lt.as_dict(lights))
+    image_check(p.out.cpu().numpy(), fwd)
+
+
+def test_trivial_material_equals_unshaded_render():
+    """k_a = 1, k_d = k_s = 0 gives s_d = 1, s_s = 0: the shaded forward is
+    bit-identical to the unshaded one and the backward agrees to rounding."""
+    g, cams, lt = lit_scene(900)
+    lt.k_ads[:] = np.array([1.0, 0.0, 0.0, 0.0], np.float32)
+    tfs = S.bump_tfs(3, 52)
+    lights = lights_of(cams, "headlight")
+    p, tens, lit, luts = lit_forward(g, cams, tfs, lt, lights)
+    q = SplatPipeline(g.n, cams, n_tf=len(tfs))
+    q.project(*tens, luts)
+    q.bin_sort()
+    q.composite(luts)
+    torch.cuda.synchronize()
+    assert torch.equal(p.out, q.out) and torch.equal(p.n_contrib, q.n_contrib)
+    dout = dev(np.random.default_rng(53).standard_normal(p.out.shape).astype(np.float32))
+    ga = [torch.zeros_like(t) for t in tens]
+    gb = [torch.zeros_like(t) for t in tens]
+    gn, gk = torch.zeros_like(lit[0]), torch.zeros_like(lit[1])
+    p.backward(dout, *ga, gn, gk)
+    q.backward(dout, *gb)
+    torch.cuda.synchronize()
+    for a, b in zip(ga, gb):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-5 * float(b.abs().max()))
+    assert float(p.grad_shade[:, 1].abs().max()) > 0  # ds_s is live even with k_s = 0
+
+
+@pytest.mark.parametrize("kind", ["headlight", "fixed"])
+def test_lit_backward_matches_oracle(kind):
+    g, cams, lt = lit_scene(700)
+    tfs = S.bump_tfs(2, 54)
+    bg = (0.1, 0.0, 0.2)
+    lights = lights_of(cams, kind)
+    p, tens, lit, luts = lit_forward(g, cams, tfs, lt, lights, bg)
+    d = lt.as_dict(lights)
+    proj, bins, fwd = O.render(cams, g, tfs, bg=bg, record=True, lighting=d)
+    image_check(p.out.cpu().numpy(), fwd)
+    dout = np.random.default_rng(55).standard_normal(fwd["out"].shape)
+    dout[fwd["flag"]] = 0.0  # near-threshold decisions: excluded, as in the image check
+    grads = [torch.zeros_like(t) for t in tens]
+    gn, gk = torch.zeros_like(lit[0]), torch.zeros_like(lit[1])
+    p.backward(dev(dout.astype(np.float32)), *grads, gn, gk)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd(proj, cams, bins, tfs, bg, fwd, dout)
+    got2 = p.grad2d.cpu().numpy().reshape(len(cams), g.n, 8)
+    gsh = p.grad_shade.cpu().numpy().reshape(len(cams), g.n, 2)
+    for k, name in enumerate(["du_x", "du_y", "da", "db", "dc", "dv", "dw"]):
+        grad_check(got2[..., k], g2[..., k], name)
+    grad_check(gsh[..., 0], g2[..., 7], "ds_d")
+    grad_check(gsh[..., 1], g2[..., 8], "ds_s")
+    gm, gl, gq = O.params_grad(cams, g, proj, g2)
+    dn, dka, dkd, dks, db, dm_sh = O.lighting_grad(cams, g, d, proj, g2)
+    grad_check(grads[0].cpu().numpy()[:, :3], gm[:, :3] + dm_sh, "mean")
+    grad_check(grads[0].cpu().numpy()[:, 3], gm[:, 3], "v")
+    grad_check(grads[1].cpu().numpy()[:, :3], gl[:, :3], "logscale")
+    grad_check(grads[1].cpu().numpy()[:, 3], gl[:, 3], "w")
+    grad_check(grads[2].cpu().numpy(), gq, "quat")
+    gn, gk = gn.cpu().numpy(), gk.cpu().numpy()
+    grad_check(gn[:, :3], dn, "normal")
+    grad_check(gn[:, 3], db, "beta")
+    grad_check(gk[:, 0], dka, "k_a")
+    grad_check(gk[:, 1], dkd, "k_d")
+    grad_check(gk[:, 2], dks, "k_s")
+    assert not gk[:, 3].any()
+
+
+def test_lit_autograd_function():
+    g, cams, lt = lit_scene(1200)
+    tfs = S.bump_tfs(1, 56)
+    luts = lut_tensor(tfs)
+    lights = headlight_dirs(cams)
+    p = SplatPipeline(g.n, cams, n_tf=1)
+    mean_v = dev(g.mean_v).requires_grad_()
+    ls, q = dev(g.logscale_w).requires_grad_(), dev(g.quat).requires_grad_()
+    nb, k = dev(lt.normal_beta).requires_grad_(), dev(lt.k_ads).requires_grad_()
+    out = render(mean_v, ls, q, p, luts, (0.0, 0.0, 0.0), normal_beta=nb, k_ads=k,
+                 light_dirs=lights)
+    w = torch.randn_like(out)
+    (out * w).sum().backward()
+    ref = [torch.zeros_like(t) for t in (mean_v, ls, q, nb, k)]
+    p.backward(w.contiguous(), *ref)
+    close = lambda x, y: bool(((x - y).abs() <= 1e-5 * y.abs().max() + 1e-4 * y.abs()).all())
+    for got, r in zip((mean_v.grad, ls.grad, q.grad, nb.grad, k.grad), ref):
+        assert close(got, r)
