@@ -342,6 +342,51 @@ veg_status veg_l1_loss(const float* out, const float* target, int64_t n_records,
                        cudaStream_t stream);
 
 /*
+ * veg_l1_ssim_loss -- the training image loss of Sec. 4.2,
+ *   loss = (1 - lambda) L1 + lambda (1 - SSIM),  lambda = 0.2 in the paper,
+ * over n_images RGBA images [n_images][height][width][4] (the fourth channel
+ * takes no part).  L1 = mean |out - target| over RGB; SSIM (Wang et al.
+ * 2004) = mean over RGB pixels of the structural similarity index under an
+ * 11 x 11 Gaussian window (sigma 1.5, normalised, zero padding at the image
+ * border) with C1 = 0.01^2, C2 = 0.03^2.  Writes grad = dloss/dout (same
+ * shape, 0 on the fourth channel; sign(0) = 0 for the L1 part) and the device
+ * float[3] loss = (loss, L1, SSIM).  workspace >=
+ * veg_l1_ssim_loss_workspace_size bytes (16-byte aligned); per-tile sums are
+ * reduced in a fixed order, so the result is deterministic.  n_images <=
+ * 65535; lambda in [0, 1].
+ */
+veg_status veg_l1_ssim_loss_workspace_size(int64_t n_images, int32_t height, int32_t width,
+                                           size_t* bytes);
+veg_status veg_l1_ssim_loss(const float* out, const float* target, int64_t n_images,
+                            int32_t height, int32_t width, float lambda, float* grad, float* loss,
+                            void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * veg_adam_step -- one Adam step (Kingma and Ba, bias-corrected) on the
+ * Gaussians' stored parameters, the optimiser of the paper's training
+ * (Sec. 4.2, 5.1).  Five packed device arrays [n][4], each optional (NULL
+ * param = skipped): 0 raw (mu, v), 1 raw (log-scale, w), 2 quaternion,
+ * 3 (normal, beta), 4 (k_a, k_d, k_s, -).  v and w are stored raw and
+ * activated by the logistic sigmoid (Sec. 3.3); every other value is used as
+ * stored.  grad[a] holds dL/d(rendered value) (as accumulated by
+ * veg_composite_bwd and veg_shade_bwd); for the sigmoid components the raw
+ * gradient g s (1 - s) is formed here.  exp_avg / exp_avg_sq are the moment
+ * arrays (zero before step 1).  rendered[0], rendered[1] (optional) receive
+ * the activated (mu, sigmoid(v)) and (log-scale, sigmoid(w)) for the next
+ * render.  lr: host float[20], per array and component.  step >= 1.  All
+ * arrays 16-byte aligned.  One launch.
+ */
+typedef struct veg_adam_arrays {
+  float* param[5];
+  const float* grad[5];
+  float* exp_avg[5];
+  float* exp_avg_sq[5];
+  float* rendered[2];
+} veg_adam_arrays;
+veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, const float* lr, float beta1,
+                         float beta2, float eps, int32_t step, cudaStream_t stream);
+
+/*
  * veg_render -- convenience forward: veg_project (with the TF cull), then
  * veg_bin_sort, then veg_composite_fwd, all scratch in `workspace`
  * (>= veg_render_workspace_size bytes).  Same outputs as

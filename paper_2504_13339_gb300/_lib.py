@@ -45,6 +45,12 @@ class veg_tf(ctypes.Structure):
                 ("view_tf", ctypes.c_void_p)]
 
 
+class veg_adam_arrays(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p * 5), ("grad", ctypes.c_void_p * 5),
+                ("exp_avg", ctypes.c_void_p * 5), ("exp_avg_sq", ctypes.c_void_p * 5),
+                ("rendered", ctypes.c_void_p * 2)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _CAMS = ctypes.POINTER(veg_camera)
@@ -74,6 +80,11 @@ _SIGS = {
     "veg_render": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, veg_tf, _P, _I64, _P, _SZ, _P, _P,
                                   _P]),
     "veg_shade": (ctypes.c_int, [_CAMS, _I32, _P, _I64, _P, _P, _P, _P, _P]),
+    "veg_l1_ssim_loss_workspace_size": (ctypes.c_int, [_I64, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "veg_l1_ssim_loss": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, ctypes.c_float, _P, _P, _P, _SZ,
+                                        _P]),
+    "veg_adam_step": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, _I32, _P]),
     "veg_shade_bwd": (ctypes.c_int, [_CAMS, _I32, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
@@ -251,6 +262,44 @@ def veg_shade_bwd(cams, mean_v, normal_beta, k_ads, light_dirs, tiles_touched, g
                                 _ptr(grad_shade), _ptr(grad_mean_v), _ptr(grad_normal_beta),
                                 _ptr(grad_k_ads), _stream(stream)))
     del keep
+
+
+def veg_l1_ssim_loss_workspace_size(n_images, height, width) -> int:
+    out = _SZ()
+    _check("veg_l1_ssim_loss_workspace_size",
+           load().veg_l1_ssim_loss_workspace_size(n_images, height, width, ctypes.byref(out)))
+    return out.value
+
+
+def veg_l1_ssim_loss(out, target, grad, loss, workspace, lam=0.2, stream=None):
+    """out/target/grad [..., H, W, 4]; loss: device float[3]."""
+    H, W = out.shape[-3], out.shape[-2]
+    n_img = out.numel() // (H * W * 4)
+    _check("veg_l1_ssim_loss",
+           load().veg_l1_ssim_loss(_ptr(out), _ptr(target), n_img, H, W, float(lam), _ptr(grad),
+                                   _ptr(loss), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(),
+                                   _stream(stream)))
+
+
+def adam_arrays(params, grads, exp_avg, exp_avg_sq, rendered=(None, None)):
+    """veg_adam_arrays from five-element lists of tensors (or None)."""
+    a = veg_adam_arrays()
+    for i in range(5):
+        a.param[i] = None if params[i] is None else params[i].data_ptr()
+        a.grad[i] = None if grads[i] is None else grads[i].data_ptr()
+        a.exp_avg[i] = None if exp_avg[i] is None else exp_avg[i].data_ptr()
+        a.exp_avg_sq[i] = None if exp_avg_sq[i] is None else exp_avg_sq[i].data_ptr()
+    for i in range(2):
+        a.rendered[i] = None if rendered[i] is None else rendered[i].data_ptr()
+    return a
+
+
+def veg_adam_step(arrays, n, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    lrs = (ctypes.c_float * 20)(*[float(x) for x in np.asarray(lr, np.float64).ravel()])
+    _check("veg_adam_step",
+           load().veg_adam_step(ctypes.byref(arrays), n, ctypes.cast(lrs, ctypes.c_void_p),
+                                beta1, beta2, eps, step, _stream(stream)))
 
 
 def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,

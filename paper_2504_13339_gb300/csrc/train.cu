@@ -1,0 +1,353 @@
+// Training-side kernels (Sec. 4.2): the image loss (1 - lambda) L1 +
+// lambda (1 - SSIM) with its gradient, and the Adam step on the Gaussians'
+// raw parameters with the sigmoid activations of v and w.
+//
+// SSIM follows Wang et al. (2004): per colour channel, local means,
+// variances and covariance under an 11 x 11 Gaussian window (sigma 1.5,
+// normalised), zero padding at the image border, C1 = 0.01^2, C2 = 0.03^2.
+// With S_q the index at pixel q and m1 = E[x], s11 = E[x^2], s12 = E[xy]
+// its window statistics,
+//   dS_q/dx_p = win(p - q) (dS_q/dm1 + 2 x_p dS_q/ds11 + y_p dS_q/ds12),
+// so the gradient is three window sums of per-pixel partial derivatives.
+//
+// One CTA of 256 threads owns a 16 x 16 tile of one image: it stages the
+// 36 x 36 input region (10-pixel halo) of both images, filters the five
+// products over the 26 x 26 region whose statistics the tile's gradient
+// needs (separable: rows, then columns), forms S and the three partials
+// there, filters those back to the tile, and writes the combined gradient.
+// Per-CTA sums of |x - y| and S go to a workspace and are reduced in a fixed
+// order by a second kernel, so the loss is deterministic.
+#include <cmath>
+
+#include "veg_internal.cuh"
+
+namespace veg {
+
+namespace {
+
+constexpr int kT = 16;             // output tile
+constexpr int kR = 5;              // window radius
+constexpr int kS = kT + 2 * kR;    // 26: statistics region
+constexpr int kI = kT + 4 * kR;    // 36: input region
+constexpr float kC1 = 0.01f * 0.01f;
+constexpr float kC2 = 0.03f * 0.03f;
+
+struct Window {
+  float w[2 * kR + 1];
+};
+
+struct LossSmem {
+  float x[3][kI * kI];  // inputs, per channel (zero outside the image)
+  float y[3][kI * kI];
+  float h[5][kI * kS];  // row pass of x, y, xx, yy, xy
+  float d[3][kS * kS];  // dS/dm1, dS/ds11, dS/ds12 (zero outside the image)
+  float e[3][kS * kT];  // row pass of the partials
+};
+
+__global__ void __launch_bounds__(256)
+    l1_ssim_kernel(Window win, const float4* __restrict__ out, const float4* __restrict__ tgt,
+                   int H, int W, int tiles_x, float lam, float inv_count,
+                   float4* __restrict__ grad, double2* __restrict__ partial) {
+  extern __shared__ float4 smem_raw[];
+  LossSmem& sm = *reinterpret_cast<LossSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x, img = blockIdx.y;
+  const int tx0 = (tile % tiles_x) * kT, ty0 = (tile / tiles_x) * kT;
+  const int64_t base = (int64_t)img * H * W;
+
+  for (int e = tid; e < kI * kI; e += 256) {
+    const int r = e / kI, c = e - r * kI;
+    const int gy = ty0 - 2 * kR + r, gx = tx0 - 2 * kR + c;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+      a = out[base + (int64_t)gy * W + gx];
+      b = tgt[base + (int64_t)gy * W + gx];
+    }
+    sm.x[0][e] = a.x;
+    sm.x[1][e] = a.y;
+    sm.x[2][e] = a.z;
+    sm.y[0][e] = b.x;
+    sm.y[1][e] = b.y;
+    sm.y[2][e] = b.z;
+  }
+  const int py = tid / kT, px = tid - py * kT;  // this thread's output pixel
+  const bool inside = ty0 + py < H && tx0 + px < W;
+  float g[3];
+  float l1 = 0.f, ssum = 0.f;
+
+  for (int ch = 0; ch < 3; ++ch) {
+    __syncthreads();
+    const float* X = sm.x[ch];
+    const float* Y = sm.y[ch];
+    // row pass of the five products over 36 rows x 26 columns
+    for (int e = tid; e < kI * kS; e += 256) {
+      const int r = e / kS, c = e - r * kS;
+      const float* xr = X + r * kI + c;
+      const float* yr = Y + r * kI + c;
+      float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * kR; ++k) {
+        const float a = xr[k], b = yr[k], wk = win.w[k];
+        hx = fmaf(wk, a, hx);
+        hy = fmaf(wk, b, hy);
+        hxx = fmaf(wk, a * a, hxx);
+        hyy = fmaf(wk, b * b, hyy);
+        hxy = fmaf(wk, a * b, hxy);
+      }
+      sm.h[0][e] = hx;
+      sm.h[1][e] = hy;
+      sm.h[2][e] = hxx;
+      sm.h[3][e] = hyy;
+      sm.h[4][e] = hxy;
+    }
+    __syncthreads();
+    // column pass: statistics, S and its partials over the 26 x 26 region
+    for (int e = tid; e < kS * kS; e += 256) {
+      const int r = e / kS, c = e - r * kS;
+      const int gy = ty0 - kR + r, gx = tx0 - kR + c;
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        float m1 = 0.f, m2 = 0.f, s11 = 0.f, s22 = 0.f, s12 = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kR; ++k) {
+          const int o = (r + k) * kS + c;
+          const float wk = win.w[k];
+          m1 = fmaf(wk, sm.h[0][o], m1);
+          m2 = fmaf(wk, sm.h[1][o], m2);
+          s11 = fmaf(wk, sm.h[2][o], s11);
+          s22 = fmaf(wk, sm.h[3][o], s22);
+          s12 = fmaf(wk, sm.h[4][o], s12);
+        }
+        const float a1 = 2.f * m1 * m2 + kC1;
+        const float a2 = 2.f * (s12 - m1 * m2) + kC2;
+        const float b1 = m1 * m1 + m2 * m2 + kC1;
+        const float b2 = (s11 - m1 * m1) + (s22 - m2 * m2) + kC2;
+        const float ib = 1.0f / (b1 * b2);
+        const float S = a1 * a2 * ib;
+        d0 = 2.f * m2 * (a2 - a1) * ib - 2.f * m1 * S * (1.0f / b1 - 1.0f / b2);
+        d1 = -S / b2;
+        d2 = 2.f * a1 * ib;
+        if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) ssum += S;
+      }
+      sm.d[0][e] = d0;
+      sm.d[1][e] = d1;
+      sm.d[2][e] = d2;
+    }
+    __syncthreads();
+    // row pass of the partials over 26 rows x 16 columns
+    for (int e = tid; e < kS * kT; e += 256) {
+      const int r = e / kT, c = e - r * kT;
+      float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * kR; ++k) {
+        const int o = r * kS + c + k;
+        const float wk = win.w[k];
+        q0 = fmaf(wk, sm.d[0][o], q0);
+        q1 = fmaf(wk, sm.d[1][o], q1);
+        q2 = fmaf(wk, sm.d[2][o], q2);
+      }
+      sm.e[0][e] = q0;
+      sm.e[1][e] = q1;
+      sm.e[2][e] = q2;
+    }
+    __syncthreads();
+    // column pass at this thread's pixel, gradient of the channel
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll
+    for (int k = 0; k <= 2 * kR; ++k) {
+      const int o = (py + k) * kT + px;
+      const float wk = win.w[k];
+      q0 = fmaf(wk, sm.e[0][o], q0);
+      q1 = fmaf(wk, sm.e[1][o], q1);
+      q2 = fmaf(wk, sm.e[2][o], q2);
+    }
+    const int io = (py + 2 * kR) * kI + px + 2 * kR;
+    const float xv = X[io], yv = Y[io];
+    const float dssim = q0 + 2.f * xv * q1 + yv * q2;
+    const float diff = xv - yv;
+    const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+    g[ch] = ((1.0f - lam) * sgn - lam * dssim) * inv_count;
+    if (inside) l1 += fabsf(diff);
+  }
+  if (inside) grad[base + (int64_t)(ty0 + py) * W + tx0 + px] = make_float4(g[0], g[1], g[2], 0.f);
+
+  // block sums of |x - y| and S (warp shuffles, then one warp)
+  __shared__ float s_red[2][8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+  }
+  if ((tid & 31) == 0) {
+    s_red[0][tid >> 5] = l1;
+    s_red[1][tid >> 5] = ssum;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a += s_red[0][w];
+      b += s_red[1][w];
+    }
+    partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(a, b);
+  }
+}
+
+// Sums the per-CTA partials in a fixed order: loss[0] = (1 - lam) L1 +
+// lam (1 - SSIM), loss[1] = L1, loss[2] = SSIM.
+__global__ void __launch_bounds__(1024)
+    l1_ssim_final_kernel(const double2* __restrict__ partial, int64_t n, double inv_count,
+                         float lam, float* __restrict__ loss) {
+  __shared__ double s_a[1024], s_b[1024];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    a += partial[i].x;
+    b += partial[i].y;
+  }
+  s_a[threadIdx.x] = a;
+  s_b[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s_a[threadIdx.x] += s_a[threadIdx.x + o];
+      s_b[threadIdx.x] += s_b[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double l1 = s_a[0] * inv_count, ss = s_b[0] * inv_count;
+    loss[0] = (float)((1.0 - lam) * l1 + lam * (1.0 - ss));
+    loss[1] = (float)l1;
+    loss[2] = (float)ss;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma and Ba) on the raw parameters
+// ---------------------------------------------------------------------------
+
+struct AdamArgs {
+  float4* param[5];
+  const float4* grad[5];
+  float4* m[5];
+  float4* v[5];
+  float4* rendered[2];
+  float lr[5][4];
+  float b1, b2, eps, inv_bc1, inv_sqrt_bc2;
+};
+
+__device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+__device__ __forceinline__ void adam_one(float& p, float& m, float& v, float g, float lr,
+                                         const AdamArgs& A) {
+  m = A.b1 * m + (1.0f - A.b1) * g;
+  v = A.b2 * v + (1.0f - A.b2) * g * g;
+  p -= lr * (m * A.inv_bc1) / (sqrtf(v) * A.inv_sqrt_bc2 + A.eps);
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (i >= n || A.param[a] == nullptr) return;
+  float4 p = A.param[a][i], g = A.grad[a][i], m = A.m[a][i], v = A.v[a][i];
+  if (a < 2) {  // the fourth component is sigmoid-activated
+    const float s = sigmoid_f(p.w);
+    g.w *= s * (1.0f - s);
+  }
+  adam_one(p.x, m.x, v.x, g.x, A.lr[a][0], A);
+  adam_one(p.y, m.y, v.y, g.y, A.lr[a][1], A);
+  adam_one(p.z, m.z, v.z, g.z, A.lr[a][2], A);
+  adam_one(p.w, m.w, v.w, g.w, A.lr[a][3], A);
+  A.param[a][i] = p;
+  A.m[a][i] = m;
+  A.v[a][i] = v;
+  if (a < 2 && A.rendered[a]) A.rendered[a][i] = make_float4(p.x, p.y, p.z, sigmoid_f(p.w));
+}
+
+size_t loss_ws_bytes(int64_t n_images, int H, int W) {
+  return (size_t)n_images * tiles_x_of(W) * tiles_x_of(H) * sizeof(double2);
+}
+
+}  // namespace
+
+}  // namespace veg
+
+using namespace veg;
+
+extern "C" veg_status veg_l1_ssim_loss_workspace_size(int64_t n_images, int32_t height,
+                                                      int32_t width, size_t* bytes) {
+  if (!bytes || n_images < 0 || height < 1 || width < 1 || height > 16384 || width > 16384)
+    return VEG_ERR_INVALID_ARGUMENT;
+  *bytes = loss_ws_bytes(n_images, height, width);
+  return VEG_OK;
+}
+
+extern "C" veg_status veg_l1_ssim_loss(const float* out, const float* target, int64_t n_images,
+                                       int32_t height, int32_t width, float lambda, float* grad,
+                                       float* loss, void* workspace, size_t workspace_bytes,
+                                       cudaStream_t stream) {
+  if (n_images < 1 || height < 1 || width < 1 || height > 16384 || width > 16384 || !out ||
+      !target || !grad || !loss || !workspace || !(lambda >= 0.f && lambda <= 1.f))
+    return VEG_ERR_INVALID_ARGUMENT;
+  if (!aligned16(out) || !aligned16(target) || !aligned16(grad) ||
+      (reinterpret_cast<uintptr_t>(loss) & 3) || (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return VEG_ERR_INVALID_ARGUMENT;
+  const int tx = tiles_x_of(width), ty = tiles_x_of(height);
+  if (n_images > 65535 || workspace_bytes < loss_ws_bytes(n_images, height, width))
+    return VEG_ERR_INVALID_ARGUMENT;
+  Window win;
+  double wsum = 0.0, wd[2 * kR + 1];
+  for (int k = -kR; k <= kR; ++k) wsum += (wd[k + kR] = std::exp(-(double)k * k / (2.0 * 1.5 * 1.5)));
+  for (int k = 0; k <= 2 * kR; ++k) win.w[k] = (float)(wd[k] / wsum);
+  const double count = (double)n_images * height * width * 3.0;
+  const size_t smem = sizeof(LossSmem);
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(l1_ssim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return VEG_ERR_UNSUPPORTED;
+    configured = true;
+  }
+  double2* part = reinterpret_cast<double2*>(workspace);
+  l1_ssim_kernel<<<dim3((unsigned)(tx * ty), (unsigned)n_images), 256, smem, stream>>>(
+      win, reinterpret_cast<const float4*>(out), reinterpret_cast<const float4*>(target), height,
+      width, tx, lambda, (float)(1.0 / count), reinterpret_cast<float4*>(grad), part);
+  count_launch();
+  l1_ssim_final_kernel<<<1, 1024, 0, stream>>>(part, (int64_t)tx * ty * n_images, 1.0 / count,
+                                               lambda, loss);
+  count_launch();
+  return launch_status();
+}
+
+extern "C" veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, const float* lr,
+                                    float beta1, float beta2, float eps, int32_t step,
+                                    cudaStream_t stream) {
+  if (!arrays || !lr || n < 0 || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
+    return VEG_ERR_INVALID_ARGUMENT;
+  AdamArgs A;
+  for (int a = 0; a < 5; ++a) {
+    A.param[a] = reinterpret_cast<float4*>(arrays->param[a]);
+    A.grad[a] = reinterpret_cast<const float4*>(arrays->grad[a]);
+    A.m[a] = reinterpret_cast<float4*>(arrays->exp_avg[a]);
+    A.v[a] = reinterpret_cast<float4*>(arrays->exp_avg_sq[a]);
+    if (A.param[a] && n > 0 && (!A.grad[a] || !A.m[a] || !A.v[a])) return VEG_ERR_INVALID_ARGUMENT;
+    if (!aligned16(A.param[a]) || !aligned16(A.grad[a]) || !aligned16(A.m[a]) ||
+        !aligned16(A.v[a]))
+      return VEG_ERR_INVALID_ARGUMENT;
+    for (int c = 0; c < 4; ++c) A.lr[a][c] = lr[a * 4 + c];
+  }
+  for (int a = 0; a < 2; ++a) {
+    A.rendered[a] = reinterpret_cast<float4*>(arrays->rendered[a]);
+    if (!aligned16(A.rendered[a])) return VEG_ERR_INVALID_ARGUMENT;
+  }
+  A.b1 = beta1;
+  A.b2 = beta2;
+  A.eps = eps;
+  A.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)step)));
+  A.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)beta2, (double)step)));
+  if (n == 0) return VEG_OK;
+  adam_kernel<<<dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream>>>(A, n);
+  count_launch();
+  return launch_status();
+}

@@ -72,6 +72,15 @@ class SplatPipeline:
         self.grad_shade = None
         self.set_capacity(capacity if capacity is not None else max(1 << 16, 8 * nrec))
 
+    def set_cameras(self, cams, c_cams=None):
+        """Switch to other cameras of the same count and image size (c_cams:
+        their prebuilt C structs, optional)."""
+        cams = list(cams)
+        if len(cams) != self.V or cams[0].width != self.W or cams[0].height != self.H:
+            raise ValueError("set_cameras needs the same number of views and image size")
+        self.cams = cams
+        self.c_cams = c_cams if c_cams is not None else _lib.cameras(cams)
+
     def set_capacity(self, capacity):
         self.capacity = int(capacity)
         ws = _lib.veg_bin_sort_workspace_size(self.n, self.V, self.capacity, self.W, self.H)

@@ -85,6 +85,15 @@ def orbit_cameras(n, seed, width, height, radius=3.0, el_max_deg=30.0) -> list[C
     return [orbit_camera(a, e, radius, width, height) for a, e in zip(az, el)]
 
 
+def grid_orbit_cameras(n_az, n_el, width, height, radius=3.0, el_max_deg=60.0) -> list[Camera]:
+    """A training orbit like the paper's (Sec. 5.1: 16 azimuths x 10
+    elevations): azimuths k 360/n_az, elevations evenly spaced in
+    [-el_max, el_max]."""
+    els = np.linspace(-el_max_deg, el_max_deg, n_el) if n_el > 1 else np.zeros(1)
+    return [orbit_camera(360.0 * a / n_az, float(e), radius, width, height)
+            for e in els for a in range(n_az)]
+
+
 def camera_array(cams) -> np.ndarray:
     """Pack cameras as float32 rows of 16: w2c(12), fx, fy, cx, cy."""
     rows = []
@@ -155,6 +164,32 @@ class BlobField:
                 acc += self.amp[k] * np.exp(-0.5 * q)
             out[s:s + chunk] = acc
         return out
+
+
+def field_gradient(bf, pts, chunk=1 << 20) -> np.ndarray:
+    """Gradient of the blob field at `pts` (N, 3), float64:
+    sum_k -a_k exp(-q_k/2) S_k^-1 (x - m_k) with S_k^-1 = R_k diag(1/sigma^2) R_k^T."""
+    pts = np.asarray(pts, np.float64)
+    out = np.zeros_like(pts)
+    for s in range(0, pts.shape[0], chunk):
+        p = pts[s:s + chunk]
+        acc = np.zeros_like(p)
+        for k in range(bf.amp.shape[0]):
+            d = (p - bf.center[k]) @ bf.rot[k]
+            e = bf.amp[k] * np.exp(-0.5 * ((d / bf.sigma[k]) ** 2).sum(1))
+            acc -= e[:, None] * ((d / bf.sigma[k] ** 2) @ bf.rot[k].T)
+        out[s:s + chunk] = acc
+    return out
+
+
+def gradient_lighting(g: "Gaussians", bf, ka=0.3, kd=0.7, ks=0.2, beta=20.0) -> "Lighting":
+    """Lighting whose normals follow the field (the negated, normalised
+    gradient at each mean, as a volume renderer shades by the gradient)."""
+    gr = field_gradient(bf, g.mean_v[:, :3])
+    nrm = -gr / np.maximum(np.linalg.norm(gr, axis=1, keepdims=True), 1e-12)
+    nb = np.concatenate([nrm, np.full((g.n, 1), beta)], 1).astype(np.float32)
+    k = np.tile(np.array([ka, kd, ks, 0.0], np.float32), (g.n, 1))
+    return Lighting(nb, k)
 
 
 def blob_field(n_blobs, seed) -> BlobField:
@@ -230,6 +265,17 @@ def bump_tf(seed, n_bumps=3, peak=0.8, size=LUT_SIZE) -> np.ndarray:
     return np.concatenate([rgb, op[:, None]], 1).astype(np.float32)
 
 
+def colour_ramp(seed, size=LUT_SIZE) -> np.ndarray:
+    """(size, 3) colours piecewise linear through four random colours at
+    x = 0, 1/3, 2/3, 1 (a sequential stand-in for the colormap of the
+    paper's training renders; no named colormap table is used)."""
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.uniform(0.0, 1.0, (4, 3)), axis=0)  # monotone: not diverging
+    x = np.arange(size) / (size - 1)
+    knots = np.linspace(0.0, 1.0, 4)
+    return np.stack([np.interp(x, knots, cols[:, c]) for c in range(3)], 1).astype(np.float32)
+
+
 def bump_tfs(n, seed, **kw) -> np.ndarray:
     return np.stack([bump_tf(seed * 1000 + i, **kw) for i in range(n)])
 
@@ -279,6 +325,33 @@ def plain_scene(seed=1):
     cam = look_at_camera((0.0, 0.0, 3.0), 128, 128)
     tf = bump_tf(seed + 100)[None]
     return g, [cam], tf
+
+
+def initial_model(n, bf: "BlobField", seed, weight=0.1, lighting=True):
+    """A model to train (Sec. 4.1): `n` points drawn at random from the
+    volume (uniform in the cube, as data points of a regular grid would be),
+    each a Gaussian with the field's value there, log-scales from the mean
+    spacing (reading R14), identity rotations, weight `weight`; with
+    `lighting`, random unit normals, k_a 0.3, k_d 0.6, k_s 0.2, shininess 10.
+    Returns (Gaussians, Lighting or None)."""
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(-1.0, 1.0, (n, 3))
+    f = bf.value(pts)
+    v = np.clip(f / f.max(), 0.0, 1.0)
+    mu_ls = math.log(0.5 * 2.0 / n ** (1.0 / 3.0))
+    ls = np.full((n, 3), mu_ls)
+    q = np.tile(np.array([1.0, 0.0, 0.0, 0.0]), (n, 1))
+    g = Gaussians(np.concatenate([pts, v[:, None]], 1).astype(np.float32),
+                  np.concatenate([ls, np.full((n, 1), weight)], 1).astype(np.float32),
+                  q.astype(np.float32))
+    lt = None
+    if lighting:
+        nrm = rng.standard_normal((n, 3))
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        nb = np.concatenate([nrm, np.full((n, 1), 10.0)], 1).astype(np.float32)
+        k = np.tile(np.array([0.3, 0.6, 0.2, 0.0], np.float32), (n, 1))
+        lt = Lighting(nb, k)
+    return g, lt
 
 
 def train_scene(n=1_000_000, n_blobs=8, width=1024, n_tf=4, seed=2):

@@ -1,0 +1,159 @@
+"""Opacity-guided training of VEG models (Sec. 4.2) on the GPU.
+
+Every iteration picks a random (camera, opacity map) pair of the training
+set, renders the model for it (projection, Blinn-Phong shading with the
+camera's headlight, binning, compositing), evaluates (1 - lambda) L1 +
+lambda (1 - SSIM) against the matching target image, runs the backward pass
+through compositing, shading and projection, and takes one Adam step on the
+raw parameters, which also writes the activated values for the next render.
+All of it runs in libveg.so; PyTorch holds the buffers.
+
+The opacity maps divide the scalar range into K steps, one map centred in
+each step with linear fall-off of slope K (reading R13: the colour is shared,
+the maps tabulated like every transfer function).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from .render import SplatPipeline, headlight_dirs
+
+LAMBDA_SSIM = 0.2
+
+
+def opacity_guided_luts(K, rgb, slope=None) -> np.ndarray:
+    """K RGBA tables [K][L][4]: colour `rgb` (L, 3); map k's opacity
+    max(0, 1 - slope |x - (k + 1/2)/K|) at x_j = j/(L-1), slope K by default."""
+    rgb = np.asarray(rgb, np.float32)
+    L = rgb.shape[0]
+    s = float(K) if slope is None else float(slope)
+    x = np.arange(L, dtype=np.float64) / (L - 1)
+    luts = np.empty((K, L, 4), np.float32)
+    for k in range(K):
+        centre = (k + 0.5) / K
+        luts[k, :, :3] = rgb
+        luts[k, :, 3] = np.clip(1.0 - s * np.abs(x - centre), 0.0, None)
+    return luts
+
+
+def default_lr(extent=1.0, lighting=True) -> np.ndarray:
+    """Learning rates [5][4] per packed array and component: the paper's
+    0.00025 (scalar) and 0.025 (weight) and, following the 3D Gaussian
+    splatting defaults it adopts, 1.6e-4 x scene extent (mean), 0.005
+    (log-scale), 0.001 (rotation); 0.001 for normals, shininess and the
+    lighting coefficients (our choice: the paper does not give them)."""
+    lr = np.zeros((5, 4))
+    lr[0] = [1.6e-4 * extent] * 3 + [2.5e-4]
+    lr[1] = [5e-3] * 3 + [2.5e-2]
+    lr[2] = [1e-3] * 4
+    if lighting:
+        lr[3] = [1e-3] * 4
+        lr[4] = [1e-3] * 3 + [0.0]
+    return lr
+
+
+def _logit(p):
+    p = np.clip(np.asarray(p, np.float64), 1e-4, 1.0 - 1e-4)
+    return np.log(p) - np.log1p(-p)
+
+
+class TrainParams:
+    """Raw parameters, gradients, Adam moments and the rendered arrays of a
+    model with n Gaussians, all device-resident."""
+
+    def __init__(self, g, lighting=None, device="cuda"):
+        dev = torch.device(device)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
+        mv = np.array(g.mean_v, np.float64)
+        lw = np.array(g.logscale_w, np.float64)
+        mv[:, 3] = _logit(mv[:, 3])
+        lw[:, 3] = _logit(lw[:, 3])
+        self.n = g.n
+        self.lit = lighting is not None
+        self.raw = [t(mv), t(lw), t(g.quat),
+                    t(lighting.normal_beta) if self.lit else None,
+                    t(lighting.k_ads) if self.lit else None]
+        # rendered arrays: (mu, sigmoid(v_raw)), (log-scale, sigmoid(w_raw)); the
+        # quaternion and the lighting arrays are rendered as stored
+        self.mean_v = t(g.mean_v)
+        self.logscale_w = t(g.logscale_w)
+        self.grads = [None if r is None else torch.zeros_like(r) for r in self.raw]
+        self.m = [None if r is None else torch.zeros_like(r) for r in self.raw]
+        self.v = [None if r is None else torch.zeros_like(r) for r in self.raw]
+        self.step = 0
+        self._arrays = _lib.adam_arrays(self.raw, self.grads, self.m, self.v,
+                                        (self.mean_v, self.logscale_w))
+
+    def rendered(self):
+        return self.mean_v, self.logscale_w, self.raw[2]
+
+    def zero_grad(self):
+        for gb in self.grads:
+            if gb is not None:
+                gb.zero_()
+
+    def adam(self, lr, stream=None):
+        self.step += 1
+        _lib.veg_adam_step(self._arrays, self.n, lr, self.step, stream=stream)
+
+
+class OpacityGuidedTrainer:
+    """Random (view, opacity map) per iteration, L1 + SSIM loss, Adam.
+
+    cams: the training views (same size); luts: device tensor [K][L][4];
+    targets: device tensor [V][K][H][W][4] of ground-truth images.  With
+    lighting (params.lit) every view is shaded with its headlight."""
+
+    def __init__(self, params: TrainParams, cams, luts, targets, lr=None, lam=LAMBDA_SSIM,
+                 seed=0, capacity=None, bg=(0.0, 0.0, 0.0)):
+        self.P = params
+        self.cams = list(cams)
+        self.luts = luts
+        self.targets = targets
+        self.K = luts.shape[0]
+        self.lam = float(lam)
+        self.lr = default_lr(lighting=params.lit) if lr is None else np.asarray(lr)
+        self.rng = np.random.default_rng(seed)
+        self.bg = bg
+        self.lights = headlight_dirs(self.cams).astype(np.float32)
+        self.pipe = SplatPipeline(params.n, self.cams[:1], n_tf=1, capacity=capacity)
+        self.c_cams = [_lib.cameras([c]) for c in self.cams]
+        H, W = self.cams[0].height, self.cams[0].width
+        dev = self.pipe.device
+        self.loss = torch.zeros(3, device=dev)
+        self.loss_ws = torch.empty(_lib.veg_l1_ssim_loss_workspace_size(1, H, W),
+                                   dtype=torch.uint8, device=dev)
+
+    def render(self, view, k, stream=None):
+        p, P = self.pipe, self.P
+        p.set_cameras([self.cams[view]], self.c_cams[view])
+        lut = self.luts[k:k + 1]
+        p.project(*P.rendered(), lut, stream)
+        if P.lit:
+            p.shade(P.mean_v, P.raw[3], P.raw[4], self.lights[view:view + 1], stream)
+        p.bin_sort(stream=stream)
+        p.composite(lut, self.bg, stream=stream)
+        return p.out
+
+    def step(self, view=None, k=None, stream=None):
+        """One training iteration; returns (view, map) used."""
+        if view is None:
+            view = int(self.rng.integers(len(self.cams)))
+        if k is None:
+            k = int(self.rng.integers(self.K))
+        p, P = self.pipe, self.P
+        self.render(view, k, stream)
+        _lib.veg_l1_ssim_loss(p.out, self.targets[view, k], p.loss_grad, self.loss,
+                              self.loss_ws, self.lam, stream)
+        P.zero_grad()
+        p.backward(p.loss_grad, P.grads[0], P.grads[1], P.grads[2], P.grads[3], P.grads[4],
+                   stream=stream)
+        P.adam(self.lr, stream)
+        return view, k
+
+    def overflowed(self, stream=None):
+        """True if the last binning ran out of instance capacity (host sync)."""
+        st, _ = self.pipe.status(stream)
+        return st != _lib.VEG_OK

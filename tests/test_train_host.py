@@ -1,0 +1,46 @@
+"""Host-side parts of the training path (no GPU): the opacity-guided tables
+and the raw-parameter store's activations, against the oracle."""
+import numpy as np
+
+from oracle import veg_train_oracle as TO
+from paper_2504_13339_gb300 import scenes as S
+from paper_2504_13339_gb300.train import _logit, default_lr, opacity_guided_luts
+
+
+def test_opacity_guided_luts_match_oracle():
+    rgb = S.colour_ramp(73)
+    for K, slope in ((10, None), (5, 2.5), (20, 40.0), (1, None)):
+        ours = opacity_guided_luts(K, rgb, slope)
+        ref = TO.tent_luts(K, rgb, slope)
+        assert ours.dtype == np.float32 and ours.shape == ref.shape
+        assert np.abs(ours - ref).max() <= 1e-7
+
+
+def test_logit_inverts_the_oracle_sigmoid():
+    p = np.array([1e-3, 0.1, 0.5, 0.9, 0.999])
+    assert np.allclose(TO.sigmoid(_logit(p)), p, rtol=1e-12)
+    assert np.all(np.isfinite(_logit(np.array([0.0, 1.0]))))  # clamped
+
+
+def test_default_learning_rates_follow_the_paper():
+    lr = default_lr()
+    assert lr.shape == (5, 4)
+    assert lr[0, 3] == 2.5e-4 and lr[1, 3] == 2.5e-2  # scalar and weight (Sec. 5.1)
+    assert lr[4, 3] == 0.0  # the unused fourth slot of (k_a, k_d, k_s, -)
+    assert not default_lr(lighting=False)[3:].any()
+
+
+def test_training_views_follow_the_orbit_grid():
+    cams = S.grid_orbit_cameras(16, 10, 32, 32)
+    assert len(cams) == 160
+    eyes = np.stack([-c.world_to_cam[:, :3].T @ c.world_to_cam[:, 3] for c in cams])
+    assert np.allclose(np.linalg.norm(eyes, axis=1), 3.0, atol=1e-5)
+
+
+def test_field_gradient_matches_finite_differences():
+    bf = S.blob_field(8, 3)
+    p = np.random.default_rng(0).uniform(-1, 1, (7, 3))
+    g = S.field_gradient(bf, p)
+    h = 1e-6
+    fd = np.stack([(bf.value(p + h * e) - bf.value(p - h * e)) / (2 * h) for e in np.eye(3)], 1)
+    assert np.abs(g - fd).max() <= 1e-8 * max(1.0, np.abs(g).max())
