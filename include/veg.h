@@ -387,6 +387,57 @@ veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, const float* 
                          float beta2, float eps, int32_t step, cudaStream_t stream);
 
 /*
+ * veg_grad_stats_accumulate -- the densification statistic of Sec. 4.2
+ * (3D Gaussian splatting's "view-space positional gradient"): for every view
+ * v and Gaussian i with tiles_touched[v][i] > 0, adds |(g_x W/2, g_y H/2)| to
+ * accum[i] and 1 to count[i], where (g_x, g_y) = dL/du are the first two
+ * values of grad2d [V][n][8] as written by veg_composite_bwd (the screen-mean
+ * gradient in pixels, W/2 and H/2 converting it to normalised device units).
+ * Float32 with every product, sum and square root rounded separately, views
+ * in order, one thread per Gaussian: deterministic.  accum float[n], count
+ * int32[n], device, accumulated.
+ */
+veg_status veg_grad_stats_accumulate(const float* grad2d, const int32_t* tiles_touched,
+                                     int64_t n, int32_t n_views, int32_t width, int32_t height,
+                                     float* accum, int32_t* count, cudaStream_t stream);
+
+/*
+ * veg_densify -- one clone / split / prune pass (Sec. 4.2, following 3D
+ * Gaussian splatting).  Per Gaussian i, in float32 against the thresholds of
+ * cfg (prepared by the caller):
+ *   prune  if raw w < raw_weight_threshold  (the paper's w < 0.005 on the
+ *          sigmoid-activated weight);
+ *   else, if accum[i] / count[i] >= grad_threshold (0 when count is 0):
+ *     split if max(log-scale) > log_size_threshold (ln(0.01 x scene extent)),
+ *     clone otherwise;
+ *   else keep.
+ * Outputs, in input order, into `out` (arrays of capacity out_capacity >= 2n
+ * rows): keep -> the Gaussian with its Adam moments; clone -> the Gaussian
+ * with its moments, then a copy with zero moments; split -> two children
+ * mu + R(q) diag(exp(log-scale)) z_j (z = split_normals [n][2][3], standard
+ * normal samples supplied by the caller), log-scale - log_split_factor,
+ * every other value copied, zero moments; prune -> nothing.  `in` and `out`
+ * use param / exp_avg / exp_avg_sq of veg_adam_arrays (grad ignored; a NULL
+ * param array is skipped; arrays 0-2 required); out->rendered[0..1], if
+ * given, receive the activated (mu, sigmoid(v)) and (log-scale, sigmoid(w)).
+ * *n_out (device int64) receives the output count; action (optional device
+ * int32[n]) the decision (0 prune, 1 keep, 2 clone, 3 split).  workspace >=
+ * veg_densify_workspace_size bytes, 256-byte aligned.  Three launches.
+ */
+typedef struct veg_density_config {
+  float grad_threshold;        /* 0.0002 */
+  float log_size_threshold;    /* ln(0.01 x scene extent) */
+  float raw_weight_threshold;  /* logit(0.005) */
+  float log_split_factor;      /* ln(1.6) */
+} veg_density_config;
+veg_status veg_densify_workspace_size(int64_t n, size_t* bytes);
+veg_status veg_densify(const veg_adam_arrays* in, int64_t n, const float* accum,
+                       const int32_t* count, const float* split_normals, veg_density_config cfg,
+                       const veg_adam_arrays* out, int64_t out_capacity, int64_t* n_out,
+                       int32_t* action, void* workspace, size_t workspace_bytes,
+                       cudaStream_t stream);
+
+/*
  * veg_render -- convenience forward: veg_project (with the TF cull), then
  * veg_bin_sort, then veg_composite_fwd, all scratch in `workspace`
  * (>= veg_render_workspace_size bytes).  Same outputs as

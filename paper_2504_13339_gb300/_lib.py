@@ -51,6 +51,11 @@ class veg_adam_arrays(ctypes.Structure):
                 ("rendered", ctypes.c_void_p * 2)]
 
 
+class veg_density_config(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("log_size_threshold", ctypes.c_float),
+                ("raw_weight_threshold", ctypes.c_float), ("log_split_factor", ctypes.c_float)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _CAMS = ctypes.POINTER(veg_camera)
@@ -85,6 +90,11 @@ _SIGS = {
                                         _P]),
     "veg_adam_step": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, _I32, _P]),
+    "veg_grad_stats_accumulate": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P]),
+    "veg_densify_workspace_size": (ctypes.c_int, [_I64, ctypes.POINTER(_SZ)]),
+    "veg_densify": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, _P, _P,
+                                   veg_density_config, ctypes.POINTER(veg_adam_arrays), _I64, _P,
+                                   _P, _P, _SZ, _P]),
     "veg_shade_bwd": (ctypes.c_int, [_CAMS, _I32, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
@@ -300,6 +310,28 @@ def veg_adam_step(arrays, n, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream
     _check("veg_adam_step",
            load().veg_adam_step(ctypes.byref(arrays), n, ctypes.cast(lrs, ctypes.c_void_p),
                                 beta1, beta2, eps, step, _stream(stream)))
+
+
+def veg_grad_stats_accumulate(grad2d, tiles_touched, n, n_views, width, height, accum, count,
+                              stream=None):
+    _check("veg_grad_stats_accumulate",
+           load().veg_grad_stats_accumulate(_ptr(grad2d), _ptr(tiles_touched), n, n_views, width,
+                                            height, _ptr(accum), _ptr(count), _stream(stream)))
+
+
+def veg_densify_workspace_size(n) -> int:
+    out = _SZ()
+    _check("veg_densify_workspace_size", load().veg_densify_workspace_size(n, ctypes.byref(out)))
+    return out.value
+
+
+def veg_densify(in_arrays, n, accum, count, split_normals, cfg, out_arrays, out_capacity, n_out,
+                action, workspace, stream=None):
+    _check("veg_densify",
+           load().veg_densify(ctypes.byref(in_arrays), n, _ptr(accum), _ptr(count),
+                              _ptr(split_normals), cfg, ctypes.byref(out_arrays), out_capacity,
+                              _ptr(n_out), _ptr(action), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,

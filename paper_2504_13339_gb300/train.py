@@ -14,6 +14,8 @@ the maps tabulated like every transfer function).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import torch
 
@@ -98,6 +100,88 @@ class TrainParams:
         self.step += 1
         _lib.veg_adam_step(self._arrays, self.n, lr, self.step, stream=stream)
 
+    def replace(self, n, raw, m, v, mean_v, logscale_w):
+        """Adopts new arrays of n rows (after densification); gradients
+        restart at zero."""
+        self.n = int(n)
+        self.raw, self.m, self.v = raw, m, v
+        self.mean_v, self.logscale_w = mean_v, logscale_w
+        self.grads = [None if r is None else torch.zeros_like(r) for r in raw]
+        self._arrays = _lib.adam_arrays(self.raw, self.grads, self.m, self.v,
+                                        (self.mean_v, self.logscale_w))
+
+
+def scene_extent(cams) -> float:
+    """1.1 x the largest distance of a camera centre from the centres'
+    centroid (the extent used by the densification size rule)."""
+    c = np.stack([-np.asarray(k.world_to_cam, np.float64)[:, :3].T
+                  @ np.asarray(k.world_to_cam, np.float64)[:, 3] for k in cams])
+    return 1.1 * float(np.linalg.norm(c - c.mean(0), axis=1).max())
+
+
+class DensityControl:
+    """Adaptive density control (Sec. 4.2, after 3D Gaussian splatting):
+    the positional-gradient statistic is accumulated after every backward
+    pass from `start` to `stop`; every `every` iterations in that window
+    Gaussians are cloned, split or pruned (veg_densify)."""
+
+    def __init__(self, extent, start=500, stop=20000, every=100, grad_threshold=2e-4,
+                 dense_fraction=0.01, prune_weight=0.005, split_factor=1.6, seed=0,
+                 device="cuda"):
+        self.start, self.stop, self.every = int(start), int(stop), int(every)
+        self.cfg = _lib.veg_density_config(
+            grad_threshold, math.log(dense_fraction * extent),
+            math.log(prune_weight) - math.log1p(-prune_weight), math.log(split_factor))
+        self.device = torch.device(device)
+        self.gen = torch.Generator(device=self.device)
+        self.gen.manual_seed(seed)
+        self.accum = self.count = None
+        self.n_out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.history = []
+
+    def reset(self, n):
+        self.accum = torch.zeros(n, device=self.device)
+        self.count = torch.zeros(n, dtype=torch.int32, device=self.device)
+
+    def active(self, it):
+        return self.start <= it <= self.stop
+
+    def due(self, it):
+        return self.active(it) and it > self.start and it % self.every == 0
+
+    def accumulate(self, pipe, P, stream=None):
+        if self.accum is None or self.accum.numel() != P.n:
+            self.reset(P.n)
+        _lib.veg_grad_stats_accumulate(pipe.grad2d, pipe.tiles, P.n, pipe.V, pipe.W, pipe.H,
+                                       self.accum, self.count, stream)
+
+    def apply(self, P, stream=None):
+        """Clone / split / prune; replaces P's arrays (one host sync to read
+        the new count).  Returns the new number of Gaussians."""
+        n, cap = P.n, 2 * P.n
+        if self.accum is None or self.accum.numel() != n:
+            self.reset(n)
+        new = lambda r: None if r is None else torch.empty(cap, 4, device=self.device)
+        raw = [new(r) for r in P.raw]
+        m = [new(r) for r in P.raw]
+        v = [new(r) for r in P.raw]
+        mean_v = torch.empty(cap, 4, device=self.device)
+        logscale_w = torch.empty(cap, 4, device=self.device)
+        z = torch.randn(n, 2, 3, generator=self.gen, device=self.device)
+        ws = torch.empty(max(_lib.veg_densify_workspace_size(n), 1), dtype=torch.uint8,
+                         device=self.device)
+        src = _lib.adam_arrays(P.raw, P.grads, P.m, P.v)
+        dst = _lib.adam_arrays(raw, [None] * 5, m, v, (mean_v, logscale_w))
+        _lib.veg_densify(src, n, self.accum, self.count, z, self.cfg, dst, cap, self.n_out,
+                         None, ws, stream)
+        n_new = int(self.n_out.item())
+        cut = lambda t: None if t is None else t[:n_new]
+        P.replace(n_new, [cut(t) for t in raw], [cut(t) for t in m], [cut(t) for t in v],
+                  mean_v[:n_new], logscale_w[:n_new])
+        self.reset(n_new)
+        self.history.append((n, n_new))
+        return n_new
+
 
 class OpacityGuidedTrainer:
     """Random (view, opacity map) per iteration, L1 + SSIM loss, Adam.
@@ -107,8 +191,11 @@ class OpacityGuidedTrainer:
     lighting (params.lit) every view is shaded with its headlight."""
 
     def __init__(self, params: TrainParams, cams, luts, targets, lr=None, lam=LAMBDA_SSIM,
-                 seed=0, capacity=None, bg=(0.0, 0.0, 0.0)):
+                 seed=0, capacity=None, bg=(0.0, 0.0, 0.0), density: DensityControl = None):
         self.P = params
+        self.density = density
+        self.it = 0
+        self.capacity = capacity
         self.cams = list(cams)
         self.luts = luts
         self.targets = targets
@@ -138,19 +225,28 @@ class OpacityGuidedTrainer:
         return p.out
 
     def step(self, view=None, k=None, stream=None):
-        """One training iteration; returns (view, map) used."""
+        """One training iteration; returns (view, map) used.  With density
+        control, an iteration that densifies replaces the parameter arrays
+        instead of taking the Adam step."""
         if view is None:
             view = int(self.rng.integers(len(self.cams)))
         if k is None:
             k = int(self.rng.integers(self.K))
-        p, P = self.pipe, self.P
+        self.it += 1
+        p, P, D = self.pipe, self.P, self.density
         self.render(view, k, stream)
         _lib.veg_l1_ssim_loss(p.out, self.targets[view, k], p.loss_grad, self.loss,
                               self.loss_ws, self.lam, stream)
         P.zero_grad()
         p.backward(p.loss_grad, P.grads[0], P.grads[1], P.grads[2], P.grads[3], P.grads[4],
                    stream=stream)
-        P.adam(self.lr, stream)
+        if D is not None and D.active(self.it):
+            D.accumulate(p, P, stream)
+        if D is not None and D.due(self.it):
+            D.apply(P, stream)
+            self.pipe = SplatPipeline(P.n, self.cams[:1], n_tf=1, capacity=self.capacity)
+        else:
+            P.adam(self.lr, stream)
         return view, k
 
     def overflowed(self, stream=None):

@@ -1,0 +1,155 @@
+"""Adaptive density control on the GPU vs the oracle (Sec. 4.2).
+
+Bars: the statistic, every decision, the output count and every copied
+value bit-exact (float32 decisions taken with the same rounded operations on
+both sides); split children's means within float32 rounding of the oracle's
+float64 (1e-6 of the scale), their log-scales bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import veg_density_oracle as D
+from paper_2504_13339_gb300 import _lib, scenes as S
+from paper_2504_13339_gb300.render import lut_tensor
+from paper_2504_13339_gb300.train import (DensityControl, OpacityGuidedTrainer, TrainParams,
+                                          opacity_guided_luts, scene_extent)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev(a, dtype=np.float32):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype), device="cuda")
+
+
+def test_statistic_bit_exact():
+    rng = np.random.default_rng(80)
+    V, n, W, H = 3, 5003, 800, 600
+    acc, cnt = np.zeros(n, np.float32), np.zeros(n, np.int32)
+    ga, gc = dev(acc), dev(cnt, np.int32)
+    for it in range(3):
+        g2 = rng.normal(0, 1e-4, (V, n, 8)).astype(np.float32)
+        tiles = rng.integers(0, 3, (V, n)).astype(np.int32)
+        D.grad_stat_update(acc, cnt, g2[..., :2], tiles, W, H)
+        _lib.veg_grad_stats_accumulate(dev(g2), dev(tiles, np.int32), n, V, W, H, ga, gc)
+    torch.cuda.synchronize()
+    assert np.array_equal(gc.cpu().numpy(), cnt)
+    assert np.array_equal(ga.cpu().numpy(), acc)
+
+
+def model(n, rng, lighting=True):
+    mv = np.concatenate([rng.uniform(-1, 1, (n, 3)), rng.normal(0, 2, (n, 1))], 1)
+    lw = np.concatenate([rng.normal(-4.0, 0.6, (n, 3)), rng.normal(-1, 2.5, (n, 1))], 1)
+    q = rng.standard_normal((n, 4))
+    p = [mv, lw, q, rng.normal(0, 1, (n, 4)) if lighting else None,
+         rng.uniform(0, 1, (n, 4)) if lighting else None]
+    return [None if a is None else a.astype(np.float32) for a in p]
+
+
+def run_densify(p, m, v, acc, cnt, z, th):
+    n = p[0].shape[0]
+    cfg = _lib.veg_density_config(float(th["grad"]), float(th["log_size"]),
+                                  float(th["raw_weight"]), float(th["log_split"]))
+    tin = [None if a is None else dev(a) for a in p]
+    tm = [None if a is None else dev(a) for a in m]
+    tv = [None if a is None else dev(a) for a in v]
+    cap = max(2 * n, 1)
+    out = [None if a is None else torch.full((cap, 4), np.nan, device="cuda") for a in p]
+    om = [None if a is None else torch.full((cap, 4), np.nan, device="cuda") for a in p]
+    ov = [None if a is None else torch.full((cap, 4), np.nan, device="cuda") for a in p]
+    rend = [torch.full((cap, 4), np.nan, device="cuda") for _ in range(2)]
+    n_out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    act = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(max(_lib.veg_densify_workspace_size(n), 1), dtype=torch.uint8, device="cuda")
+    src = _lib.adam_arrays(tin, [None] * 5, tm, tv)
+    dst = _lib.adam_arrays(out, [None] * 5, om, ov, rend)
+    _lib.veg_densify(src, n, dev(acc), dev(cnt, np.int32), dev(z), cfg, dst, cap, n_out, act, ws)
+    torch.cuda.synchronize()
+    k = int(n_out.item())
+    cpu = lambda ts: [None if t is None else t[:k].cpu().numpy() for t in ts]
+    return k, cpu(out), cpu(om), cpu(ov), cpu(rend), act[:n].cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 20011, 3_000_000])
+def test_densify_matches_oracle(n):
+    rng = np.random.default_rng(81 + n % 97)
+    th = D.thresholds(3.3)
+    p = model(n, rng, lighting=n < 100000)
+    m = [None if a is None else rng.normal(0, 1, a.shape).astype(np.float32) for a in p]
+    v = [None if a is None else rng.uniform(0, 1, a.shape).astype(np.float32) for a in p]
+    cnt = rng.integers(0, 5, n).astype(np.int32)
+    acc = (rng.exponential(2e-4, n) * cnt).astype(np.float32)
+    acc[: n // 50] = np.float32(th["grad"]) * cnt[: n // 50]  # exact-threshold averages
+    z = rng.standard_normal((n, 2, 3)).astype(np.float32)
+    k, out, om, ov, rend, act = run_densify(p, m, v, acc, cnt, z, th)
+    ref_act = D.classify(p[1], acc, cnt, th)
+    assert np.array_equal(act, ref_act)
+    outs = np.array([0, 1, 2, 2])[ref_act]
+    assert k == int(outs.sum())
+    if n == 0:
+        return
+    for kind in (D.PRUNE, D.KEEP, D.CLONE, D.SPLIT):
+        if n > 1000:
+            assert (ref_act == kind).sum() > 0, kind  # every branch exercised
+    if n <= 20011:
+        rp, rm, rv, _ = D.densify(p, m, v, acc, cnt, z.astype(np.float64), th)
+        split_rows = np.repeat(ref_act == D.SPLIT, outs)
+        for a in range(5):
+            if p[a] is None:
+                continue
+            same = ~split_rows if a in (0, 1) else np.ones(k, bool)
+            assert np.array_equal(out[a][same], rp[a][same].astype(np.float32)), a
+            assert np.array_equal(om[a], rm[a].astype(np.float32)), a
+            assert np.array_equal(ov[a], rv[a].astype(np.float32)), a
+        scale = np.exp(np.repeat(p[1][:, :3], outs, 0)[split_rows]).max(1, keepdims=True)
+        err = np.abs(out[0][split_rows, :3] - rp[0][split_rows, :3])
+        assert np.all(err <= 1e-6 * (1 + np.abs(rp[0][split_rows, :3])) + 1e-5 * scale)
+        assert np.array_equal(out[0][split_rows, 3], rp[0][split_rows, 3].astype(np.float32))
+        assert np.array_equal(out[1][split_rows], rp[1][split_rows].astype(np.float32))
+        sig = lambda x: 1.0 / (1.0 + np.exp(-x.astype(np.float64)))
+        assert np.allclose(rend[0][:, :3], out[0][:, :3]) and np.allclose(rend[1][:, :3], out[1][:, :3])
+        assert np.allclose(rend[0][:, 3], sig(out[0][:, 3]), rtol=1e-6, atol=1e-7)
+        assert np.allclose(rend[1][:, 3], sig(out[1][:, 3]), rtol=1e-6, atol=1e-7)
+    else:
+        # 3M Gaussians (several scan chunks): every output row sampled against
+        # its source row through the oracle's output counts
+        first = np.concatenate([[0], np.cumsum(outs)[:-1]])
+        idx = rng.choice(np.nonzero(ref_act == D.KEEP)[0], 2000)
+        assert np.array_equal(out[2][first[idx]], p[2][idx])
+        assert np.array_equal(om[0][first[idx]], m[0][idx])
+        idx = rng.choice(np.nonzero(ref_act == D.CLONE)[0], 2000)
+        assert np.array_equal(out[0][first[idx] + 1], p[0][idx])
+        assert not om[0][first[idx] + 1].any()
+
+
+def test_training_with_density_control():
+    """A short run with densification every 40 iterations: the count
+    changes, the loss stays finite and decreases, and the trainer renders
+    the densified model."""
+    bf = S.blob_field(5, 90)
+    gt, _ = S.field_gaussians(6000, 5, 90)
+    cams = S.grid_orbit_cameras(8, 2, 64, 64, el_max_deg=30.0)
+    luts = lut_tensor(opacity_guided_luts(4, S.colour_ramp(91)))
+    from paper_2504_13339_gb300.render import SplatPipeline
+    p = SplatPipeline(gt.n, cams, n_tf=4)
+    p.render(dev(gt.mean_v), dev(gt.logscale_w), dev(gt.quat), luts)
+    targets = p.out.clone()
+    g0, lt0 = S.initial_model(1500, bf, 92, weight=0.3, lighting=True)
+    P = TrainParams(g0, lt0)
+    dc = DensityControl(scene_extent(cams), start=40, stop=400, every=40, seed=93)
+    T = OpacityGuidedTrainer(P, cams, luts, targets, seed=94, density=dc)
+    losses = []
+    for _ in range(400):
+        T.step()
+        losses.append(float(T.loss[0]))
+    assert len(dc.history) == 9
+    assert any(b != a for a, b in dc.history)
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-40:]) < 0.8 * np.mean(losses[:40])
+    assert not T.overflowed()
