@@ -1,0 +1,153 @@
+"""Pins of the raymarching oracle (no GPU).
+
+Trilinear interpolation against linear fields (exact) and scipy's
+map_coordinates; box clipping against hand-computed intervals; the
+emission-absorption transmittance and colour of a constant medium in closed
+form; the early stop; Blinn-Phong shading of a linear field in closed form;
+empty volumes; multi-table consistency.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import ndimage as ndi
+
+from oracle import veg_raymarch_oracle as RM
+from paper_2504_13339_gb300 import scenes as S
+
+
+def grid(R):
+    return np.linspace(-1.0, 1.0, R)
+
+
+def linear_volume(R, a, b, c, e):
+    x = grid(R)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    return a * X + b * Y + c * Z + e
+
+
+def test_trilinear_exact_on_linear_fields_and_matches_scipy():
+    rng = np.random.default_rng(0)
+    R = 9
+    a, b, c, e = 0.3, -0.7, 0.2, 0.5
+    vol = linear_volume(R, a, b, c, e)
+    for p in rng.uniform(-1, 1, (50, 3)):
+        v, g = RM.trilinear(vol, p)
+        assert v == pytest.approx(a * p[0] + b * p[1] + c * p[2] + e, abs=1e-12)
+        assert np.allclose(g, [a, b, c], atol=1e-12)
+    rnd = rng.uniform(0, 1, (R, R, R))
+    h = 2.0 / (R - 1)
+    pts = rng.uniform(-1, 1, (200, 3))
+    coords = ((pts + 1.0) / h)[:, ::-1].T  # (z, y, x) index coordinates
+    ref = ndi.map_coordinates(rnd, coords, order=1)
+    got = np.array([RM.trilinear(rnd, p)[0] for p in pts])
+    assert np.allclose(got, ref, atol=1e-12)
+
+
+def test_box_clipping():
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
+    eye, d = RM.camera_ray(cam, 16, 16)  # the centre pixel looks at the origin
+    assert np.allclose(d, [0, 0, -1])
+    assert np.allclose(RM.clip_box(eye, d, cam.near), (2.0, 4.0))
+    assert RM.clip_box(eye, -d, cam.near) is None
+    # a ray passing beside the box misses it
+    assert RM.clip_box(np.array([0.0, 1.5, 3.0]), np.array([0.0, 0.0, -1.0]), 0.2) is None
+
+
+def test_constant_medium_closed_form():
+    """v = 0.5 everywhere, a constant table (rgb, A), no shading: n equal
+    samples of alpha = 1 - (1-A)^(Delta/h), so T = (1-alpha)^n and
+    C = rgb (1 - T) + T bg."""
+    R = 17
+    vol = np.full((R, R, R), 0.5)
+    lut = S.constant_tf([0.9, 0.4, 0.1, 0.05]).astype(np.float64)[None]
+    rgb, A = lut[0, 0, :3], lut[0, 0, 3]  # the table's float32 values
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
+    h = 2.0 / (R - 1)
+    step = h / 2
+    bg = (0.2, 0.3, 0.4)
+    out, flag = RM.march_pixel(cam, vol, lut, 16, 16, step, None, bg)
+    n = math.floor(2.0 / step)
+    alpha = 1.0 - (1.0 - A) ** (step / h)
+    T = (1.0 - alpha) ** n
+    assert out[0, 3] == pytest.approx(T, rel=1e-12)
+    assert np.allclose(out[0, :3], rgb * (1 - T) + T * np.array(bg), rtol=1e-12)
+    # the step size does not change the medium: T -> (1 - A)^(L/h)
+    out2, _ = RM.march_pixel(cam, vol, lut, 16, 16, h / 8, None, bg)
+    assert out2[0, 3] == pytest.approx((1 - A) ** (2.0 / h), rel=1e-9)
+
+
+def test_early_stop_after_crossing():
+    R = 9
+    vol = np.full((R, R, R), 0.5)
+    lut = S.constant_tf([1.0, 1.0, 1.0, 0.85]).astype(np.float64)[None]
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
+    h = 2.0 / (R - 1)
+    out, _ = RM.march_pixel(cam, vol, lut, 16, 16, h / 2, None)
+    alpha = 1.0 - (1.0 - lut[0, 0, 3]) ** 0.5
+    k = 1
+    while (1 - alpha) ** k >= RM.T_STOP:  # samples until T falls below 1e-4
+        k += 1
+    assert k < 2.0 / (h / 2)  # stops inside the box
+    assert out[0, 3] == pytest.approx((1 - alpha) ** k, rel=1e-12)
+    assert out[0, 3] < RM.T_STOP <= out[0, 3] / (1 - alpha)
+
+
+def test_shading_of_a_linear_field_closed_form():
+    """v = 0.3 x + 0.5 has the gradient (0.3, 0, 0) everywhere: every sample
+    has the normal -x, so its colour is (k_a + k_d |n.l|) C + k_s |n.h|^beta."""
+    R = 17
+    vol = linear_volume(R, 0.3, 0.0, 0.0, 0.5)
+    lut = S.constant_tf([0.2, 0.6, 0.9, 0.02]).astype(np.float64)[None]
+    rgb = lut[0, 0, :3]
+    cam = S.orbit_camera(35.0, 20.0, 3.0, 41, 41)
+    mat = (0.3, 0.6, 0.25, 12.0)
+    i, j = 8, 29  # off the optical axis: the view and light directions differ
+    out, _ = RM.march_pixel(cam, vol, lut, i, j, 1.0 / 16, mat)
+    eye, d = RM.camera_ray(cam, i, j)
+    light = -np.asarray(cam.world_to_cam, np.float64)[2, :3]
+    n = np.array([-1.0, 0.0, 0.0])
+    hv = (-d + light) / np.linalg.norm(-d + light)
+    c = (mat[0] + mat[1] * abs(n @ light)) * rgb + mat[2] * abs(n @ hv) ** mat[3]
+    T = out[0, 3]
+    assert 0.05 < T < 0.95
+    assert np.allclose(out[0, :3], c * (1 - T), rtol=1e-12)
+
+
+def test_sample_positions_closed_form():
+    """v = 0.5 + 0.4 z seen along the z axis through a table that is exactly
+    linear (opacity 0.02 + 0.1 v, grey level v): sample k sits at
+    z_k = 1 - (k + 1/2) Delta, so every sample's alpha and colour is known
+    and the composite is a short explicit product."""
+    R = 17
+    vol = linear_volume(R, 0.0, 0.0, 0.4, 0.5)
+    x = np.arange(256) / 255
+    lut = np.stack([x, x, x, 0.02 + 0.1 * x], 1)[None]
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
+    h = 2.0 / (R - 1)
+    step = 0.1
+    out, _ = RM.march_pixel(cam, vol, lut, 16, 16, step, None)
+    C, T = 0.0, 1.0
+    for k in range(20):  # L = 2, 2 / 0.1 = 20 samples
+        v = 0.5 + 0.4 * (1.0 - (k + 0.5) * step)
+        a = 1.0 - (1.0 - (0.02 + 0.1 * v)) ** (step / h)
+        C += T * a * v
+        T *= 1.0 - a
+    assert out[0, 3] == pytest.approx(T, rel=1e-12)
+    assert out[0, 0] == pytest.approx(C, rel=1e-12)
+
+
+def test_empty_volume_and_multi_table_consistency():
+    R = 9
+    rng = np.random.default_rng(1)
+    vol = rng.uniform(0, 1, (R, R, R))
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 12, 10)
+    empty = S.constant_tf([1, 1, 1, 0]).astype(np.float64)[None]
+    out, _ = RM.render(cam, vol, empty, 0.1, bg=(0.1, 0.2, 0.3))
+    assert np.allclose(out[..., :3], [0.1, 0.2, 0.3]) and np.all(out[..., 3] == 1.0)
+    tfs = S.bump_tfs(2, 5).astype(np.float64)
+    mat = (0.3, 0.6, 0.2, 10.0)
+    both, _ = RM.render(cam, vol, tfs, 0.05, mat)
+    for t in range(2):
+        one, _ = RM.render(cam, vol, tfs[t:t + 1], 0.05, mat)
+        assert np.array_equal(both[t], one[0])
