@@ -16,8 +16,11 @@ Readings (the paper names the renderer, not its parameters; listed in the
 design notes):
   R24 volume: R^3 vertex values at x_i = -1 + 2 i/(R-1) on each axis, layout
       [z][y][x]; the value at a point of [-1,1]^3 is the trilinear
-      interpolation of its cell's eight vertices; the gradient is the exact
-      derivative of that interpolant inside the cell.
+      interpolation of its cell's eight vertices.  The gradient is, as volume
+      renderers precompute it, central differences at the vertices
+      ((v[i+1] - v[i-1]) / 2h; one-sided (v[1] - v[0]) / h and
+      (v[R-1] - v[R-2]) / h on the boundary faces) interpolated trilinearly
+      like the value, so it is continuous across cells.
   R25 rays: the camera model of the splatting path (pinhole, OpenCV axes,
       pixel (i, j) at the point (i, j)); direction d = normalised R^T
       ((i - cx)/fx, (j - cy)/fy, 1) from the camera centre; the ray is
@@ -34,6 +37,10 @@ design notes):
       c = (k_a + k_d |n.l|) C(v) + k_s |n.h|^beta (specular 0 where n.l = 0).
   R28 compositing: front to back, C += T alpha c, T *= 1 - alpha; the ray
       stops after the sample that brings T below 1e-4.  Output (C + T bg, T).
+  Flags (for float32 comparisons): a pixel is flagged when its sample count
+  floor((t1 - t0)/Delta) has a fraction within 1e-3 of an integer, when a
+  transmittance comes within a relative 1e-3 of 1e-4, or when a gradient norm
+  comes within a factor 10 of the shading cut 1e-6.
 """
 from __future__ import annotations
 
@@ -66,25 +73,44 @@ def clip_box(eye, d, near):
     return (t0, t1) if t1 > t0 else None
 
 
-def trilinear(vol, p):
-    """Value and gradient (d/dx, d/dy, d/dz) of the trilinear interpolant at
-    p in [-1,1]^3; vol[z][y][x]."""
+def vertex_gradients(vol):
+    """(R, R, R, 3) gradient (d/dx, d/dy, d/dz) at every vertex: central
+    differences inside, one-sided on the boundary faces (reading R24)."""
+    v = np.asarray(vol, np.float64)
+    R = v.shape[0]
+    h = 2.0 / (R - 1)
+    out = np.zeros(v.shape + (3,))
+    for comp, axis in ((0, 2), (1, 1), (2, 0)):  # x is the last array axis
+        d = np.zeros_like(v)
+        sl = lambda a, b: tuple(slice(a, b) if ax == axis else slice(None) for ax in range(3))
+        d[sl(1, R - 1)] = (v[sl(2, R)] - v[sl(0, R - 2)]) / (2 * h)
+        d[sl(0, 1)] = (v[sl(1, 2)] - v[sl(0, 1)]) / h
+        d[sl(R - 1, R)] = (v[sl(R - 1, R)] - v[sl(R - 2, R - 1)]) / h
+        out[..., comp] = d
+    return out
+
+
+def trilinear(vol, p, grads=None):
+    """Value and gradient (d/dx, d/dy, d/dz) at p in [-1,1]^3: trilinear
+    interpolation of the vertex values and of the vertex gradients
+    (vertex_gradients(vol) unless given); vol[z][y][x]."""
     R = vol.shape[0]
     h = 2.0 / (R - 1)
+    if grads is None:
+        grads = vertex_gradients(vol)
     g = (np.asarray(p, np.float64) + 1.0) / h  # grid coordinates (x, y, z)
     i = np.clip(np.floor(g).astype(int), 0, R - 2)
     f = g - i
     x0, y0, z0 = i
     c = vol[z0:z0 + 2, y0:y0 + 2, x0:x0 + 2].astype(np.float64)  # [z][y][x]
+    cg = grads[z0:z0 + 2, y0:y0 + 2, x0:x0 + 2]
     fx, fy, fz = f
     wx = np.array([1 - fx, fx])
     wy = np.array([1 - fy, fy])
     wz = np.array([1 - fz, fz])
     val = np.einsum("zyx,z,y,x->", c, wz, wy, wx)
-    dx = np.einsum("zyx,z,y,x->", c, wz, wy, np.array([-1.0, 1.0])) / h
-    dy = np.einsum("zyx,z,y,x->", c, wz, np.array([-1.0, 1.0]), wx) / h
-    dz = np.einsum("zyx,z,y,x->", c, np.array([-1.0, 1.0]), wy, wx) / h
-    return val, np.array([dx, dy, dz])
+    grad = np.einsum("zyxc,z,y,x->c", cg, wz, wy, wx)
+    return val, grad
 
 
 def tf_lookup(lut, v):
@@ -109,9 +135,13 @@ def march_pixel(cam, vol, luts, i, j, step, material=None, bg=(0.0, 0.0, 0.0)):
     live = np.ones(nT, bool)
     near_stop = np.zeros(nT, bool)
     seg = clip_box(eye, d, cam.near)
+    grads = vertex_gradients(vol) if material is not None else np.zeros(vol.shape + (3,))
     if seg is not None:
         t0, t1 = seg
         n = int(np.floor((t1 - t0) / step))
+        frac = (t1 - t0) / step - n
+        if frac < 1e-3 or frac > 1.0 - 1e-3:
+            near_stop[:] = True
         w2c = np.asarray(cam.world_to_cam, np.float64)
         light = -w2c[2, :3]
         e = -d
@@ -120,10 +150,12 @@ def march_pixel(cam, vol, luts, i, j, step, material=None, bg=(0.0, 0.0, 0.0)):
             if not live.any():
                 break
             p = eye + (t0 + (k + 0.5) * step) * d
-            v, g = trilinear(vol, p)
+            v, g = trilinear(vol, p, grads)
             shade = None
             if material is not None:
                 gn = np.linalg.norm(g)
+                if GRAD_EPS / 10 < gn < GRAD_EPS * 10:
+                    near_stop[live] = True
                 if gn > GRAD_EPS:
                     nrm = -g / gn
                     ka, kd, ks, beta = material

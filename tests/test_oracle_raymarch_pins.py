@@ -44,6 +44,26 @@ def test_trilinear_exact_on_linear_fields_and_matches_scipy():
     assert np.allclose(got, ref, atol=1e-12)
 
 
+def test_vertex_gradients_closed_forms():
+    """Central differences are exact for quadratics inside (2x for x^2);
+    the one-sided boundary difference of x^2 is x0 + x1."""
+    R = 11
+    x = grid(R)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    g = RM.vertex_gradients(X * X + 3 * Y - Z * Z * 0.5)
+    assert np.allclose(g[:, :, 1:-1, 0], 2 * X[:, :, 1:-1], atol=1e-12)
+    assert np.allclose(g[:, :, 0, 0], x[0] + x[1], atol=1e-12)
+    assert np.allclose(g[:, :, -1, 0], x[-1] + x[-2], atol=1e-12)
+    assert np.allclose(g[..., 1], 3.0, atol=1e-12)
+    assert np.allclose(g[1:-1, :, :, 2], -Z[1:-1], atol=1e-12)
+    # interpolated gradients are continuous across a cell face
+    vol = np.random.default_rng(2).uniform(0, 1, (R, R, R))
+    face = -1.0 + 2.0 * 4 / (R - 1)
+    a = RM.trilinear(vol, [face - 1e-9, 0.13, -0.4])[1]
+    b = RM.trilinear(vol, [face + 1e-9, 0.13, -0.4])[1]
+    assert np.allclose(a, b, atol=1e-6)
+
+
 def test_box_clipping():
     cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
     eye, d = RM.camera_ray(cam, 16, 16)  # the centre pixel looks at the origin
