@@ -32,22 +32,21 @@ design notes):
       convention of VTK's scalar opacity unit distance); colour C(v); both
       from the transfer function tables (reading R6's interpolation).
   R27 shading: Blinn-Phong with global k_a, k_d, k_s, beta, the normal
-      n = -grad/|grad| (no shading where |grad| <= 1e-6), l = headlight (the
-      camera's backward optical axis), e = -d, h = (e + l)/|e + l|:
-      c = (k_a + k_d |n.l|) C(v) + k_s |n.h|^beta (specular 0 where n.l = 0).
+      n = -grad/|grad|, l = headlight (the camera's backward optical axis),
+      e = -d, h = (e + l)/|e + l|: c = (k_a + k_d |n.l|) C(v) + k_s |n.h|^beta
+      (specular 0 where n.l = 0).  Where the gradient vanishes there is no
+      normal and only the ambient term remains: c = k_a C(v).
   R28 compositing: front to back, C += T alpha c, T *= 1 - alpha; the ray
       stops after the sample that brings T below 1e-4.  Output (C + T bg, T).
   Flags (for float32 comparisons): a pixel is flagged when its sample count
-  floor((t1 - t0)/Delta) has a fraction within 1e-3 of an integer, when a
-  transmittance comes within a relative 1e-3 of 1e-4, or when a gradient norm
-  comes within a factor 10 of the shading cut 1e-6.
+  floor((t1 - t0)/Delta) has a fraction within 1e-3 of an integer or when a
+  transmittance comes within a relative 1e-3 of 1e-4.
 """
 from __future__ import annotations
 
 import numpy as np
 
 T_STOP = 1e-4
-GRAD_EPS = 1e-6
 
 
 def camera_ray(cam, i, j):
@@ -154,15 +153,15 @@ def march_pixel(cam, vol, luts, i, j, step, material=None, bg=(0.0, 0.0, 0.0)):
             shade = None
             if material is not None:
                 gn = np.linalg.norm(g)
-                if GRAD_EPS / 10 < gn < GRAD_EPS * 10:
-                    near_stop[live] = True
-                if gn > GRAD_EPS:
+                ka, kd, ks, beta = material
+                if gn > 0.0:
                     nrm = -g / gn
-                    ka, kd, ks, beta = material
                     nl = abs(nrm @ light)
                     sd = ka + kd * nl
                     ss = ks * abs(nrm @ hv) ** beta if nl > 0 else 0.0
                     shade = (sd, ss)
+                else:
+                    shade = (ka, 0.0)
             for t in range(nT):
                 if not live[t]:
                     continue

@@ -157,6 +157,19 @@ def test_sample_positions_closed_form():
     assert out[0, 0] == pytest.approx(C, rel=1e-12)
 
 
+def test_flat_volume_keeps_only_the_ambient_term():
+    """A constant volume has no gradient, hence no normal: every shaded
+    sample has the colour k_a C."""
+    R = 9
+    vol = np.full((R, R, R), 0.5)
+    lut = S.constant_tf([0.9, 0.4, 0.1, 0.05]).astype(np.float64)[None]
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
+    plain, _ = RM.march_pixel(cam, vol, lut, 10, 20, 0.05, None)
+    lit, _ = RM.march_pixel(cam, vol, lut, 10, 20, 0.05, (0.3, 0.6, 0.2, 8.0))
+    assert lit[0, 3] == plain[0, 3]
+    assert np.allclose(lit[0, :3], 0.3 * plain[0, :3], rtol=1e-12)
+
+
 def test_empty_volume_and_multi_table_consistency():
     R = 9
     rng = np.random.default_rng(1)
