@@ -438,6 +438,41 @@ veg_status veg_densify(const veg_adam_arrays* in, int64_t n, const float* accum,
                        cudaStream_t stream);
 
 /*
+ * veg_volume_prepare -- packs a scalar volume for veg_raymarch: volume
+ * float [R][R][R] (x fastest) of vertex values at x_i = -1 + 2i/(R-1) on
+ * each axis of [-1,1]^3; vol4 float4 [R][R][R] receives (value, dv/dx,
+ * dv/dy, dv/dz) with central-difference gradients ((v[i+1] - v[i-1]) / 2h,
+ * one-sided on the boundary faces; h = 2/(R-1)).  2 <= R <= 2048; vol4
+ * 16-byte aligned.  One launch.
+ */
+veg_status veg_volume_prepare(const float* volume, int32_t resolution, float* vol4,
+                              cudaStream_t stream);
+
+/*
+ * veg_raymarch -- emission-absorption raymarching of the prepared volume,
+ * the renderer of the paper's ground-truth images (Sec. 4.2, 5.1: raymarched
+ * with an emission-absorption model, Blinn-Phong shaded with a headlight).
+ * Per pixel of every view (camera model of veg_project): the ray from the
+ * camera centre through the pixel, clipped to [-1,1]^3 and t >= near, is
+ * sampled at t0 + (k + 1/2) step for k < floor((t1 - t0) / step); a sample's
+ * value v and gradient are trilinear blends of vol4; its opacity is
+ * alpha = 1 - (1 - A(v))^(step / h) (A per unit distance h, the grid
+ * spacing) and its colour C(v), both from the tables of `tf` (linear
+ * interpolation as in veg_composite_fwd); with `material`, the colour is
+ * (k_a + k_d |n.l|) C + k_s |n.h|^beta with n the normalised gradient
+ * (k_a C where the gradient vanishes), l the headlight (camera backward axis)
+ * and h the half vector of l and the view direction.  Front-to-back
+ * compositing stops once T < 1e-4.  out [V][n_tf][H][W][4] = (C + T bg, T)
+ * (one image per view with tf.view_tf).  bg host float[3] or NULL (black).
+ */
+typedef struct veg_material {
+  float ka, kd, ks, beta;
+} veg_material;
+veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vol4,
+                        int32_t resolution, veg_tf tf, float step, const veg_material* material,
+                        const float* bg, float* out, cudaStream_t stream);
+
+/*
  * veg_render -- convenience forward: veg_project (with the TF cull), then
  * veg_bin_sort, then veg_composite_fwd, all scratch in `workspace`
  * (>= veg_render_workspace_size bytes).  Same outputs as

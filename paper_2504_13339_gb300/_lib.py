@@ -56,6 +56,11 @@ class veg_density_config(ctypes.Structure):
                 ("raw_weight_threshold", ctypes.c_float), ("log_split_factor", ctypes.c_float)]
 
 
+class veg_material(ctypes.Structure):
+    _fields_ = [("ka", ctypes.c_float), ("kd", ctypes.c_float), ("ks", ctypes.c_float),
+                ("beta", ctypes.c_float)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _CAMS = ctypes.POINTER(veg_camera)
@@ -90,6 +95,9 @@ _SIGS = {
                                         _P]),
     "veg_adam_step": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, _I32, _P]),
+    "veg_volume_prepare": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "veg_raymarch": (ctypes.c_int, [_CAMS, _I32, _P, _I32, veg_tf, ctypes.c_float,
+                                    ctypes.POINTER(veg_material), _P, _P, _P]),
     "veg_grad_stats_accumulate": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P]),
     "veg_densify_workspace_size": (ctypes.c_int, [_I64, ctypes.POINTER(_SZ)]),
     "veg_densify": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, _P, _P,
@@ -332,6 +340,20 @@ def veg_densify(in_arrays, n, accum, count, split_normals, cfg, out_arrays, out_
                               _ptr(split_normals), cfg, ctypes.byref(out_arrays), out_capacity,
                               _ptr(n_out), _ptr(action), _ptr(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def veg_volume_prepare(volume, vol4, stream=None):
+    _check("veg_volume_prepare",
+           load().veg_volume_prepare(_ptr(volume), volume.shape[0], _ptr(vol4), _stream(stream)))
+
+
+def veg_raymarch(cams, vol4, tf, step, out, material=None, bg=(0.0, 0.0, 0.0), stream=None):
+    """material: (k_a, k_d, k_s, beta) or None (unshaded)."""
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    mat = None if material is None else ctypes.byref(veg_material(*[float(m) for m in material]))
+    _check("veg_raymarch",
+           load().veg_raymarch(cams, len(cams), _ptr(vol4), vol4.shape[0], tf, float(step), mat,
+                               ctypes.cast(bgc, ctypes.c_void_p), _ptr(out), _stream(stream)))
 
 
 def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,

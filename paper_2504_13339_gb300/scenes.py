@@ -192,6 +192,19 @@ def gradient_lighting(g: "Gaussians", bf, ka=0.3, kd=0.7, ks=0.2, beta=20.0) -> 
     return Lighting(nb, k)
 
 
+def field_volume(bf, R) -> np.ndarray:
+    """The blob field sampled at the R^3 vertices x_i = -1 + 2i/(R-1),
+    layout [z][y][x], normalised by its largest vertex value (float32): the
+    gridded volume of a structured dataset."""
+    x = np.linspace(-1.0, 1.0, R)
+    out = np.empty((R, R, R), np.float32)
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    for k in range(R):  # one z slice at a time
+        pts = np.stack([X.ravel(), Y.ravel(), np.full(X.size, x[k])], 1)
+        out[k] = bf.value(pts).reshape(R, R)
+    return (out / out.max()).astype(np.float32)
+
+
 def blob_field(n_blobs, seed) -> BlobField:
     rng = np.random.default_rng(seed)
     amp = rng.uniform(0.3, 1.0, n_blobs)
