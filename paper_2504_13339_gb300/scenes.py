@@ -367,6 +367,33 @@ def initial_model(n, bf: "BlobField", seed, weight=0.1, lighting=True):
     return g, lt
 
 
+def vertex_model(vol, n, seed, weight=0.1, lighting=True):
+    """The paper's initialisation (Sec. 4.1): `n` vertices of the gridded
+    volume drawn at random without replacement (connectivity dropped), each a
+    Gaussian at the vertex carrying its value; scales from the mean spacing
+    of n points (reading R14), identity rotations, weight `weight`; lighting
+    as in initial_model.  Returns (Gaussians, Lighting or None)."""
+    R = vol.shape[0]
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(R ** 3, size=n, replace=False)
+    z, y, x = np.unravel_index(idx, (R, R, R))
+    grid = np.linspace(-1.0, 1.0, R)
+    pts = np.stack([grid[x], grid[y], grid[z]], 1)
+    v = vol.reshape(-1)[idx].astype(np.float64)
+    mu_ls = math.log(0.5 * 2.0 / n ** (1.0 / 3.0))
+    g = Gaussians(np.concatenate([pts, v[:, None]], 1).astype(np.float32),
+                  np.concatenate([np.full((n, 3), mu_ls), np.full((n, 1), weight)], 1)
+                  .astype(np.float32),
+                  np.tile(np.array([1.0, 0.0, 0.0, 0.0], np.float32), (n, 1)))
+    lt = None
+    if lighting:
+        nrm = rng.standard_normal((n, 3))
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        nb = np.concatenate([nrm, np.full((n, 1), 10.0)], 1).astype(np.float32)
+        lt = Lighting(nb, np.tile(np.array([0.3, 0.6, 0.2, 0.0], np.float32), (n, 1)))
+    return g, lt
+
+
 def train_scene(n=1_000_000, n_blobs=8, width=1024, n_tf=4, seed=2):
     """Training-step workload: blob-field Gaussians, a target made from a
     perturbed copy, `n_tf` bump TFs, one orbit view."""

@@ -44,3 +44,14 @@ def test_field_gradient_matches_finite_differences():
     h = 1e-6
     fd = np.stack([(bf.value(p + h * e) - bf.value(p - h * e)) / (2 * h) for e in np.eye(3)], 1)
     assert np.abs(g - fd).max() <= 1e-8 * max(1.0, np.abs(g).max())
+
+
+def test_vertex_model_takes_vertices_and_their_values():
+    vol = S.field_volume(S.blob_field(3, 5), 17)
+    g, lt = S.vertex_model(vol, 300, 6)
+    x = np.linspace(-1, 1, 17)
+    idx = np.rint((g.mean_v[:, :3] + 1) * 8).astype(int)  # grid indices (x, y, z)
+    assert np.allclose(x[idx], g.mean_v[:, :3], atol=1e-6)
+    assert np.array_equal(g.mean_v[:, 3], vol[idx[:, 2], idx[:, 1], idx[:, 0]])
+    assert len({tuple(r) for r in idx}) == 300  # without replacement
+    assert lt.normal_beta.shape == (300, 4)
