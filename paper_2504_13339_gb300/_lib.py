@@ -61,6 +61,27 @@ class veg_material(ctypes.Structure):
                 ("beta", ctypes.c_float)]
 
 
+_VP = ctypes.c_void_p
+
+
+class veg_train_args(ctypes.Structure):
+    _fields_ = [("raw", _VP * 5), ("grad", _VP * 5), ("exp_avg", _VP * 5),
+                ("exp_avg_sq", _VP * 5), ("mean_v", _VP), ("logscale_w", _VP),
+                ("n", ctypes.c_int64), ("cams", ctypes.POINTER(veg_camera)),
+                ("n_cams", ctypes.c_int32), ("light_dirs", _VP), ("luts", _VP),
+                ("lut_size", ctypes.c_int32), ("n_maps", ctypes.c_int32), ("targets", _VP),
+                ("bg", ctypes.c_float * 3), ("lambda_", ctypes.c_float),
+                ("lr", ctypes.c_float * 20), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("lit", ctypes.c_int32),
+                ("tf_group", ctypes.c_int32), ("splat_geo", _VP), ("splat_aux", _VP),
+                ("tiles_touched", _VP), ("rect", _VP), ("splat_shade", _VP),
+                ("grad_shade", _VP), ("binsort_ws", _VP), ("binsort_ws_bytes", ctypes.c_size_t),
+                ("capacity", ctypes.c_int64), ("vals", _VP), ("tile_ranges", _VP),
+                ("tile_order", _VP), ("out", _VP), ("n_contrib", _VP), ("loss_grad", _VP),
+                ("grad2d", _VP), ("loss", _VP), ("loss_ws", _VP),
+                ("loss_ws_bytes", ctypes.c_size_t), ("stat_accum", _VP), ("stat_count", _VP)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _CAMS = ctypes.POINTER(veg_camera)
@@ -96,6 +117,8 @@ _SIGS = {
     "veg_adam_step": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, _I32, _P]),
     "veg_volume_prepare": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "veg_train_step": (ctypes.c_int, [ctypes.POINTER(veg_train_args), _I32, _I32, _I32, _I32,
+                                      _P]),
     "veg_raymarch": (ctypes.c_int, [_CAMS, _I32, _P, _I32, veg_tf, ctypes.c_float,
                                     ctypes.POINTER(veg_material), _P, _P, _P]),
     "veg_grad_stats_accumulate": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P]),
@@ -340,6 +363,12 @@ def veg_densify(in_arrays, n, accum, count, split_normals, cfg, out_arrays, out_
                               _ptr(split_normals), cfg, ctypes.byref(out_arrays), out_capacity,
                               _ptr(n_out), _ptr(action), _ptr(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def veg_train_step(args, view, k, adam_step, accumulate_stats, stream=None):
+    _check("veg_train_step", load().veg_train_step(ctypes.byref(args), view, k, adam_step,
+                                                   1 if accumulate_stats else 0,
+                                                   _stream(stream)))
 
 
 def veg_volume_prepare(volume, vol4, stream=None):

@@ -85,6 +85,7 @@ class SplatPipeline:
         self.capacity = int(capacity)
         ws = _lib.veg_bin_sort_workspace_size(self.n, self.V, self.capacity, self.W, self.H)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.ws[:256].zero_()  # status header: no binning yet, no overflow
         self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
 
     # -- stages ------------------------------------------------------------

@@ -191,11 +191,14 @@ class OpacityGuidedTrainer:
     lighting (params.lit) every view is shaded with its headlight."""
 
     def __init__(self, params: TrainParams, cams, luts, targets, lr=None, lam=LAMBDA_SSIM,
-                 seed=0, capacity=None, bg=(0.0, 0.0, 0.0), density: DensityControl = None):
+                 seed=0, capacity=None, bg=(0.0, 0.0, 0.0), density: DensityControl = None,
+                 native=True):
         self.P = params
         self.density = density
         self.it = 0
         self.capacity = capacity
+        self.native = bool(native)
+        self._args = None
         self.cams = list(cams)
         self.luts = luts
         self.targets = targets
@@ -224,6 +227,46 @@ class OpacityGuidedTrainer:
         p.composite(lut, self.bg, stream=stream)
         return p.out
 
+    def _build_args(self):
+        """The native executor's view of every buffer (rebuilt whenever the
+        arrays change, i.e. after densification)."""
+        p, P, D = self.pipe, self.P, self.density
+        if p.splat_shade is None:
+            p.splat_shade = torch.empty(p.V * p.n, 2, device=p.device)
+            p.grad_shade = torch.empty(p.V * p.n, 2, device=p.device)
+        ptr = lambda t: None if t is None else t.data_ptr()
+        a = _lib.veg_train_args()
+        for i in range(5):
+            a.raw[i], a.grad[i] = ptr(P.raw[i]), ptr(P.grads[i])
+            a.exp_avg[i], a.exp_avg_sq[i] = ptr(P.m[i]), ptr(P.v[i])
+        a.mean_v, a.logscale_w, a.n = P.mean_v.data_ptr(), P.logscale_w.data_ptr(), P.n
+        self._c_all = _lib.cameras(self.cams)
+        self._lights_c = np.ascontiguousarray(self.lights, np.float32)
+        a.cams, a.n_cams = self._c_all, len(self.cams)
+        a.light_dirs = self._lights_c.ctypes.data
+        a.luts, a.lut_size, a.n_maps = self.luts.data_ptr(), self.luts.shape[1], self.K
+        a.targets = self.targets.data_ptr()
+        a.bg[:] = [float(b) for b in self.bg]
+        a.lambda_ = self.lam
+        a.lr[:] = [float(x) for x in np.asarray(self.lr, np.float64).ravel()]
+        a.beta1, a.beta2, a.eps = 0.9, 0.999, 1e-15
+        a.lit, a.tf_group = 1 if P.lit else 0, 0
+        a.splat_geo, a.splat_aux = p.geo.data_ptr(), p.aux.data_ptr()
+        a.tiles_touched, a.rect = p.tiles.data_ptr(), p.rect.data_ptr()
+        a.splat_shade, a.grad_shade = p.splat_shade.data_ptr(), p.grad_shade.data_ptr()
+        a.binsort_ws, a.binsort_ws_bytes = p.ws.data_ptr(), p.ws.numel()
+        a.capacity, a.vals = p.capacity, p.vals.data_ptr()
+        a.tile_ranges, a.tile_order = p.ranges.data_ptr(), p.order.data_ptr()
+        a.out, a.n_contrib = p.out.data_ptr(), p.n_contrib.data_ptr()
+        a.loss_grad, a.grad2d = p.loss_grad.data_ptr(), p.grad2d.data_ptr()
+        a.loss, a.loss_ws = self.loss.data_ptr(), self.loss_ws.data_ptr()
+        a.loss_ws_bytes = self.loss_ws.numel()
+        if D is not None:
+            if D.accum is None or D.accum.numel() != P.n:
+                D.reset(P.n)
+            a.stat_accum, a.stat_count = D.accum.data_ptr(), D.count.data_ptr()
+        self._args = a
+
     def step(self, view=None, k=None, stream=None):
         """One training iteration; returns (view, map) used.  With density
         control, an iteration that densifies replaces the parameter arrays
@@ -233,6 +276,8 @@ class OpacityGuidedTrainer:
         if k is None:
             k = int(self.rng.integers(self.K))
         self.it += 1
+        if self.native:
+            return self._native_step(view, k, stream)
         p, P, D = self.pipe, self.P, self.density
         self.render(view, k, stream)
         _lib.veg_l1_ssim_loss(p.out, self.targets[view, k], p.loss_grad, self.loss,
@@ -247,6 +292,21 @@ class OpacityGuidedTrainer:
             self.pipe = SplatPipeline(P.n, self.cams[:1], n_tf=1, capacity=self.capacity)
         else:
             P.adam(self.lr, stream)
+        return view, k
+
+    def _native_step(self, view, k, stream):
+        P, D = self.P, self.density
+        if self._args is None:
+            self._build_args()
+        due = D is not None and D.due(self.it)
+        accumulate = D is not None and D.active(self.it)
+        _lib.veg_train_step(self._args, view, k, 0 if due else P.step + 1, accumulate, stream)
+        if due:
+            D.apply(P, stream)
+            self.pipe = SplatPipeline(P.n, self.cams[:1], n_tf=1, capacity=self.capacity)
+            self._args = None
+        else:
+            P.step += 1
         return view, k
 
     def overflowed(self, stream=None):

@@ -206,3 +206,22 @@ def test_training_reduces_the_loss():
     assert np.all(np.isfinite(losses))
     assert losses[-50:].mean() < 0.8 * losses[:50].mean(), (losses[:50].mean(),
                                                              losses[-50:].mean())
+
+
+def test_native_step_equals_the_python_sequence():
+    """veg_train_step issues the same stages as the Python sequence: after
+    three iterations (same views and maps) the parameters agree up to the
+    order of the backward's float atomics."""
+    g, lt, cams, luts, tg = small_training_set(seed=95)
+    runs = []
+    for native in (True, False):
+        P = TrainParams(g, lt)
+        T = OpacityGuidedTrainer(P, cams, lut_tensor(luts), dev(tg), native=native)
+        for v, k in ((0, 1), (1, 2), (1, 0)):
+            T.step(view=v, k=k)
+        torch.cuda.synchronize()
+        runs.append(([x.cpu().numpy() for x in P.raw], float(T.loss[0])))
+    (a, la), (b, lb) = runs
+    assert la == pytest.approx(lb, rel=1e-5)
+    for x, y in zip(a, b):
+        assert np.allclose(x, y, rtol=1e-5, atol=1e-6)
