@@ -473,6 +473,68 @@ veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vo
                         const float* bg, float* out, cudaStream_t stream);
 
 /*
+ * veg_train_step -- one opacity-guided training iteration (Sec. 4.2) issued
+ * from native code: veg_project (culled by the chosen table) ->
+ * veg_shade (headlight of the chosen view, if lit) -> veg_bin_sort ->
+ * veg_tile_order -> veg_composite_fwd -> veg_l1_ssim_loss against
+ * targets[view][map] -> zeroing of the gradients -> veg_composite_bwd
+ * (full chain) -> veg_shade_bwd (if lit) -> veg_grad_stats_accumulate (if
+ * stat_accum is given and accumulate_stats) -> veg_adam_step (if
+ * adam_step >= 1).  Every buffer is the caller's (the library allocates
+ * nothing); the arrays and sizes follow the entry points named above.  No
+ * host synchronisation: instance-capacity overflow is reported later by
+ * veg_sync_status on binsort_ws.  Returns the first failing status.
+ */
+typedef struct veg_train_args {
+  /* model: raw parameters, gradients, Adam moments ([n][4] each; arrays 3,
+   * 4 may be NULL when unlit) and the rendered (activated) arrays */
+  float* raw[5];
+  float* grad[5];
+  float* exp_avg[5];
+  float* exp_avg_sq[5];
+  float* mean_v;
+  float* logscale_w;
+  int64_t n;
+  /* training set: host cameras and headlights, device tables and targets */
+  const veg_camera* cams;
+  int32_t n_cams;
+  const float* light_dirs; /* host [n_cams][3] */
+  const float* luts;       /* device [n_maps][lut_size][4] */
+  int32_t lut_size, n_maps;
+  const float* targets;    /* device [n_cams][n_maps][H][W][4] */
+  float bg[3];
+  float lambda;            /* SSIM weight of the loss */
+  float lr[20];
+  float beta1, beta2, eps;
+  int32_t lit;
+  int32_t tf_group;
+  /* render buffers for one view of n records */
+  float* splat_geo;
+  float* splat_aux;
+  int32_t* tiles_touched;
+  int16_t* rect;
+  float* splat_shade;      /* [n][2], if lit */
+  float* grad_shade;       /* [n][2], if lit */
+  void* binsort_ws;
+  size_t binsort_ws_bytes;
+  int64_t capacity;
+  uint32_t* vals;
+  int32_t* tile_ranges;
+  int32_t* tile_order;
+  float* out;              /* [H][W][4] */
+  int32_t* n_contrib;
+  float* loss_grad;        /* [H][W][4] */
+  float* grad2d;           /* [n][8] */
+  float* loss;             /* device float[3] */
+  void* loss_ws;
+  size_t loss_ws_bytes;
+  float* stat_accum;       /* optional densification statistic */
+  int32_t* stat_count;
+} veg_train_args;
+veg_status veg_train_step(const veg_train_args* args, int32_t view, int32_t map,
+                          int32_t adam_step, int32_t accumulate_stats, cudaStream_t stream);
+
+/*
  * veg_render -- convenience forward: veg_project (with the TF cull), then
  * veg_bin_sort, then veg_composite_fwd, all scratch in `workspace`
  * (>= veg_render_workspace_size bytes).  Same outputs as
