@@ -30,6 +30,9 @@ namespace {
 
 constexpr int kBatch = 256;
 constexpr int kWarps = 8;
+// One splat is staged per thread and the backward indexes its per-splat
+// shared arrays by thread: the batch must equal the 256-thread block.
+static_assert(kBatch == 32 * kWarps, "batch size must equal the block size");
 
 // 2^x with the hardware approximation (ex2.approx.ftz), x = power * log2(e).
 __device__ __forceinline__ float gauss_of(float power) {
