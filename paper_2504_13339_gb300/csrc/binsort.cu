@@ -9,10 +9,13 @@
 //   2. emit the pairs in that depth order with key = view * tiles + tile and
 //      stable-sort them by that key alone -- ceil(bits/8) passes over M.
 // A stable sort by tile of a sequence already ordered by (depth, index)
-// yields (view, tile, depth, index) order.  Both stages use one hand-written
-// LSD radix sort (reduce / scan / stable scatter, 8-bit digits, 2048 items
-// per block).  The instance count M lives only on the device; later kernels
-// read it from the workspace header, so no host round trip is needed.
+// yields (view, tile, depth, index) order.  Records that touch no tile
+// (culled) are dropped first by a stable compaction, so only the visible
+// ones are depth-sorted.  Both stages use one hand-written LSD radix sort
+// (reduce / scan / stable scatter, 8-bit digits, 2048-item chunks, grid-
+// stride blocks).  The visible and instance counts live only on the device;
+// later kernels read them from the workspace header, so no host round trip
+// is needed and no block works past them.
 #include <algorithm>
 
 #include "veg_internal.cuh"
@@ -75,33 +78,42 @@ __device__ __forceinline__ T block_exclusive_scan256(T x, T* s_warp) {
 // radix sort kernels (u32 keys, u32 values, one 1..8-bit digit per pass)
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ int chunks_of(int64_t n) {
+  return (int)((n + kTileItems - 1) / kTileItems);
+}
+
+// Per-chunk digit histograms; hist is [256][nblocks] (nblocks = the chunk
+// capacity), blocks stride over the chunks that hold items.
 __global__ void __launch_bounds__(kThreads)
     radix_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, int shift, int nbits,
                       uint32_t* __restrict__ hist, int nblocks) {
   __shared__ uint32_t s_hist[256];
-  s_hist[threadIdx.x] = 0;
-  __syncthreads();
   const int64_t n = cnt.get();
-  const int64_t base = (int64_t)blockIdx.x * kTileItems;
+  const int nch = chunks_of(n);
   const uint32_t mask = (1u << nbits) - 1u;
-  if (base < n) {
+  for (int b = blockIdx.x; b < nch; b += gridDim.x) {
+    s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)b * kTileItems;
 #pragma unroll 4
     for (int j = 0; j < kItems; ++j) {
       int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
       if (i < n) atomicAdd(&s_hist[(__ldg(&keys[i]) >> shift) & mask], 1u);
     }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + b] = s_hist[threadIdx.x];
   }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
 }
 
-// One block per digit: exclusive scan in place of that digit's per-block
-// counts, and the digit total.
+// One block per digit: exclusive scan in place of that digit's per-chunk
+// counts (the chunks that hold items), and the digit total.
 __global__ void __launch_bounds__(1024)
-    radix_scan_rows_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ totals) {
+    radix_scan_rows_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ totals,
+                           Count cnt) {
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_total;
   uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
+  nblocks = chunks_of(cnt.get());
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t carry = 0;
   for (int base = 0; base < nblocks; base += 1024 * 4) {
@@ -161,61 +173,65 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ uint32_t s_keys[kTileItems];
   __shared__ uint32_t s_vals[kTileItems];
   const int64_t n = cnt.get();
-  const int64_t base = (int64_t)blockIdx.x * kTileItems;
-  if (base >= n) return;
+  const int nch = chunks_of(n);
+  if ((int)blockIdx.x >= nch) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t mask = (1u << nbits) - 1u;
+  const uint32_t dpre = block_exclusive_scan256<uint32_t>(totals[tid], s_warp);
+  for (int b = blockIdx.x; b < nch; b += gridDim.x) {
+    const int64_t base = (int64_t)b * kTileItems;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) s_whist[w][tid] = 0;
-  uint32_t dpre = block_exclusive_scan256<uint32_t>(totals[tid], s_warp);
-  s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + blockIdx.x];
-  __syncthreads();
+    for (int w = 0; w < 8; ++w) s_whist[w][tid] = 0;
+    s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + b];
+    __syncthreads();
 
-  uint32_t k[kItems], v[kItems], r[kItems];
-  const unsigned lt = lanemask_lt();
+    uint32_t k[kItems], v[kItems], r[kItems];
+    const unsigned lt = lanemask_lt();
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
-    bool valid = i < n;
-    k[j] = valid ? kin[i] : 0u;
-    v[j] = valid ? vin[i] : 0u;
-    uint32_t d = valid ? ((k[j] >> shift) & mask) : 256u;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
-    r[j] = before + __popc(peers & lt);
-    __syncwarp();
-    if (d < 256u && (peers & lt) == 0) s_whist[warp][d] = before + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  // per digit: exclusive prefix over warps, and the block's digit count
-  uint32_t run = 0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    uint32_t c = s_whist[w][tid];
-    s_whist[w][tid] = run;
-    run += c;
-  }
-  s_bstart[tid] = block_exclusive_scan256<uint32_t>(run, s_warp);
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
-    if (i < n) {
-      uint32_t d = (k[j] >> shift) & mask;
-      uint32_t pos = s_bstart[d] + s_whist[warp][d] + r[j];
-      s_keys[pos] = k[j];
-      s_vals[pos] = v[j];
+    for (int j = 0; j < kItems; ++j) {
+      int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+      bool valid = i < n;
+      k[j] = valid ? kin[i] : 0u;
+      v[j] = valid ? vin[i] : 0u;
+      uint32_t d = valid ? ((k[j] >> shift) & mask) : 256u;
+      unsigned peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
+      r[j] = before + __popc(peers & lt);
+      __syncwarp();
+      if (d < 256u && (peers & lt) == 0) s_whist[warp][d] = before + __popc(peers);
+      __syncwarp();
     }
-  }
-  __syncthreads();
-  const int cnt_valid = (int)min((int64_t)kTileItems, n - base);
-  for (int p = tid; p < cnt_valid; p += kThreads) {
-    uint32_t key = s_keys[p];
-    uint32_t d = (key >> shift) & mask;
-    uint32_t g = s_dbase[d] + (uint32_t)p - s_bstart[d];
-    kout[g] = key;
-    vout[g] = s_vals[p];
+    __syncthreads();
+    // per digit: exclusive prefix over warps, and the block's digit count
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = run;
+      run += c;
+    }
+    s_bstart[tid] = block_exclusive_scan256<uint32_t>(run, s_warp);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+      if (i < n) {
+        uint32_t d = (k[j] >> shift) & mask;
+        uint32_t pos = s_bstart[d] + s_whist[warp][d] + r[j];
+        s_keys[pos] = k[j];
+        s_vals[pos] = v[j];
+      }
+    }
+    __syncthreads();
+    const int cnt_valid = (int)min((int64_t)kTileItems, n - base);
+    for (int p = tid; p < cnt_valid; p += kThreads) {
+      uint32_t key = s_keys[p];
+      uint32_t d = (key >> shift) & mask;
+      uint32_t g = s_dbase[d] + (uint32_t)p - s_bstart[d];
+      kout[g] = key;
+      vout[g] = s_vals[p];
+    }
+    __syncthreads();  // the next chunk reuses the shared arrays
   }
 }
 
@@ -223,20 +239,95 @@ __global__ void __launch_bounds__(kThreads, 4)
 // binning kernels
 // ---------------------------------------------------------------------------
 
-__global__ void depth_keys_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
-                                  int64_t nrec, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ vals) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrec) return;
-  keys[i] = tiles[i] > 0 ? __float_as_uint(geo[i].z) : 0xffffffffu;
-  vals[i] = (uint32_t)i;
+// Per-chunk counts of the records that touch a tile (index order).
+__global__ void __launch_bounds__(kThreads)
+    visible_count_kernel(const int32_t* __restrict__ tiles, int64_t nrec,
+                         unsigned long long* __restrict__ bsum) {
+  __shared__ unsigned s_warp[8];
+  const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
+  unsigned c = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) c += (base + k < nrec && tiles[base + k] > 0) ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < 8; ++w) t += s_warp[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// Stable compaction: the visible records' depth keys and indices, in index
+// order, at [0, n_visible).
+__global__ void __launch_bounds__(kThreads)
+    visible_scatter_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
+                           int64_t nrec, const unsigned long long* __restrict__ bsum,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  __shared__ unsigned long long s_warp[8];
+  const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
+  bool vis[kItems];
+  unsigned long long c = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    vis[k] = base + k < nrec && tiles[base + k] > 0;
+    c += vis[k] ? 1ull : 0ull;
+  }
+  unsigned long long run = bsum[blockIdx.x] + block_exclusive_scan256<unsigned long long>(c, s_warp);
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    if (!vis[k]) continue;
+    keys[run] = __float_as_uint(geo[base + k].z);
+    vals[run] = (uint32_t)(base + k);
+    ++run;
+  }
+}
+
+// Exclusive scan of per-chunk counts in one block; the total to *total.
+__global__ void __launch_bounds__(1024)
+    chunk_scan_kernel(unsigned long long* __restrict__ bsum, int nb,
+                      unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned long long s_total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const unsigned long long x = i < nb ? bsum[i] : 0ull;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned long long w = s_warp[lane];
+      unsigned long long wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      s_warp[lane] = wi - w;
+      if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    if (i < nb) bsum[i] = carry + s_warp[warp] + inc - x;
+    carry += s_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
 }
 
 // Per-block sums of tiles_touched taken in depth order.
 __global__ void __launch_bounds__(kThreads)
     count_reduce_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
-                        int64_t nrec, unsigned long long* __restrict__ bsum) {
+                        Count cnt, unsigned long long* __restrict__ bsum) {
   __shared__ unsigned long long s[kThreads];
+  const int64_t nrec = cnt.get();
   const int64_t base = (int64_t)blockIdx.x * kTileItems;
   unsigned long long acc = 0;
   for (int j = 0; j < kItems; ++j) {
@@ -298,9 +389,10 @@ __global__ void __launch_bounds__(1024)
 // saturated to 0xffffffff (any value >= capacity is never emitted).
 __global__ void __launch_bounds__(kThreads)
     count_down_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
-                      int64_t nrec, const unsigned long long* __restrict__ bsum,
+                      Count cnt, const unsigned long long* __restrict__ bsum,
                       uint32_t* __restrict__ offsets) {
   __shared__ unsigned long long s_warp[8];
+  const int64_t nrec = cnt.get();
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
   uint32_t c[kItems];
   unsigned long long sum = 0;
@@ -327,9 +419,10 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(256)
     emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                int64_t nrec, int64_t n_per_view, int tiles_x, int tiles_per_view,
+                Count visible, int64_t n_per_view, int tiles_x, int tiles_per_view,
                 int64_t capacity, uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
   const int lane = threadIdx.x & 31;
+  const int64_t nrec = visible.get();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t g = 0, cnt = 0, off = 0xffffffffu;
   short4 rc = make_short4(0, 0, 0, 0);
@@ -452,13 +545,29 @@ Layout carve(void* ws, int64_t nrec, int64_t capacity) {
   return L;
 }
 
+// Blocks for a pass over at most `nblocks` chunks: one wave of the scatter
+// (4 CTAs per SM) at most; the kernels stride over the chunks that hold items.
+int pass_grid(int nblocks) {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (sms[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 1;
+    sms[dev] = v;
+  }
+  return std::max(1, std::min(nblocks, 4 * sms[dev]));
+}
+
 void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                 Count cnt, int shift, int nbits, int nblocks, const Layout& L,
                 cudaStream_t stream) {
-  radix_hist_kernel<<<nblocks, kThreads, 0, stream>>>(kin, cnt, shift, nbits, L.hist, nblocks);
-  radix_scan_rows_kernel<<<256, 1024, 0, stream>>>(L.hist, nblocks, L.totals);
-  radix_scatter_kernel<<<nblocks, kThreads, 0, stream>>>(kin, vin, kout, vout, cnt, shift, nbits,
-                                                         L.hist, L.totals, nblocks);
+  const int grid = pass_grid(nblocks);
+  radix_hist_kernel<<<grid, kThreads, 0, stream>>>(kin, cnt, shift, nbits, L.hist, nblocks);
+  radix_scan_rows_kernel<<<256, 1024, 0, stream>>>(L.hist, nblocks, L.totals, cnt);
+  radix_scatter_kernel<<<grid, kThreads, 0, stream>>>(kin, vin, kout, vout, cnt, shift, nbits,
+                                                      L.hist, L.totals, nblocks);
   count_launch(3);
 }
 
@@ -488,19 +597,23 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
     cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), stream);
     return launch_status();
   }
-  // 1. depth sort of all (view, Gaussian) records
-  depth_keys_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(geo, tiles, nrec, L.dk0, L.dv0);
-  count_launch();
-  Count cr{nrec, nullptr, 0};
+  // 1. the visible records (touching a tile) in index order, then their
+  //    depth sort
+  visible_count_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, nrec, L.bsum);
+  chunk_scan_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, &L.hdr->n_visible);
+  visible_scatter_kernel<<<L.nb_rec, kThreads, 0, stream>>>(geo, tiles, nrec, L.bsum, L.dk0,
+                                                            L.dv0);
+  count_launch(3);
+  Count cr{0, &L.hdr->n_visible, nrec};
   radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 0, 8, L.nb_rec, L, stream);
   radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 8, 8, L.nb_rec, L, stream);
   radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 16, 8, L.nb_rec, L, stream);
   radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 24, 8, L.nb_rec, L, stream);
   const uint32_t* order = L.dv0;
   // 2. instance offsets in depth order, total into the header
-  count_reduce_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, nrec, L.bsum);
+  count_reduce_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, cr, L.bsum);
   count_top_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, L.hdr, capacity);
-  count_down_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, nrec, L.bsum, L.offsets);
+  count_down_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, cr, L.bsum, L.offsets);
   count_launch(3);
   // 3. emit (tile key, record) pairs, then stable sort by tile key
   int bits = 1;
@@ -515,7 +628,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
     vbuf[0] = L.iv0;
     vbuf[1] = vals;
   }
-  emit_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(tiles, rect, order, L.offsets, nrec, n,
+  emit_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(tiles, rect, order, L.offsets, cr, n,
                                                        tiles_x, tiles_per_view, capacity, kbuf[0],
                                                        vbuf[0]);
   count_launch();

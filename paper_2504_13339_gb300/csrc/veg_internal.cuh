@@ -42,7 +42,9 @@ struct Carver {
 struct WsHeader {
   unsigned long long n_instances;  // total tile instances of the last binning
   unsigned int flags;              // VEG_FLAG_* bits
-  unsigned int pad[61];
+  unsigned int pad0;
+  unsigned long long n_visible;    // records that touch a tile (last binning)
+  unsigned int pad[58];
 };
 static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
 constexpr unsigned int FLAG_CAPACITY = 1u;
