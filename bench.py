@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--width", type=int, default=1024)
     ap.add_argument("--workload", default="train",
-                    choices=["train", "plain", "sweep", "batched", "serve", "opt"])
+                    choices=["train", "plain", "sweep", "batched", "serve", "opt", "raymarch"])
     ap.add_argument("--lighting", action="store_true",
                     help="train step with Blinn-Phong shading (headlight, Eq. 2-3)")
     ap.add_argument("--opt-views", type=int, default=16,
@@ -785,6 +785,101 @@ def run_opt(args):
         "data": "synthetic"}), flush=True)
 
 
+# FP32 operations (an FMA counts 2) per raymarch sample, from the kernel:
+# position and grid coordinates 12, trilinear value + gradient (7 float4
+# lerps) 56, shading (normalisation, two dot products, power) 30; per table
+# evaluation: table lerp 8, clamp 2, opacity correction 4, shaded colour 6,
+# compositing 7, stop test 1.
+MARCH_FLOPS = {"sample": 98, "table": 28}
+
+
+def run_raymarch(args):
+    """The ground-truth renderer of the paper's training images (Sec. 4.2,
+    5.1): a 256^3 scalar volume (8-blob field) raymarched with
+    emission-absorption and headlight Blinn-Phong for 160 views x 10 opacity
+    maps at 800x800 (one launch per view, one sample pass per 8 maps)."""
+    import torch
+
+    import __graft_entry__
+    from oracle import veg_raymarch_oracle as RM
+    from paper_2504_13339_gb300 import _lib, scenes as S
+    from paper_2504_13339_gb300.render import lut_tensor
+    from paper_2504_13339_gb300.train import opacity_guided_luts
+    __graft_entry__.build()
+    size, K, R = 800, 10, 256
+    cams = S.grid_orbit_cameras(16, 10, size, size)
+    lut_np = opacity_guided_luts(K, S.colour_ramp(11))
+    luts = lut_tensor(lut_np)
+    vol = S.field_volume(S.blob_field(8, 12), R)
+    v4 = torch.empty(R, R, R, 4, device="cuda")
+    _lib.veg_volume_prepare(torch.as_tensor(vol, device="cuda"), v4)
+    out = torch.empty(len(cams), K, size, size, 4, device="cuda")
+    step = (2.0 / (R - 1)) / 2
+    mat = (0.3, 0.6, 0.25, 12.0)
+    tf = _lib.tf_desc(luts)
+    c_cams = [_lib.cameras([c]) for c in cams]
+
+    def render_all(stats=None):
+        for v in range(len(cams)):
+            _lib.veg_raymarch(c_cams[v], v4, tf, step, out[v:v + 1], mat, stats=stats)
+    for _ in range(max(args.warmup, 1)):
+        render_all()
+    reps = max(1, min(args.steps, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    a.record()
+    for _ in range(reps):
+        render_all()
+    b.record()
+    b.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / reps
+    st = torch.zeros(2, dtype=torch.int64, device="cuda")
+    render_all(st)
+    torch.cuda.synchronize()
+    samples, tables = (int(x) for x in st.cpu().numpy())
+    flops = MARCH_FLOPS["sample"] * samples + MARCH_FLOPS["table"] * tables
+    props = torch.cuda.get_device_properties(0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    px = len(cams) * K * size * size
+    line = {
+        "workload": "raymarched ground truth: 256^3 volume (8-blob field), 160 views x 10 "
+                    "opacity maps, 800x800, emission-absorption, headlight Blinn-Phong, step "
+                    "half the grid spacing",
+        "metric": "Mpix/s", "value": round(px / (ms * 1e-3) / 1e6, 1), "unit": "Mpix/s",
+        "ms_per_set": round(ms, 2), "images": len(cams) * K, "reps": reps, "clocks": clk,
+        "work": {"samples": samples, "table_evaluations": tables},
+        "roofline": {"bound": "alu", "kernel": "raymarch_kernel<8>/<2>",
+                     "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4),
+                     "flops_model": "98 per sample + 28 per table evaluation (FMA = 2)"},
+        "data": "synthetic"}
+    if not args.no_cpu_baseline:
+        rng = np.random.default_rng(3)
+        vol64 = vol.astype(np.float64)
+        luts64 = lut_np.astype(np.float64)
+        n_px = 12
+        t0 = time.perf_counter()
+        for _ in range(n_px):
+            RM.march_pixel(cams[37], vol64, luts64, int(rng.integers(200, 600)),
+                           int(rng.integers(200, 600)), step, mat)
+        dt = (time.perf_counter() - t0) / n_px
+        line["cpu_baseline"] = {"value": round(K / dt / 1e6, 8), "unit": "Mpix/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{n_px} rays through the volume's centre region, "
+                                          f"10 maps each, numpy single thread"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -793,7 +888,7 @@ def main():
         run_gpu(args)
     else:
         {"plain": run_plain, "sweep": run_sweep, "batched": run_batched,
-         "serve": run_serve, "opt": run_opt}[args.workload](args)
+         "serve": run_serve, "opt": run_opt, "raymarch": run_raymarch}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -464,13 +464,16 @@ veg_status veg_volume_prepare(const float* volume, int32_t resolution, float* vo
  * and h the half vector of l and the view direction.  Front-to-back
  * compositing stops once T < 1e-4.  out [V][n_tf][H][W][4] = (C + T bg, T)
  * (one image per view with tf.view_tf).  bg host float[3] or NULL (black).
+ * stats: optional device uint64[2] accumulating (samples taken per ray and
+ * table group, table evaluations); NULL skips the instrumented kernel.
  */
 typedef struct veg_material {
   float ka, kd, ks, beta;
 } veg_material;
 veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vol4,
                         int32_t resolution, veg_tf tf, float step, const veg_material* material,
-                        const float* bg, float* out, cudaStream_t stream);
+                        const float* bg, float* out, unsigned long long* stats,
+                        cudaStream_t stream);
 
 /*
  * veg_train_step -- one opacity-guided training iteration (Sec. 4.2) issued

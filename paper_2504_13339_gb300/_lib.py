@@ -120,7 +120,7 @@ _SIGS = {
     "veg_train_step": (ctypes.c_int, [ctypes.POINTER(veg_train_args), _I32, _I32, _I32, _I32,
                                       _P]),
     "veg_raymarch": (ctypes.c_int, [_CAMS, _I32, _P, _I32, veg_tf, ctypes.c_float,
-                                    ctypes.POINTER(veg_material), _P, _P, _P]),
+                                    ctypes.POINTER(veg_material), _P, _P, _P, _P]),
     "veg_grad_stats_accumulate": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P]),
     "veg_densify_workspace_size": (ctypes.c_int, [_I64, ctypes.POINTER(_SZ)]),
     "veg_densify": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, _P, _P,
@@ -376,13 +376,15 @@ def veg_volume_prepare(volume, vol4, stream=None):
            load().veg_volume_prepare(_ptr(volume), volume.shape[0], _ptr(vol4), _stream(stream)))
 
 
-def veg_raymarch(cams, vol4, tf, step, out, material=None, bg=(0.0, 0.0, 0.0), stream=None):
+def veg_raymarch(cams, vol4, tf, step, out, material=None, bg=(0.0, 0.0, 0.0), stats=None,
+                 stream=None):
     """material: (k_a, k_d, k_s, beta) or None (unshaded)."""
     bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
     mat = None if material is None else ctypes.byref(veg_material(*[float(m) for m in material]))
     _check("veg_raymarch",
            load().veg_raymarch(cams, len(cams), _ptr(vol4), vol4.shape[0], tf, float(step), mat,
-                               ctypes.cast(bgc, ctypes.c_void_p), _ptr(out), _stream(stream)))
+                               ctypes.cast(bgc, ctypes.c_void_p), _ptr(out), _ptr(stats),
+                               _stream(stream)))
 
 
 def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,

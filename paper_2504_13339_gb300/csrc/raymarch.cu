@@ -64,9 +64,13 @@ __global__ void __launch_bounds__(256)
   out[i] = make_float4(vol[i], diff(x, sx), diff(y, sy), diff(z, sz));
 }
 
-template <int TG>
+// stats (instrumented build): samples taken (per ray and table group) and
+// table evaluations (samples x live tables).
+template <int TG, bool STATS>
 __global__ void __launch_bounds__(256)
-    raymarch_kernel(MarchArgs A, RaySet rs, float4* __restrict__ out) {
+    raymarch_kernel(MarchArgs A, RaySet rs, float4* __restrict__ out,
+                    unsigned long long* __restrict__ stats) {
+  unsigned long long n_samp = 0, n_tab = 0;
   extern __shared__ float4 s_lut[];
   const int wi = blockIdx.x;
   const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
@@ -83,7 +87,9 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int px = (tile % A.tiles_x) * VEG_TILE + (threadIdx.x & 15);
   const int py = (tile / A.tiles_x) * VEG_TILE + (threadIdx.x >> 4);
-  if (px >= A.width || py >= A.height) return;
+  const bool inside = px < A.width && py < A.height;
+  if (!STATS && !inside) return;
+  if (inside) {
   const RayView& V = rs.v[view];
   // ray direction R^T ((px - cx)/fx, (py - cy)/fy, 1), normalised
   const float ux = (px - V.cx) / V.fx, uy = (py - V.cy) / V.fy;
@@ -165,6 +171,10 @@ __global__ void __launch_bounds__(256)
         }
       }
       const TfPos q = tf_pos(s.x, L);
+      if (STATS) {
+        ++n_samp;
+        n_tab += (unsigned)__popc(live);
+      }
 #pragma unroll
       for (int tt = 0; tt < TG; ++tt) {
         if (!(live & (1u << tt))) continue;
@@ -187,25 +197,44 @@ __global__ void __launch_bounds__(256)
     out[o] = make_float4(fmaf(T[tt], A.bg0, Cr[tt]), fmaf(T[tt], A.bg1, Cg[tt]),
                          fmaf(T[tt], A.bg2, Cb[tt]), T[tt]);
   }
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_samp += __shfl_down_sync(0xffffffffu, n_samp, o);
+      n_tab += __shfl_down_sync(0xffffffffu, n_tab, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats[0], n_samp);
+      atomicAdd(&stats[1], n_tab);
+    }
+  }
 }
 
-template <int TG>
+template <int TG, bool STATS>
 veg_status launch_march(const MarchArgs& A, const RaySet& rs, int n_views, float4* out,
-                        cudaStream_t stream) {
+                        unsigned long long* stats, cudaStream_t stream) {
   const size_t smem = (size_t)TG * A.lut_size * sizeof(float4);
   static size_t configured = 0;
   if (smem > configured) {
     if (smem > 227 * 1024) return VEG_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(raymarch_kernel<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(raymarch_kernel<TG, STATS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return VEG_ERR_UNSUPPORTED;
     configured = smem;
   }
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
-  raymarch_kernel<TG><<<grid, 256, smem, stream>>>(A, rs, out);
+  raymarch_kernel<TG, STATS><<<grid, 256, smem, stream>>>(A, rs, out, stats);
   count_launch();
   return launch_status();
+}
+
+template <int TG>
+veg_status launch_march_s(const MarchArgs& A, const RaySet& rs, int n_views, float4* out,
+                          unsigned long long* stats, cudaStream_t stream) {
+  return stats ? launch_march<TG, true>(A, rs, n_views, out, stats, stream)
+               : launch_march<TG, false>(A, rs, n_views, out, nullptr, stream);
 }
 
 }  // namespace
@@ -229,7 +258,7 @@ extern "C" veg_status veg_volume_prepare(const float* volume, int32_t resolution
 extern "C" veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vol4,
                                    int32_t resolution, veg_tf tf, float step,
                                    const veg_material* material, const float* bg, float* out,
-                                   cudaStream_t stream) {
+                                   unsigned long long* stats, cudaStream_t stream) {
   veg_status st = check_cameras(cams, n_views);
   if (st != VEG_OK) return st;
   if (!vol4 || !out || resolution < 2 || resolution > 2048 || !(step > 0.0f) || !tf.lut ||
@@ -278,8 +307,8 @@ extern "C" veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, cons
   }
   float4* o = reinterpret_cast<float4*>(out);
   const int g = tf.view_tf ? 1 : std::min(tf.n_tf, 8);
-  if (g <= 1) return launch_march<1>(A, rs, n_views, o, stream);
-  if (g <= 2) return launch_march<2>(A, rs, n_views, o, stream);
-  if (g <= 4) return launch_march<4>(A, rs, n_views, o, stream);
-  return launch_march<8>(A, rs, n_views, o, stream);
+  if (g <= 1) return launch_march_s<1>(A, rs, n_views, o, stats, stream);
+  if (g <= 2) return launch_march_s<2>(A, rs, n_views, o, stats, stream);
+  if (g <= 4) return launch_march_s<4>(A, rs, n_views, o, stats, stream);
+  return launch_march_s<8>(A, rs, n_views, o, stats, stream);
 }

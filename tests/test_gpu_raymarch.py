@@ -109,3 +109,22 @@ def test_training_size_on_sampled_pixels():
             assert np.all(np.abs(got[0, t, j, i] - ref[t]) <= IMG_TOL), (i, j, t)
             checked += 1
     assert checked >= 200
+
+
+def test_instrumented_run_is_identical_and_counts_samples():
+    vol = S.field_volume(S.blob_field(4, 110), 17)
+    cams = S.orbit_cameras(2, 111, 40, 28)
+    luts = S.bump_tfs(3, 112)
+    v4 = prepared(vol)
+    plain = march(cams, v4, luts, 0.06, MAT)
+    lt = lut_tensor(luts)
+    out = torch.empty(len(cams), 3, 28, 40, 4, device="cuda")
+    st = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _lib.veg_raymarch(_lib.cameras(cams), v4, _lib.tf_desc(lt), 0.06, out, MAT, stats=st)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), plain)
+    samples, tables = (int(x) for x in st.cpu().numpy())
+    # every sample of a ray evaluates at most the three tables of its group
+    assert 0 < samples <= tables <= 3 * samples
+    # no ray is longer than the box diagonal
+    assert samples <= 2 * 40 * 28 * (2 * 3 ** 0.5 / 0.06 + 1)
