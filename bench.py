@@ -67,8 +67,8 @@ def parse():
     ap.add_argument("--lighting", action="store_true",
                     help="train step with Blinn-Phong shading (headlight, Eq. 2-3)")
     ap.add_argument("--opt-views", type=int, default=16,
-                    help="opt workload: azimuths of the 16 x 10 training orbit (fewer for a "
-                         "small profiling case)")
+                    help="opt and raymarch workloads: azimuths of the 16 x 10 training orbit "
+                         "(fewer, with one elevation, for a small profiling case)")
     ap.add_argument("--opt-densify-every", type=int, default=100,
                     help="opt workload: densify every this many steps during the run "
                          "(0 = off); the paper densifies every 100 iterations")
@@ -763,6 +763,8 @@ def run_opt(args):
         densify_note = (f"every {every} steps (clone/split/prune); Gaussians "
                         + " -> ".join(str(c) for c in counts))
     px = len(cams) * K * size * size
+    cpu = None if args.no_cpu_baseline else cpu_baseline_opt(cams, luts.cpu().numpy(), g0, lt0,
+                                                             targets, args)
     print(json.dumps({
         "workload": "opacity-guided training step: 500k Gaussians from random vertices of a "
                     f"256^3 volume, 800x800, 10 tent maps, {len(cams)} views, Blinn-Phong "
@@ -782,7 +784,81 @@ def run_opt(args):
         "paper_context": "16.8-44.2 steps/s on an A40 for its four datasets (30k iterations "
                          "in 11.3-29.7 min, including densification; the table of evaluation "
                          "results, Sec. 5)",
+        "cpu_baseline": cpu,
         "data": "synthetic"}), flush=True)
+
+
+def cpu_baseline_opt(cams, luts, g, lt, targets, args, n_samples=4, seed=21):
+    """The oracle on a bounded sample of the training step: per sample step
+    one occupied tile of a random (view, map) -- its shaded blend and
+    backward, the L1 + SSIM loss over the tile's window, the projection and
+    shading gradients of its Gaussians -- plus 1/occupied of the projection
+    and of the Adam step; the time x occupied tiles estimates one step."""
+    from oracle import veg_oracle as O
+    from oracle import veg_train_oracle as TO
+    rng = np.random.default_rng(seed)
+    luts = np.asarray(luts, np.float64)
+    tgt = targets.cpu() if hasattr(targets, "cpu") else targets
+    total, occ_sum = 0.0, 0
+    for _ in range(n_samples):
+        v, k = int(rng.integers(len(cams))), int(rng.integers(luts.shape[0]))
+        cam, lut = cams[v], luts[k:k + 1]
+        proj = O.project32(cam, g, lut)
+        ok = proj["count"] > 0
+        x0, y0, x1, y1 = (proj["rect"][ok, c] for c in range(4))
+        d = np.zeros((cam.tiles_y + 1, cam.tiles_x + 1), np.int64)
+        np.add.at(d, (y0, x0), 1)
+        np.add.at(d, (y0, x1), -1)
+        np.add.at(d, (y1, x0), -1)
+        np.add.at(d, (y1, x1), 1)
+        occ = np.nonzero(np.cumsum(np.cumsum(d, 0), 1)[:-1, :-1].ravel())[0]
+        if occ.size == 0:
+            continue
+        tile = int(rng.choice(occ))
+        light = O.headlight(cam)
+        t0 = time.perf_counter()
+        O.project32(cam, g.subset(np.arange(g.n)[: max(1, g.n // occ.size)]), lut)
+        lists = O.tile_lists(proj, cam, [tile])
+        bins = O.bins_from_lists([lists], 1, cam.tiles_x * cam.tiles_y)
+        idx = lists[tile]
+        sub = np.zeros(g.n, bool)
+        sub[idx] = True
+        lighting = lt.as_dict([light])
+        f = O.shade64(cam, light, g.mean_v[:, :3].astype(np.float64)[sub],
+                      lighting["normal"][sub], lighting["ka"][sub], lighting["kd"][sub],
+                      lighting["ks"][sub], lighting["beta"][sub])
+        shade = np.zeros((g.n, 2))
+        shade[sub] = np.stack([f["s_d"], f["s_s"]], 1)
+        proj["shade"] = shade
+        fwd = O.composite_fwd([proj], [cam], bins, lut, tiles=[tile], record=True)
+        px, py = O._tile_pixels(cam, tile)
+        ys, xs = slice(max(0, py.min() - 10), py.max() + 11), slice(max(0, px.min() - 10),
+                                                                     px.max() + 11)
+        t_img = tgt[v, k, ys, xs].numpy().astype(np.float64)
+        _, _, _, gcrop = TO.l1_ssim_loss(fwd["out"][0, 0, ys, xs], t_img)
+        dout = np.zeros_like(fwd["out"])
+        dout[0, 0, ys, xs] = gcrop
+        g2 = O.composite_bwd([proj], [cam], bins, lut, (0, 0, 0), fwd, dout, tiles=[tile])
+        touched = np.nonzero(np.abs(g2[0]).sum(1))[0]
+        if touched.size:
+            pr = {kk: (vv[touched] if isinstance(vv, np.ndarray) and vv.shape[:1] == (g.n,)
+                       else vv) for kk, vv in proj.items()}
+            O.params_grad([cam], g.subset(touched), [pr], g2[:, touched])
+            lt_sub = {kk: (vv[touched] if kk != "lights" else vv) for kk, vv in lighting.items()}
+            O.lighting_grad([cam], g.subset(touched), lt_sub, [pr], g2[:, touched])
+        m = max(1, g.n // occ.size)
+        arr = [rng.normal(0, 1, (m, 4)) for _ in range(5)]
+        TO.adam_step([a.copy() for a in arr], arr, [np.zeros((m, 4))] * 5,
+                     [np.zeros((m, 4))] * 5, np.full((5, 4), 1e-3), 1)
+        total += (time.perf_counter() - t0) * occ.size
+        occ_sum += occ.size
+    step_s = total / max(1, n_samples)
+    return {"value": round(1.0 / step_s, 6), "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_samples} sample steps, each one occupied tile of a random (view, map) "
+                      f"(shaded blend and backward, L1+SSIM over its window, projection and "
+                      f"shading gradients) + 1/occupied of projection and Adam, scaled by the "
+                      f"occupied tiles (mean {occ_sum / max(1, n_samples):.0f}); numpy single "
+                      f"thread"}
 
 
 # FP32 operations (an FMA counts 2) per raymarch sample, from the kernel:
@@ -807,7 +883,8 @@ def run_raymarch(args):
     from paper_2504_13339_gb300.train import opacity_guided_luts
     __graft_entry__.build()
     size, K, R = 800, 10, 256
-    cams = S.grid_orbit_cameras(16, 10, size, size)
+    n_az = args.opt_views
+    cams = S.grid_orbit_cameras(n_az, 10 if n_az >= 16 else 1, size, size)
     lut_np = opacity_guided_luts(K, S.colour_ramp(11))
     luts = lut_tensor(lut_np)
     vol = S.field_volume(S.blob_field(8, 12), R)
@@ -852,9 +929,9 @@ def run_raymarch(args):
     achieved = flops / (ms * 1e-3) / 1e12
     px = len(cams) * K * size * size
     line = {
-        "workload": "raymarched ground truth: 256^3 volume (8-blob field), 160 views x 10 "
-                    "opacity maps, 800x800, emission-absorption, headlight Blinn-Phong, step "
-                    "half the grid spacing",
+        "workload": f"raymarched ground truth: 256^3 volume (8-blob field), {len(cams)} views "
+                    "x 10 opacity maps, 800x800, emission-absorption, headlight Blinn-Phong, "
+                    "step half the grid spacing",
         "metric": "Mpix/s", "value": round(px / (ms * 1e-3) / 1e6, 1), "unit": "Mpix/s",
         "ms_per_set": round(ms, 2), "images": len(cams) * K, "reps": reps, "clocks": clk,
         "work": {"samples": samples, "table_evaluations": tables},
