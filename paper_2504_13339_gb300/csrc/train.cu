@@ -13,8 +13,9 @@
 // One CTA of 256 threads owns a 16 x 16 tile of one image: it stages the
 // 36 x 36 input region (10-pixel halo) of both images, filters the five
 // products over the 26 x 26 region whose statistics the tile's gradient
-// needs (separable: rows, then columns), forms S and the three partials
-// there, filters those back to the tile, and writes the combined gradient.
+// needs (separable: rows, then columns; each thread four outputs from
+// registers), forms S and the three partials there, filters those back to
+// the tile, and writes the combined gradient.
 // Per-CTA sums of |x - y| and S go to a workspace and are reduced in a fixed
 // order by a second kernel, so the loss is deterministic.
 #include <cmath>
@@ -42,9 +43,16 @@ struct LossSmem {
   float h[5][kI * kS];  // row pass of x, y, xx, yy, xy
   float d[3][kS * kS];  // dS/dm1, dS/ds11, dS/ds12 (zero outside the image)
   float e[3][kS * kT];  // row pass of the partials
+  float g[3][kT * kT];  // gradient of the SSIM sum per channel
 };
 
-__global__ void __launch_bounds__(256)
+// Every window pass is register-blocked: a thread computes four consecutive
+// outputs along its row (or column) from 14 staged values, so each loaded
+// value serves up to four outputs and eleven taps.  Three CTAs per SM.
+constexpr int kB = 4;            // outputs per thread and pass
+constexpr int kW = kB + 2 * kR;  // 14 values per thread and pass
+
+__global__ void __launch_bounds__(256, 3)
     l1_ssim_kernel(Window win, const float4* __restrict__ out, const float4* __restrict__ tgt,
                    int H, int W, int tiles_x, float lam, float inv_count,
                    float4* __restrict__ grad, double2* __restrict__ partial) {
@@ -54,7 +62,6 @@ __global__ void __launch_bounds__(256)
   const int tile = blockIdx.x, img = blockIdx.y;
   const int tx0 = (tile % tiles_x) * kT, ty0 = (tile / tiles_x) * kT;
   const int64_t base = (int64_t)img * H * W;
-
   for (int e = tid; e < kI * kI; e += 256) {
     const int r = e / kI, c = e - r * kI;
     const int gy = ty0 - 2 * kR + r, gx = tx0 - 2 * kR + c;
@@ -70,107 +77,148 @@ __global__ void __launch_bounds__(256)
     sm.y[1][e] = b.y;
     sm.y[2][e] = b.z;
   }
-  const int py = tid / kT, px = tid - py * kT;  // this thread's output pixel
-  const bool inside = ty0 + py < H && tx0 + px < W;
-  float g[3];
-  float l1 = 0.f, ssum = 0.f;
-
+  float ssum = 0.f;
   for (int ch = 0; ch < 3; ++ch) {
     __syncthreads();
     const float* X = sm.x[ch];
     const float* Y = sm.y[ch];
-    // row pass of the five products over 36 rows x 26 columns
-    for (int e = tid; e < kI * kS; e += 256) {
-      const int r = e / kS, c = e - r * kS;
-      const float* xr = X + r * kI + c;
-      const float* yr = Y + r * kI + c;
-      float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
+    // row pass of the five products: 36 rows x 26 columns, 7 segments a row
+    if (tid < kI * 7) {
+      const int r = tid / 7, c0 = (tid % 7) * kB;
+      float xv[kW], yv[kW];
 #pragma unroll
-      for (int k = 0; k <= 2 * kR; ++k) {
-        const float a = xr[k], b = yr[k], wk = win.w[k];
-        hx = fmaf(wk, a, hx);
-        hy = fmaf(wk, b, hy);
-        hxx = fmaf(wk, a * a, hxx);
-        hyy = fmaf(wk, b * b, hyy);
-        hxy = fmaf(wk, a * b, hxy);
+      for (int i = 0; i < kW; ++i) {
+        const bool ok = c0 + i < kI;
+        xv[i] = ok ? X[r * kI + c0 + i] : 0.f;
+        yv[i] = ok ? Y[r * kI + c0 + i] : 0.f;
       }
-      sm.h[0][e] = hx;
-      sm.h[1][e] = hy;
-      sm.h[2][e] = hxx;
-      sm.h[3][e] = hyy;
-      sm.h[4][e] = hxy;
-    }
-    __syncthreads();
-    // column pass: statistics, S and its partials over the 26 x 26 region
-    for (int e = tid; e < kS * kS; e += 256) {
-      const int r = e / kS, c = e - r * kS;
-      const int gy = ty0 - kR + r, gx = tx0 - kR + c;
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-        float m1 = 0.f, m2 = 0.f, s11 = 0.f, s22 = 0.f, s12 = 0.f;
+#pragma unroll
+      for (int o = 0; o < kB; ++o) {
+        float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
 #pragma unroll
         for (int k = 0; k <= 2 * kR; ++k) {
-          const int o = (r + k) * kS + c;
-          const float wk = win.w[k];
-          m1 = fmaf(wk, sm.h[0][o], m1);
-          m2 = fmaf(wk, sm.h[1][o], m2);
-          s11 = fmaf(wk, sm.h[2][o], s11);
-          s22 = fmaf(wk, sm.h[3][o], s22);
-          s12 = fmaf(wk, sm.h[4][o], s12);
+          const float a = xv[o + k], b = yv[o + k], wk = win.w[k];
+          hx = fmaf(wk, a, hx);
+          hy = fmaf(wk, b, hy);
+          hxx = fmaf(wk, a * a, hxx);
+          hyy = fmaf(wk, b * b, hyy);
+          hxy = fmaf(wk, a * b, hxy);
         }
-        const float a1 = 2.f * m1 * m2 + kC1;
-        const float a2 = 2.f * (s12 - m1 * m2) + kC2;
-        const float b1 = m1 * m1 + m2 * m2 + kC1;
-        const float b2 = (s11 - m1 * m1) + (s22 - m2 * m2) + kC2;
-        const float ib = 1.0f / (b1 * b2);
-        const float S = a1 * a2 * ib;
-        d0 = 2.f * m2 * (a2 - a1) * ib - 2.f * m1 * S * (1.0f / b1 - 1.0f / b2);
-        d1 = -S / b2;
-        d2 = 2.f * a1 * ib;
-        if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) ssum += S;
+        if (c0 + o < kS) {
+          const int e = r * kS + c0 + o;
+          sm.h[0][e] = hx;
+          sm.h[1][e] = hy;
+          sm.h[2][e] = hxx;
+          sm.h[3][e] = hyy;
+          sm.h[4][e] = hxy;
+        }
       }
-      sm.d[0][e] = d0;
-      sm.d[1][e] = d1;
-      sm.d[2][e] = d2;
     }
     __syncthreads();
-    // row pass of the partials over 26 rows x 16 columns
-    for (int e = tid; e < kS * kT; e += 256) {
-      const int r = e / kT, c = e - r * kT;
-      float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+    // column pass: statistics, S and its partials over the 26 x 26 region,
+    // 7 segments of four rows per column
+    if (tid < kS * 7) {
+      const int c = tid % kS, r0 = (tid / kS) * kB;
+      float st[5][kB];
 #pragma unroll
-      for (int k = 0; k <= 2 * kR; ++k) {
-        const int o = r * kS + c + k;
-        const float wk = win.w[k];
-        q0 = fmaf(wk, sm.d[0][o], q0);
-        q1 = fmaf(wk, sm.d[1][o], q1);
-        q2 = fmaf(wk, sm.d[2][o], q2);
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int o = 0; o < kB; ++o) st[q][o] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        float hv[kW];
+#pragma unroll
+        for (int i = 0; i < kW; ++i) hv[i] = r0 + i < kI ? sm.h[q][(r0 + i) * kS + c] : 0.f;
+#pragma unroll
+        for (int o = 0; o < kB; ++o)
+#pragma unroll
+          for (int k = 0; k <= 2 * kR; ++k) st[q][o] = fmaf(win.w[k], hv[o + k], st[q][o]);
       }
-      sm.e[0][e] = q0;
-      sm.e[1][e] = q1;
-      sm.e[2][e] = q2;
+#pragma unroll
+      for (int o = 0; o < kB; ++o) {
+        const int r = r0 + o;
+        if (r >= kS) break;
+        const int gy = ty0 - kR + r, gx = tx0 - kR + c;
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+          const float m1 = st[0][o], m2 = st[1][o], s11 = st[2][o], s22 = st[3][o];
+          const float s12 = st[4][o];
+          const float a1 = 2.f * m1 * m2 + kC1;
+          const float a2 = 2.f * (s12 - m1 * m2) + kC2;
+          const float b1 = m1 * m1 + m2 * m2 + kC1;
+          const float b2 = (s11 - m1 * m1) + (s22 - m2 * m2) + kC2;
+          const float ib = 1.0f / (b1 * b2);
+          const float S = a1 * a2 * ib;
+          d0 = 2.f * m2 * (a2 - a1) * ib - 2.f * m1 * S * (1.0f / b1 - 1.0f / b2);
+          d1 = -S / b2;
+          d2 = 2.f * a1 * ib;
+          if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) ssum += S;
+        }
+        const int e = r * kS + c;
+        sm.d[0][e] = d0;
+        sm.d[1][e] = d1;
+        sm.d[2][e] = d2;
+      }
     }
     __syncthreads();
-    // column pass at this thread's pixel, gradient of the channel
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+    // row pass of the partials: 26 rows x 16 columns, 4 segments a row
+    if (tid < kS * 4) {
+      const int r = tid / 4, c0 = (tid % 4) * kB;
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const int o = (py + k) * kT + px;
-      const float wk = win.w[k];
-      q0 = fmaf(wk, sm.e[0][o], q0);
-      q1 = fmaf(wk, sm.e[1][o], q1);
-      q2 = fmaf(wk, sm.e[2][o], q2);
+      for (int q = 0; q < 3; ++q) {
+        float dv[kW];
+#pragma unroll
+        for (int i = 0; i < kW; ++i) dv[i] = sm.d[q][r * kS + c0 + i];
+#pragma unroll
+        for (int o = 0; o < kB; ++o) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], dv[o + k], acc);
+          sm.e[q][r * kT + c0 + o] = acc;
+        }
+      }
     }
-    const int io = (py + 2 * kR) * kI + px + 2 * kR;
-    const float xv = X[io], yv = Y[io];
-    const float dssim = q0 + 2.f * xv * q1 + yv * q2;
-    const float diff = xv - yv;
-    const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-    g[ch] = ((1.0f - lam) * sgn - lam * dssim) * inv_count;
-    if (inside) l1 += fabsf(diff);
+    __syncthreads();
+    // column pass of the partials: 16 columns x 4 segments of four rows
+    if (tid < kT * 4) {
+      const int c = tid % kT, r0 = (tid / kT) * kB;
+      float q3[3][kB];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float ev[kW];
+#pragma unroll
+        for (int i = 0; i < kW; ++i) ev[i] = sm.e[q][(r0 + i) * kT + c];
+#pragma unroll
+        for (int o = 0; o < kB; ++o) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], ev[o + k], acc);
+          q3[q][o] = acc;
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < kB; ++o) {
+        const int io = (r0 + o + 2 * kR) * kI + c + 2 * kR;
+        sm.g[ch][(r0 + o) * kT + c] = q3[0][o] + 2.f * X[io] * q3[1][o] + Y[io] * q3[2][o];
+      }
+    }
   }
-  if (inside) grad[base + (int64_t)(ty0 + py) * W + tx0 + px] = make_float4(g[0], g[1], g[2], 0.f);
-
+  __syncthreads();
+  // combine with the L1 part and write this thread's pixel
+  const int py = tid / kT, px = tid - py * kT;
+  float l1 = 0.f;
+  if (ty0 + py < H && tx0 + px < W) {
+    const int io = (py + 2 * kR) * kI + px + 2 * kR;
+    float gg[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float diff = sm.x[ch][io] - sm.y[ch][io];
+      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+      gg[ch] = ((1.0f - lam) * sgn - lam * sm.g[ch][tid]) * inv_count;
+      l1 += fabsf(diff);
+    }
+    grad[base + (int64_t)(ty0 + py) * W + tx0 + px] = make_float4(gg[0], gg[1], gg[2], 0.f);
+  }
   // block sums of |x - y| and S (warp shuffles, then one warp)
   __shared__ float s_red[2][8];
 #pragma unroll
@@ -297,7 +345,8 @@ extern "C" veg_status veg_l1_ssim_loss(const float* out, const float* target, in
     return VEG_ERR_INVALID_ARGUMENT;
   Window win;
   double wsum = 0.0, wd[2 * kR + 1];
-  for (int k = -kR; k <= kR; ++k) wsum += (wd[k + kR] = std::exp(-(double)k * k / (2.0 * 1.5 * 1.5)));
+  for (int k = -kR; k <= kR; ++k)
+    wsum += (wd[k + kR] = std::exp(-(double)k * k / (2.0 * 1.5 * 1.5)));
   for (int k = 0; k <= 2 * kR; ++k) win.w[k] = (float)(wd[k] / wsum);
   const double count = (double)n_images * height * width * 3.0;
   const size_t smem = sizeof(LossSmem);
