@@ -149,7 +149,8 @@ veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int64_t n,
                         int32_t* tile_ranges, cudaStream_t stream);
 
 /*
- * veg_tile_order -- a processing order for the compositing kernels: the
+ * veg_tile_order -- a processing order for the compositing kernels (a
+ * scheduling aid of this library; the paper has no counterpart): the
  * indices 0..count-1 of tile_ranges [count][2] (count = views * tiles), the
  * tiles with the longest lists first (bucketed by floor(log2(length)), empty
  * tiles last).  Passing it to veg_composite_fwd/bwd schedules the heaviest
@@ -312,7 +313,9 @@ veg_status veg_shade(const veg_camera* cams, int32_t n_views, const float* mean_
                      float* splat_shade, cudaStream_t stream);
 
 /*
- * veg_shade_bwd -- chains grad_shade [n_views][n][2] = (dL/ds_d, dL/ds_s), as
+ * veg_shade_bwd -- the backward pass of Eq. 2-3 (Sec. 4.2 trains the normals
+ * and lighting coefficients): chains grad_shade [n_views][n][2] =
+ * (dL/ds_d, dL/ds_s), as
  * written by veg_composite_bwd, through veg_shade and ACCUMULATES (+=) the sum
  * over views into grad_mean_v [n][4] (dL/dmu in xyz; w untouched),
  * grad_normal_beta [n][4] = (dL/dnormal, dL/dbeta) and grad_k_ads [n][4] =
@@ -438,7 +441,8 @@ veg_status veg_densify(const veg_adam_arrays* in, int64_t n, const float* accum,
                        cudaStream_t stream);
 
 /*
- * veg_volume_prepare -- packs a scalar volume for veg_raymarch: volume
+ * veg_volume_prepare -- packs a scalar volume (the gridded data of Sec. 3.1
+ * and 4.1) for veg_raymarch: volume
  * float [R][R][R] (x fastest) of vertex values at x_i = -1 + 2i/(R-1) on
  * each axis of [-1,1]^3; vol4 float4 [R][R][R] receives (value, dv/dx,
  * dv/dy, dv/dz) with central-difference gradients ((v[i+1] - v[i-1]) / 2h,
