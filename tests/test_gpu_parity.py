@@ -363,3 +363,62 @@ def test_full_size_crop_gradients(train_full):
     grad_check(got[1][touched, :3], gl[:, :3], "logscale")
     grad_check(got[1][touched, 3], gl[:, 3], "w")
     grad_check(got[2][touched], gq, "quat")
+
+
+# ----------------------------------------------------------------------------
+# seeded sweep of random small configurations
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_configurations_match_oracle(seed):
+    """Random Gaussian counts, views, ragged image sizes, table counts (every
+    TF-group size), background and shading: tile lists bit-exact, images and
+    every gradient within the bars."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(50, 700))
+    V = int(rng.integers(1, 4))
+    W, H = int(rng.integers(17, 70)), int(rng.integers(17, 70))
+    n_tf = int(rng.choice([1, 2, 3, 5, 8]))
+    g = S.uniform_gaussians(n, 2000 + seed, logscale_mean=float(rng.uniform(-3.3, -2.6)),
+                            logscale_std=0.4)
+    g.logscale_w[:, 3] = rng.uniform(0.2, 1.0, n)
+    cams = S.orbit_cameras(V, 3000 + seed, W, H)
+    tfs = S.bump_tfs(n_tf, 4000 + seed)
+    bg = tuple(float(x) for x in rng.uniform(0.0, 0.3, 3))
+    tf_group = int(rng.choice([0, 1, 2, 4, 8]))
+    lit = seed % 2 == 1
+    lt = S.random_lighting(n, 5000 + seed) if lit else None
+    lights = np.stack([O.headlight(c) for c in cams]) if lit else None
+    p = SplatPipeline(n, cams, n_tf=n_tf, tf_group=tf_group)
+    tens = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
+    luts = lut_tensor(tfs)
+    p.project(*tens, luts)
+    lit_t = None
+    if lit:
+        lit_t = (dev(lt.normal_beta), dev(lt.k_ads))
+        p.shade(tens[0], *lit_t, lights)
+    p.bin_sort(want_keys=True)
+    p.composite(luts, bg)
+    torch.cuda.synchronize()
+    d = lt.as_dict(lights) if lit else None
+    proj, bins, fwd = O.render(cams, g, tfs, bg=bg, record=True, lighting=d)
+    m = int(p.status()[1])
+    assert m == bins["keys"].size
+    assert np.array_equal(p.vals.cpu().numpy()[:m], bins["vals"])
+    image_check(p.out.cpu().numpy(), fwd)
+    dout = np.random.default_rng(6000 + seed).standard_normal(fwd["out"].shape)
+    dout[fwd["flag"]] = 0.0
+    grads = [torch.zeros_like(t) for t in tens]
+    extra = [torch.zeros_like(t) for t in lit_t] if lit else [None, None]
+    p.backward(dev(dout.astype(np.float32)), *grads, *extra)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd(proj, cams, bins, tfs, bg, fwd, dout)
+    gm, gl, gq = O.params_grad(cams, g, proj, g2)
+    if lit:
+        dn, dka, dkd, dks, db, dm = O.lighting_grad(cams, g, d, proj, g2)
+        gm[:, :3] += dm
+        grad_check(extra[0].cpu().numpy()[:, :3], dn, "normal")
+        grad_check(extra[1].cpu().numpy()[:, 1], dkd, "k_d")
+    grad_check(grads[0].cpu().numpy(), gm, "mean_v")
+    grad_check(grads[1].cpu().numpy(), gl, "logscale_w")
+    grad_check(grads[2].cpu().numpy(), gq, "quat")

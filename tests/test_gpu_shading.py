@@ -192,3 +192,71 @@ def test_lit_autograd_function():
     close = lambda x, y: bool(((x - y).abs() <= 1e-5 * y.abs().max() + 1e-4 * y.abs()).all())
     for got, r in zip((mean_v.grad, ls.grad, q.grad, nb.grad, k.grad), ref):
         assert close(got, r)
+
+
+def test_lit_one_table_per_view_matches_oracle():
+    """Shading with one table per view (veg_tf.view_tf): the TG = 1 shaded
+    forward and backward against the oracle rendering each view with its
+    own table."""
+    from paper_2504_13339_gb300 import _lib
+    g, cams, lt = lit_scene(700)
+    tfs = S.bump_tfs(3, 57)
+    view_tf = [2, 0, 1]
+    lights = lights_of(cams, "headlight")
+    p = SplatPipeline(g.n, cams, n_tf=1)
+    tens = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
+    lit = (dev(lt.normal_beta), dev(lt.k_ads))
+    luts = lut_tensor(tfs)
+    vt = torch.as_tensor(np.asarray(view_tf, np.int32), device="cuda")
+    desc = _lib.tf_desc(luts, vt)
+    p.project(*tens, None)
+    p.shade(tens[0], *lit, lights)
+    p.bin_sort()
+    _lib.veg_composite_fwd(p.c_cams, p.n, p.geo, p.aux, p.vals, p.ranges, desc, (0, 0, 0), 0,
+                           p.out, p.n_contrib, tile_order=p.order, splat_shade=p.splat_shade)
+    dout = np.random.default_rng(58).standard_normal(p.out.shape)
+    d = lt.as_dict(lights)
+    refs = []
+    for v, cam in enumerate(cams):
+        dv_ = {**d, "lights": d["lights"][v:v + 1]}
+        proj, bins, fwd = O.render([cam], g, tfs[view_tf[v]:view_tf[v] + 1], cull=False,
+                                   record=True, lighting=dv_)
+        image_check(p.out.cpu().numpy()[v:v + 1], fwd)
+        dd = dout[v:v + 1].copy()
+        dd[fwd["flag"]] = 0.0
+        dout[v:v + 1] = dd
+        refs.append((proj, bins, fwd, dv_, cam))
+    grads = [torch.zeros_like(t) for t in tens]
+    gn, gk = torch.zeros_like(lit[0]), torch.zeros_like(lit[1])
+    _lib.veg_composite_bwd(p.c_cams, p._g, p.geo, p.aux, p.tiles,
+                           p.vals, p.ranges, desc, (0, 0, 0), 0, p.out, p.n_contrib,
+                           dev(dout.astype(np.float32)), None, grads[0], grads[1], grads[2],
+                           p.grad2d, tile_order=p.order, splat_shade=p.splat_shade,
+                           grad_shade=p.grad_shade)
+    _lib.veg_shade_bwd(p.c_cams, tens[0], lit[0], lit[1], lights, p.tiles, p.grad_shade,
+                       grads[0], gn, gk)
+    torch.cuda.synchronize()
+    gm = np.zeros((g.n, 4))
+    gl = np.zeros((g.n, 4))
+    gq = np.zeros((g.n, 4))
+    gnr = np.zeros((g.n, 4))
+    gkr = np.zeros((g.n, 4))
+    for v, (proj, bins, fwd, dv_, cam) in enumerate(refs):
+        t = tfs[view_tf[v]:view_tf[v] + 1]
+        g2 = O.composite_bwd(proj, [cam], bins, t, (0, 0, 0), fwd, dout[v:v + 1])
+        a, b, c = O.params_grad([cam], g, proj, g2)
+        dn, dka, dkd, dks, db, dm = O.lighting_grad([cam], g, dv_, proj, g2)
+        gm += a
+        gm[:, :3] += dm
+        gl += b
+        gq += c
+        gnr[:, :3] += dn
+        gnr[:, 3] += db
+        gkr[:, 0] += dka
+        gkr[:, 1] += dkd
+        gkr[:, 2] += dks
+    grad_check(grads[0].cpu().numpy(), gm, "mean_v")
+    grad_check(grads[1].cpu().numpy(), gl, "logscale_w")
+    grad_check(grads[2].cpu().numpy(), gq, "quat")
+    grad_check(gn.cpu().numpy(), gnr, "normal_beta")
+    grad_check(gk.cpu().numpy(), gkr, "k_ads")
