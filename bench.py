@@ -146,6 +146,11 @@ def setup_train(args, device):
     p.render(*tens, luts)  # sizes the instance capacity for this scene
     _, m = p.status()
     p.set_capacity(int(m * 1.15) + 4096)
+    # TF group sizes for this shape (autotuner, untimed; cached per shape)
+    from paper_2504_13339_gb300 import autotune
+    p.render(*tens, luts)
+    p.l1(target)
+    p.tuned = autotune.tune(p, luts, dout=p.loss_grad)
     grads = [torch.zeros_like(x) for x in tens]
     lighting = None
     if getattr(args, "lighting", False):
@@ -343,6 +348,8 @@ def run_gpu(args):
                    "n_gaussians": g.n, "width": cams[0].width,
                    "height": cams[0].height, "n_tf": len(tfs), "views": len(cams),
                    "tile_instances": int(m), "l2": "flushed between timed steps (512 MB write)",
+                   "tf_group": {"fwd": p.tuned["fwd"], "bwd": p.tuned["bwd"],
+                                "source": "autotuned at setup (untimed)"},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "mpix_per_s": round(mpix, 2),
         "stages_ms": {"composite_fwd": round(fwd_avg, 4), "composite_bwd": round(bwd_avg, 4),

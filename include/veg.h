@@ -220,7 +220,8 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  * tile_order: optional device int32 [V * tiles] from veg_tile_order (the
  * order in which tiles are scheduled; NULL = row-major; results do not
  * depend on it).
- * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default).
+ * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default, 1;
+ * the autotuner of the Python package picks per shape).
  * splat_shade: optional device float [V][n][2] of Blinn-Phong factors
  * (s_d, s_s) from veg_shade (8-byte aligned); when given, each splat is
  * blended with the colour s_d rgb + s_s of Eq. 2 instead of rgb.  Opacity,

@@ -695,9 +695,13 @@ size_t bwd_smem_bytes(int TG, int L, bool lit) {
          (size_t)kWarps * kBatch;
 }
 
+// TF group size: the caller's choice, else 1 for the forward (measured
+// fastest at the training-step and sweep shapes: each TF stops at its own
+// termination) and up to 4 for the backward (whose replay shares each
+// splat's geometry and reductions across the group).
 int pick_group(int tf_group, int n_tf, bool bwd) {
   int g = tf_group;
-  if (g <= 0) g = std::min(n_tf, 4);
+  if (g <= 0) g = bwd ? std::min(n_tf, 4) : 1;
   if (g <= 1) return 1;
   if (g <= 2) return 2;
   if (g <= 4 || bwd) return 4;
