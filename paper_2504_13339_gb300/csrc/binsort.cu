@@ -11,7 +11,8 @@
 // A stable sort by tile of a sequence already ordered by (depth, index)
 // yields (view, tile, depth, index) order.  Records that touch no tile
 // (culled) are dropped first by a stable compaction, so only the visible
-// ones are depth-sorted.  Both stages use one hand-written LSD radix sort
+// ones are depth-sorted (inputs of at most 2^16 records instead sort the
+// culled ones last: the same order with fewer launches).  Both stages use one hand-written LSD radix sort
 // (reduce / scan / stable scatter, 8-bit digits, 2048-item chunks, grid-
 // stride blocks).  The visible and instance counts live only on the device;
 // later kernels read them from the workspace header, so no host round trip
@@ -27,6 +28,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTileItems = kThreads * kItems;  // 2048 items per radix block
+constexpr int64_t kSmallRecords = 1 << 16;      // below: no compaction before the sort
 
 // Number of items to process: a fixed count, or min(*dev, cap).
 struct Count {
@@ -238,6 +240,18 @@ __global__ void __launch_bounds__(kThreads, 4)
 // ---------------------------------------------------------------------------
 // binning kernels
 // ---------------------------------------------------------------------------
+
+// Depth keys of all records, culled ones (touching no tile) as 0xffffffff so
+// that the stable sort puts them last: the path for small inputs, where one
+// launch costs more than sorting the culled records.
+__global__ void depth_keys_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
+                                  int64_t nrec, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrec) return;
+  keys[i] = tiles[i] > 0 ? __float_as_uint(geo[i].z) : 0xffffffffu;
+  vals[i] = (uint32_t)i;
+}
 
 // Per-chunk counts of the records that touch a tile (index order).
 __global__ void __launch_bounds__(kThreads)
@@ -598,13 +612,20 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
     return launch_status();
   }
   // 1. the visible records (touching a tile) in index order, then their
-  //    depth sort
-  visible_count_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, nrec, L.bsum);
-  chunk_scan_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, &L.hdr->n_visible);
-  visible_scatter_kernel<<<L.nb_rec, kThreads, 0, stream>>>(geo, tiles, nrec, L.bsum, L.dk0,
-                                                            L.dv0);
-  count_launch(3);
+  //    depth sort; small inputs sort every record with culled ones last
+  //    (same order, fewer launches)
   Count cr{0, &L.hdr->n_visible, nrec};
+  if (nrec <= kSmallRecords) {
+    depth_keys_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(geo, tiles, nrec, L.dk0, L.dv0);
+    count_launch();
+    cr = Count{nrec, nullptr, 0};
+  } else {
+    visible_count_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, nrec, L.bsum);
+    chunk_scan_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, &L.hdr->n_visible);
+    visible_scatter_kernel<<<L.nb_rec, kThreads, 0, stream>>>(geo, tiles, nrec, L.bsum, L.dk0,
+                                                              L.dv0);
+    count_launch(3);
+  }
   radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 0, 8, L.nb_rec, L, stream);
   radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 8, 8, L.nb_rec, L, stream);
   radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 16, 8, L.nb_rec, L, stream);
