@@ -5,7 +5,8 @@ Default workload (the training step): 1M Gaussians sampled from an 8-blob
 scalar field, one 1024x1024 view, 4 transfer functions, L1 loss against a
 target rendered from a perturbed copy.  A step is one pass of the whole hot
 path: projection, tile binning + radix sort, compositing of all 4 TFs, L1
-loss, compositing backward, projection backward.  Inputs are resident in HBM
+loss, compositing backward, projection backward, and the Adam step on the
+raw parameters (sigmoid-activated scalar and weight).  Inputs are resident in HBM
 when the timed region starts; L2 is flushed (512 MB write) between timed
 steps, outside the timed spans.  Prints one JSON line.
 
@@ -33,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpix/s render & train steps/s, p50/p99 serve latency vs plain path, same GB300"
 WORKLOAD = ("train step: 1M blob-field Gaussians (8 blobs), 1024x1024, 4 TFs, L1 vs "
-            "perturbed-copy target; project+bin/sort+composite fwd+L1+composite bwd+project bwd")
+            "perturbed-copy target; project+bin/sort+composite fwd+L1+composite bwd+project bwd"
+            "+Adam")
 FP32_LANES_PER_SM = 128
 
 # FP32 operations per work unit (an FMA counts 2), taken from the kernels'
@@ -130,6 +132,27 @@ class ClockSampler:
 # GPU arm
 # ----------------------------------------------------------------------------
 
+class StepModel:
+    """The trained model of the training step: raw parameters with Adam
+    state (sigmoid-activated v and w), the rendered arrays, gradients, and
+    optionally the Blinn-Phong lighting parameters with headlights."""
+
+    def __init__(self, g, cams, lighting=None):
+        from paper_2504_13339_gb300.render import headlight_dirs
+        from paper_2504_13339_gb300.train import TrainParams, default_lr
+        self.P = TrainParams(g, lighting)
+        self.lr = default_lr(lighting=lighting is not None)
+        self.lights = headlight_dirs(cams) if lighting is not None else None
+
+    @property
+    def tens(self):
+        return self.P.rendered()
+
+    @property
+    def grads(self):
+        return self.P.grads
+
+
 def setup_train(args, device):
     import torch
 
@@ -138,35 +161,31 @@ def setup_train(args, device):
 
     g, tgt_g, cams, tfs = S.train_scene(n=args.n, width=args.width)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=device)
-    tens = (t(g.mean_v), t(g.logscale_w), t(g.quat))
+    lt = S.random_lighting(g.n, 3) if getattr(args, "lighting", False) else None
+    model = StepModel(g, cams, lt)
     luts = lut_tensor(tfs, device)
     p = SplatPipeline(g.n, cams, n_tf=len(tfs), capacity=8 * g.n)
     # target: render of the perturbed copy (synthetic input data)
     target = p.render(t(tgt_g.mean_v), t(tgt_g.logscale_w), t(tgt_g.quat), luts).clone()
-    p.render(*tens, luts)  # sizes the instance capacity for this scene
+    p.render(*model.tens, luts)  # sizes the instance capacity for this scene
     _, m = p.status()
-    p.set_capacity(int(m * 1.15) + 4096)
+    p.set_capacity(int(m * 1.25) + 4096)  # headroom: the model trains during the run
     # TF group sizes for this shape (autotuner, untimed; cached per shape)
     from paper_2504_13339_gb300 import autotune
-    p.render(*tens, luts)
+    p.render(*model.tens, luts)
     p.l1(target)
     p.tuned = autotune.tune(p, luts, dout=p.loss_grad)
-    grads = [torch.zeros_like(x) for x in tens]
-    lighting = None
-    if getattr(args, "lighting", False):
-        from paper_2504_13339_gb300.render import headlight_dirs
-        lt = S.random_lighting(g.n, 3)
-        lighting = (t(lt.normal_beta), t(lt.k_ads), headlight_dirs(cams))
-        grads += [torch.zeros_like(lighting[0]), torch.zeros_like(lighting[1])]
-    return p, tens, luts, target, grads, cams, tfs, g, m, lighting
+    return p, model, luts, target, cams, tfs, g, m
 
 
-def gpu_step(p, tens, luts, target, grads, ev=None, lighting=None):
-    for gb in grads:
-        gb.zero_()
-    p.project(*tens, luts)
-    if lighting is not None:
-        p.shade(tens[0], *lighting)
+def gpu_step(p, model, luts, target, ev=None):
+    """One training step: projection, (shading,) binning, compositing, L1,
+    compositing backward, projection (and shading) backward, Adam."""
+    P = model.P
+    P.zero_grad()
+    p.project(*model.tens, luts)
+    if model.lights is not None:
+        p.shade(P.mean_v, P.raw[3], P.raw[4], model.lights)
     p.bin_sort()
     if ev is not None:
         ev[0].record()
@@ -179,9 +198,10 @@ def gpu_step(p, tens, luts, target, grads, ev=None, lighting=None):
     p.backward_2d(p.loss_grad)
     if ev is not None:
         ev[3].record()
-    p.project_backward(*grads[:3])
-    if lighting is not None:
-        p.shade_backward(grads[0], grads[3], grads[4])
+    p.project_backward(*P.grads[:3])
+    if model.lights is not None:
+        p.shade_backward(P.grads[0], P.grads[3], P.grads[4])
+    P.adam(model.lr)
 
 
 def source_hash(*names):
@@ -242,7 +262,8 @@ def run_gpu(args):
         dist.barrier()
     _lib.load()
 
-    p, tens, luts, target, grads, cams, tfs, g, m, lighting = setup_train(args, device)
+    p, model, luts, target, cams, tfs, g, m = setup_train(args, device)
+    lighting = model.lights
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
 
@@ -252,7 +273,7 @@ def run_gpu(args):
             dist.barrier()
 
     for _ in range(max(args.warmup, 3)):
-        gpu_step(p, tens, luts, target, grads, lighting=lighting)
+        gpu_step(p, model, luts, target)
     st, m2 = p.status()
     assert st == _lib.VEG_OK, "instance capacity overflow during warm-up"
 
@@ -267,11 +288,14 @@ def run_gpu(args):
         flush.zero_()
         e = evs[k]
         e[4].record(stream)
-        gpu_step(p, tens, luts, target, grads, ev=e[:4], lighting=lighting)
+        gpu_step(p, model, luts, target, ev=e[:4])
         e[5].record(stream)
     barrier()
     launches = _lib.veg_kernel_launches() - launches0
     clk = clocks.stop()
+    st_end, m_end = p.status()
+    assert st_end == _lib.VEG_OK, "instance capacity overflow during the timed steps"
+
     step_ms = [e[4].elapsed_time(e[5]) for e in evs]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
@@ -289,7 +313,7 @@ def run_gpu(args):
         ev2[k][0].record(stream)
         target.copy_(tgt_host, non_blocking=True)
         luts.copy_(lut_host, non_blocking=True)
-        gpu_step(p, tens, luts, target, grads, lighting=lighting)
+        gpu_step(p, model, luts, target)
         loss_host.copy_(p.loss, non_blocking=True)
         ev2[k][1].record(stream)
     barrier()
@@ -303,7 +327,7 @@ def run_gpu(args):
     fst = torch.zeros(len(FWD_FLOPS), dtype=torch.int64, device=device)
     bst = torch.zeros(len(BWD_FLOPS), dtype=torch.int64, device=device)
     p.unshade()
-    p.project(*tens, luts)
+    p.project(*model.tens, luts)
     p.bin_sort()
     p.composite(luts, stats=fst)
     p.l1(target)
@@ -347,7 +371,8 @@ def run_gpu(args):
                                            "its backward" if lighting is not None else ""),
                    "n_gaussians": g.n, "width": cams[0].width,
                    "height": cams[0].height, "n_tf": len(tfs), "views": len(cams),
-                   "tile_instances": int(m), "l2": "flushed between timed steps (512 MB write)",
+                   "tile_instances": int(m), "tile_instances_after_timing": int(m_end),
+                   "l2": "flushed between timed steps (512 MB write)",
                    "tf_group": {"fwd": p.tuned["fwd"], "bwd": p.tuned["bwd"],
                                 "source": "autotuned at setup (untimed)"},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -405,6 +430,14 @@ class OracleSample:
         self.occupied = int(occ.size)
         self.order = np.random.default_rng(seed).permutation(occ)
         self.k = 0
+        # the Adam step's share: 1/occupied of the Gaussians' three arrays
+        from oracle import veg_train_oracle as TO
+        self.TO = TO
+        m = max(1, self.g.n // self.occupied)
+        rng = np.random.default_rng(seed + 1)
+        self.adam = ([rng.normal(0, 1, (m, 4)) for _ in range(3)],
+                     [rng.normal(0, 1, (m, 4)) for _ in range(3)],
+                     [np.zeros((m, 4)) for _ in range(3)], [np.zeros((m, 4)) for _ in range(3)])
 
     def step(self):
         O, cam, g = self.O, self.cams[0], self.g
@@ -430,6 +463,8 @@ class OracleSample:
             prs = {k: (v[touched] if isinstance(v, np.ndarray) and v.shape[:1] == (g.n,) else v)
                    for k, v in self.proj.items()}
             O.params_grad(self.cams, g.subset(touched), [prs], g2[:, touched])
+        pa, ga, ma, va = self.adam
+        self.TO.adam_step(pa, ga, ma, va, np.full((3, 4), 1e-3), self.k)
 
 
 def cpu_baseline(args):
@@ -444,8 +479,8 @@ def cpu_baseline(args):
     return {"value": round(1.0 / full, 6), "unit": "steps/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} of {s.occupied} occupied tiles (each: 1/{s.occupied} of the "
                       f"projection, the tile's lists, blend of {len(s.tfs)} TFs, target, L1, "
-                      f"blend backward, projection backward), scaled by {s.occupied}; "
-                      f"numpy single thread"}
+                      f"blend backward, projection backward, 1/{s.occupied} of the Adam step), "
+                      f"scaled by {s.occupied}; numpy single thread"}
 
 
 def run_reference(args):
