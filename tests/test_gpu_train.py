@@ -209,19 +209,28 @@ def test_training_reduces_the_loss():
 
 
 def test_native_step_equals_the_python_sequence():
-    """veg_train_step issues the same stages as the Python sequence: after
-    three iterations (same views and maps) the parameters agree up to the
-    order of the backward's float atomics."""
+    """veg_train_step issues the same stages as the Python sequence: the
+    loss and every gradient of an iteration agree up to the order of the
+    backward's float atomics, and the parameters after three iterations
+    agree within two Adam steps (an element whose gradient is near zero may
+    step either way when the summation order differs)."""
+    from paper_2504_13339_gb300.train import default_lr
     g, lt, cams, luts, tg = small_training_set(seed=95)
     runs = []
     for native in (True, False):
         P = TrainParams(g, lt)
         T = OpacityGuidedTrainer(P, cams, lut_tensor(luts), dev(tg), native=native)
-        for v, k in ((0, 1), (1, 2), (1, 0)):
+        T.step(view=0, k=1)
+        torch.cuda.synchronize()
+        first = (float(T.loss[0]), [x.cpu().numpy() for x in P.grads])
+        for v, k in ((1, 2), (1, 0)):
             T.step(view=v, k=k)
         torch.cuda.synchronize()
-        runs.append(([x.cpu().numpy() for x in P.raw], float(T.loss[0])))
-    (a, la), (b, lb) = runs
-    assert la == pytest.approx(lb, rel=1e-5)
-    for x, y in zip(a, b):
-        assert np.allclose(x, y, rtol=1e-5, atol=1e-6)
+        runs.append((first, [x.cpu().numpy() for x in P.raw]))
+    ((la, ga), pa), ((lb, gb), pb) = runs
+    assert la == pytest.approx(lb, rel=1e-6)
+    for x, y in zip(ga, gb):
+        assert np.abs(x - y).max() <= 1e-4 * np.abs(y).max()
+    lr = default_lr()
+    for a, (x, y) in enumerate(zip(pa, pb)):
+        assert np.all(np.abs(x - y) <= 2 * 3 * lr[a][None, :] + 1e-6), a
