@@ -46,6 +46,17 @@ __device__ __forceinline__ float power_of(float dx, float dy, float na, float nb
   return __fmaf_rn(na, mul(dx, dx), __fmaf_rn(nc, mul(dy, dy), mul(nb, mul(dx, dy))));
 }
 
+// The same exponent from the splat centre (ux, uy) and the pixel pxy, with
+// the offsets d = u - p and their squares d2 formed as float32 pairs (same
+// rounding as the scalar form); also returns dxy = dx dy.
+__device__ __forceinline__ float power_at(float ux, float uy, float2 pxy, float na, float nb,
+                                          float nc, float2& d, float2& d2, float& dxy) {
+  d = sub2(make_float2(ux, uy), pxy);
+  d2 = mul2(d, d);
+  dxy = mul(d.x, d.y);
+  return __fmaf_rn(na, d2.x, __fmaf_rn(nc, d2.y, mul(nb, dxy)));
+}
+
 // Lowest exponent at which some TF of the group can still reach alpha >=
 // 1/255: alpha = A w G <= max_t(A_t w) e^power, which stays below 1/255 for
 // power < ln(1/(255 max_t A_t w)).  The bound is lowered by 1e-3 to absorb
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
   const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
   const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
   const bool inside = px < A.width && py < A.height;
-  const float fx = (float)px, fy = (float)py;
+  const float2 fxy = make_float2((float)px, (float)py);
   const int2 rg = A.ranges[wi];
   float T[TG], Cr[TG], Cg[TG], Cb[TG];
   int last[TG];
@@ -303,8 +314,10 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
       const int j0 = s_list[warp][k], j1 = s_list[warp][k + 1];
       const float4 g0 = s_geo[j0], g1 = s_geo[j1];
       const float2 c0 = s_c[j0], c1 = s_c[j1];
-      const float p0 = power_of(sub(g0.x, fx), sub(g0.y, fy), g0.z, g0.w, c0.x);
-      const float p1 = power_of(sub(g1.x, fx), sub(g1.y, fy), g1.z, g1.w, c1.x);
+      float2 d0, d1, q0, q1;
+      float x0, x1;
+      const float p0 = power_at(g0.x, g0.y, fxy, g0.z, g0.w, c0.x, d0, q0, x0);
+      const float p1 = power_at(g1.x, g1.y, fxy, g1.z, g1.w, c1.x, d1, q1, x1);
       const bool e0 = !(p0 < c0.y || p0 > 0.0f), e1 = !(p1 < c1.y || p1 > 0.0f);
       if (STATS) {
         n_it += 2;
@@ -317,7 +330,9 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
       const int j = s_list[warp][k];
       const float4 sg = s_geo[j];
       const float2 sc = s_c[j];
-      const float power = power_of(sub(sg.x, fx), sub(sg.y, fy), sg.z, sg.w, sc.x);
+      float2 d, d2;
+      float dxy;
+      const float power = power_at(sg.x, sg.y, fxy, sg.z, sg.w, sc.x, d, d2, dxy);
       if (STATS) ++n_it;
       if (!(power < sc.y || power > 0.0f)) {
         if (STATS) ++n_eval;
@@ -495,7 +510,7 @@ __global__ void __launch_bounds__(256, 3)
   const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
   const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
   const bool inside = px < A.width && py < A.height;
-  const float fx = (float)px, fy = (float)py;
+  const float2 fxy = make_float2((float)px, (float)py);
   const int2 rg = A.ranges[wi];
 
   float T[TG], S[TG], K[TG], gr[TG], gg[TG], gb[TG], gs[TG];
@@ -587,13 +602,13 @@ __global__ void __launch_bounds__(256, 3)
       }
     };
     // gradient parts of one pair: u_x, u_y, conic a, b, c, v, w (and s_d)
-    auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float dx, float dy, float dvv,
+    auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float2 d, float dvv,
                           float dww, float dsd) {
-      v[0] = dp * (2.0f * sg.z * dx + sg.w * dy);
-      v[1] = dp * (2.0f * sc * dy + sg.w * dx);
-      v[2] = dp * (-0.5f * dx * dx);
-      v[3] = dp * (-dx * dy);
-      v[4] = dp * (-0.5f * dy * dy);
+      v[0] = dp * (2.0f * sg.z * d.x + sg.w * d.y);
+      v[1] = dp * (2.0f * sc * d.y + sg.w * d.x);
+      v[2] = dp * (-0.5f * d.x * d.x);
+      v[3] = dp * (-d.x * d.y);
+      v[4] = dp * (-0.5f * d.y * d.y);
       v[5] = dvv;
       v[6] = dww;
       v[7] = LIT ? dsd : 0.0f;
@@ -611,10 +626,10 @@ __global__ void __launch_bounds__(256, 3)
       if (STATS) n_it += 1 + (unsigned)has1;
       const float4 sg0 = s_geo[j0], sg1 = s_geo[j1];
       const float2 sc0 = s_c[j0], sc1 = s_c[j1];
-      const float dx0 = sub(sg0.x, fx), dy0 = sub(sg0.y, fy);
-      const float dx1 = sub(sg1.x, fx), dy1 = sub(sg1.y, fy);
-      const float p0 = power_of(dx0, dy0, sg0.z, sg0.w, sc0.x);
-      const float p1 = power_of(dx1, dy1, sg1.z, sg1.w, sc1.x);
+      float2 d0, d1, q0, q1;
+      float x0, x1;
+      const float p0 = power_at(sg0.x, sg0.y, fxy, sg0.z, sg0.w, sc0.x, d0, q0, x0);
+      const float p1 = power_at(sg1.x, sg1.y, fxy, sg1.z, sg1.w, sc1.x, d1, q1, x1);
       const bool ev0 = idx0 < my_max && p0 <= 0.0f && p0 >= sc0.y;
       const bool ev1 = has1 && idx1 < my_max && p1 <= 0.0f && p1 >= sc1.y;
       const float G0 = ev0 ? gauss_of(p0) : 0.f;
@@ -630,8 +645,8 @@ __global__ void __launch_bounds__(256, 3)
       if (LIT) nz = nz || dd0 != 0.f || ds0 != 0.f || dd1 != 0.f || ds1 != 0.f;
       if (__any_sync(0xffffffffu, nz)) {
         float v[16];
-        pair_parts(v, dp0, sg0, sc0.x, dx0, dy0, dv0, dw0, dd0);
-        pair_parts(v + 8, dp1, sg1, sc1.x, dx1, dy1, dv1, dw1, dd1);
+        pair_parts(v, dp0, sg0, sc0.x, d0, dv0, dw0, dd0);
+        pair_parts(v + 8, dp1, sg1, sc1.x, d1, dv1, dw1, dd1);
         // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
         const float r = warp_reduce_scatter16(v, lane);
         const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
