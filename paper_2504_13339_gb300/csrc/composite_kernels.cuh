@@ -65,7 +65,20 @@ __device__ __forceinline__ float power_at(float ux, float uy, float2 pxy, float 
 // never changes a decision.  With max_t A_t w < 1/255 no pair can blend.
 __device__ __forceinline__ float power_cutoff(float max_aw) {
   if (!(max_aw >= kAlphaMin)) return 1.0f;
-  return __logf(kAlphaMin / max_aw) - 1e-3f;
+  return __logf(kAlphaMin) - __logf(max_aw) - 1e-3f;
+}
+
+// Hardware approximations (relative error of a few 1e-7), used only where
+// a bound carries a far wider margin.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Minimum of q(d) = a dx^2 + 2 b dx dy + c dy^2 (a, c > 0, positive
@@ -76,7 +89,7 @@ __device__ __forceinline__ float conic_min_over_rect(float a, float b, float c, 
                                                      float x1, float y0, float y1) {
   if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) return 0.0f;
   auto qf = [&](float x, float y) { return a * x * x + 2.0f * b * x * y + c * y * y; };
-  const float ia = 1.0f / a, ic = 1.0f / c;
+  const float ia = rcp_approx(a), ic = rcp_approx(c);
   float m = qf(x0, fminf(fmaxf(-b * x0 * ic, y0), y1));
   m = fminf(m, qf(x1, fminf(fmaxf(-b * x1 * ic, y0), y1)));
   m = fminf(m, qf(fminf(fmaxf(-b * y0 * ia, x0), x1), y0));
@@ -101,9 +114,9 @@ __device__ __forceinline__ unsigned warp_block_mask(float rx, float ry, float a,
   if (!(cut < 0.0f)) return 0u;
   const float det = a * c - b * b;
   if (!(det > 1e-3f * a * c)) return 0xffu;
-  const float r2 = -2.0f * cut;
-  const float hx = sqrtf(r2 * c / det) * 1.002f + 0.02f;
-  const float hy = sqrtf(r2 * a / det) * 1.002f + 0.02f;
+  const float r2 = -2.0f * cut, r2_det = r2 * rcp_approx(det);
+  const float hx = sqrt_approx(r2_det * c) * 1.002f + 0.02f;
+  const float hy = sqrt_approx(r2_det * a) * 1.002f + 0.02f;
   const float r2m = r2 * 1.002f + 1e-4f;
   const float x0 = rx - hx, x1 = rx + hx, y0 = ry - hy, y1 = ry + hy;
   unsigned m = 0u;
@@ -133,20 +146,29 @@ __device__ __forceinline__ unsigned lanemask_lt_() {
 }
 
 // Compacts the batch positions whose mask has this warp's bit, in order.
-__device__ __forceinline__ int build_warp_list(const unsigned char* s_mask, unsigned char* list,
-                                               int cnt) {
+// Lane l reads the masks of positions 8l .. 8l + 7 as one 64-bit word
+// (positions past the batch's count hold empty masks); an exclusive warp
+// scan of the per-lane hit counts places each lane's hits in the list.
+static_assert(kBatch == 32 * 8, "one 64-bit mask word per lane");
+__device__ __forceinline__ int build_warp_list(const unsigned char* s_mask, unsigned char* list) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = lanemask_lt_();
-  int n = 0;
-  for (int c = 0; c < cnt; c += 32) {
-    const int j = c + lane;
-    const bool hit = j < cnt && ((s_mask[j] >> warp) & 1u);
-    const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    if (hit) list[n + __popc(bal & lt)] = (unsigned char)j;
-    n += __popc(bal);
+  const unsigned long long m = reinterpret_cast<const unsigned long long*>(s_mask)[lane];
+  unsigned long long bits = (m >> warp) & 0x0101010101010101ull;  // bit 8k: position 8l + k
+  const int c = __popcll(bits);
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  int pos = incl - c;
+  while (bits) {
+    const int b = __ffsll((long long)bits) - 1;
+    list[pos++] = (unsigned char)(8 * lane + (b >> 3));
+    bits &= bits - 1;
   }
   __syncwarp();
-  return n;
+  return __shfl_sync(0xffffffffu, incl, 31);
 }
 
 __device__ __forceinline__ void pixel_of(int tile, int tiles_x, int& px, int& py) {
@@ -245,7 +267,7 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
   __shared__ float4 s_geo[kBatch];   // u_x, u_y, -a/2, -b
   __shared__ float2 s_c[kBatch];     // -c/2, exponent cutoff
   __shared__ float4 s_col[TG * kBatch];
-  __shared__ unsigned char s_mask[kBatch];
+  __shared__ __align__(8) unsigned char s_mask[kBatch];
   __shared__ unsigned char s_list[kWarps][kBatch];
   const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
   const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
@@ -279,8 +301,10 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : 4))
     if ((int)threadIdx.x < cnt)
       stage_splat<TG, false, LIT>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col,
                                     nullptr, nullptr, nullptr, s_mask);
+    else
+      s_mask[threadIdx.x] = 0;
     __syncthreads();
-    const int nw = build_warp_list(s_mask, s_list[warp], cnt);
+    const int nw = build_warp_list(s_mask, s_list[warp]);
     const bool act0 = act != 0u;
     int jstop = cnt;  // 1 + batch position where this pixel terminated
     // Eq. 1 update of every live TF of the group with splat j (exponent G).
@@ -552,15 +576,16 @@ __global__ void __launch_bounds__(256, 3)
 
   for (int start = rg.x; start < rg.x + block_max; start += kBatch) {
     const int i = start + threadIdx.x;
-    const int cnt = min(kBatch, rg.y - start);
     uint32_t my_rec = 0;
     if (i < rg.y) {
       my_rec = stage_splat<TG, true, LIT>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col, s_slope, s_A,
                                           s_sh, s_mask);
       if (!LIT) s_idx[threadIdx.x] = my_rec;
+    } else {
+      s_mask[threadIdx.x] = 0;
     }
     __syncthreads();
-    const int nw = build_warp_list(s_mask, my_list, cnt);
+    const int nw = build_warp_list(s_mask, my_list);
     // replayed blend of splat j at list position idx for every TF of the
     // group: accumulates dL/dG, dL/dv, dL/dw (and dL/ds_d, dL/ds_s) of this
     // pixel
