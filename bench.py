@@ -780,9 +780,14 @@ def run_opt(args):
           if every > 0 else None)
     T = OpacityGuidedTrainer(P, cams, luts, targets, seed=14, capacity=16 * n0, density=dc)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    # held-out score: 32 fixed (view, map) pairs, evaluated untimed
+    hr = np.random.default_rng(16)
+    held = list(zip(hr.integers(len(cams), size=32), hr.integers(K, size=32)))
+    eval_init = T.evaluate(held)
     for _ in range(max(args.warmup, 3)):
         T.step()
     assert not T.overflowed()
+    eval_start = T.evaluate(held)
     Kst = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(Kst)]
@@ -791,17 +796,30 @@ def run_opt(args):
     clocks = ClockSampler(0)
     torch.cuda.synchronize()
     clocks.start()
+    densified = []  # timed steps that densified
     for k in range(Kst):
         flush.zero_()
+        n_events = len(dc.history) if dc is not None else 0
         ev[k][0].record()
         T.step()
         ev[k][1].record()
         losses.append(T.loss[0].clone())
+        if dc is not None and len(dc.history) != n_events:
+            densified.append(k)
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = _lib.veg_kernel_launches() - launches0
     assert not T.overflowed(), "instance capacity overflow while timing"
-    ms = float(np.sum([x.elapsed_time(y) for x, y in ev]))
+    step_ms = np.array([x.elapsed_time(y) for x, y in ev])
+    ms = float(step_ms.sum())
+    # a densifying step and the next one (which rebuilds the executor's
+    # arguments) against the median of the other steps
+    near = set(densified) | {k + 1 for k in densified}
+    others = [t for k, t in enumerate(step_ms) if k not in near]
+    med = float(np.median(others)) if others else float("nan")
+    event_ms = [float(step_ms[k] + (step_ms[k + 1] if k + 1 < Kst else med) - 2 * med)
+                for k in densified]
+    eval_end = T.evaluate(held)
     lo = torch.stack(losses).cpu().numpy()
     q = max(1, Kst // 10)
     densify_note = "off"
@@ -821,8 +839,13 @@ def run_opt(args):
         "ms_per_step": round(ms / Kst, 4), "steps": Kst, "warmup": max(args.warmup, 3),
         "gpu_launches_per_step": round(launches / Kst, 1), "clocks": clk,
         "densify": densify_note,
+        "densify_event_ms": (round(float(np.mean(event_ms)), 3) if event_ms else None),
+        "median_step_ms": round(med, 4),
         "loss_first_tenth": round(float(lo[:q].mean()), 5),
         "loss_last_tenth": round(float(lo[-q:].mean()), 5),
+        "held_out_loss": {"pairs": "32 fixed random (view, map) pairs, untimed",
+                          "initial": round(eval_init, 5), "before_timed": round(eval_start, 5),
+                          "after_timed": round(eval_end, 5)},
         "targets": {"renderer": "veg_raymarch (emission-absorption, headlight Blinn-Phong, "
                                 "step = half the grid spacing)",
                     "images": len(cams) * K, "ms": round(march_ms, 2),

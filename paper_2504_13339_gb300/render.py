@@ -50,10 +50,10 @@ class SplatPipeline:
         self.c_cams = _lib.cameras(self.cams)
         nrec = self.V * self.n
         dev = self.device
-        self.geo = torch.empty(nrec, 4, device=dev)
-        self.aux = torch.empty(nrec, 4, device=dev)
-        self.tiles = torch.empty(nrec, dtype=torch.int32, device=dev)
-        self.rect = torch.empty(nrec, 4, dtype=torch.int16, device=dev)
+        self.splat_shade = None
+        self.grad_shade = None
+        self._shade_rows = None
+        self._records(self.n)
         self.tiles_x = (self.W + 15) // 16
         self.tiles_per_view = self.tiles_x * ((self.H + 15) // 16)
         self.ranges = torch.empty(self.V * self.tiles_per_view, 2, dtype=torch.int32, device=dev)
@@ -65,12 +65,55 @@ class SplatPipeline:
         self.loss_grad = torch.empty_like(self.out)
         self.loss_ws = torch.empty(_lib.veg_l1_loss_workspace_size(), dtype=torch.uint8,
                                    device=dev)
-        self.grad2d = torch.empty(nrec * 2, 4, device=dev)
         self.keys = None
         self._lit = None  # (mean_v, normal_beta, k_ads, light_dirs) when shaded
-        self.splat_shade = None
-        self.grad_shade = None
         self.set_capacity(capacity if capacity is not None else max(1 << 16, 8 * nrec))
+
+    def _records(self, rows):
+        """Allocates the per-record buffers for up to `rows` Gaussians per view
+        and views their first n."""
+        self.rows = int(rows)
+        nr, dev = self.V * self.rows, self.device
+        self._rec = (torch.empty(nr, 4, device=dev), torch.empty(nr, 4, device=dev),
+                     torch.empty(nr, dtype=torch.int32, device=dev),
+                     torch.empty(nr, 4, dtype=torch.int16, device=dev),
+                     torch.empty(nr * 2, 4, device=dev))
+        shaded = self._shade_rows is not None
+        self._shade_rows = None
+        if shaded:
+            self.ensure_shade_buffers()
+        self._view_records()
+
+    def _view_records(self):
+        nr = self.V * self.n
+        geo, aux, tiles, rect, grad2d = self._rec
+        self.geo, self.aux, self.tiles, self.rect = geo[:nr], aux[:nr], tiles[:nr], rect[:nr]
+        self.grad2d = grad2d[:2 * nr]
+        if self._shade_rows is not None:
+            self.splat_shade = self._shade_rows[0][:nr]
+            self.grad_shade = self._shade_rows[1][:nr]
+        else:
+            self.splat_shade = self.grad_shade = None
+
+    def ensure_shade_buffers(self):
+        """Per-(view, Gaussian) Blinn-Phong factors and their gradients."""
+        if self._shade_rows is None:
+            nr = self.V * self.rows
+            self._shade_rows = (torch.empty(nr, 2, device=self.device),
+                                torch.empty(nr, 2, device=self.device))
+            self._view_records()
+
+    def resize(self, n):
+        """Adapts the pipeline to n Gaussians per view (after densification):
+        the buffers stay when n fits the allocated rows, else they are
+        reallocated with 25% headroom.  The binning status is kept."""
+        n = int(n)
+        self.n = n
+        if n > self.rows:
+            self._records(n + n // 4)
+            self.set_capacity(self.capacity)
+        else:
+            self._view_records()
 
     def set_cameras(self, cams, c_cams=None):
         """Switch to other cameras of the same count and image size (c_cams:
@@ -83,7 +126,7 @@ class SplatPipeline:
 
     def set_capacity(self, capacity):
         self.capacity = int(capacity)
-        ws = _lib.veg_bin_sort_workspace_size(self.n, self.V, self.capacity, self.W, self.H)
+        ws = _lib.veg_bin_sort_workspace_size(self.rows, self.V, self.capacity, self.W, self.H)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
         self.ws[:256].zero_()  # status header: no binning yet, no overflow
         self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
@@ -99,9 +142,7 @@ class SplatPipeline:
     def shade(self, mean_v, normal_beta, k_ads, light_dirs, stream=None):
         """Blinn-Phong factors of every view (veg_shade); later composites and
         backward passes are shaded until `unshade`."""
-        if self.splat_shade is None:
-            self.splat_shade = torch.empty(self.V * self.n, 2, device=self.device)
-            self.grad_shade = torch.empty(self.V * self.n, 2, device=self.device)
+        self.ensure_shade_buffers()
         light_dirs = np.asarray(light_dirs, np.float32).reshape(self.V, 3)
         self._lit = (mean_v, normal_beta, k_ads, light_dirs)
         _lib.veg_shade(self.c_cams, mean_v, normal_beta, k_ads, light_dirs, self.splat_shade,

@@ -85,6 +85,10 @@ class TrainParams:
         self.m = [None if r is None else torch.zeros_like(r) for r in self.raw]
         self.v = [None if r is None else torch.zeros_like(r) for r in self.raw]
         self.step = 0
+        # the full-capacity arrays behind the row views above:
+        # (rows, raw, m, v, mean_v, logscale_w) and the gradients' (rows, grads)
+        self.store = (self.n, self.raw, self.m, self.v, self.mean_v, self.logscale_w)
+        self._grad_store = (self.n, self.grads)
         self._arrays = _lib.adam_arrays(self.raw, self.grads, self.m, self.v,
                                         (self.mean_v, self.logscale_w))
 
@@ -100,15 +104,30 @@ class TrainParams:
         self.step += 1
         _lib.veg_adam_step(self._arrays, self.n, lr, self.step, stream=stream)
 
-    def replace(self, n, raw, m, v, mean_v, logscale_w):
-        """Adopts new arrays of n rows (after densification); gradients
-        restart at zero."""
-        self.n = int(n)
-        self.raw, self.m, self.v = raw, m, v
-        self.mean_v, self.logscale_w = mean_v, logscale_w
-        self.grads = [None if r is None else torch.zeros_like(r) for r in raw]
+    def replace(self, n, store):
+        """Adopts the first n rows of `store` = (rows, raw, m, v, mean_v,
+        logscale_w), full-capacity arrays (after densification); gradients
+        restart at zero, in their own storage while it has room.  Returns the
+        storage given up."""
+        n = int(n)
+        rows, raw, m, v, mean_v, logscale_w = store
+        if n > rows:
+            raise ValueError("replace: n exceeds the storage's rows")
+        cut = lambda t: None if t is None else t[:n]
+        old, self.store, self.n = self.store, store, n
+        self.raw, self.m, self.v = [cut(t) for t in raw], [cut(t) for t in m], [cut(t) for t in v]
+        self.mean_v, self.logscale_w = mean_v[:n], logscale_w[:n]
+        grows, gfull = self._grad_store
+        if n > grows:
+            grows = n + n // 4
+            gfull = [None if r is None else torch.empty(grows, 4, device=r.device)
+                     for r in raw]
+            self._grad_store = (grows, gfull)
+        self.grads = [cut(t) for t in gfull]
+        self.zero_grad()
         self._arrays = _lib.adam_arrays(self.raw, self.grads, self.m, self.v,
                                         (self.mean_v, self.logscale_w))
+        return old
 
 
 def scene_extent(cams) -> float:
@@ -138,10 +157,33 @@ class DensityControl:
         self.accum = self.count = None
         self.n_out = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.history = []
+        # buffers kept between densifications: the statistic's storage, the
+        # spare parameter storage that receives the next output (the storage
+        # the parameters give up becomes the next spare), draws, workspace
+        self._stat = None
+        self._spare = None
+        self._z = None
+        self._ws = None
 
     def reset(self, n):
-        self.accum = torch.zeros(n, device=self.device)
-        self.count = torch.zeros(n, dtype=torch.int32, device=self.device)
+        if self._stat is None or self._stat[0].numel() < n:
+            rows = n + n // 4
+            self._stat = (torch.empty(rows, device=self.device),
+                          torch.empty(rows, dtype=torch.int32, device=self.device))
+        self.accum, self.count = self._stat[0][:n], self._stat[1][:n]
+        self.accum.zero_()
+        self.count.zero_()
+
+    def _output_store(self, P, rows):
+        """Parameter storage with at least `rows` rows for veg_densify's output."""
+        s = self._spare
+        if s is None or s[0] < rows or [t is None for t in s[1]] != [t is None for t in P.raw]:
+            cap = rows + rows // 4
+            new = lambda r: None if r is None else torch.empty(cap, 4, device=self.device)
+            s = (cap, [new(r) for r in P.raw], [new(r) for r in P.raw], [new(r) for r in P.raw],
+                 torch.empty(cap, 4, device=self.device), torch.empty(cap, 4, device=self.device))
+        self._spare = None
+        return s
 
     def active(self, it):
         return self.start <= it <= self.stop
@@ -158,26 +200,24 @@ class DensityControl:
     def apply(self, P, stream=None):
         """Clone / split / prune; replaces P's arrays (one host sync to read
         the new count).  Returns the new number of Gaussians."""
-        n, cap = P.n, 2 * P.n
+        n = P.n
         if self.accum is None or self.accum.numel() != n:
             self.reset(n)
-        new = lambda r: None if r is None else torch.empty(cap, 4, device=self.device)
-        raw = [new(r) for r in P.raw]
-        m = [new(r) for r in P.raw]
-        v = [new(r) for r in P.raw]
-        mean_v = torch.empty(cap, 4, device=self.device)
-        logscale_w = torch.empty(cap, 4, device=self.device)
-        z = torch.randn(n, 2, 3, generator=self.gen, device=self.device)
-        ws = torch.empty(max(_lib.veg_densify_workspace_size(n), 1), dtype=torch.uint8,
-                         device=self.device)
+        store = self._output_store(P, 2 * n)
+        cap, raw, m, v, mean_v, logscale_w = store
+        if self._z is None or self._z.numel() < 6 * n:
+            self._z = torch.empty(6 * (n + n // 4), device=self.device)
+        z = self._z[:6 * n].view(n, 2, 3)
+        torch.randn(n, 2, 3, generator=self.gen, out=z)
+        wsb = max(_lib.veg_densify_workspace_size(n), 1)
+        if self._ws is None or self._ws.numel() < wsb:
+            self._ws = torch.empty(wsb + wsb // 4, dtype=torch.uint8, device=self.device)
         src = _lib.adam_arrays(P.raw, P.grads, P.m, P.v)
         dst = _lib.adam_arrays(raw, [None] * 5, m, v, (mean_v, logscale_w))
         _lib.veg_densify(src, n, self.accum, self.count, z, self.cfg, dst, cap, self.n_out,
-                         None, ws, stream)
+                         None, self._ws, stream)
         n_new = int(self.n_out.item())
-        cut = lambda t: None if t is None else t[:n_new]
-        P.replace(n_new, [cut(t) for t in raw], [cut(t) for t in m], [cut(t) for t in v],
-                  mean_v[:n_new], logscale_w[:n_new])
+        self._spare = P.replace(n_new, store)
         self.reset(n_new)
         self.history.append((n, n_new))
         return n_new
@@ -199,6 +239,7 @@ class OpacityGuidedTrainer:
         self.capacity = capacity
         self.native = bool(native)
         self._args = None
+        self._c_all = None
         self.cams = list(cams)
         self.luts = luts
         self.targets = targets
@@ -227,21 +268,34 @@ class OpacityGuidedTrainer:
         p.composite(lut, self.bg, stream=stream)
         return p.out
 
+    def evaluate(self, pairs, stream=None):
+        """Mean (1 - lambda) L1 + lambda (1 - SSIM) over the given (view, map)
+        pairs with the current parameters; no gradient or update is kept (the
+        pipeline's per-step buffers are overwritten)."""
+        p = self.pipe
+        vals = torch.empty(len(pairs), device=p.device)
+        loss = torch.zeros(3, device=p.device)
+        for i, (view, k) in enumerate(pairs):
+            self.render(int(view), int(k), stream)
+            _lib.veg_l1_ssim_loss(p.out, self.targets[int(view), int(k)], p.loss_grad, loss,
+                                  self.loss_ws, self.lam, stream)
+            vals[i] = loss[0]
+        return float(vals.mean()) if len(pairs) else float("nan")
+
     def _build_args(self):
         """The native executor's view of every buffer (rebuilt whenever the
         arrays change, i.e. after densification)."""
         p, P, D = self.pipe, self.P, self.density
-        if p.splat_shade is None:
-            p.splat_shade = torch.empty(p.V * p.n, 2, device=p.device)
-            p.grad_shade = torch.empty(p.V * p.n, 2, device=p.device)
+        p.ensure_shade_buffers()
         ptr = lambda t: None if t is None else t.data_ptr()
         a = _lib.veg_train_args()
         for i in range(5):
             a.raw[i], a.grad[i] = ptr(P.raw[i]), ptr(P.grads[i])
             a.exp_avg[i], a.exp_avg_sq[i] = ptr(P.m[i]), ptr(P.v[i])
         a.mean_v, a.logscale_w, a.n = P.mean_v.data_ptr(), P.logscale_w.data_ptr(), P.n
-        self._c_all = _lib.cameras(self.cams)
-        self._lights_c = np.ascontiguousarray(self.lights, np.float32)
+        if self._c_all is None:
+            self._c_all = _lib.cameras(self.cams)
+            self._lights_c = np.ascontiguousarray(self.lights, np.float32)
         a.cams, a.n_cams = self._c_all, len(self.cams)
         a.light_dirs = self._lights_c.ctypes.data
         a.luts, a.lut_size, a.n_maps = self.luts.data_ptr(), self.luts.shape[1], self.K
@@ -289,7 +343,7 @@ class OpacityGuidedTrainer:
             D.accumulate(p, P, stream)
         if D is not None and D.due(self.it):
             D.apply(P, stream)
-            self.pipe = SplatPipeline(P.n, self.cams[:1], n_tf=1, capacity=self.capacity)
+            self.pipe.resize(P.n)
         else:
             P.adam(self.lr, stream)
         return view, k
@@ -303,7 +357,7 @@ class OpacityGuidedTrainer:
         _lib.veg_train_step(self._args, view, k, 0 if due else P.step + 1, accumulate, stream)
         if due:
             D.apply(P, stream)
-            self.pipe = SplatPipeline(P.n, self.cams[:1], n_tf=1, capacity=self.capacity)
+            self.pipe.resize(P.n)
             self._args = None
         else:
             P.step += 1

@@ -153,3 +153,45 @@ def test_training_with_density_control():
     assert np.all(np.isfinite(losses))
     assert np.mean(losses[-40:]) < 0.8 * np.mean(losses[:40])
     assert not T.overflowed()
+
+
+def test_densify_into_reused_storage_matches_fresh_buffers():
+    """Each densification writes into the storage the parameters gave up the
+    time before: the result is bit for bit that of fresh buffers whatever the
+    reused storage held, and the storage is reused while the count fits."""
+    g, lt = S.initial_model(3000, S.blob_field(4, 120), 121, weight=0.3, lighting=True)
+
+    def controller(P):
+        return DensityControl(2.0, start=0, stop=100, every=1, seed=123)
+
+    def load_stats(dc, n, seed):
+        r = np.random.default_rng(seed)
+        cnt = r.integers(1, 4, n).astype(np.int32)
+        dc.reset(n)
+        dc.count.copy_(dev(cnt, np.int32))
+        # about 7% of the statistics above the 2e-4 threshold
+        dc.accum.copy_(dev(cnt * r.uniform(0.0, 2.15e-4, n)))
+
+    P1, P2 = TrainParams(g, lt), TrainParams(g, lt)
+    d1, d2 = controller(P1), controller(P2)
+    spare = d2._output_store(P2, 2 * g.n)
+    for t in spare[1] + spare[2] + spare[3] + [spare[4], spare[5]]:
+        if t is not None:
+            t.fill_(float("nan"))
+    d2._spare = spare
+    first = spare[1][0].data_ptr()
+    for it in range(3):
+        for P, dc in ((P1, d1), (P2, d2)):
+            load_stats(dc, P.n, 124 + it)
+            if dc is d1:
+                dc._spare = None  # fresh buffers every time
+        n1, n2 = d1.apply(P1), d2.apply(P2)
+        assert n1 == n2 and n1 != g.n
+        arrays = lambda P: [t for t in P.raw + P.m + P.v + [P.mean_v, P.logscale_w]
+                            if t is not None]
+        for a, b in zip(arrays(P1), arrays(P2)):
+            assert torch.equal(a, b)
+        assert all(not x.any() for x in P2.grads if x is not None)
+    # outputs 1 and 3 share the storage first poisoned (2n fits its rows)
+    assert P2.store[1][0].data_ptr() == first
+

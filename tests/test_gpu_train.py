@@ -196,6 +196,8 @@ def test_training_reduces_the_loss():
     g0, _ = S.initial_model(3000, bf, 77, weight=0.3, lighting=False)
     P = TrainParams(g0)
     T = OpacityGuidedTrainer(P, cams, luts, targets, seed=78)
+    held = [(v, k) for v in range(0, 16, 3) for k in range(4)]
+    eval0 = T.evaluate(held)
     losses = []
     for _ in range(300):
         T.step()
@@ -206,6 +208,26 @@ def test_training_reduces_the_loss():
     assert np.all(np.isfinite(losses))
     assert losses[-50:].mean() < 0.8 * losses[:50].mean(), (losses[:50].mean(),
                                                              losses[-50:].mean())
+    eval1 = T.evaluate(held)
+    assert eval1 < 0.8 * eval0, (eval0, eval1)
+
+
+def test_evaluate_scores_a_pair_as_the_step_does():
+    """evaluate() renders and scores a (view, map) pair as an iteration does
+    before its update, and changes no parameter."""
+    g, lt, cams, luts, tg = small_training_set(seed=96)
+    P = TrainParams(g, lt)
+    T = OpacityGuidedTrainer(P, cams, lut_tensor(luts), dev(tg))
+    before = [x.clone() for x in P.raw]
+    e = T.evaluate([(1, 2)])
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(before, P.raw))
+    T.step(view=1, k=2)
+    torch.cuda.synchronize()
+    assert float(T.loss[0]) == pytest.approx(e, rel=1e-6)
+    pair = [T.evaluate([(v, k)]) for v, k in ((0, 0), (1, 1))]
+    assert T.evaluate([(0, 0), (1, 1)]) == pytest.approx(np.mean(pair), rel=1e-6)
+    assert T.evaluate([]) != T.evaluate([])  # nan for no pairs
 
 
 def test_native_step_equals_the_python_sequence():

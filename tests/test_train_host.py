@@ -55,3 +55,23 @@ def test_vertex_model_takes_vertices_and_their_values():
     assert np.array_equal(g.mean_v[:, 3], vol[idx[:, 2], idx[:, 1], idx[:, 0]])
     assert len({tuple(r) for r in idx}) == 300  # without replacement
     assert lt.normal_beta.shape == (300, 4)
+
+
+def test_pipeline_resize_keeps_buffers_while_the_count_fits():
+    """After densification the pipeline adopts the new count in place while
+    it fits the allocated rows (host logic; CPU tensors, no kernel runs)."""
+    from paper_2504_13339_gb300 import build
+    from paper_2504_13339_gb300.render import SplatPipeline
+    build.build()
+    cams = S.orbit_cameras(2, 125, 48, 32)
+    p = SplatPipeline(100, cams, n_tf=1, device="cpu")
+    p.ensure_shade_buffers()
+    p.resize(110)  # beyond the rows: reallocated with headroom
+    ptrs = [t.data_ptr() for t in p._rec], p.ws.data_ptr()
+    for n in (120, 137, 60):
+        p.resize(n)
+        assert ([t.data_ptr() for t in p._rec], p.ws.data_ptr()) == ptrs
+        assert p.geo.shape[0] == 2 * n and p.grad2d.shape[0] == 4 * n
+        assert p.splat_shade.shape[0] == 2 * n and p.tiles.shape[0] == 2 * n
+    p.resize(138)
+    assert p.rows >= 138 and p.geo.shape[0] == 2 * 138 and p.splat_shade.shape[0] == 276
