@@ -152,6 +152,23 @@ class StepModel:
     def grads(self):
         return self.P.grads
 
+    def snapshot(self):
+        """Device copies of the parameters and the Adam state."""
+        P = self.P
+        keep = lambda ts: [None if t is None else t.clone() for t in ts]
+        return keep(P.raw), keep(P.m), keep(P.v), P.mean_v.clone(), P.logscale_w.clone(), P.step
+
+    def restore(self, snap):
+        """Puts the model back into a snapshot's state."""
+        raw, m, v, mean_v, logscale_w, step = snap
+        P = self.P
+        for dst, src in zip(P.raw + P.m + P.v, raw + m + v):
+            if dst is not None:
+                dst.copy_(src)
+        P.mean_v.copy_(mean_v)
+        P.logscale_w.copy_(logscale_w)
+        P.step = step
+
 
 def setup_train(args, device):
     import torch
@@ -278,6 +295,7 @@ def run_gpu(args):
     assert st == _lib.VEG_OK, "instance capacity overflow during warm-up"
 
     # ---- device-timed loop -------------------------------------------------
+    start_state = model.snapshot()  # the end-to-end loop repeats these steps
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
     clocks = ClockSampler(local)
@@ -320,18 +338,46 @@ def run_gpu(args):
     fwd_flops = flops_of(FWD_FLOPS, f)
     bwd_flops = flops_of(BWD_FLOPS_LIT if lighting is not None else BWD_FLOPS, b)
     # ---- end to end through the public API with host buffers ---------------
+    # the same K steps again from the same model state (the model trains
+    # during the run, so later steps are heavier)
+    model.restore(start_state)
+    del start_state
     tgt_host = target.cpu().pin_memory()
     lut_host = luts.cpu().pin_memory()
     loss_host = torch.empty(1).pin_memory()
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(K)]
+    # double-buffered inputs: step k+1's copy runs on a second stream during
+    # step k (it starts no earlier than step k's timed span); step k waits
+    # for its own copy, and a buffer is refilled only after the step that
+    # read it has finished
+    copy_stream = torch.cuda.Stream(device)
+    tgt_dev, lut_dev = [target, torch.empty_like(target)], [luts, torch.empty_like(luts)]
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+
+    def prefetch(k, after):
+        nxt = k % 2
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(after)
+            if k >= 2:
+                copy_stream.wait_event(free[nxt])
+            tgt_dev[nxt].copy_(tgt_host, non_blocking=True)
+            lut_dev[nxt].copy_(lut_host, non_blocking=True)
+            ready[nxt].record(copy_stream)
+
     barrier()
     for k in range(K):
         flush.zero_()
         ev2[k][0].record(stream)
-        target.copy_(tgt_host, non_blocking=True)
-        luts.copy_(lut_host, non_blocking=True)
-        gpu_step(p, model, luts, target)
+        if k == 0:
+            prefetch(0, ev2[0][0])
+        if k + 1 < K:
+            prefetch(k + 1, ev2[k][0])
+        cur = k % 2
+        stream.wait_event(ready[cur])
+        gpu_step(p, model, lut_dev[cur], tgt_dev[cur])
+        free[cur].record(stream)
         loss_host.copy_(p.loss, non_blocking=True)
         ev2[k][1].record(stream)
     barrier()
@@ -390,7 +436,12 @@ def run_gpu(args):
                  "timing": f"work counted after the timed steps, paired with the last {last}"},
         "clocks": clk,
         "e2e": {"value": round(whole_job_rate(K, world, e2e_ms), 3), "unit": "steps/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+                "copies": "target images and tables from pinned host memory on a second "
+                          "stream, double-buffered: step k+1's copy overlaps step k's compute "
+                          "and starts inside step k's timed span; the loss read back after "
+                          "every step",
+                "steps": "the timed steps repeated from the same model state"},
         "gpu_launches": int(launches),
         "roofline": roofline,
     }
