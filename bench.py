@@ -199,11 +199,16 @@ def gpu_step(p, model, luts, target, ev=None):
     """One training step: projection, (shading,) binning, compositing, L1,
     compositing backward, projection (and shading) backward, Adam."""
     P = model.P
+    timed = ev is not None and len(ev) > 6
     P.zero_grad()
+    if timed:
+        ev[6].record()
     p.project(*model.tens, luts)
     if model.lights is not None:
         p.shade(P.mean_v, P.raw[3], P.raw[4], model.lights)
     p.bin_sort()
+    if timed:
+        ev[7].record()
     if ev is not None:
         ev[0].record()
     p.composite(luts)
@@ -218,7 +223,11 @@ def gpu_step(p, model, luts, target, ev=None):
     p.project_backward(*P.grads[:3])
     if model.lights is not None:
         p.shade_backward(P.grads[0], P.grads[3], P.grads[4])
+    if ev is not None and len(ev) > 4:
+        ev[4].record()
     P.adam(model.lr)
+    if ev is not None and len(ev) > 4:
+        ev[5].record()
 
 
 def source_hash(*names):
@@ -297,7 +306,7 @@ def run_gpu(args):
     # ---- device-timed loop -------------------------------------------------
     start_state = model.snapshot()  # the end-to-end loop repeats these steps
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(K)]
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -305,16 +314,18 @@ def run_gpu(args):
     for k in range(K):
         flush.zero_()
         e = evs[k]
-        e[4].record(stream)
-        gpu_step(p, model, luts, target, ev=e[:4])
-        e[5].record(stream)
+        e[8].record(stream)
+        gpu_step(p, model, luts, target, ev=e[:8])
+        e[9].record(stream)
     barrier()
     launches = _lib.veg_kernel_launches() - launches0
     clk = clocks.stop()
     st_end, m_end = p.status()
     assert st_end == _lib.VEG_OK, "instance capacity overflow during the timed steps"
 
-    step_ms = [e[4].elapsed_time(e[5]) for e in evs]
+    step_ms = [e[8].elapsed_time(e[9]) for e in evs]
+    adam_ms = [e[4].elapsed_time(e[5]) for e in evs]
+    bin_ms = [e[6].elapsed_time(e[7]) for e in evs]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
     total_ms = max_over_ranks(float(np.sum(step_ms)), world, device)
@@ -428,7 +439,12 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "mpix_per_s": round(mpix, 2),
         "stages_ms": {"composite_fwd": round(fwd_avg, 4), "composite_bwd": round(bwd_avg, 4),
-                      "other": round(total_ms / K - fwd_avg - bwd_avg, 4)},
+                      "adam": round(float(np.mean(adam_ms)), 4),
+                      "projection_binning": round(float(np.mean(bin_ms)), 4),
+                      "other": round(total_ms / K - fwd_avg - bwd_avg - float(np.mean(adam_ms))
+                                     - float(np.mean(bin_ms)), 4)},
+        "steps_per_s_without_adam": round(K / ((float(np.sum(step_ms)) -
+                                                float(np.sum(adam_ms))) * 1e-3), 3),
         "work": {"fwd": dict(zip(FWD_FLOPS, (int(x) for x in f))),
                  "bwd": dict(zip(BWD_FLOPS, (int(x) for x in b))),
                  "fwd_tflops": round(fwd_flops / (fwd_last * 1e-3) / 1e12, 3),

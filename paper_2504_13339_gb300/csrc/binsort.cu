@@ -84,8 +84,8 @@ __device__ __forceinline__ int chunks_of(int64_t n) {
   return (int)((n + kTileItems - 1) / kTileItems);
 }
 
-// Per-chunk digit histograms; hist is [256][nblocks] (nblocks = the chunk
-// capacity), blocks stride over the chunks that hold items.
+// Per-chunk digit histograms; hist is [2^nbits][nblocks] (nblocks = the
+// chunk capacity), blocks stride over the chunks that hold items.
 __global__ void __launch_bounds__(kThreads)
     radix_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, int shift, int nbits,
                       uint32_t* __restrict__ hist, int nblocks) {
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t n = cnt.get();
   const int nch = chunks_of(n);
   const uint32_t mask = (1u << nbits) - 1u;
+  const bool digit = threadIdx.x <= mask;
   for (int b = blockIdx.x; b < nch; b += gridDim.x) {
     s_hist[threadIdx.x] = 0;
     __syncthreads();
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kThreads)
       if (i < n) atomicAdd(&s_hist[(__ldg(&keys[i]) >> shift) & mask], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblocks + b] = s_hist[threadIdx.x];
+    if (digit) hist[(int64_t)threadIdx.x * nblocks + b] = s_hist[threadIdx.x];
   }
 }
 
@@ -179,12 +180,13 @@ __global__ void __launch_bounds__(kThreads, 4)
   if ((int)blockIdx.x >= nch) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t mask = (1u << nbits) - 1u;
-  const uint32_t dpre = block_exclusive_scan256<uint32_t>(totals[tid], s_warp);
+  const bool digit = (uint32_t)tid <= mask;  // rows of hist and totals exist for digits only
+  const uint32_t dpre = block_exclusive_scan256<uint32_t>(digit ? totals[tid] : 0u, s_warp);
   for (int b = blockIdx.x; b < nch; b += gridDim.x) {
     const int64_t base = (int64_t)b * kTileItems;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s_whist[w][tid] = 0;
-    s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + b];
+    if (digit) s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + b];
     __syncthreads();
 
     uint32_t k[kItems], v[kItems], r[kItems];
@@ -579,7 +581,7 @@ void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32
                 cudaStream_t stream) {
   const int grid = pass_grid(nblocks);
   radix_hist_kernel<<<grid, kThreads, 0, stream>>>(kin, cnt, shift, nbits, L.hist, nblocks);
-  radix_scan_rows_kernel<<<256, 1024, 0, stream>>>(L.hist, nblocks, L.totals, cnt);
+  radix_scan_rows_kernel<<<1 << nbits, 1024, 0, stream>>>(L.hist, nblocks, L.totals, cnt);
   radix_scatter_kernel<<<grid, kThreads, 0, stream>>>(kin, vin, kout, vout, cnt, shift, nbits,
                                                       L.hist, L.totals, nblocks);
   count_launch(3);
