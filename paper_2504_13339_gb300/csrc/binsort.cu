@@ -42,6 +42,12 @@ struct Count {
   }
 };
 
+__device__ __forceinline__ float rcp_approx_f(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -97,11 +103,18 @@ __global__ void __launch_bounds__(kThreads)
   for (int b = blockIdx.x; b < nch; b += gridDim.x) {
     s_hist[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)b * kTileItems;
-#pragma unroll 4
-    for (int j = 0; j < kItems; ++j) {
-      int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
-      if (i < n) atomicAdd(&s_hist[(__ldg(&keys[i]) >> shift) & mask], 1u);
+    // each thread counts 8 consecutive keys, loaded as two 16-byte vectors
+    // (the key arrays are 256-byte aligned) before any shared-memory update
+    const int64_t i0 = (int64_t)b * kTileItems + (int64_t)threadIdx.x * kItems;
+    if (i0 + kItems <= n) {
+      const uint4* src = reinterpret_cast<const uint4*>(keys + i0);
+      const uint4 a = __ldg(src), c = __ldg(src + 1);
+      const uint32_t k[kItems] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) atomicAdd(&s_hist[(k[j] >> shift) & mask], 1u);
+    } else {
+      for (int j = 0; j < kItems; ++j)
+        if (i0 + j < n) atomicAdd(&s_hist[(__ldg(&keys[i0 + j]) >> shift) & mask], 1u);
     }
     __syncthreads();
     if (digit) hist[(int64_t)threadIdx.x * nblocks + b] = s_hist[threadIdx.x];
@@ -473,7 +486,17 @@ __global__ void __launch_bounds__(256)
     const uint32_t o_g = __shfl_sync(0xffffffffu, g, lo);
     if (p < stop) {
       const int local = (int)(p - o_off);
-      const int ry = local / o_wx, rx = local - ry * o_wx;
+      // quotient by a float reciprocal (within one of the floor: local is
+      // below the rect's area, at most 1024^2 tiles), corrected to the floor
+      int ry = (int)((float)local * rcp_approx_f((float)o_wx));
+      int rx = local - ry * o_wx;
+      if (rx < 0) {
+        --ry;
+        rx += o_wx;
+      } else if (rx >= o_wx) {
+        ++ry;
+        rx -= o_wx;
+      }
       ikeys[p] = o_kb + (uint32_t)((o_y0 + ry) * tiles_x + o_x0 + rx);
       ivals[p] = o_g;
     }
@@ -580,7 +603,9 @@ void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32
                 Count cnt, int shift, int nbits, int nblocks, const Layout& L,
                 cudaStream_t stream) {
   const int grid = pass_grid(nblocks);
-  radix_hist_kernel<<<grid, kThreads, 0, stream>>>(kin, cnt, shift, nbits, L.hist, nblocks);
+  // the histogram kernel is light (28 registers, 1 KB): twice the blocks
+  radix_hist_kernel<<<std::min(nblocks, 2 * grid), kThreads, 0, stream>>>(kin, cnt, shift, nbits,
+                                                                         L.hist, nblocks);
   radix_scan_rows_kernel<<<1 << nbits, 1024, 0, stream>>>(L.hist, nblocks, L.totals, cnt);
   radix_scatter_kernel<<<grid, kThreads, 0, stream>>>(kin, vin, kout, vout, cnt, shift, nbits,
                                                       L.hist, L.totals, nblocks);
