@@ -260,3 +260,65 @@ def test_lit_one_table_per_view_matches_oracle():
     grad_check(grads[2].cpu().numpy(), gq, "quat")
     grad_check(gn.cpu().numpy(), gnr, "normal_beta")
     grad_check(gk.cpu().numpy(), gkr, "k_ads")
+
+
+def test_full_size_lit_crop_gradients():
+    """The shaded training step's scene at full size (1M Gaussians, 1024^2,
+    4 TFs, headlight): every gradient of a loss on a 64x64 crop against the
+    oracle, for the Gaussians the crop touches; all others stay zero."""
+    g, _, cams, tfs = S.train_scene()
+    cam = cams[0]
+    lt = S.random_lighting(g.n, 3)
+    lights = np.stack([O.headlight(cam)])
+    p = SplatPipeline(g.n, cams, n_tf=len(tfs), capacity=16_000_000)
+    tens = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
+    lit = (dev(lt.normal_beta), dev(lt.k_ads))
+    luts = lut_tensor(tfs)
+    p.project(*tens, luts)
+    p.shade(tens[0], *lit, lights)
+    p.bin_sort()
+    p.composite(luts)
+    x0 = y0 = 480
+    tiles = [(y0 // 16 + j) * cam.tiles_x + x0 // 16 + i for j in range(4) for i in range(4)]
+    d = lt.as_dict(lights)
+    pr = O.project32(cam, g, tfs)
+    O.attach_shading([pr], [cam], g, d)
+    bins = O.bins_from_lists([O.tile_lists(pr, cam, tiles)], 1, cam.tiles_x * cam.tiles_y)
+    fwd = O.composite_fwd([pr], cams, bins, tfs, tiles=tiles, record=True)
+    out = p.out.cpu().numpy()
+    for t in tiles:
+        px, py = O._tile_pixels(cam, t)
+        ok = ~fwd["flag"][0][:, py, px]
+        assert np.all(np.abs(out[0][:, py, px] - fwd["out"][0][:, py, px])[ok] <= IMG_TOL), t
+    dout = np.zeros(fwd["out"].shape)
+    dout[..., y0:y0 + 64, x0:x0 + 64, :] = np.random.default_rng(57).standard_normal(
+        (1, len(tfs), 64, 64, 4))
+    dout[fwd["flag"]] = 0.0
+    grads = [torch.zeros_like(t) for t in tens]
+    gn, gk = torch.zeros_like(lit[0]), torch.zeros_like(lit[1])
+    p.backward(dev(dout.astype(np.float32)), *grads, gn, gk)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd([pr], cams, bins, tfs, (0, 0, 0), fwd, dout, tiles=tiles)
+    touched = np.nonzero(np.abs(g2[0]).sum(1))[0]
+    assert touched.size > 100
+    gs = g.subset(touched)
+    prs = {k: (v[touched] if isinstance(v, np.ndarray) and v.shape[:1] == (g.n,) else v)
+           for k, v in pr.items()}
+    ds = {k: (v[touched] if k != "lights" else v) for k, v in d.items()}
+    gm, gl, gq = O.params_grad(cams, gs, [prs], g2[:, touched])
+    dn, dka, dkd, dks, db, dm_sh = O.lighting_grad(cams, gs, ds, [prs], g2[:, touched])
+    got = [t.cpu().numpy() for t in grads]
+    gn, gk = gn.cpu().numpy(), gk.cpu().numpy()
+    others = np.setdiff1d(np.arange(g.n), touched)
+    for a in got + [gn, gk]:
+        assert not a[others].any()
+    grad_check(got[0][touched, :3], gm[:, :3] + dm_sh, "mean")
+    grad_check(got[0][touched, 3], gm[:, 3], "v")
+    grad_check(got[1][touched, :3], gl[:, :3], "logscale")
+    grad_check(got[1][touched, 3], gl[:, 3], "w")
+    grad_check(got[2][touched], gq, "quat")
+    grad_check(gn[touched, :3], dn, "normal")
+    grad_check(gn[touched, 3], db, "beta")
+    grad_check(gk[touched, 0], dka, "k_a")
+    grad_check(gk[touched, 1], dkd, "k_d")
+    grad_check(gk[touched, 2], dks, "k_s")
