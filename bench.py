@@ -835,8 +835,12 @@ def run_opt(args):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record()
+    cmask = torch.empty(_lib.veg_raymarch_cells_count(R, MARCH_CELL), dtype=torch.int32,
+                        device="cuda")
+    _lib.veg_raymarch_cells(v4, tf_all, MARCH_CELL, cmask)
     for v in range(len(cams)):
-        _lib.veg_raymarch(c_cams[v], v4, tf_all, step, targets[v:v + 1], gt_material)
+        _lib.veg_raymarch_masked(c_cams[v], v4, tf_all, step, targets[v:v + 1], cmask,
+                                 MARCH_CELL, gt_material)
     b.record()
     b.synchronize()
     march_ms = a.elapsed_time(b)
@@ -913,7 +917,7 @@ def run_opt(args):
         "held_out_loss": {"pairs": "32 fixed random (view, map) pairs, untimed",
                           "initial": round(eval_init, 5), "before_timed": round(eval_start, 5),
                           "after_timed": round(eval_end, 5)},
-        "targets": {"renderer": "veg_raymarch (emission-absorption, headlight Blinn-Phong, "
+        "targets": {"renderer": "veg_raymarch_masked (emission-absorption, headlight Blinn-Phong, "
                                 "step = half the grid spacing)",
                     "images": len(cams) * K, "ms": round(march_ms, 2),
                     "mpix_per_s": round(px / (march_ms * 1e-3) / 1e6, 1)},
@@ -1002,8 +1006,10 @@ def cpu_baseline_opt(cams, luts, g, lt, targets, args, n_samples=4, seed=21):
 # position and grid coordinates 12, trilinear value + gradient (7 float4
 # lerps) 56, shading (normalisation, two dot products, power) 30; per table
 # evaluation: table lerp 8, clamp 2, opacity correction 4, shaded colour 6,
-# compositing 7, stop test 1.
-MARCH_FLOPS = {"sample": 98, "table": 28}
+# compositing 7, stop test 1; a sample skipped as empty costs its position
+# and grid coordinates (12).
+MARCH_FLOPS = {"sample": 98, "table": 28, "skipped": 12}
+MARCH_CELL = 8  # macrocell edge (vertex cells) of the empty-space masks
 
 
 def run_raymarch(args):
@@ -1032,10 +1038,15 @@ def run_raymarch(args):
     mat = (0.3, 0.6, 0.25, 12.0)
     tf = _lib.tf_desc(luts)
     c_cams = [_lib.cameras([c]) for c in cams]
+    mask = torch.empty(_lib.veg_raymarch_cells_count(R, MARCH_CELL), dtype=torch.int32,
+                       device="cuda")
 
     def render_all(stats=None):
+        # the set's empty-space masks (one launch), then one launch per view
+        _lib.veg_raymarch_cells(v4, tf, MARCH_CELL, mask)
         for v in range(len(cams)):
-            _lib.veg_raymarch(c_cams[v], v4, tf, step, out[v:v + 1], mat, stats=stats)
+            _lib.veg_raymarch_masked(c_cams[v], v4, tf, step, out[v:v + 1], mask, MARCH_CELL,
+                                     mat, stats=stats)
     for _ in range(max(args.warmup, 1)):
         render_all()
     reps = max(1, min(args.steps, 3))
@@ -1050,11 +1061,12 @@ def run_raymarch(args):
     b.synchronize()
     clk = clocks.stop()
     ms = a.elapsed_time(b) / reps
-    st = torch.zeros(2, dtype=torch.int64, device="cuda")
+    st = torch.zeros(3, dtype=torch.int64, device="cuda")
     render_all(st)
     torch.cuda.synchronize()
-    samples, tables = (int(x) for x in st.cpu().numpy())
-    flops = MARCH_FLOPS["sample"] * samples + MARCH_FLOPS["table"] * tables
+    samples, tables, skipped = (int(x) for x in st.cpu().numpy())
+    flops = (MARCH_FLOPS["sample"] * samples + MARCH_FLOPS["table"] * tables +
+             MARCH_FLOPS["skipped"] * skipped)
     props = torch.cuda.get_device_properties(0)
     peaks = {}
     try:
@@ -1071,11 +1083,14 @@ def run_raymarch(args):
                     "step half the grid spacing",
         "metric": "Mpix/s", "value": round(px / (ms * 1e-3) / 1e6, 1), "unit": "Mpix/s",
         "ms_per_set": round(ms, 2), "images": len(cams) * K, "reps": reps, "clocks": clk,
-        "work": {"samples": samples, "table_evaluations": tables},
+        "work": {"samples": samples, "table_evaluations": tables, "samples_skipped": skipped},
+        "empty_space": f"macrocells of {MARCH_CELL}^3 vertex cells; a sample whose macrocell has "
+                       "no opacity for any live table is skipped (images identical)",
         "roofline": {"bound": "alu", "kernel": "raymarch_kernel<8>/<2>",
                      "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4),
-                     "flops_model": "98 per sample + 28 per table evaluation (FMA = 2)"},
+                     "flops_model": "98 per sample + 28 per table evaluation + 12 per skipped "
+                                    "sample (FMA = 2)"},
         "data": "synthetic"}
     if not args.no_cpu_baseline:
         rng = np.random.default_rng(3)

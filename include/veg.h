@@ -481,6 +481,39 @@ veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vo
                         cudaStream_t stream);
 
 /*
+ * veg_raymarch_cells -- empty-space acceleration for veg_raymarch_masked
+ * (not part of the paper's method; it only skips work): the vertex cells of
+ * the prepared volume are grouped into macrocells of cell^3 (cell a power
+ * of two, 1..64; ceil((R-1)/cell) macrocells per axis, x fastest), and
+ * mask[macrocell] bit t (t < 32) is set when table t of `tf` can give a
+ * sample in the macrocell a positive opacity: some table entry that values
+ * within the macrocell's vertex range (widened by 1e-6, plus one entry on
+ * each side) interpolate between has a positive opacity.  Every bit is set
+ * for a macrocell holding a NaN vertex, and for every macrocell when
+ * tf.n_tf > 32.  veg_raymarch_cells_count gives the number of macrocells
+ * (the length of `mask`, device uint32).  One launch.
+ */
+veg_status veg_raymarch_cells_count(int32_t resolution, int32_t cell, int64_t* count);
+veg_status veg_raymarch_cells(const float* vol4, int32_t resolution, veg_tf tf, int32_t cell,
+                              uint32_t* mask, cudaStream_t stream);
+
+/*
+ * veg_raymarch_masked -- veg_raymarch with an empty-space mask from
+ * veg_raymarch_cells (the same vol4, tf tables and cell; NULL = none): a
+ * sample whose macrocell has no positive opacity for any table of its group
+ * still compositing is skipped.  Such a sample has opacity exactly 0 in all
+ * of them and leaves colour and transmittance unchanged, so the images are
+ * identical to veg_raymarch's.  stats: optional device uint64[3] with a
+ * mask ((samples taken, table evaluations, samples skipped); samples taken
+ * excludes skipped ones), uint64[2] without.
+ */
+veg_status veg_raymarch_masked(const veg_camera* cams, int32_t n_views, const float* vol4,
+                               int32_t resolution, veg_tf tf, float step,
+                               const veg_material* material, const float* bg,
+                               const uint32_t* cell_mask, int32_t cell, float* out,
+                               unsigned long long* stats, cudaStream_t stream);
+
+/*
  * veg_train_step -- one opacity-guided training iteration (Sec. 4.2) issued
  * from native code: veg_project (culled by the chosen table) ->
  * veg_shade (headlight of the chosen view, if lit) -> veg_bin_sort ->

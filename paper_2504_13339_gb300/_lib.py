@@ -121,6 +121,11 @@ _SIGS = {
                                       _P]),
     "veg_raymarch": (ctypes.c_int, [_CAMS, _I32, _P, _I32, veg_tf, ctypes.c_float,
                                     ctypes.POINTER(veg_material), _P, _P, _P, _P]),
+    "veg_raymarch_cells_count": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(ctypes.c_int64)]),
+    "veg_raymarch_cells": (ctypes.c_int, [_P, _I32, veg_tf, _I32, _P, _P]),
+    "veg_raymarch_masked": (ctypes.c_int, [_CAMS, _I32, _P, _I32, veg_tf, ctypes.c_float,
+                                           ctypes.POINTER(veg_material), _P, _P, _I32, _P, _P,
+                                           _P]),
     "veg_grad_stats_accumulate": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P]),
     "veg_densify_workspace_size": (ctypes.c_int, [_I64, ctypes.POINTER(_SZ)]),
     "veg_densify": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, _P, _P,
@@ -385,6 +390,30 @@ def veg_raymarch(cams, vol4, tf, step, out, material=None, bg=(0.0, 0.0, 0.0), s
            load().veg_raymarch(cams, len(cams), _ptr(vol4), vol4.shape[0], tf, float(step), mat,
                                ctypes.cast(bgc, ctypes.c_void_p), _ptr(out), _ptr(stats),
                                _stream(stream)))
+
+
+def veg_raymarch_cells_count(resolution, cell) -> int:
+    c = ctypes.c_int64(0)
+    _check("veg_raymarch_cells_count",
+           load().veg_raymarch_cells_count(int(resolution), int(cell), ctypes.byref(c)))
+    return int(c.value)
+
+
+def veg_raymarch_cells(vol4, tf, cell, mask, stream=None):
+    """mask: device int32/uint32 tensor of veg_raymarch_cells_count entries."""
+    _check("veg_raymarch_cells",
+           load().veg_raymarch_cells(_ptr(vol4), vol4.shape[0], tf, int(cell), _ptr(mask),
+                                     _stream(stream)))
+
+
+def veg_raymarch_masked(cams, vol4, tf, step, out, cell_mask, cell, material=None,
+                        bg=(0.0, 0.0, 0.0), stats=None, stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
+    mat = None if material is None else ctypes.byref(veg_material(*[float(m) for m in material]))
+    _check("veg_raymarch_masked",
+           load().veg_raymarch_masked(cams, len(cams), _ptr(vol4), vol4.shape[0], tf, float(step),
+                                      mat, ctypes.cast(bgc, ctypes.c_void_p), _ptr(cell_mask),
+                                      int(cell), _ptr(out), _ptr(stats), _stream(stream)))
 
 
 def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w, grad_quat,

@@ -25,6 +25,19 @@ namespace veg {
 
 namespace {
 
+// Hardware approximations of 2^x and log2 x (the opacity correction), whose
+// errors stay far below the image tolerance.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 struct RayView {
   float r[9];      // world-to-camera rotation, row-major
   float eye[3];    // camera centre
@@ -47,6 +60,10 @@ struct MarchArgs {
   bool shade;
   float ka, kd, ks, beta;
   float bg0, bg1, bg2;
+  // empty-space skipping: per-macrocell table masks (veg_raymarch_cells)
+  // over macrocells of 2^cell_shift vertex cells per axis, or null
+  const uint32_t* cell_mask;
+  int cell_shift, cells;
 };
 
 __global__ void __launch_bounds__(256)
@@ -64,13 +81,59 @@ __global__ void __launch_bounds__(256)
   out[i] = make_float4(vol[i], diff(x, sx), diff(y, sy), diff(z, sz));
 }
 
-// stats (instrumented build): samples taken (per ray and table group) and
-// table evaluations (samples x live tables).
+// Per macrocell (cell^3 vertex cells, vertices [c cell, c cell + cell] per
+// axis clipped to the grid): bit t (t < 32) set when table t can give a
+// sample in the cell a nonzero opacity.  A sample's value is a trilinear
+// blend of the cell's vertex values, so it lies in their [min, max] up to
+// rounding; the test widens the range by 1e-6 and takes the table entries
+// that values in it interpolate between, with one more entry on each side,
+// and sets the bit when any of them has a positive opacity (interpolating
+// two non-positive entries gives a clamped opacity of 0).  A NaN vertex, or
+// more than 32 tables, sets every bit.
+__global__ void __launch_bounds__(256)
+    cell_mask_kernel(const float4* __restrict__ vol, int R, int cell, int cells,
+                     const float4* __restrict__ lut, int L, int n_tf, uint32_t* __restrict__ mask) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = (int64_t)cells * cells * cells;
+  if (i >= nc) return;
+  const int cx = (int)(i % cells), cy = (int)((i / cells) % cells), cz = (int)(i / ((int64_t)cells * cells));
+  const int x0 = cx * cell, y0 = cy * cell, z0 = cz * cell;
+  const int x1 = min(x0 + cell, R - 1), y1 = min(y0 + cell, R - 1), z1 = min(z0 + cell, R - 1);
+  float mn = 3.0e38f, mx = -3.0e38f;
+  bool nan = false;
+  for (int z = z0; z <= z1; ++z)
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const float v = __ldg(&vol[((int64_t)z * R + y) * R + x]).x;
+        nan |= v != v;
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+      }
+  uint32_t m = 0u;
+  if (nan || n_tf > 32) {
+    m = 0xffffffffu;
+  } else {
+    const float lo = fminf(fmaxf(mn - 1e-6f, 0.0f), 1.0f) * (float)(L - 1);
+    const float hi = fminf(fmaxf(mx + 1e-6f, 0.0f), 1.0f) * (float)(L - 1);
+    const int k0 = max((int)floorf(lo) - 1, 0), k1 = min((int)floorf(hi) + 2, L - 1);
+    for (int t = 0; t < n_tf; ++t)
+      for (int k = k0; k <= k1; ++k)
+        if (__ldg(&lut[(int64_t)t * L + k]).w > 0.0f) {
+          m |= 1u << t;
+          break;
+        }
+  }
+  mask[i] = m;
+}
+
+// stats (instrumented build): samples taken (per ray and table group),
+// table evaluations (samples x live tables) and, with a cell mask, samples
+// skipped as empty.
 template <int TG, bool STATS>
 __global__ void __launch_bounds__(256)
     raymarch_kernel(MarchArgs A, RaySet rs, float4* __restrict__ out,
                     unsigned long long* __restrict__ stats) {
-  unsigned long long n_samp = 0, n_tab = 0;
+  unsigned long long n_samp = 0, n_tab = 0, n_skip = 0;
   extern __shared__ float4 s_lut[];
   const int wi = blockIdx.x;
   const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
@@ -134,6 +197,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int c = 0; c < 3; ++c) hv[c] *= hn;
     const int R = A.R;
+    // the group's tables occupy bits lut0 .. lut0 + ntg - 1 of a cell mask
+    const bool skip_empty = A.cell_mask != nullptr && lut0 >= 0 && lut0 + ntg <= 32;
     for (int k = 0; k < n && live; ++k) {
       const float t = fmaf((float)k + 0.5f, A.step, ta);
       float g[3];
@@ -143,6 +208,16 @@ __global__ void __launch_bounds__(256)
         g[c] = (fmaf(t, d[c], V.eye[c]) + 1.0f) * A.inv_h;
         ic[c] = min(max((int)floorf(g[c]), 0), R - 2);
         g[c] -= (float)ic[c];
+      }
+      if (skip_empty) {
+        // every table still compositing has zero opacity in this macrocell:
+        // the sample would leave colour and transmittance unchanged
+        const int mc = ((ic[2] >> A.cell_shift) * A.cells + (ic[1] >> A.cell_shift)) * A.cells +
+                       (ic[0] >> A.cell_shift);
+        if (((__ldg(&A.cell_mask[mc]) >> lut0) & live) == 0u) {
+          if (STATS) ++n_skip;
+          continue;
+        }
       }
       const float4* base = A.vol + ((int64_t)ic[2] * R + ic[1]) * R + ic[0];
       const int64_t sy = R, sz = (int64_t)R * R;
@@ -167,7 +242,7 @@ __global__ void __launch_bounds__(256)
           const float nl = fabsf((gx * V.light[0] + gy * V.light[1] + gz * V.light[2]) * ig);
           const float nh = fabsf((gx * hv[0] + gy * hv[1] + gz * hv[2]) * ig);
           sd = A.ka + A.kd * nl;
-          ss = nl > 0.f ? A.ks * powf(nh, A.beta) : 0.f;
+          ss = nl > 0.f ? A.ks * __powf(nh, A.beta) : 0.f;
         }
       }
       const TfPos q = tf_pos(s.x, L);
@@ -180,7 +255,7 @@ __global__ void __launch_bounds__(256)
         if (!(live & (1u << tt))) continue;
         const float4 lo = s_lut[tt * L + q.k], hi = s_lut[tt * L + q.k + 1];
         const float a = fminf(fmaxf(lerp_rn(lo.w, hi.w, q), 0.0f), 1.0f);
-        const float alpha = 1.0f - exp2f(log2f(1.0f - a) * A.ratio);
+        const float alpha = a > 0.0f ? 1.0f - ex2_approx(lg2_approx(1.0f - a) * A.ratio) : 0.0f;
         const float w = T[tt] * alpha;
         Cr[tt] = fmaf(w, fmaf(sd, lerp_rn(lo.x, hi.x, q), ss), Cr[tt]);
         Cg[tt] = fmaf(w, fmaf(sd, lerp_rn(lo.y, hi.y, q), ss), Cg[tt]);
@@ -203,10 +278,12 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) {
       n_samp += __shfl_down_sync(0xffffffffu, n_samp, o);
       n_tab += __shfl_down_sync(0xffffffffu, n_tab, o);
+      n_skip += __shfl_down_sync(0xffffffffu, n_skip, o);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats[0], n_samp);
       atomicAdd(&stats[1], n_tab);
+      if (A.cell_mask) atomicAdd(&stats[2], n_skip);
     }
   }
 }
@@ -255,18 +332,56 @@ extern "C" veg_status veg_volume_prepare(const float* volume, int32_t resolution
   return launch_status();
 }
 
-extern "C" veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vol4,
-                                   int32_t resolution, veg_tf tf, float step,
-                                   const veg_material* material, const float* bg, float* out,
-                                   unsigned long long* stats, cudaStream_t stream) {
+namespace {
+
+bool cell_size_ok(int32_t cell) { return cell >= 1 && cell <= 64 && (cell & (cell - 1)) == 0; }
+
+int cells_per_axis(int32_t resolution, int32_t cell) {
+  return (resolution - 1 + cell - 1) / cell;  // macrocells covering the R - 1 vertex cells
+}
+
+}  // namespace
+
+extern "C" veg_status veg_raymarch_cells_count(int32_t resolution, int32_t cell, int64_t* count) {
+  if (!count || resolution < 2 || resolution > 2048 || !cell_size_ok(cell))
+    return VEG_ERR_INVALID_ARGUMENT;
+  const int64_t c = cells_per_axis(resolution, cell);
+  *count = c * c * c;
+  return VEG_OK;
+}
+
+extern "C" veg_status veg_raymarch_cells(const float* vol4, int32_t resolution, veg_tf tf,
+                                         int32_t cell, uint32_t* mask, cudaStream_t stream) {
+  if (!vol4 || !mask || resolution < 2 || resolution > 2048 || !cell_size_ok(cell) || !tf.lut ||
+      tf.lut_size < 2 || tf.n_tf < 1 || !aligned16(vol4) || !aligned16(tf.lut))
+    return VEG_ERR_INVALID_ARGUMENT;
+  const int c = cells_per_axis(resolution, cell);
+  const int64_t nc = (int64_t)c * c * c;
+  cell_mask_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(
+      reinterpret_cast<const float4*>(vol4), resolution, cell, c,
+      reinterpret_cast<const float4*>(tf.lut), tf.lut_size, tf.n_tf, mask);
+  count_launch();
+  return launch_status();
+}
+
+extern "C" veg_status veg_raymarch_masked(const veg_camera* cams, int32_t n_views,
+                                          const float* vol4, int32_t resolution, veg_tf tf,
+                                          float step, const veg_material* material,
+                                          const float* bg, const uint32_t* cell_mask,
+                                          int32_t cell, float* out, unsigned long long* stats,
+                                          cudaStream_t stream) {
   veg_status st = check_cameras(cams, n_views);
   if (st != VEG_OK) return st;
   if (!vol4 || !out || resolution < 2 || resolution > 2048 || !(step > 0.0f) || !tf.lut ||
       tf.lut_size < 2 || tf.n_tf < 1 || !aligned16(vol4) || !aligned16(out) ||
-      !aligned16(tf.lut))
+      !aligned16(tf.lut) || (cell_mask && !cell_size_ok(cell)))
     return VEG_ERR_INVALID_ARGUMENT;
   if (tf.lut_size > 4096) return VEG_ERR_UNSUPPORTED;
   MarchArgs A;
+  A.cell_mask = cell_mask;
+  A.cell_shift = 0;
+  while (cell_mask && (1 << A.cell_shift) < cell) ++A.cell_shift;
+  A.cells = cell_mask ? cells_per_axis(resolution, cell) : 0;
   A.vol = reinterpret_cast<const float4*>(vol4);
   A.R = resolution;
   const double h = 2.0 / (resolution - 1);
@@ -311,4 +426,12 @@ extern "C" veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, cons
   if (g <= 2) return launch_march_s<2>(A, rs, n_views, o, stats, stream);
   if (g <= 4) return launch_march_s<4>(A, rs, n_views, o, stats, stream);
   return launch_march_s<8>(A, rs, n_views, o, stats, stream);
+}
+
+extern "C" veg_status veg_raymarch(const veg_camera* cams, int32_t n_views, const float* vol4,
+                                   int32_t resolution, veg_tf tf, float step,
+                                   const veg_material* material, const float* bg, float* out,
+                                   unsigned long long* stats, cudaStream_t stream) {
+  return veg_raymarch_masked(cams, n_views, vol4, resolution, tf, step, material, bg, nullptr, 1,
+                             out, stats, stream);
 }

@@ -95,3 +95,13 @@ def test_host_side_validation_needs_no_gpu(lib):
                              None) == 1
     assert lib.veg_shade_bwd(cams, 1, fake, 8, fake, fake, light, fake, fake, fake + 8, fake,
                              fake, None) == 1
+
+
+def test_raymarch_cell_count_host_logic(lib):
+    from paper_2504_13339_gb300 import _lib
+    assert _lib.veg_raymarch_cells_count(256, 8) == 32 ** 3
+    assert _lib.veg_raymarch_cells_count(19, 4) == 5 ** 3
+    assert _lib.veg_raymarch_cells_count(2, 1) == 1
+    for bad in ((256, 3), (256, 0), (256, 128), (1, 4), (4096, 8)):
+        with pytest.raises(RuntimeError):
+            _lib.veg_raymarch_cells_count(*bad)

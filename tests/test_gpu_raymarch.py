@@ -128,3 +128,90 @@ def test_instrumented_run_is_identical_and_counts_samples():
     assert 0 < samples <= tables <= 3 * samples
     # no ray is longer than the box diagonal
     assert samples <= 2 * 40 * 28 * (2 * 3 ** 0.5 / 0.06 + 1)
+
+
+def cell_masks_numpy(vol, luts, cell):
+    """The macrocell table masks by their definition, in float32 like the
+    kernel: vertex range of each macrocell, widened by 1e-6, the table
+    entries it interpolates between plus one on each side."""
+    R, L = vol.shape[0], luts.shape[1]
+    c = -(-(R - 1) // cell)
+    m = np.zeros((c, c, c), np.uint32)
+    f32 = np.float32
+    for z in range(c):
+        for y in range(c):
+            for x in range(c):
+                blk = vol[z * cell:min(z * cell + cell, R - 1) + 1,
+                          y * cell:min(y * cell + cell, R - 1) + 1,
+                          x * cell:min(x * cell + cell, R - 1) + 1]
+                if np.isnan(blk).any() or luts.shape[0] > 32:
+                    m[z, y, x] = 0xffffffff
+                    continue
+                lo = min(max(f32(blk.min()) - f32(1e-6), f32(0)), f32(1)) * f32(L - 1)
+                hi = min(max(f32(blk.max()) + f32(1e-6), f32(0)), f32(1)) * f32(L - 1)
+                k0, k1 = max(int(np.floor(lo)) - 1, 0), min(int(np.floor(hi)) + 2, L - 1)
+                for t in range(luts.shape[0]):
+                    if (luts[t, k0:k1 + 1, 3] > 0).any():
+                        m[z, y, x] |= np.uint32(1 << t)
+    return m.ravel()
+
+
+@pytest.mark.parametrize("cell", [2, 4])
+def test_cell_masks_follow_their_definition(cell):
+    vol = S.field_volume(S.blob_field(4, 113), 19)  # 18 vertex cells: ragged at cell 4
+    luts = opacity_guided_luts(10, S.colour_ramp(114))
+    v4 = prepared(vol)
+    n = _lib.veg_raymarch_cells_count(19, cell)
+    assert n == (-(-18 // cell)) ** 3
+    mask = torch.zeros(n, dtype=torch.int32, device="cuda")
+    _lib.veg_raymarch_cells(v4, _lib.tf_desc(lut_tensor(luts)), cell, mask)
+    got = mask.cpu().numpy().view(np.uint32)
+    ref = cell_masks_numpy(vol, luts, cell)
+    assert np.array_equal(got, ref)
+    # many macrocells hold only values where map 0 (opaque at 0) has opacity
+    assert (got == 1).sum() > n // 3 and len(np.unique(got)) > 4
+
+
+def masked_and_plain(vol, cams, luts, step, material, view_tf=None, cell=4):
+    v4 = prepared(vol)
+    lt = lut_tensor(luts)
+    vt = None if view_tf is None else torch.as_tensor(np.asarray(view_tf, np.int32),
+                                                      device="cuda")
+    tf = _lib.tf_desc(lt, vt)
+    n_out = 1 if view_tf is not None else lt.shape[0]
+    shape = (len(cams), n_out, cams[0].height, cams[0].width, 4)
+    plain, masked = torch.empty(shape, device="cuda"), torch.empty(shape, device="cuda")
+    st0 = torch.zeros(2, dtype=torch.int64, device="cuda")
+    st1 = torch.zeros(3, dtype=torch.int64, device="cuda")
+    c_cams = _lib.cameras(cams)
+    _lib.veg_raymarch(c_cams, v4, tf, step, plain, material, stats=st0)
+    mask = torch.empty(_lib.veg_raymarch_cells_count(vol.shape[0], cell), dtype=torch.int32,
+                       device="cuda")
+    _lib.veg_raymarch_cells(v4, _lib.tf_desc(lt), cell, mask)
+    _lib.veg_raymarch_masked(c_cams, v4, tf, step, masked, mask, cell, material, stats=st1)
+    torch.cuda.synchronize()
+    return plain.cpu().numpy(), masked.cpu().numpy(), st0.cpu().numpy(), st1.cpu().numpy()
+
+
+def test_masked_raymarch_is_bit_identical_and_skips():
+    """Skipping macrocells whose live tables have no opacity changes no
+    image bit; taken + skipped samples equal the plain run's samples."""
+    vol = S.field_volume(S.blob_field(6, 115), 33)
+    cams = S.orbit_cameras(2, 116, 40, 28)
+    luts = opacity_guided_luts(10, S.colour_ramp(117))
+    plain, masked, st0, st1 = masked_and_plain(vol, cams, luts, 2.0 / 32 / 2, MAT)
+    assert np.array_equal(plain, masked)
+    assert st1[0] + st1[2] == st0[0] and st1[2] > 0 and st1[1] <= st0[1]
+    one_p, one_m, _, _ = masked_and_plain(vol, cams, luts, 0.04, None, view_tf=[9, 3])
+    assert np.array_equal(one_p, one_m)
+
+
+def test_masked_raymarch_at_training_size():
+    """256^3 volume, 800 x 800, the 10 maps, shaded: masked images equal the
+    plain ones for two views, and most samples are skipped."""
+    vol = S.field_volume(S.blob_field(8, 118), 256)
+    cams = S.grid_orbit_cameras(16, 10, 800, 800)[40:42]
+    luts = opacity_guided_luts(10, S.colour_ramp(119))
+    plain, masked, st0, st1 = masked_and_plain(vol, cams, luts, (2.0 / 255) / 2, MAT, cell=8)
+    assert np.array_equal(plain, masked)
+    assert st1[0] + st1[2] == st0[0] and st1[2] > st1[0]
