@@ -776,31 +776,13 @@ CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
   return A;
 }
 
-// Allows `dyn` bytes of dynamic shared memory for `kern` and prefers the
-// largest shared-memory carveout (once per size increase); refuses sizes
-// beyond the 227 KB a CTA may hold.
-template <typename K>
-veg_status prepare_smem(K kern, size_t dyn, size_t* configured) {
-  if (dyn <= *configured) return VEG_OK;
-  cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return VEG_ERR_CUDA;
-  if (fa.sharedSizeBytes + dyn > 227 * 1024) return VEG_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-    return VEG_ERR_UNSUPPORTED;
-  *configured = dyn;
-  return VEG_OK;
-}
-
 template <int TG, bool STATS, bool LIT>
 veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc,
                         unsigned long long* stats, cudaStream_t stream) {
   const size_t smem = (size_t)TG * A.lut_size * sizeof(float4);
   auto kern = composite_fwd_kernel<TG, STATS, LIT>;
-  static size_t configured = 0;
-  veg_status st = prepare_smem(kern, smem, &configured);
+  static SmemRecord configured;
+  veg_status st = prepare_smem(kern, smem, configured, true);
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
@@ -815,8 +797,8 @@ veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const
                         unsigned long long* stats, cudaStream_t stream) {
   const size_t smem = bwd_smem_bytes(TG, A.lut_size, LIT);
   auto kern = composite_bwd_kernel<TG, STATS, LIT>;
-  static size_t configured = 0;
-  veg_status st = prepare_smem(kern, smem, &configured);
+  static SmemRecord configured;
+  veg_status st = prepare_smem(kern, smem, configured, true);
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);

@@ -292,14 +292,9 @@ template <int TG, bool STATS>
 veg_status launch_march(const MarchArgs& A, const RaySet& rs, int n_views, float4* out,
                         unsigned long long* stats, cudaStream_t stream) {
   const size_t smem = (size_t)TG * A.lut_size * sizeof(float4);
-  static size_t configured = 0;
-  if (smem > configured) {
-    if (smem > 227 * 1024) return VEG_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(raymarch_kernel<TG, STATS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return VEG_ERR_UNSUPPORTED;
-    configured = smem;
-  }
+  static SmemRecord configured;  // default carveout: the volume samples want L1
+  veg_status st = prepare_smem(raymarch_kernel<TG, STATS>, smem, configured, false);
+  if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
   raymarch_kernel<TG, STATS><<<grid, 256, smem, stream>>>(A, rs, out, stats);

@@ -350,13 +350,9 @@ extern "C" veg_status veg_l1_ssim_loss(const float* out, const float* target, in
   for (int k = 0; k <= 2 * kR; ++k) win.w[k] = (float)(wd[k] / wsum);
   const double count = (double)n_images * height * width * 3.0;
   const size_t smem = sizeof(LossSmem);
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(l1_ssim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return VEG_ERR_UNSUPPORTED;
-    configured = true;
-  }
+  static SmemRecord configured;
+  veg_status st = prepare_smem(l1_ssim_kernel, smem, configured, false);
+  if (st != VEG_OK) return st;
   double2* part = reinterpret_cast<double2*>(workspace);
   l1_ssim_kernel<<<dim3((unsigned)(tx * ty), (unsigned)n_images), 256, smem, stream>>>(
       win, reinterpret_cast<const float4*>(out), reinterpret_cast<const float4*>(target), height,

@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "veg.h"
 
 namespace veg {
@@ -22,6 +25,40 @@ veg_status launch_status();
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Largest dynamic shared-memory size one kernel has been configured for, per
+// device (the attribute belongs to the function on each device).  The slow
+// path holds a lock, so the attribute only grows under concurrent callers.
+struct SmemRecord {
+  static constexpr int kDevices = 64;
+  std::atomic<size_t> bytes[kDevices];
+  std::mutex lock;
+};
+
+// Allows `dyn` bytes of dynamic shared memory for `kern` on the current
+// device (and, with max_carveout, prefers the largest shared-memory
+// carveout), once per size increase; refuses sizes beyond the 227 KB a CTA
+// may hold.
+template <typename K>
+veg_status prepare_smem(K kern, size_t dyn, SmemRecord& rec, bool max_carveout) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SmemRecord::kDevices)
+    return VEG_ERR_CUDA;
+  if (dyn <= rec.bytes[dev].load(std::memory_order_acquire)) return VEG_OK;
+  std::lock_guard<std::mutex> guard(rec.lock);
+  if (dyn <= rec.bytes[dev].load(std::memory_order_acquire)) return VEG_OK;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return VEG_ERR_CUDA;
+  if (fa.sharedSizeBytes + dyn > 227 * 1024) return VEG_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+      cudaSuccess)
+    return VEG_ERR_UNSUPPORTED;
+  if (max_carveout && cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return VEG_ERR_UNSUPPORTED;
+  rec.bytes[dev].store(dyn, std::memory_order_release);
+  return VEG_OK;
+}
 
 // Bump allocator over a caller-provided workspace (256-byte aligned pieces).
 struct Carver {
@@ -96,6 +133,7 @@ __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b);
 __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float dv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+
 // Paired float32 operations (one f32x2 instruction on sm_100-family GPUs);
 // each half is rounded exactly like its scalar counterpart above.
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
