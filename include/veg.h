@@ -391,6 +391,24 @@ veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, const float* 
                          float beta2, float eps, int32_t step, cudaStream_t stream);
 
 /*
+ * veg_adam_step_counted -- veg_adam_step with the step number kept on the
+ * device, so that a captured CUDA graph can replay the optimiser: `counter`
+ * (device, 16-byte aligned, caller-owned, zeroed before the first step)
+ * holds the steps taken; each call advances it by one (one single-thread
+ * launch) and takes the step with t = the new count, its bias corrections
+ * computed in double on the device as veg_adam_step computes them on the
+ * host.  Two launches (one with n = 0).
+ */
+typedef struct veg_adam_counter {
+  int64_t step;
+  float inv_bc1;      /* 1 / (1 - beta1^t) of the last step */
+  float inv_sqrt_bc2; /* 1 / sqrt(1 - beta2^t) of the last step */
+} veg_adam_counter;
+veg_status veg_adam_step_counted(const veg_adam_arrays* arrays, int64_t n, const float* lr,
+                                 float beta1, float beta2, float eps, veg_adam_counter* counter,
+                                 cudaStream_t stream);
+
+/*
  * veg_grad_stats_accumulate -- the densification statistic of Sec. 4.2
  * (3D Gaussian splatting's "view-space positional gradient"): for every view
  * v and Gaussian i with tiles_touched[v][i] > 0, adds |(g_x W/2, g_y H/2)| to

@@ -116,6 +116,9 @@ _SIGS = {
                                         _P]),
     "veg_adam_step": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, _I32, _P]),
+    "veg_adam_step_counted": (ctypes.c_int, [ctypes.POINTER(veg_adam_arrays), _I64, _P,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_float, _P,
+                                             _P]),
     "veg_volume_prepare": (ctypes.c_int, [_P, _I32, _P, _P]),
     "veg_train_step": (ctypes.c_int, [ctypes.POINTER(veg_train_args), _I32, _I32, _I32, _I32,
                                       _P]),
@@ -346,6 +349,16 @@ def veg_adam_step(arrays, n, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream
     _check("veg_adam_step",
            load().veg_adam_step(ctypes.byref(arrays), n, ctypes.cast(lrs, ctypes.c_void_p),
                                 beta1, beta2, eps, step, _stream(stream)))
+
+
+def veg_adam_step_counted(arrays, n, lr, counter, beta1=0.9, beta2=0.999, eps=1e-15,
+                          stream=None):
+    """counter: 16-byte device tensor (e.g. torch.zeros(2, dtype=torch.int64)) holding the
+    steps taken, zeroed before the first step; advanced by one on the device."""
+    lrs = (ctypes.c_float * 20)(*[float(x) for x in np.asarray(lr, np.float64).ravel()])
+    _check("veg_adam_step_counted",
+           load().veg_adam_step_counted(ctypes.byref(arrays), n, ctypes.cast(lrs, ctypes.c_void_p),
+                                        beta1, beta2, eps, _ptr(counter), _stream(stream)))
 
 
 def veg_grad_stats_accumulate(grad2d, tiles_touched, n, n_views, width, height, accum, count,

@@ -282,30 +282,42 @@ struct AdamArgs {
   float4* rendered[2];
   float lr[5][4];
   float b1, b2, eps, inv_bc1, inv_sqrt_bc2;
+  const veg_adam_counter* counter;  // bias corrections from here when set
 };
 
 __device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 __device__ __forceinline__ void adam_one(float& p, float& m, float& v, float g, float lr,
-                                         const AdamArgs& A) {
+                                         const AdamArgs& A, float inv_bc1, float inv_sqrt_bc2) {
   m = A.b1 * m + (1.0f - A.b1) * g;
   v = A.b2 * v + (1.0f - A.b2) * g * g;
-  p -= lr * (m * A.inv_bc1) / (sqrtf(v) * A.inv_sqrt_bc2 + A.eps);
+  p -= lr * (m * inv_bc1) / (sqrtf(v) * inv_sqrt_bc2 + A.eps);
+}
+
+// Advances the step counter and stores the step's bias corrections
+// 1 / (1 - beta1^t) and 1 / sqrt(1 - beta2^t) (double, like the host path).
+__global__ void adam_count_kernel(veg_adam_counter* c, float b1, float b2) {
+  const int64_t t = c->step + 1;
+  c->step = t;
+  c->inv_bc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+  c->inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - pow((double)b2, (double)t)));
 }
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (i >= n || A.param[a] == nullptr) return;
+  const float inv_bc1 = A.counter ? A.counter->inv_bc1 : A.inv_bc1;
+  const float inv_sqrt_bc2 = A.counter ? A.counter->inv_sqrt_bc2 : A.inv_sqrt_bc2;
   float4 p = A.param[a][i], g = A.grad[a][i], m = A.m[a][i], v = A.v[a][i];
   if (a < 2) {  // the fourth component is sigmoid-activated
     const float s = sigmoid_f(p.w);
     g.w *= s * (1.0f - s);
   }
-  adam_one(p.x, m.x, v.x, g.x, A.lr[a][0], A);
-  adam_one(p.y, m.y, v.y, g.y, A.lr[a][1], A);
-  adam_one(p.z, m.z, v.z, g.z, A.lr[a][2], A);
-  adam_one(p.w, m.w, v.w, g.w, A.lr[a][3], A);
+  adam_one(p.x, m.x, v.x, g.x, A.lr[a][0], A, inv_bc1, inv_sqrt_bc2);
+  adam_one(p.y, m.y, v.y, g.y, A.lr[a][1], A, inv_bc1, inv_sqrt_bc2);
+  adam_one(p.z, m.z, v.z, g.z, A.lr[a][2], A, inv_bc1, inv_sqrt_bc2);
+  adam_one(p.w, m.w, v.w, g.w, A.lr[a][3], A, inv_bc1, inv_sqrt_bc2);
   A.param[a][i] = p;
   A.m[a][i] = m;
   A.v[a][i] = v;
@@ -364,13 +376,15 @@ extern "C" veg_status veg_l1_ssim_loss(const float* out, const float* target, in
   return launch_status();
 }
 
-extern "C" veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, const float* lr,
-                                    float beta1, float beta2, float eps, int32_t step,
-                                    cudaStream_t stream) {
-  if (!arrays || !lr || n < 0 || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) ||
+namespace {
+
+// The arrays and hyper-parameters of one step (step < 1: corrections from
+// the device counter).
+veg_status adam_args(const veg_adam_arrays* arrays, int64_t n, const float* lr, float beta1,
+                     float beta2, float eps, int32_t step, AdamArgs& A) {
+  if (!arrays || !lr || n < 0 || !(beta1 >= 0.f && beta1 < 1.f) ||
       !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
     return VEG_ERR_INVALID_ARGUMENT;
-  AdamArgs A;
   for (int a = 0; a < 5; ++a) {
     A.param[a] = reinterpret_cast<float4*>(arrays->param[a]);
     A.grad[a] = reinterpret_cast<const float4*>(arrays->grad[a]);
@@ -389,10 +403,42 @@ extern "C" veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, co
   A.b1 = beta1;
   A.b2 = beta2;
   A.eps = eps;
-  A.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)step)));
-  A.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)beta2, (double)step)));
-  if (n == 0) return VEG_OK;
+  A.inv_bc1 = A.inv_sqrt_bc2 = 1.0f;
+  if (step >= 1) {
+    A.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)step)));
+    A.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)beta2, (double)step)));
+  }
+  A.counter = nullptr;
+  return VEG_OK;
+}
+
+}  // namespace
+
+extern "C" veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, const float* lr,
+                                    float beta1, float beta2, float eps, int32_t step,
+                                    cudaStream_t stream) {
+  if (step < 1) return VEG_ERR_INVALID_ARGUMENT;
+  AdamArgs A;
+  veg_status st = adam_args(arrays, n, lr, beta1, beta2, eps, step, A);
+  if (st != VEG_OK || n == 0) return st;
   adam_kernel<<<dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream>>>(A, n);
   count_launch();
+  return launch_status();
+}
+
+extern "C" veg_status veg_adam_step_counted(const veg_adam_arrays* arrays, int64_t n,
+                                            const float* lr, float beta1, float beta2, float eps,
+                                            veg_adam_counter* counter, cudaStream_t stream) {
+  if (!counter || (reinterpret_cast<uintptr_t>(counter) & 15)) return VEG_ERR_INVALID_ARGUMENT;
+  AdamArgs A;
+  veg_status st = adam_args(arrays, n, lr, beta1, beta2, eps, 0, A);
+  if (st != VEG_OK) return st;
+  A.counter = counter;
+  adam_count_kernel<<<1, 1, 0, stream>>>(counter, beta1, beta2);
+  count_launch();
+  if (n > 0) {
+    adam_kernel<<<dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream>>>(A, n);
+    count_launch();
+  }
   return launch_status();
 }

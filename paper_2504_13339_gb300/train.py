@@ -85,6 +85,7 @@ class TrainParams:
         self.m = [None if r is None else torch.zeros_like(r) for r in self.raw]
         self.v = [None if r is None else torch.zeros_like(r) for r in self.raw]
         self.step = 0
+        self.counter = None  # device step counter (use_device_counter)
         # the full-capacity arrays behind the row views above:
         # (rows, raw, m, v, mean_v, logscale_w) and the gradients' (rows, grads)
         self.store = (self.n, self.raw, self.m, self.v, self.mean_v, self.logscale_w)
@@ -102,7 +103,20 @@ class TrainParams:
 
     def adam(self, lr, stream=None):
         self.step += 1
-        _lib.veg_adam_step(self._arrays, self.n, lr, self.step, stream=stream)
+        if self.counter is not None:
+            _lib.veg_adam_step_counted(self._arrays, self.n, lr, self.counter, stream=stream)
+        else:
+            _lib.veg_adam_step(self._arrays, self.n, lr, self.step, stream=stream)
+
+    def use_device_counter(self):
+        """Keeps the Adam step number on the device (veg_adam_step_counted), so
+        that a captured CUDA graph can replay the step; the host count `step`
+        then only advances with eager calls."""
+        if self.counter is None:
+            dev = self.raw[0].device
+            self.counter = torch.zeros(2, dtype=torch.int64, device=dev)
+            self.counter[0] = self.step
+        return self.counter
 
     def replace(self, n, store):
         """Adopts the first n rows of `store` = (rows, raw, m, v, mean_v,

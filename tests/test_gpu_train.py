@@ -130,6 +130,38 @@ def test_adam_matches_oracle():
     assert np.allclose(rend[1].cpu().numpy(), lw, rtol=1e-5, atol=1e-6)
 
 
+def test_counted_adam_equals_host_step():
+    """veg_adam_step_counted (step number on the device) takes the same
+    steps as veg_adam_step, bit for bit, and advances its counter."""
+    rng = np.random.default_rng(73)
+    n = 2049
+    raw = [rng.normal(0, 1, (n, 4)).astype(np.float32) for _ in range(5)]
+    lr = rng.uniform(1e-3, 5e-2, (5, 4))
+    runs = []
+    for counted in (False, True):
+        p = [dev(r) for r in raw]
+        gr = [torch.zeros_like(t) for t in p]
+        m = [torch.zeros_like(t) for t in p]
+        v = [torch.zeros_like(t) for t in p]
+        rend = [torch.zeros_like(p[0]), torch.zeros_like(p[1])]
+        arrays = _lib.adam_arrays(p, gr, m, v, rend)
+        counter = torch.zeros(2, dtype=torch.int64, device="cuda")
+        grng = np.random.default_rng(74)
+        for step in range(1, 6):
+            for a in range(5):
+                gr[a].copy_(dev(grng.normal(0, 1, (n, 4)).astype(np.float32)))
+            if counted:
+                _lib.veg_adam_step_counted(arrays, n, lr, counter)
+            else:
+                _lib.veg_adam_step(arrays, n, lr, step)
+        torch.cuda.synchronize()
+        runs.append([t.cpu().numpy() for t in p + m + v + rend])
+        if counted:
+            assert int(counter[0]) == 5
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
+
 def small_training_set(n=300, size=(48, 40), n_views=2, K=3, seed=74):
     bf = S.blob_field(4, seed)
     g, lt = S.initial_model(n, bf, seed + 1, weight=0.5)
@@ -254,5 +286,59 @@ def test_native_step_equals_the_python_sequence():
     for x, y in zip(ga, gb):
         assert np.abs(x - y).max() <= 1e-4 * np.abs(y).max()
     lr = default_lr()
+    for a, (x, y) in enumerate(zip(pa, pb)):
+        assert np.all(np.abs(x - y) <= 2 * 3 * lr[a][None, :] + 1e-6), a
+
+
+def test_graph_replayed_training_step_matches_eager():
+    """The whole training step (zeroing, project, bin, composite, L1, both
+    backward passes, Adam with the device step counter) captured once as a
+    CUDA graph and replayed takes the same three steps as the eager calls:
+    losses within float32 summation-order noise, parameters within two Adam
+    steps (the backward's float atomics may order sums differently)."""
+    from paper_2504_13339_gb300.graphs import CapturedStep
+    from paper_2504_13339_gb300.render import SplatPipeline
+    from paper_2504_13339_gb300.train import default_lr
+    g, lt, cams, luts, tg = small_training_set(seed=97)
+    cams = cams[:1]
+    lut = lut_tensor(luts[:2])
+    target = dev(tg[:1, :2])
+    lr = default_lr(lighting=False)
+    runs = []
+    for graphed in (False, True):
+        P = TrainParams(g)
+        P.use_device_counter()
+        p = SplatPipeline(P.n, cams, n_tf=2)
+        start = ([t.clone() for t in P.raw[:3]], [t.clone() for t in P.m[:3]],
+                 [t.clone() for t in P.v[:3]], P.mean_v.clone(), P.logscale_w.clone())
+
+        def step():
+            P.zero_grad()
+            p.project(P.mean_v, P.logscale_w, P.raw[2], lut)
+            p.bin_sort()
+            p.composite(lut)
+            p.l1(target)
+            p.backward_2d(p.loss_grad)
+            p.project_backward(*P.grads[:3])
+            P.adam(lr)
+        losses = []
+        if graphed:
+            cs = CapturedStep(step)  # its two warm-up steps run eagerly: restore
+            for dst, src in zip(P.raw[:3] + P.m[:3] + P.v[:3] + [P.mean_v, P.logscale_w],
+                                start[0] + start[1] + start[2] + [start[3], start[4]]):
+                dst.copy_(src)
+            P.counter.zero_()
+            for _ in range(3):
+                cs.replay()
+                losses.append(p.loss.clone())
+        else:
+            for _ in range(3):
+                step()
+                losses.append(p.loss.clone())
+        torch.cuda.synchronize()
+        assert int(P.counter[0]) == 3
+        runs.append(([float(x) for x in losses], [t.cpu().numpy() for t in P.raw[:3]]))
+    (la, pa), (lb, pb) = runs
+    assert np.allclose(la, lb, rtol=1e-5)
     for a, (x, y) in enumerate(zip(pa, pb)):
         assert np.all(np.abs(x - y) <= 2 * 3 * lr[a][None, :] + 1e-6), a
