@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libveg.so")
 
 VEG_OK = 0
+VEG_MAX_VIEWS = 64  # include/veg.h
 VEG_ERR_CAPACITY = 2
 STATUS_NAMES = {0: "VEG_OK", 1: "VEG_ERR_INVALID_ARGUMENT", 2: "VEG_ERR_CAPACITY",
                 3: "VEG_ERR_CUDA", 4: "VEG_ERR_TIMEOUT", 5: "VEG_ERR_UNSUPPORTED"}

@@ -17,7 +17,8 @@ veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 cudaStream_t stream) {
   CompArgs A = make_args(cams, geo, aux, vals, ranges, order, tf, bg, shade);
   (void)n;
-  const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, false);
+  const int TG =
+      tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, false, tf.lut_size, shade != nullptr);
   if (shade) {
     if (stats) return VEG_ERR_UNSUPPORTED;
     switch (TG) {
@@ -146,7 +147,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
                          reinterpret_cast<const float4*>(splat_aux), vals,
                          reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
                          splat_shade);
-  const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, true);
+  const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, true, tf.lut_size, lit);
   const float4* o4 = reinterpret_cast<const float4*>(out);
   const float4* d4 = reinterpret_cast<const float4*>(dL_dout);
   if (lit) {

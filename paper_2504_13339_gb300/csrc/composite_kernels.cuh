@@ -742,14 +742,20 @@ size_t bwd_smem_bytes(int TG, int L, bool lit) {
 // TF group size: the caller's choice, else 1 for the forward (measured
 // fastest at the training-step and sweep shapes: each TF stops at its own
 // termination) and up to 4 for the backward (whose replay shares each
-// splat's geometry and reductions across the group).
-int pick_group(int tf_group, int n_tf, bool bwd) {
+// splat's geometry and reductions across the group); halved until the
+// group's shared memory fits one CTA (227 KB).  The group size changes no
+// result; one table of up to 4096 entries always fits.
+int pick_group(int tf_group, int n_tf, bool bwd, int lut_size, bool lit) {
   int g = tf_group;
   if (g <= 0) g = bwd ? std::min(n_tf, 4) : 1;
-  if (g <= 1) return 1;
-  if (g <= 2) return 2;
-  if (g <= 4 || bwd) return 4;
-  return 8;
+  g = g <= 1 ? 1 : g <= 2 ? 2 : (g <= 4 || bwd) ? 4 : 8;
+  auto fits = [&](int tg) {
+    const size_t bytes = bwd ? bwd_smem_bytes(tg, lut_size, lit) + 1024
+                             : (size_t)tg * lut_size * 16 + (size_t)tg * kBatch * 16 + 9 * 1024;
+    return bytes <= (size_t)227 * 1024;
+  };
+  while (g > 1 && !fits(g)) g /= 2;
+  return g;
 }
 
 CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,

@@ -416,7 +416,10 @@ extern "C" veg_status veg_raymarch_masked(const veg_camera* cams, int32_t n_view
     V.near_plane = cams[v].near_plane;
   }
   float4* o = reinterpret_cast<float4*>(out);
-  const int g = tf.view_tf ? 1 : std::min(tf.n_tf, 8);
+  // tables per sample pass: up to 8, halved until they fit a CTA's shared
+  // memory (one table of up to 4096 entries always fits)
+  int g = tf.view_tf ? 1 : std::min(tf.n_tf, 8);
+  while (g > 1 && (size_t)g * tf.lut_size * sizeof(float4) > (size_t)227 * 1024) g /= 2;
   if (g <= 1) return launch_march_s<1>(A, rs, n_views, o, stats, stream);
   if (g <= 2) return launch_march_s<2>(A, rs, n_views, o, stats, stream);
   if (g <= 4) return launch_march_s<4>(A, rs, n_views, o, stats, stream);

@@ -95,6 +95,20 @@ def test_host_side_validation_needs_no_gpu(lib):
                              None) == 1
     assert lib.veg_shade_bwd(cams, 1, fake, 8, fake, fake, light, fake, fake, fake + 8, fake,
                              fake, None) == 1
+    # Adam: the device step counter must be given and 16-byte aligned
+    arrays = _lib.veg_adam_arrays()
+    lrs = (ctypes.c_float * 20)()
+    assert lib.veg_adam_step_counted(ctypes.byref(arrays), 0, lrs, 0.9, 0.999, 1e-15, None,
+                                     None) == 1
+    assert lib.veg_adam_step_counted(ctypes.byref(arrays), 0, lrs, 0.9, 0.999, 1e-15, fake + 8,
+                                     None) == 1
+    assert lib.veg_adam_step(ctypes.byref(arrays), 0, lrs, 0.9, 0.999, 1e-15, 0, None) == 1
+    # raymarching: the mask's cell size is checked on the host
+    tf16 = _lib.veg_tf(fake, 16, 1)
+    assert lib.veg_raymarch_cells(fake, 16, tf16, 3, fake, None) == 1
+    assert lib.veg_raymarch_cells(fake, 16, tf16, 128, fake, None) == 1
+    assert lib.veg_raymarch_masked(cams, 1, fake, 16, tf16, 0.1, None, None, fake, 3, fake,
+                                   None, None) == 1
 
 
 def test_raymarch_cell_count_host_logic(lib):

@@ -284,6 +284,110 @@ def test_l1_loss_matches_oracle():
 
 
 # ----------------------------------------------------------------------------
+# maximum sizes: 4096-entry tables, 64 views, 16384-pixel rows
+# ----------------------------------------------------------------------------
+
+def test_largest_tables_every_group_and_backward():
+    """Tables of 4096 entries (the largest accepted) for 5 TFs: every TF
+    group gives the same image bit for bit (groups too large for a CTA's
+    shared memory are halved), the image and every gradient match the
+    oracle."""
+    g, cams = small_multiview()
+    g = g.subset(np.arange(500))
+    base = S.bump_tfs(5, 121)
+    x = np.linspace(0.0, 1.0, 4096)
+    xs = np.linspace(0.0, 1.0, base.shape[1])
+    tfs = np.stack([np.stack([np.interp(x, xs, t[:, c]) for c in range(4)], 1)
+                    for t in base]).astype(np.float32)
+    imgs = []
+    for group in (0, 1, 2, 4, 8):
+        p, st, m, tens, luts = gpu_forward(g, cams, tfs, tf_group=group)
+        assert st == _lib.VEG_OK
+        imgs.append(p.out.cpu().numpy())
+    assert all(np.array_equal(imgs[0], im) for im in imgs[1:])
+    proj, bins, fwd = O.render(cams, g, tfs, record=True)
+    image_check(imgs[0], fwd)
+    p, st, m, tens, luts = gpu_forward(g, cams, tfs)
+    dout = np.random.default_rng(122).standard_normal(fwd["out"].shape)
+    dout[fwd["flag"]] = 0.0
+    grads = [torch.zeros_like(t) for t in tens]
+    p.backward(dev(dout.astype(np.float32)), *grads)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd(proj, cams, bins, tfs, (0, 0, 0), fwd, dout)
+    gm, gl, gq = O.params_grad(cams, g, proj, g2)
+    grad_check(grads[0].cpu().numpy()[:, :3], gm[:, :3], "mean")
+    grad_check(grads[0].cpu().numpy()[:, 3], gm[:, 3], "v")
+    grad_check(grads[1].cpu().numpy(), gl, "logscale_w")
+    grad_check(grads[2].cpu().numpy(), gq, "quat")
+
+
+def test_maximum_view_count():
+    """VEG_MAX_VIEWS (64) views in one projection, binning and compositing
+    launch: every view's tile lists bit-exact and images within the bar."""
+    g = S.uniform_gaussians(400, 123, logscale_mean=-2.6)
+    cams = S.orbit_cameras(_lib.VEG_MAX_VIEWS, 124, 24, 20)
+    tfs = S.bump_tfs(2, 125)
+    p, st, m, _, _ = gpu_forward(g, cams, tfs)
+    assert st == _lib.VEG_OK
+    proj, bins, fwd = O.render(cams, g, tfs)
+    assert m == bins["keys"].size
+    assert np.array_equal(p.vals[:m].cpu().numpy().astype(np.uint32), bins["vals"])
+    assert np.array_equal(p.keys[:m].cpu().numpy().view(np.uint64), bins["keys"])
+    assert np.array_equal(p.ranges.cpu().numpy().reshape(len(cams), -1, 2), bins["ranges"])
+    image_check(p.out.cpu().numpy(), fwd)
+
+
+def test_widest_image_row():
+    """A 16384 x 16 image (1024 tiles in one row, the largest width): tile
+    lists and images bit-exact / within the bar on tiles at both ends and in
+    the middle, and the gradients of a loss on those tiles."""
+    rng = np.random.default_rng(126)
+    n = 3000
+    mv = np.zeros((n, 4), np.float32)
+    mv[:, 0] = rng.uniform(-1.3, 1.3, n)
+    mv[:, 1] = rng.normal(0.0, 0.002, n)
+    mv[:, 2] = rng.uniform(-0.5, 0.5, n)
+    mv[:, 3] = rng.uniform(0.0, 1.0, n)
+    ls = np.zeros((n, 4), np.float32)
+    ls[:, :3] = rng.normal(-5.8, 0.3, (n, 3))
+    ls[:, 3] = rng.uniform(0.3, 1.0, n)
+    q = rng.standard_normal((n, 4)).astype(np.float32)
+    g = S.Gaussians(mv, ls, q / np.linalg.norm(q, axis=1, keepdims=True))
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 16384, 16)
+    tfs = S.bump_tfs(1, 127)
+    p, st, m, tens, luts = gpu_forward(g, [cam], tfs)
+    assert st == _lib.VEG_OK and cam.tiles_x == 1024
+    tiles = [0, 1, 511, 512, 1022, 1023]
+    pr = O.project32(cam, g, tfs)
+    assert np.array_equal(p.tiles.cpu().numpy(), pr["count"])
+    lists = O.tile_lists(pr, cam, tiles)
+    rng_t = p.ranges.cpu().numpy()
+    vals = p.vals.cpu().numpy()
+    for t in tiles:
+        lo, hi = rng_t[t]
+        assert np.array_equal(vals[lo:hi].astype(np.int64), lists[t]), t
+    assert sum(len(lists[t]) for t in tiles) > 50
+    bins = O.bins_from_lists([lists], 1, cam.tiles_x * cam.tiles_y)
+    fwd = O.composite_fwd([pr], [cam], bins, tfs, tiles=tiles, record=True)
+    out = p.out.cpu().numpy()
+    dout = np.zeros(fwd["out"].shape)
+    for t in tiles:
+        px, py = O._tile_pixels(cam, t)
+        ok = ~fwd["flag"][0][:, py, px]
+        assert np.all(np.abs(out[0][:, py, px] - fwd["out"][0][:, py, px])[ok] <= IMG_TOL), t
+        dout[0][:, py, px] = rng.standard_normal(dout[0][:, py, px].shape)
+    dout[fwd["flag"]] = 0.0
+    grads = [torch.zeros_like(t) for t in tens]
+    p.backward(dev(dout.astype(np.float32)), *grads)
+    torch.cuda.synchronize()
+    g2 = O.composite_bwd([pr], [cam], bins, tfs, (0, 0, 0), fwd, dout, tiles=tiles)
+    gm, gl, gq = O.params_grad([cam], g, [pr], g2)
+    grad_check(grads[0].cpu().numpy(), gm, "mean_v")
+    grad_check(grads[1].cpu().numpy(), gl, "logscale_w")
+    grad_check(grads[2].cpu().numpy(), gq, "quat")
+
+
+# ----------------------------------------------------------------------------
 # the training-step workload at full size: 1M Gaussians, 1024^2, 4 TFs
 # ----------------------------------------------------------------------------
 
