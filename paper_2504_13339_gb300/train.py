@@ -86,6 +86,7 @@ class TrainParams:
         self.v = [None if r is None else torch.zeros_like(r) for r in self.raw]
         self.step = 0
         self.counter = None  # device step counter (use_device_counter)
+        self.flat_grads = None  # one buffer behind the gradients (use_flat_gradients)
         # the full-capacity arrays behind the row views above:
         # (rows, raw, m, v, mean_v, logscale_w) and the gradients' (rows, grads)
         self.store = (self.n, self.raw, self.m, self.v, self.mean_v, self.logscale_w)
@@ -107,6 +108,26 @@ class TrainParams:
             _lib.veg_adam_step_counted(self._arrays, self.n, lr, self.counter, stream=stream)
         else:
             _lib.veg_adam_step(self._arrays, self.n, lr, self.step, stream=stream)
+
+    def use_flat_gradients(self):
+        """Re-points the gradient arrays into one flat buffer `flat_grads`
+        (zeroed), so that a data-parallel step all-reduces them with one
+        collective."""
+        if self.flat_grads is None:
+            live = [g for g in self.grads if g is not None]
+            flat = torch.zeros(sum(g.numel() for g in live), device=live[0].device)
+            off, grads = 0, []
+            for g in self.grads:
+                if g is None:
+                    grads.append(None)
+                    continue
+                grads.append(flat[off:off + g.numel()].view_as(g))
+                off += g.numel()
+            self.flat_grads, self.grads = flat, grads
+            self._grad_store = (self.n, grads)
+            self._arrays = _lib.adam_arrays(self.raw, self.grads, self.m, self.v,
+                                            (self.mean_v, self.logscale_w))
+        return self.flat_grads
 
     def use_device_counter(self):
         """Keeps the Adam step number on the device (veg_adam_step_counted), so
@@ -132,7 +153,23 @@ class TrainParams:
         self.raw, self.m, self.v = [cut(t) for t in raw], [cut(t) for t in m], [cut(t) for t in v]
         self.mean_v, self.logscale_w = mean_v[:n], logscale_w[:n]
         grows, gfull = self._grad_store
-        if n > grows:
+        if self.flat_grads is not None:
+            # one contiguous [n][4] run per array, so the flat buffer stays whole
+            live = sum(r is not None for r in raw)
+            if self.flat_grads.numel() < live * n * 4:
+                self.flat_grads = torch.zeros(live * (n + n // 4) * 4,
+                                              device=self.flat_grads.device)
+            off, gfull = 0, []
+            for r in raw:
+                if r is None:
+                    gfull.append(None)
+                    continue
+                gfull.append(self.flat_grads[off:off + n * 4].view(n, 4))
+                off += n * 4
+            self.flat_grads = self.flat_grads[:off] if off else self.flat_grads
+            grows = n
+            self._grad_store = (grows, gfull)
+        elif n > grows:
             grows = n + n // 4
             gfull = [None if r is None else torch.empty(grows, 4, device=r.device)
                      for r in raw]
