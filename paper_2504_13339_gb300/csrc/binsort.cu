@@ -587,16 +587,16 @@ Layout carve(void* ws, int64_t nrec, int64_t capacity) {
 // Blocks for a pass over at most `nblocks` chunks: one wave of the scatter
 // (4 CTAs per SM) at most; the kernels stride over the chunks that hold items.
 int pass_grid(int nblocks) {
-  static int sms[64] = {0};
+  static std::atomic<int> sms[64];  // per device, 0 until queried
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-  if (sms[dev] == 0) {
-    int v = 0;
+  int v = sms[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
       v = 1;
-    sms[dev] = v;
+    sms[dev].store(v, std::memory_order_relaxed);
   }
-  return std::max(1, std::min(nblocks, 4 * sms[dev]));
+  return std::max(1, std::min(nblocks, 4 * v));
 }
 
 void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
