@@ -58,6 +58,7 @@ constexpr int kLossBlocks = 1024;
 __global__ void __launch_bounds__(256)
     l1_kernel(const float4* __restrict__ out, const float4* __restrict__ target, int64_t n,
               float inv_count, float4* __restrict__ grad, float* __restrict__ partials) {
+  pdl_enter();
   __shared__ float s[256];
   float acc = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(kLossBlocks)
     l1_final_kernel(const float* __restrict__ partials, float inv_count, float* __restrict__ loss) {
+  pdl_enter();
   __shared__ double s[kLossBlocks];
   s[threadIdx.x] = (double)partials[threadIdx.x];
   __syncthreads();
@@ -157,10 +159,10 @@ extern "C" veg_status veg_l1_loss(const float* out, const float* target, int64_t
     return VEG_ERR_INVALID_ARGUMENT;
   const float inv = n_records > 0 ? (float)(1.0 / (3.0 * (double)n_records)) : 0.f;
   float* partials = static_cast<float*>(workspace);
-  l1_kernel<<<kLossBlocks, 256, 0, stream>>>(reinterpret_cast<const float4*>(out),
+  launch_k(l1_kernel, kLossBlocks, 256, 0, stream, reinterpret_cast<const float4*>(out),
                                              reinterpret_cast<const float4*>(target), n_records,
                                              inv, reinterpret_cast<float4*>(grad), partials);
-  l1_final_kernel<<<1, kLossBlocks, 0, stream>>>(partials, inv, loss);
+  launch_k(l1_final_kernel, 1, kLossBlocks, 0, stream, partials, inv, loss);
   count_launch(2);
   return launch_status();
 }

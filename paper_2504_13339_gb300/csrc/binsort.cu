@@ -95,6 +95,7 @@ __device__ __forceinline__ int chunks_of(int64_t n) {
 __global__ void __launch_bounds__(kThreads)
     radix_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, int shift, int nbits,
                       uint32_t* __restrict__ hist, int nblocks) {
+  pdl_enter();
   __shared__ uint32_t s_hist[256];
   const int64_t n = cnt.get();
   const int nch = chunks_of(n);
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(1024)
     radix_scan_rows_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ totals,
                            Count cnt) {
+  pdl_enter();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_total;
   uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(kThreads, 4)
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, Count cnt,
                          int shift, int nbits, const uint32_t* __restrict__ hist,
                          const uint32_t* __restrict__ totals, int nblocks) {
+  pdl_enter();
   __shared__ uint32_t s_whist[8][256];
   __shared__ uint32_t s_dbase[256];
   __shared__ uint32_t s_bstart[256];
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 __global__ void depth_keys_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
                                   int64_t nrec, uint32_t* __restrict__ keys,
                                   uint32_t* __restrict__ vals) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nrec) return;
   keys[i] = tiles[i] > 0 ? __float_as_uint(geo[i].z) : 0xffffffffu;
@@ -272,6 +276,7 @@ __global__ void depth_keys_kernel(const float4* __restrict__ geo, const int32_t*
 __global__ void __launch_bounds__(kThreads)
     visible_count_kernel(const int32_t* __restrict__ tiles, int64_t nrec,
                          unsigned long long* __restrict__ bsum) {
+  pdl_enter();
   __shared__ unsigned s_warp[8];
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
   unsigned c = 0;
@@ -294,6 +299,7 @@ __global__ void __launch_bounds__(kThreads)
     visible_scatter_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
                            int64_t nrec, const unsigned long long* __restrict__ bsum,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  pdl_enter();
   __shared__ unsigned long long s_warp[8];
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
   bool vis[kItems];
@@ -317,6 +323,7 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(1024)
     chunk_scan_kernel(unsigned long long* __restrict__ bsum, int nb,
                       unsigned long long* __restrict__ total) {
+  pdl_enter();
   __shared__ unsigned long long s_warp[32];
   __shared__ unsigned long long s_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -355,6 +362,7 @@ __global__ void __launch_bounds__(1024)
 __global__ void __launch_bounds__(kThreads)
     count_reduce_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
                         Count cnt, unsigned long long* __restrict__ bsum) {
+  pdl_enter();
   __shared__ unsigned long long s[kThreads];
   const int64_t nrec = cnt.get();
   const int64_t base = (int64_t)blockIdx.x * kTileItems;
@@ -377,6 +385,7 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(1024)
     count_top_kernel(unsigned long long* __restrict__ bsum, int nb, WsHeader* __restrict__ hdr,
                      int64_t capacity) {
+  pdl_enter();
   __shared__ unsigned long long s_warp[32];
   __shared__ unsigned long long s_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -420,6 +429,7 @@ __global__ void __launch_bounds__(kThreads)
     count_down_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
                       Count cnt, const unsigned long long* __restrict__ bsum,
                       uint32_t* __restrict__ offsets) {
+  pdl_enter();
   __shared__ unsigned long long s_warp[8];
   const int64_t nrec = cnt.get();
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
@@ -450,6 +460,7 @@ __global__ void __launch_bounds__(256)
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
                 Count visible, int64_t n_per_view, int tiles_x, int tiles_per_view,
                 int64_t capacity, uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int64_t nrec = visible.get();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -504,6 +515,7 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count) {
+  pdl_enter();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) ranges[i] = make_int2(0, 0);
 }
@@ -514,6 +526,7 @@ __global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count) {
 // marks "no neighbour".
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
                               int2* __restrict__ ranges) {
+  pdl_enter();
   const int64_t n = cnt.get();
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= n) return;
@@ -543,6 +556,7 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
 __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
                               Count cnt, const float4* __restrict__ geo, int tiles_per_view, int tb,
                               uint64_t* __restrict__ keys64) {
+  pdl_enter();
   const int64_t n = cnt.get();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -604,10 +618,10 @@ void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32
                 cudaStream_t stream) {
   const int grid = pass_grid(nblocks);
   // the histogram kernel is light (28 registers, 1 KB): twice the blocks
-  radix_hist_kernel<<<std::min(nblocks, 2 * grid), kThreads, 0, stream>>>(kin, cnt, shift, nbits,
+  launch_k(radix_hist_kernel, std::min(nblocks, 2 * grid), kThreads, 0, stream, kin, cnt, shift, nbits,
                                                                          L.hist, nblocks);
-  radix_scan_rows_kernel<<<1 << nbits, 1024, 0, stream>>>(L.hist, nblocks, L.totals, cnt);
-  radix_scatter_kernel<<<grid, kThreads, 0, stream>>>(kin, vin, kout, vout, cnt, shift, nbits,
+  launch_k(radix_scan_rows_kernel, 1 << nbits, 1024, 0, stream, L.hist, nblocks, L.totals, cnt);
+  launch_k(radix_scatter_kernel, grid, kThreads, 0, stream, kin, vin, kout, vout, cnt, shift, nbits,
                                                       L.hist, L.totals, nblocks);
   count_launch(3);
 }
@@ -632,7 +646,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   const int64_t nranges = (int64_t)tiles_per_view * n_views;
   Layout L = carve(ws, nrec, capacity);
 
-  zero_ranges_kernel<<<grid_for(nranges, 256), 256, 0, stream>>>(ranges, nranges);
+  launch_k(zero_ranges_kernel, grid_for(nranges, 256), 256, 0, stream, ranges, nranges);
   count_launch();
   if (nrec == 0) {
     cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), stream);
@@ -643,13 +657,13 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   //    (same order, fewer launches)
   Count cr{0, &L.hdr->n_visible, nrec};
   if (nrec <= kSmallRecords) {
-    depth_keys_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(geo, tiles, nrec, L.dk0, L.dv0);
+    launch_k(depth_keys_kernel, grid_for(nrec, 256), 256, 0, stream, geo, tiles, nrec, L.dk0, L.dv0);
     count_launch();
     cr = Count{nrec, nullptr, 0};
   } else {
-    visible_count_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, nrec, L.bsum);
-    chunk_scan_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, &L.hdr->n_visible);
-    visible_scatter_kernel<<<L.nb_rec, kThreads, 0, stream>>>(geo, tiles, nrec, L.bsum, L.dk0,
+    launch_k(visible_count_kernel, L.nb_rec, kThreads, 0, stream, tiles, nrec, L.bsum);
+    launch_k(chunk_scan_kernel, 1, 1024, 0, stream, L.bsum, L.nb_rec, &L.hdr->n_visible);
+    launch_k(visible_scatter_kernel, L.nb_rec, kThreads, 0, stream, geo, tiles, nrec, L.bsum, L.dk0,
                                                               L.dv0);
     count_launch(3);
   }
@@ -659,9 +673,9 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 24, 8, L.nb_rec, L, stream);
   const uint32_t* order = L.dv0;
   // 2. instance offsets in depth order, total into the header
-  count_reduce_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, cr, L.bsum);
-  count_top_kernel<<<1, 1024, 0, stream>>>(L.bsum, L.nb_rec, L.hdr, capacity);
-  count_down_kernel<<<L.nb_rec, kThreads, 0, stream>>>(tiles, order, cr, L.bsum, L.offsets);
+  launch_k(count_reduce_kernel, L.nb_rec, kThreads, 0, stream, tiles, order, cr, L.bsum);
+  launch_k(count_top_kernel, 1, 1024, 0, stream, L.bsum, L.nb_rec, L.hdr, capacity);
+  launch_k(count_down_kernel, L.nb_rec, kThreads, 0, stream, tiles, order, cr, L.bsum, L.offsets);
   count_launch(3);
   // 3. emit (tile key, record) pairs, then stable sort by tile key
   int bits = 1;
@@ -676,7 +690,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
     vbuf[0] = L.iv0;
     vbuf[1] = vals;
   }
-  emit_kernel<<<grid_for(nrec, 256), 256, 0, stream>>>(tiles, rect, order, L.offsets, cr, n,
+  launch_k(emit_kernel, grid_for(nrec, 256), 256, 0, stream, tiles, rect, order, L.offsets, cr, n,
                                                        tiles_x, tiles_per_view, capacity, kbuf[0],
                                                        vbuf[0]);
   count_launch();
@@ -691,10 +705,10 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   }
   const uint32_t* fkeys = kbuf[passes & 1];
   // 4. per-tile ranges and optional 64-bit keys
-  ranges_kernel<<<grid_for(capacity, 1024), 256, 0, stream>>>(fkeys, ci, ranges);
+  launch_k(ranges_kernel, grid_for(capacity, 1024), 256, 0, stream, fkeys, ci, ranges);
   count_launch();
   if (keys) {
-    keys64_kernel<<<grid_for(capacity, 256), 256, 0, stream>>>(
+    launch_k(keys64_kernel, grid_for(capacity, 256), 256, 0, stream, 
         fkeys, vals, ci, geo, tiles_per_view, tile_bits_of(tiles_per_view), keys);
     count_launch();
   }
@@ -709,6 +723,7 @@ namespace {
 // the CTA schedule, never a result.
 __global__ void __launch_bounds__(1024)
     tile_order_kernel(const int2* __restrict__ ranges, int count, int32_t* __restrict__ order) {
+  pdl_enter();
   __shared__ unsigned s_cnt[33];
   __shared__ unsigned s_off[33];
   if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
@@ -738,7 +753,7 @@ __global__ void __launch_bounds__(1024)
 
 veg_status tile_order_launch(const int2* ranges, int count, int32_t* order, cudaStream_t stream) {
   if (count == 0) return VEG_OK;
-  tile_order_kernel<<<1, 1024, 0, stream>>>(ranges, count, order);
+  launch_k(tile_order_kernel, 1, 1024, 0, stream, ranges, count, order);
   count_launch();
   return launch_status();
 }

@@ -267,6 +267,7 @@ template <int TG, bool STATS, bool LIT>
 __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : (TG == 1 ? 5 : 4)))
     composite_fwd_kernel(CompArgs A, float4* __restrict__ out, int32_t* __restrict__ n_contrib,
                          unsigned long long* __restrict__ stats) {
+  pdl_enter();
   extern __shared__ float4 s_lut[];  // [TG][L]
   __shared__ float4 s_geo[kBatch];   // u_x, u_y, -a/2, -b
   __shared__ float2 s_c[kBatch];     // -c/2, exponent cutoff
@@ -504,6 +505,7 @@ __global__ void __launch_bounds__(256, 3)
                          const int32_t* __restrict__ n_contrib, const float4* __restrict__ dout,
                          float4* __restrict__ grad2d, float2* __restrict__ grad_shade,
                          unsigned long long* __restrict__ stats) {
+  pdl_enter();
   constexpr int kAcc = LIT ? 12 : 8;  // accumulator slots per splat
   unsigned long long n_rep = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0, n_free = 0,
                      n_grad = 0;
@@ -792,7 +794,7 @@ veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
-  kern<<<grid, 256, smem, stream>>>(A, out, nc, stats);
+  launch_k(kern, grid, 256, smem, stream, A, out, nc, stats);
   count_launch();
   return launch_status();
 }
@@ -808,7 +810,7 @@ veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
-  kern<<<grid, 256, smem, stream>>>(A, out, nc, dout, grad2d, grad_shade, stats);
+  launch_k(kern, grid, 256, smem, stream, A, out, nc, dout, grad2d, grad_shade, stats);
   count_launch();
   return launch_status();
 }

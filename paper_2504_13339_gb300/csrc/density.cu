@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256)
     grad_stats_kernel(const float4* __restrict__ grad2d, const int32_t* __restrict__ tiles,
                       int64_t n, int n_views, float hx, float hy, float* __restrict__ accum,
                       int32_t* __restrict__ count) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float a = accum[i];
@@ -105,6 +106,7 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int* tot
 __global__ void __launch_bounds__(256)
     density_classify_kernel(DensityArgs A, int64_t n, int32_t* __restrict__ action,
                             int64_t* __restrict__ block_sums) {
+  pdl_enter();
   __shared__ int s_warp[9];
   const int64_t base = (int64_t)blockIdx.x * kBlockItems + (int64_t)threadIdx.x * kItems;
   int cnt = 0;
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(256)
 // writes the grand total to *n_out.
 __global__ void __launch_bounds__(1024)
     density_scan_kernel(int64_t* __restrict__ block_sums, int64_t nb, int64_t* __restrict__ n_out) {
+  pdl_enter();
   __shared__ int64_t s[1024];
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -182,6 +185,7 @@ __device__ void write_out(const DensityArgs& A, int64_t i, int64_t o, int child,
 __global__ void __launch_bounds__(256)
     density_scatter_kernel(DensityArgs A, int64_t n, const int32_t* __restrict__ action,
                            const int64_t* __restrict__ block_offsets) {
+  pdl_enter();
   __shared__ int s_warp[9];
   const int64_t base = (int64_t)blockIdx.x * kBlockItems + (int64_t)threadIdx.x * kItems;
   int32_t act[kItems];
@@ -235,7 +239,7 @@ extern "C" veg_status veg_grad_stats_accumulate(const float* grad2d, const int32
       (reinterpret_cast<uintptr_t>(count) & 3))
     return VEG_ERR_INVALID_ARGUMENT;
   if (n == 0) return VEG_OK;
-  grad_stats_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+  launch_k(grad_stats_kernel, (unsigned)((n + 255) / 256), 256, 0, stream, 
       reinterpret_cast<const float4*>(grad2d), tiles_touched, n, n_views, 0.5f * (float)width,
       0.5f * (float)height, accum, count);
   count_launch();
@@ -294,9 +298,9 @@ extern "C" veg_status veg_densify(const veg_adam_arrays* in, int64_t n, const fl
     if (cudaMemsetAsync(n_out, 0, sizeof(int64_t), stream) != cudaSuccess) return VEG_ERR_CUDA;
     return VEG_OK;
   }
-  density_classify_kernel<<<(unsigned)nb, 256, 0, stream>>>(A, n, act, sums);
-  density_scan_kernel<<<1, 1024, 0, stream>>>(sums, nb, n_out);
-  density_scatter_kernel<<<(unsigned)nb, 256, 0, stream>>>(A, n, act, sums);
+  launch_k(density_classify_kernel, (unsigned)nb, 256, 0, stream, A, n, act, sums);
+  launch_k(density_scan_kernel, 1, 1024, 0, stream, sums, nb, n_out);
+  launch_k(density_scatter_kernel, (unsigned)nb, 256, 0, stream, A, n, act, sums);
   count_launch(3);
   return launch_status();
 }

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(256)
                        const int32_t* __restrict__ view_tf, float4* __restrict__ geo,
                        float4* __restrict__ aux,
                        int32_t* __restrict__ tiles, short4* __restrict__ rect) {
+  pdl_enter();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int view = blockIdx.y;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(128)
                        int64_t n, const int32_t* __restrict__ tiles,
                        const float4* __restrict__ grad2d, float4* __restrict__ grad_mean_v,
                        float4* __restrict__ grad_logscale_w, float4* __restrict__ grad_quat) {
+  pdl_enter();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 mv = mean_v[i], lw = logscale_w[i], q = quat[i];
@@ -302,7 +304,7 @@ veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const 
   if (g.n == 0) return VEG_OK;
   dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)n_views);
   const float4* lut = cull_tf ? reinterpret_cast<const float4*>(cull_tf->lut) : nullptr;
-  project_fwd_kernel<<<grid, 256, 0, stream>>>(
+  launch_k(project_fwd_kernel, grid, 256, 0, stream, 
       cs, reinterpret_cast<const float4*>(g.mean_v), reinterpret_cast<const float4*>(g.logscale_w),
       reinterpret_cast<const float4*>(g.quat), g.n, lut, cull_tf ? cull_tf->lut_size : 0,
       cull_tf ? cull_tf->n_tf : 0, cull_tf ? cull_tf->view_tf : nullptr, geo, aux, tiles, rect);
@@ -315,7 +317,7 @@ veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
                               float4* gq, cudaStream_t stream) {
   if (g.n == 0) return VEG_OK;
   dim3 grid((unsigned)((g.n + 127) / 128));
-  project_bwd_kernel<<<grid, 128, 0, stream>>>(
+  launch_k(project_bwd_kernel, grid, 128, 0, stream, 
       cs, n_views, reinterpret_cast<const float4*>(g.mean_v),
       reinterpret_cast<const float4*>(g.logscale_w), reinterpret_cast<const float4*>(g.quat), g.n,
       tiles, grad2d, gm, gl, gq);

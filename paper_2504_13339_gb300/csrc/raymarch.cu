@@ -68,6 +68,7 @@ struct MarchArgs {
 
 __global__ void __launch_bounds__(256)
     volume_prepare_kernel(const float* __restrict__ vol, int R, float inv_h, float4* __restrict__ out) {
+  pdl_enter();
   const int64_t n = (int64_t)R * R * R;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     cell_mask_kernel(const float4* __restrict__ vol, int R, int cell, int cells,
                      const float4* __restrict__ lut, int L, int n_tf, uint32_t* __restrict__ mask) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = (int64_t)cells * cells * cells;
   if (i >= nc) return;
@@ -133,6 +135,7 @@ template <int TG, bool STATS>
 __global__ void __launch_bounds__(256)
     raymarch_kernel(MarchArgs A, RaySet rs, float4* __restrict__ out,
                     unsigned long long* __restrict__ stats) {
+  pdl_enter();
   unsigned long long n_samp = 0, n_tab = 0, n_skip = 0;
   extern __shared__ float4 s_lut[];
   const int wi = blockIdx.x;
@@ -297,7 +300,7 @@ veg_status launch_march(const MarchArgs& A, const RaySet& rs, int n_views, float
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
   dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
-  raymarch_kernel<TG, STATS><<<grid, 256, smem, stream>>>(A, rs, out, stats);
+  launch_k(raymarch_kernel<TG, STATS>, grid, 256, smem, stream, A, rs, out, stats);
   count_launch();
   return launch_status();
 }
@@ -321,7 +324,7 @@ extern "C" veg_status veg_volume_prepare(const float* volume, int32_t resolution
     return VEG_ERR_INVALID_ARGUMENT;
   const int64_t n = (int64_t)resolution * resolution * resolution;
   const float inv_h = (float)((resolution - 1) / 2.0);
-  volume_prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+  launch_k(volume_prepare_kernel, (unsigned)((n + 255) / 256), 256, 0, stream, 
       volume, resolution, inv_h, reinterpret_cast<float4*>(vol4));
   count_launch();
   return launch_status();
@@ -352,7 +355,7 @@ extern "C" veg_status veg_raymarch_cells(const float* vol4, int32_t resolution, 
     return VEG_ERR_INVALID_ARGUMENT;
   const int c = cells_per_axis(resolution, cell);
   const int64_t nc = (int64_t)c * c * c;
-  cell_mask_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(
+  launch_k(cell_mask_kernel, (unsigned)((nc + 255) / 256), 256, 0, stream, 
       reinterpret_cast<const float4*>(vol4), resolution, cell, c,
       reinterpret_cast<const float4*>(tf.lut), tf.lut_size, tf.n_tf, mask);
   count_launch();

@@ -58,6 +58,7 @@ __device__ __forceinline__ ShadeTerms shade_terms(const float l[3], const float 
 __global__ void __launch_bounds__(256)
     shade_kernel(LightSet ls, const float4* __restrict__ mean_v, const float4* __restrict__ nb,
                  const float4* __restrict__ kad, int64_t n, float2* __restrict__ out) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int v = blockIdx.y;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(128)
                      const int32_t* __restrict__ tiles, const float2* __restrict__ gshade,
                      float4* __restrict__ gmean, float4* __restrict__ gnb,
                      float4* __restrict__ gk) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 m = mean_v[i], nb = nbv[i], k = kadv[i];
@@ -165,7 +167,7 @@ extern "C" veg_status veg_shade(const veg_camera* cams, int32_t n_views, const f
   st = fill_lights(cams, n_views, light_dirs, &ls);
   if (st != VEG_OK || n == 0) return st;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)n_views);
-  shade_kernel<<<grid, 256, 0, stream>>>(
+  launch_k(shade_kernel, grid, 256, 0, stream, 
       ls, reinterpret_cast<const float4*>(mean_v), reinterpret_cast<const float4*>(normal_beta),
       reinterpret_cast<const float4*>(k_ads), n, reinterpret_cast<float2*>(splat_shade));
   count_launch();
@@ -191,7 +193,7 @@ extern "C" veg_status veg_shade_bwd(const veg_camera* cams, int32_t n_views, con
   LightSet ls;
   st = fill_lights(cams, n_views, light_dirs, &ls);
   if (st != VEG_OK || n == 0) return st;
-  shade_bwd_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(
+  launch_k(shade_bwd_kernel, (unsigned)((n + 127) / 128), 128, 0, stream, 
       ls, n_views, reinterpret_cast<const float4*>(mean_v),
       reinterpret_cast<const float4*>(normal_beta), reinterpret_cast<const float4*>(k_ads), n,
       tiles_touched, reinterpret_cast<const float2*>(grad_shade),

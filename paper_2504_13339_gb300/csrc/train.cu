@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(256, 3)
     l1_ssim_kernel(Window win, const float4* __restrict__ out, const float4* __restrict__ tgt,
                    int H, int W, int tiles_x, float lam, float inv_count,
                    float4* __restrict__ grad, double2* __restrict__ partial) {
+  pdl_enter();
   extern __shared__ float4 smem_raw[];
   LossSmem& sm = *reinterpret_cast<LossSmem*>(smem_raw);
   const int tid = threadIdx.x;
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(256, 3)
 __global__ void __launch_bounds__(1024)
     l1_ssim_final_kernel(const double2* __restrict__ partial, int64_t n, double inv_count,
                          float lam, float* __restrict__ loss) {
+  pdl_enter();
   __shared__ double s_a[1024], s_b[1024];
   double a = 0.0, b = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -297,6 +299,7 @@ __device__ __forceinline__ void adam_one(float& p, float& m, float& v, float g, 
 // Advances the step counter and stores the step's bias corrections
 // 1 / (1 - beta1^t) and 1 / sqrt(1 - beta2^t) (double, like the host path).
 __global__ void adam_count_kernel(veg_adam_counter* c, float b1, float b2) {
+  pdl_enter();
   const int64_t t = c->step + 1;
   c->step = t;
   c->inv_bc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
@@ -304,6 +307,7 @@ __global__ void adam_count_kernel(veg_adam_counter* c, float b1, float b2) {
 }
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, int64_t n) {
+  pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (i >= n || A.param[a] == nullptr) return;
@@ -366,11 +370,11 @@ extern "C" veg_status veg_l1_ssim_loss(const float* out, const float* target, in
   veg_status st = prepare_smem(l1_ssim_kernel, smem, configured, false);
   if (st != VEG_OK) return st;
   double2* part = reinterpret_cast<double2*>(workspace);
-  l1_ssim_kernel<<<dim3((unsigned)(tx * ty), (unsigned)n_images), 256, smem, stream>>>(
+  launch_k(l1_ssim_kernel, dim3((unsigned)(tx * ty), (unsigned)n_images), 256, smem, stream, 
       win, reinterpret_cast<const float4*>(out), reinterpret_cast<const float4*>(target), height,
       width, tx, lambda, (float)(1.0 / count), reinterpret_cast<float4*>(grad), part);
   count_launch();
-  l1_ssim_final_kernel<<<1, 1024, 0, stream>>>(part, (int64_t)tx * ty * n_images, 1.0 / count,
+  launch_k(l1_ssim_final_kernel, 1, 1024, 0, stream, part, (int64_t)tx * ty * n_images, 1.0 / count,
                                                lambda, loss);
   count_launch();
   return launch_status();
@@ -421,7 +425,7 @@ extern "C" veg_status veg_adam_step(const veg_adam_arrays* arrays, int64_t n, co
   AdamArgs A;
   veg_status st = adam_args(arrays, n, lr, beta1, beta2, eps, step, A);
   if (st != VEG_OK || n == 0) return st;
-  adam_kernel<<<dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream>>>(A, n);
+  launch_k(adam_kernel, dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream, A, n);
   count_launch();
   return launch_status();
 }
@@ -434,10 +438,10 @@ extern "C" veg_status veg_adam_step_counted(const veg_adam_arrays* arrays, int64
   veg_status st = adam_args(arrays, n, lr, beta1, beta2, eps, 0, A);
   if (st != VEG_OK) return st;
   A.counter = counter;
-  adam_count_kernel<<<1, 1, 0, stream>>>(counter, beta1, beta2);
+  launch_k(adam_count_kernel, 1, 1, 0, stream, counter, beta1, beta2);
   count_launch();
   if (n > 0) {
-    adam_kernel<<<dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream>>>(A, n);
+    launch_k(adam_kernel, dim3((unsigned)((n + 255) / 256), 5), 256, 0, stream, A, n);
     count_launch();
   }
   return launch_status();

@@ -60,6 +60,33 @@ veg_status prepare_smem(K kern, size_t dyn, SmemRecord& rec, bool max_carveout) 
   return VEG_OK;
 }
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_enter(): it waits until the kernel before it in the stream has
+// finished and its writes are visible, then lets the next kernel be
+// scheduled early (both are no-ops for a kernel launched without the
+// attribute).  launch_k launches with the attribute, so a kernel's launch
+// and block scheduling overlap the tail of the one before it.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+void launch_k(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+              A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // Bump allocator over a caller-provided workspace (256-byte aligned pieces).
 struct Carver {
   char* base;
