@@ -355,8 +355,10 @@ veg_status veg_l1_loss(const float* out, const float* target, int64_t n_records,
  * border) with C1 = 0.01^2, C2 = 0.03^2.  Writes grad = dloss/dout (same
  * shape, 0 on the fourth channel; sign(0) = 0 for the L1 part) and the device
  * float[3] loss = (loss, L1, SSIM).  workspace >=
- * veg_l1_ssim_loss_workspace_size bytes (16-byte aligned); per-tile sums are
- * reduced in a fixed order, so the result is deterministic.  n_images <=
+ * veg_l1_ssim_loss_workspace_size bytes (16-byte aligned; it holds the
+ * per-tile sums and the per-pixel partial derivatives of S, 36 B per pixel
+ * and image); per-tile sums are reduced in a fixed order, so the result is
+ * deterministic.  Three launches.  n_images <=
  * 65535; lambda in [0, 1].
  */
 veg_status veg_l1_ssim_loss_workspace_size(int64_t n_images, int32_t height, int32_t width,

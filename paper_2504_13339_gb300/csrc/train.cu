@@ -10,14 +10,11 @@
 //   dS_q/dx_p = win(p - q) (dS_q/dm1 + 2 x_p dS_q/ds11 + y_p dS_q/ds12),
 // so the gradient is three window sums of per-pixel partial derivatives.
 //
-// One CTA of 256 threads owns a 16 x 16 tile of one image: it stages the
-// 36 x 36 input region (10-pixel halo) of both images, filters the five
-// products over the 26 x 26 region whose statistics the tile's gradient
-// needs (separable: rows, then columns; each thread four outputs from
-// registers), forms S and the three partials there, filters those back to
-// the tile, and writes the combined gradient.
-// Per-CTA sums of |x - y| and S go to a workspace and are reduced in a fixed
-// order by a second kernel, so the loss is deterministic.
+// The statistics kernel computes S and the three partials once per pixel
+// (16 x 16 tiles staging a 26 x 26 input region) and stores the partials in
+// workspace planes; the gradient kernel filters the planes back.  Per-CTA
+// sums of |x - y| and S go to the workspace and are reduced in a fixed order
+// by a third kernel, so the loss is deterministic.
 #include <cmath>
 
 #include "veg_internal.cuh"
@@ -28,8 +25,7 @@ namespace {
 
 constexpr int kT = 16;             // output tile
 constexpr int kR = 5;              // window radius
-constexpr int kS = kT + 2 * kR;    // 26: statistics region
-constexpr int kI = kT + 4 * kR;    // 36: input region
+constexpr int kS = kT + 2 * kR;    // 26: a tile with the window's halo
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -37,35 +33,43 @@ struct Window {
   float w[2 * kR + 1];
 };
 
-struct LossSmem {
-  float x[3][kI * kI];  // inputs, per channel (zero outside the image)
-  float y[3][kI * kI];
-  float h[5][kI * kS];  // row pass of x, y, xx, yy, xy
-  float d[3][kS * kS];  // dS/dm1, dS/ds11, dS/ds12 (zero outside the image)
-  float e[3][kS * kT];  // row pass of the partials
-  float g[3][kT * kT];  // gradient of the SSIM sum per channel
-};
-
-// Every window pass is register-blocked: a thread computes four consecutive
-// outputs along its row (or column) from 14 staged values, so each loaded
-// value serves up to four outputs and eleven taps.  Three CTAs per SM.
+// Two kernels per image, both on 16 x 16 tiles with a 5-pixel halo:
+// l1_ssim_stats_kernel filters the five products (separable: rows, then
+// columns; each thread four outputs from registers) for the tile's own
+// pixels, forms S and its three partials there (per channel; written to
+// workspace planes) and the per-tile sums of |x - y| and S;
+// l1_ssim_grad_kernel filters the nine partial planes back (zero outside the
+// image) and writes the combined gradient.  Every statistic is computed once
+// per pixel instead of over an overlapping 26 x 26 region per tile.
 constexpr int kB = 4;            // outputs per thread and pass
 constexpr int kW = kB + 2 * kR;  // 14 values per thread and pass
 
-__global__ void __launch_bounds__(256, 3)
-    l1_ssim_kernel(Window win, const float4* __restrict__ out, const float4* __restrict__ tgt,
-                   int H, int W, int tiles_x, float lam, float inv_count,
-                   float4* __restrict__ grad, double2* __restrict__ partial) {
+struct StatsSmem {
+  float x[3][kS * kS];  // inputs, per channel (zero outside the image)
+  float y[3][kS * kS];
+  float h[3][5][kS * kT];  // row pass of x, y, xx, yy, xy (26 rows x 16 columns)
+};
+
+struct GradSmem {
+  float d[9][kS * kS];  // dS/dm1, dS/ds11, dS/ds12 per channel (zero outside the image)
+  float e[9][kS * kT];  // row pass of the partials
+  float g[9][kT * kT];  // column pass: the three window sums per channel
+};
+
+__global__ void __launch_bounds__(256)
+    l1_ssim_stats_kernel(Window win, const float4* __restrict__ out, const float4* __restrict__ tgt,
+                         int H, int W, int tiles_x, float* __restrict__ planes,
+                         double2* __restrict__ partial) {
   pdl_enter();
   extern __shared__ float4 smem_raw[];
-  LossSmem& sm = *reinterpret_cast<LossSmem*>(smem_raw);
+  StatsSmem& sm = *reinterpret_cast<StatsSmem*>(smem_raw);
   const int tid = threadIdx.x;
   const int tile = blockIdx.x, img = blockIdx.y;
   const int tx0 = (tile % tiles_x) * kT, ty0 = (tile / tiles_x) * kT;
-  const int64_t base = (int64_t)img * H * W;
-  for (int e = tid; e < kI * kI; e += 256) {
-    const int r = e / kI, c = e - r * kI;
-    const int gy = ty0 - 2 * kR + r, gx = tx0 - 2 * kR + c;
+  const int64_t HW = (int64_t)H * W, base = (int64_t)img * HW;
+  for (int e = tid; e < kS * kS; e += 256) {
+    const int r = e / kS, c = e - r * kS;
+    const int gy = ty0 - kR + r, gx = tx0 - kR + c;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
       a = out[base + (int64_t)gy * W + gx];
@@ -78,149 +82,92 @@ __global__ void __launch_bounds__(256, 3)
     sm.y[1][e] = b.y;
     sm.y[2][e] = b.z;
   }
-  float ssum = 0.f;
-  for (int ch = 0; ch < 3; ++ch) {
-    __syncthreads();
+  __syncthreads();
+  // row pass of the five products: 3 channels x 26 rows x 4 segments
+  for (int item = tid; item < 3 * kS * 4; item += 256) {
+    const int ch = item / (kS * 4), rem = item - ch * (kS * 4);
+    const int r = rem / 4, c0 = (rem % 4) * kB;
     const float* X = sm.x[ch];
     const float* Y = sm.y[ch];
-    // row pass of the five products: 36 rows x 26 columns, 7 segments a row
-    if (tid < kI * 7) {
-      const int r = tid / 7, c0 = (tid % 7) * kB;
-      float xv[kW], yv[kW];
+    float xv[kW], yv[kW];
 #pragma unroll
-      for (int i = 0; i < kW; ++i) {
-        const bool ok = c0 + i < kI;
-        xv[i] = ok ? X[r * kI + c0 + i] : 0.f;
-        yv[i] = ok ? Y[r * kI + c0 + i] : 0.f;
-      }
-#pragma unroll
-      for (int o = 0; o < kB; ++o) {
-        float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
-#pragma unroll
-        for (int k = 0; k <= 2 * kR; ++k) {
-          const float a = xv[o + k], b = yv[o + k], wk = win.w[k];
-          hx = fmaf(wk, a, hx);
-          hy = fmaf(wk, b, hy);
-          hxx = fmaf(wk, a * a, hxx);
-          hyy = fmaf(wk, b * b, hyy);
-          hxy = fmaf(wk, a * b, hxy);
-        }
-        if (c0 + o < kS) {
-          const int e = r * kS + c0 + o;
-          sm.h[0][e] = hx;
-          sm.h[1][e] = hy;
-          sm.h[2][e] = hxx;
-          sm.h[3][e] = hyy;
-          sm.h[4][e] = hxy;
-        }
-      }
+    for (int i = 0; i < kW; ++i) {
+      xv[i] = X[r * kS + c0 + i];
+      yv[i] = Y[r * kS + c0 + i];
     }
-    __syncthreads();
-    // column pass: statistics, S and its partials over the 26 x 26 region,
-    // 7 segments of four rows per column
-    if (tid < kS * 7) {
-      const int c = tid % kS, r0 = (tid / kS) * kB;
-      float st[5][kB];
 #pragma unroll
-      for (int q = 0; q < 5; ++q)
+    for (int o = 0; o < kB; ++o) {
+      float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
 #pragma unroll
-        for (int o = 0; o < kB; ++o) st[q][o] = 0.f;
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        float hv[kW];
-#pragma unroll
-        for (int i = 0; i < kW; ++i) hv[i] = r0 + i < kI ? sm.h[q][(r0 + i) * kS + c] : 0.f;
-#pragma unroll
-        for (int o = 0; o < kB; ++o)
-#pragma unroll
-          for (int k = 0; k <= 2 * kR; ++k) st[q][o] = fmaf(win.w[k], hv[o + k], st[q][o]);
+      for (int k = 0; k <= 2 * kR; ++k) {
+        const float a = xv[o + k], b = yv[o + k], wk = win.w[k];
+        hx = fmaf(wk, a, hx);
+        hy = fmaf(wk, b, hy);
+        hxx = fmaf(wk, a * a, hxx);
+        hyy = fmaf(wk, b * b, hyy);
+        hxy = fmaf(wk, a * b, hxy);
       }
-#pragma unroll
-      for (int o = 0; o < kB; ++o) {
-        const int r = r0 + o;
-        if (r >= kS) break;
-        const int gy = ty0 - kR + r, gx = tx0 - kR + c;
-        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-          const float m1 = st[0][o], m2 = st[1][o], s11 = st[2][o], s22 = st[3][o];
-          const float s12 = st[4][o];
-          const float a1 = 2.f * m1 * m2 + kC1;
-          const float a2 = 2.f * (s12 - m1 * m2) + kC2;
-          const float b1 = m1 * m1 + m2 * m2 + kC1;
-          const float b2 = (s11 - m1 * m1) + (s22 - m2 * m2) + kC2;
-          const float ib = 1.0f / (b1 * b2);
-          const float S = a1 * a2 * ib;
-          d0 = 2.f * m2 * (a2 - a1) * ib - 2.f * m1 * S * (1.0f / b1 - 1.0f / b2);
-          d1 = -S / b2;
-          d2 = 2.f * a1 * ib;
-          if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) ssum += S;
-        }
-        const int e = r * kS + c;
-        sm.d[0][e] = d0;
-        sm.d[1][e] = d1;
-        sm.d[2][e] = d2;
-      }
-    }
-    __syncthreads();
-    // row pass of the partials: 26 rows x 16 columns, 4 segments a row
-    if (tid < kS * 4) {
-      const int r = tid / 4, c0 = (tid % 4) * kB;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float dv[kW];
-#pragma unroll
-        for (int i = 0; i < kW; ++i) dv[i] = sm.d[q][r * kS + c0 + i];
-#pragma unroll
-        for (int o = 0; o < kB; ++o) {
-          float acc = 0.f;
-#pragma unroll
-          for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], dv[o + k], acc);
-          sm.e[q][r * kT + c0 + o] = acc;
-        }
-      }
-    }
-    __syncthreads();
-    // column pass of the partials: 16 columns x 4 segments of four rows
-    if (tid < kT * 4) {
-      const int c = tid % kT, r0 = (tid / kT) * kB;
-      float q3[3][kB];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float ev[kW];
-#pragma unroll
-        for (int i = 0; i < kW; ++i) ev[i] = sm.e[q][(r0 + i) * kT + c];
-#pragma unroll
-        for (int o = 0; o < kB; ++o) {
-          float acc = 0.f;
-#pragma unroll
-          for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], ev[o + k], acc);
-          q3[q][o] = acc;
-        }
-      }
-#pragma unroll
-      for (int o = 0; o < kB; ++o) {
-        const int io = (r0 + o + 2 * kR) * kI + c + 2 * kR;
-        sm.g[ch][(r0 + o) * kT + c] = q3[0][o] + 2.f * X[io] * q3[1][o] + Y[io] * q3[2][o];
-      }
+      const int e = r * kT + c0 + o;
+      sm.h[ch][0][e] = hx;
+      sm.h[ch][1][e] = hy;
+      sm.h[ch][2][e] = hxx;
+      sm.h[ch][3][e] = hyy;
+      sm.h[ch][4][e] = hxy;
     }
   }
   __syncthreads();
-  // combine with the L1 part and write this thread's pixel
-  const int py = tid / kT, px = tid - py * kT;
-  float l1 = 0.f;
-  if (ty0 + py < H && tx0 + px < W) {
-    const int io = (py + 2 * kR) * kI + px + 2 * kR;
-    float gg[3];
+  // column pass: statistics, S and its partials at the tile's pixels,
+  // 3 channels x 16 columns x 4 segments of four rows
+  float ssum = 0.f;
+  if (tid < 3 * kT * 4) {
+    const int ch = tid / (kT * 4), rem = tid - ch * (kT * 4);
+    const int c = rem % kT, r0 = (rem / kT) * kB;
+    float st[5][kB];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const float diff = sm.x[ch][io] - sm.y[ch][io];
-      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-      gg[ch] = ((1.0f - lam) * sgn - lam * sm.g[ch][tid]) * inv_count;
-      l1 += fabsf(diff);
+    for (int q = 0; q < 5; ++q) {
+      float hv[kW];
+#pragma unroll
+      for (int i = 0; i < kW; ++i) hv[i] = sm.h[ch][q][(r0 + i) * kT + c];
+#pragma unroll
+      for (int o = 0; o < kB; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], hv[o + k], acc);
+        st[q][o] = acc;
+      }
     }
-    grad[base + (int64_t)(ty0 + py) * W + tx0 + px] = make_float4(gg[0], gg[1], gg[2], 0.f);
+    const int gx = tx0 + c;
+#pragma unroll
+    for (int o = 0; o < kB; ++o) {
+      const int gy = ty0 + r0 + o;
+      if (gy >= H || gx >= W) continue;
+      const float m1 = st[0][o], m2 = st[1][o], s11 = st[2][o], s22 = st[3][o];
+      const float s12 = st[4][o];
+      const float a1 = 2.f * m1 * m2 + kC1;
+      const float a2 = 2.f * (s12 - m1 * m2) + kC2;
+      const float b1 = m1 * m1 + m2 * m2 + kC1;
+      const float b2 = (s11 - m1 * m1) + (s22 - m2 * m2) + kC2;
+      const float ib = 1.0f / (b1 * b2);
+      const float S = a1 * a2 * ib;
+      const int64_t px = (int64_t)gy * W + gx;
+      float* P = planes + ((int64_t)img * 9 + ch * 3) * HW + px;
+      P[0] = 2.f * m2 * (a2 - a1) * ib - 2.f * m1 * S * (1.0f / b1 - 1.0f / b2);
+      P[HW] = -S / b2;
+      P[2 * HW] = 2.f * a1 * ib;
+      ssum += S;
+    }
   }
-  // block sums of |x - y| and S (warp shuffles, then one warp)
+  // this thread's pixel: |x - y| over RGB
+  float l1 = 0.f;
+  {
+    const int py = tid / kT, px = tid - py * kT;
+    if (ty0 + py < H && tx0 + px < W) {
+      const int io = (py + kR) * kS + px + kR;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) l1 += fabsf(sm.x[ch][io] - sm.y[ch][io]);
+    }
+  }
+  // block sums of |x - y| and S (warp shuffles, then one thread)
   __shared__ float s_red[2][8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -239,6 +186,77 @@ __global__ void __launch_bounds__(256, 3)
       b += s_red[1][w];
     }
     partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(a, b);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    l1_ssim_grad_kernel(Window win, const float4* __restrict__ out, const float4* __restrict__ tgt,
+                        int H, int W, int tiles_x, float lam, float inv_count,
+                        const float* __restrict__ planes, float4* __restrict__ grad) {
+  pdl_enter();
+  extern __shared__ float4 smem_raw[];
+  GradSmem& sm = *reinterpret_cast<GradSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x, img = blockIdx.y;
+  const int tx0 = (tile % tiles_x) * kT, ty0 = (tile / tiles_x) * kT;
+  const int64_t HW = (int64_t)H * W, base = (int64_t)img * HW;
+  for (int e = tid; e < 9 * kS * kS; e += 256) {
+    const int q = e / (kS * kS), rem = e - q * (kS * kS);
+    const int r = rem / kS, c = rem - r * kS;
+    const int gy = ty0 - kR + r, gx = tx0 - kR + c;
+    sm.d[q][rem] = (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                       ? planes[((int64_t)img * 9 + q) * HW + (int64_t)gy * W + gx]
+                       : 0.f;
+  }
+  __syncthreads();
+  // row pass of the partials: 9 planes x 26 rows x 4 segments
+  for (int item = tid; item < 9 * kS * 4; item += 256) {
+    const int q = item / (kS * 4), rem = item - q * (kS * 4);
+    const int r = rem / 4, c0 = (rem % 4) * kB;
+    float dv[kW];
+#pragma unroll
+    for (int i = 0; i < kW; ++i) dv[i] = sm.d[q][r * kS + c0 + i];
+#pragma unroll
+    for (int o = 0; o < kB; ++o) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], dv[o + k], acc);
+      sm.e[q][r * kT + c0 + o] = acc;
+    }
+  }
+  __syncthreads();
+  // column pass: 9 planes x 16 columns x 4 segments of four rows
+  for (int item = tid; item < 9 * kT * 4; item += 256) {
+    const int q = item / (kT * 4), rem = item - q * (kT * 4);
+    const int c = rem % kT, r0 = (rem / kT) * kB;
+    float ev[kW];
+#pragma unroll
+    for (int i = 0; i < kW; ++i) ev[i] = sm.e[q][(r0 + i) * kT + c];
+#pragma unroll
+    for (int o = 0; o < kB; ++o) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], ev[o + k], acc);
+      sm.g[q][(r0 + o) * kT + c] = acc;
+    }
+  }
+  __syncthreads();
+  // combine with the L1 part and write this thread's pixel
+  const int py = tid / kT, px = tid - py * kT;
+  if (ty0 + py < H && tx0 + px < W) {
+    const int64_t o = base + (int64_t)(ty0 + py) * W + tx0 + px;
+    const float4 a = out[o], b = tgt[o];
+    const float xs[3] = {a.x, a.y, a.z}, ys[3] = {b.x, b.y, b.z};
+    float gg[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float g = sm.g[ch * 3][tid] + 2.f * xs[ch] * sm.g[ch * 3 + 1][tid] +
+                      ys[ch] * sm.g[ch * 3 + 2][tid];
+      const float diff = xs[ch] - ys[ch];
+      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+      gg[ch] = ((1.0f - lam) * sgn - lam * g) * inv_count;
+    }
+    grad[o] = make_float4(gg[0], gg[1], gg[2], 0.f);
   }
 }
 
@@ -328,8 +346,13 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, int64_t n) {
   if (a < 2 && A.rendered[a]) A.rendered[a][i] = make_float4(p.x, p.y, p.z, sigmoid_f(p.w));
 }
 
+// Workspace: per-tile (|x - y|, S) sums, then nine float planes per image
+// (dS/dm1, dS/ds11, dS/ds12 per channel).
+size_t loss_part_bytes(int64_t n_images, int H, int W) {
+  return round_up((size_t)n_images * tiles_x_of(W) * tiles_x_of(H) * sizeof(double2), 256);
+}
 size_t loss_ws_bytes(int64_t n_images, int H, int W) {
-  return (size_t)n_images * tiles_x_of(W) * tiles_x_of(H) * sizeof(double2);
+  return loss_part_bytes(n_images, H, W) + (size_t)n_images * 9 * H * W * sizeof(float);
 }
 
 }  // namespace
@@ -365,15 +388,21 @@ extern "C" veg_status veg_l1_ssim_loss(const float* out, const float* target, in
     wsum += (wd[k + kR] = std::exp(-(double)k * k / (2.0 * 1.5 * 1.5)));
   for (int k = 0; k <= 2 * kR; ++k) win.w[k] = (float)(wd[k] / wsum);
   const double count = (double)n_images * height * width * 3.0;
-  const size_t smem = sizeof(LossSmem);
-  static SmemRecord configured;
-  veg_status st = prepare_smem(l1_ssim_kernel, smem, configured, false);
+  static SmemRecord cfg_stats, cfg_grad;
+  veg_status st = prepare_smem(l1_ssim_stats_kernel, sizeof(StatsSmem), cfg_stats, false);
+  if (st == VEG_OK) st = prepare_smem(l1_ssim_grad_kernel, sizeof(GradSmem), cfg_grad, false);
   if (st != VEG_OK) return st;
   double2* part = reinterpret_cast<double2*>(workspace);
-  launch_k(l1_ssim_kernel, dim3((unsigned)(tx * ty), (unsigned)n_images), 256, smem, stream, 
-      win, reinterpret_cast<const float4*>(out), reinterpret_cast<const float4*>(target), height,
-      width, tx, lambda, (float)(1.0 / count), reinterpret_cast<float4*>(grad), part);
-  count_launch();
+  float* planes = reinterpret_cast<float*>(static_cast<char*>(workspace) +
+                                           loss_part_bytes(n_images, height, width));
+  const dim3 grid((unsigned)(tx * ty), (unsigned)n_images);
+  const float4* o4 = reinterpret_cast<const float4*>(out);
+  const float4* t4 = reinterpret_cast<const float4*>(target);
+  launch_k(l1_ssim_stats_kernel, grid, 256, sizeof(StatsSmem), stream, win, o4, t4, height, width,
+           tx, planes, part);
+  launch_k(l1_ssim_grad_kernel, grid, 256, sizeof(GradSmem), stream, win, o4, t4, height, width,
+           tx, lambda, (float)(1.0 / count), planes, reinterpret_cast<float4*>(grad));
+  count_launch(2);
   launch_k(l1_ssim_final_kernel, 1, 1024, 0, stream, part, (int64_t)tx * ty * n_images, 1.0 / count,
                                                lambda, loss);
   count_launch();
