@@ -123,12 +123,13 @@ __global__ void __launch_bounds__(128)
     for (int c = 0; c < 3; ++c) dm[c] -= (ghv[c] - S.vh[c] * pv) * iv;
   }
   if (!any) return;
-  float4 a = gmean[i];
-  gmean[i] = make_float4(a.x + dm[0], a.y + dm[1], a.z + dm[2], a.w);
-  float4 b = gnb[i];
-  gnb[i] = make_float4(b.x + dn[0], b.y + dn[1], b.z + dn[2], b.w + dbeta);
-  float4 c = gk[i];
-  gk[i] = make_float4(c.x + dka, c.y + dkd, c.z + dks, c.w);
+  // add into the gradients with vector reductions (no read round trip)
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(gmean + i), "f"(dm[0]),
+               "f"(dm[1]), "f"(dm[2]), "f"(0.0f) : "memory");
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(gnb + i), "f"(dn[0]),
+               "f"(dn[1]), "f"(dn[2]), "f"(dbeta) : "memory");
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(gk + i), "f"(dka),
+               "f"(dkd), "f"(dks), "f"(0.0f) : "memory");
 }
 
 veg_status fill_lights(const veg_camera* cams, int n_views, const float* light_dirs,
