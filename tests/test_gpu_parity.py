@@ -121,6 +121,69 @@ def test_capacity_overflow_keeps_front_instances():
     assert np.array_equal(p.vals[:cap].cpu().numpy(), vals[srt])
 
 
+def front_instances(proj, cams, n, cap):
+    """Expected lists when only the first `cap` instances survive: records
+    of all views in (depth bits, record index) order, each record's tiles
+    row-major, the first `cap` kept, then stably sorted by (view, tile)."""
+    tpv = cams[0].tiles_x * cams[0].tiles_y
+    tb = max(1, int(np.ceil(np.log2(max(tpv, 2)))))
+    recs = []
+    for v, pr in enumerate(proj):
+        dbits = pr["geo"][:, 2].astype(np.float32).view(np.uint32)
+        for i in np.nonzero(pr["count"] > 0)[0]:
+            recs.append((int(dbits[i]), v * n + int(i), v, i))
+    recs.sort()
+    keys, vals = [], []
+    for d, r, v, i in recs:
+        x0, y0, x1, y1 = proj[v]["rect"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                keys.append((v << (tb + 32)) | ((ty * cams[0].tiles_x + tx) << 32) | d)
+                vals.append(r)
+    keys = np.array(keys[:cap], np.uint64)
+    vals = np.array(vals[:cap], np.uint32)
+    srt = np.argsort(keys >> np.uint64(32), kind="stable")
+    keys, vals = keys[srt], vals[srt]
+    lists = ((keys >> np.uint64(32 + tb)) * np.uint64(tpv)
+             + ((keys >> np.uint64(32)) & np.uint64((1 << tb) - 1))).astype(np.int64)
+    ranges = np.zeros((len(cams) * tpv, 2), np.int64)
+    for k in np.unique(lists):
+        w = np.nonzero(lists == k)[0]
+        ranges[k] = (w[0], w[-1] + 1)
+    return keys, vals, ranges
+
+
+@pytest.mark.parametrize("n,views,W,H", [
+    (4096, 1, 256, 256),  # 256 lists, ~38k instances
+    (4097, 1, 128, 128),  # 64 lists, ~16k instances
+    (2048, 2, 256, 128),  # two views: the view bits of the key
+    (300, 1, 272, 256),   # 17 x 16 tiles: 272 lists
+])
+@pytest.mark.parametrize("cut", [None, 3])
+def test_bins_and_capacity_overflow_across_sizes_and_views(n, views, W, H, cut):
+    """Tile lists bit-exact, and with a third of the instances' capacity the
+    first instances in emission order kept (every view at once)."""
+    g = S.uniform_gaussians(n, 170 + n, logscale_mean=-3.0)
+    cams = (S.orbit_cameras(views, 171, W, H) if views > 1
+            else [S.look_at_camera((0.0, 0.0, 3.0), W, H)])
+    tfs = S.bump_tfs(1, 172)
+    proj = [O.project32(c, g, tfs) for c in cams]
+    M = sum(int(pr["count"].sum()) for pr in proj)
+    cap = None if cut is None else M // cut
+    p, st, m, _, _ = gpu_forward(g, cams, tfs, capacity=cap)
+    keys, vals, ranges = front_instances(proj, cams, g.n, M if cap is None else cap)
+    if cap is None:  # the helper itself against the oracle's binning
+        bins = O.bin_sort(proj, cams)
+        assert np.array_equal(keys, bins["keys"]) and np.array_equal(vals, bins["vals"])
+        assert np.array_equal(ranges, bins["ranges"].reshape(-1, 2))
+    assert m == M
+    assert st == (_lib.VEG_OK if cap is None else _lib.VEG_ERR_CAPACITY)
+    k = vals.size
+    assert np.array_equal(p.vals[:k].cpu().numpy().astype(np.uint32), vals)
+    assert np.array_equal(p.keys[:k].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(p.ranges.cpu().numpy().reshape(-1, 2), ranges)
+
+
 def test_empty_and_fully_culled():
     g, cams, tfs = S.plain_scene()
     empty = g.subset(np.arange(0))
