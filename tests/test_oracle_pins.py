@@ -238,6 +238,34 @@ def test_multi_view_keys_carry_the_view():
                               b["vals"][view == vi].astype(int))
 
 
+def test_direct_tile_lists_rebuild_the_sorted_bins():
+    """The per-tile lists by a direct rectangle test (used to check sampled
+    tiles of large scenes) and their packing equal the sorted binning on
+    every tile of every view."""
+    g, _, tf = S.plain_scene()
+    g = g.subset(np.arange(400))
+    cams = S.orbit_cameras(2, 7, 72, 40)
+    proj = [O.project32(c, g, tf) for c in cams]
+    b = O.bin_sort(proj, cams)
+    nt = cams[0].tiles_x * cams[0].tiles_y
+    lists = [O.tile_lists(proj[v], cams[v], range(nt), view=v) for v in range(2)]
+    packed = O.bins_from_lists(lists, 2, nt)
+    assert np.array_equal(packed["vals"], b["vals"])
+    assert np.array_equal(packed["ranges"], b["ranges"])
+
+
+def test_camera_centre_and_headlight_closed_forms():
+    """The camera matrices are stored in float32: centres and axes hold to
+    its rounding."""
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 64, 64)
+    assert np.allclose(O.camera_centre(cam), [0.0, 0.0, 3.0], atol=1e-12)
+    assert np.allclose(O.headlight(cam), [0.0, 0.0, 1.0], atol=1e-12)
+    for c in S.orbit_cameras(5, 11, 32, 32):  # radius 3, looking at the origin
+        e = O.camera_centre(c)
+        assert abs(np.linalg.norm(e) - 3.0) < 1e-6
+        assert np.allclose(O.headlight(c), e / 3.0, atol=1e-6)
+
+
 # ----------------------------------------------------------------------------
 # compositing closed forms (Eq. 1, alpha = O(v) w)
 # ----------------------------------------------------------------------------
