@@ -30,7 +30,7 @@ from __future__ import annotations
 import math
 import time
 from collections import deque
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 import torch
@@ -109,7 +109,7 @@ class RenderServer:
         self.device = torch.device(device)
         self.models = {k: tuple(t.contiguous() for t in v) for k, v in models.items()}
         self.tf_bank = tf_bank.contiguous()
-        self.lim = limits or SlotLimits()
+        self.lim = replace(limits or SlotLimits())  # the caller's limits stay as given
         self.lim.views = min(self.lim.views, int(max_batch))
         self.bg = tuple(float(b) for b in bg)
         self.keep = keep_images
@@ -117,11 +117,10 @@ class RenderServer:
         used = 0
         for _ in range(n_slots):
             b = _SlotBuffers(self.lim, self.device)
+            if mem_budget is not None and self.slots and used + b.nbytes() > mem_budget:
+                break  # admission by memory: no more slots than fit (at least one)
             used += b.nbytes()
             self.slots.append(_Slot(torch.cuda.Stream(self.device), b))
-            if mem_budget is not None and used > mem_budget and len(self.slots) > 1:
-                self.slots.pop()  # admission by memory: no more slots than fit
-                break
         self.bytes = used
         self.inst = {}  # (model, W, H) -> tile instances per view (largest seen)
         self.batch_sizes = []
