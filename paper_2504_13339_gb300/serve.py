@@ -20,7 +20,8 @@ the device and admits render requests (model, camera, TF, resolution):
 * Latency = result ready (the batch's completion event observed on the host)
   minus arrival time.  The per-(model, resolution) instance estimate is
   learned from completed batches; a batch that overflowed its instance
-  buffer is rendered again one request at a time.
+  buffer is rendered again one request at a time, and a request whose own
+  render still overflows carries that status.
 
 `fifo_serve` is the comparison path: one request at a time, in arrival order,
 each as a plain single-view render.
@@ -47,6 +48,7 @@ class Request:
     arrival: float   # seconds, on the server clock
     done: float = math.nan
     image: torch.Tensor | None = None  # [H][W][4] when kept
+    status: int = 0  # VEG_OK, or VEG_ERR_CAPACITY if even its own render overflowed
 
     @property
     def latency(self):
@@ -176,6 +178,7 @@ class RenderServer:
             for r in batch:
                 out = self._launch(slot, [r])
                 slot.event.synchronize()
+                r.status = _lib.veg_sync_status(b.ws, slot.stream)[0]
                 self._complete(slot, [r], out)
         else:
             H, W = r0.camera.height, r0.camera.width
