@@ -13,7 +13,9 @@ coefficients and the means.
 
 `VEGRender` wraps forward/backward as a torch.autograd.Function so that the
 sigmoid activations of the stored scalar and weight (Sec. 3.3) and the
-optimiser stay in torch.
+optimiser stay in torch.  Its backward reads the pipeline's forward buffers,
+so a pipeline serves one render awaiting backward at a time (a second
+composite before that backward makes it raise).
 """
 from __future__ import annotations
 
@@ -67,6 +69,7 @@ class SplatPipeline:
                                    device=dev)
         self.keys = None
         self._lit = None  # (mean_v, normal_beta, k_ads, light_dirs) when shaded
+        self.generation = 0  # composites so far: a backward must follow its own forward
         self.set_capacity(capacity if capacity is not None else max(1 << 16, 8 * nrec))
 
     def _records(self, rows):
@@ -105,8 +108,9 @@ class SplatPipeline:
 
     def resize(self, n):
         """Adapts the pipeline to n Gaussians per view (after densification):
-        the buffers stay when n fits the allocated rows, else they are
-        reallocated with 25% headroom.  The binning status is kept."""
+        the buffers stay when n fits the allocated rows (the binning status
+        is kept), else they are reallocated with 25% headroom and the
+        binning workspace starts afresh (no binning yet)."""
         n = int(n)
         self.n = n
         if n > self.rows:
@@ -167,6 +171,7 @@ class SplatPipeline:
         return _lib.veg_sync_status(self.ws, stream)
 
     def composite(self, luts, bg=(0.0, 0.0, 0.0), stats=None, stream=None):
+        self.generation += 1
         self._luts = luts
         self._bg = tuple(float(b) for b in bg)
         _lib.veg_composite_fwd(self.c_cams, self.n, self.geo, self.aux, self.vals, self.ranges,
@@ -277,6 +282,7 @@ class VEGRender(torch.autograd.Function):
             pipeline.bin_sort()
         out = pipeline.composite(luts, bg)
         ctx.pipeline = pipeline
+        ctx.generation = pipeline.generation
         ctx.lit = lit
         if lit:
             ctx.save_for_backward(mean_v, logscale_w, quat, normal_beta, k_ads)
@@ -288,6 +294,9 @@ class VEGRender(torch.autograd.Function):
     def backward(ctx, dout):
         saved = ctx.saved_tensors
         p = ctx.pipeline
+        if p.generation != ctx.generation:
+            raise RuntimeError("the pipeline composited again after this render: its buffers no "
+                               "longer hold it (use one pipeline per render awaiting backward)")
         gm, gl, gq = (torch.zeros_like(t) for t in saved[:3])
         if ctx.lit:
             gn = torch.zeros_like(saved[3])
