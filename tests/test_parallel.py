@@ -136,3 +136,37 @@ def test_flat_gradients_survive_densification():
             assert not gr.any()
         P.flat_grads.fill_(2.0)
         assert all(bool((gr == 2.0).all()) for gr in P.grads)
+
+
+def _rank_steps(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2504_13339_gb300 import parallel
+
+        class P:  # only what sync_step reads
+            raw = [torch.zeros(1)]
+            step = 5 + rank  # rank 1 took one extra step
+        try:
+            parallel.sync_step(P)
+            out[rank] = "no error"
+        except RuntimeError as e:
+            out[rank] = str(e)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_ranks_at_different_steps_are_reported_on_every_rank():
+    world = 2
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_steps, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(100)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert "different steps (5 .. 6)" in out[r]
