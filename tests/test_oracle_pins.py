@@ -243,12 +243,14 @@ def test_direct_tile_lists_rebuild_the_sorted_bins():
     tiles of large scenes) and their packing equal the sorted binning on
     every tile of every view."""
     g, _, tf = S.plain_scene()
-    g = g.subset(np.arange(400))
-    cams = S.orbit_cameras(2, 7, 72, 40)
+    g = g.subset(np.arange(60))  # few Gaussians: empty tiles among occupied ones
+    cams = S.orbit_cameras(2, 7, 200, 120)
     proj = [O.project32(c, g, tf) for c in cams]
     b = O.bin_sort(proj, cams)
     nt = cams[0].tiles_x * cams[0].tiles_y
     lists = [O.tile_lists(proj[v], cams[v], range(nt), view=v) for v in range(2)]
+    empty = [(v, t) for v in range(2) for t in range(nt) if len(lists[v][t]) == 0]
+    assert 0 < len(empty) < 2 * nt
     packed = O.bins_from_lists(lists, 2, nt)
     assert np.array_equal(packed["vals"], b["vals"])
     assert np.array_equal(packed["ranges"], b["ranges"])

@@ -188,14 +188,19 @@ def test_empty_volume_and_multi_table_consistency():
 
 def test_table_lookup_closed_forms():
     """Linear interpolation over [0, 1] (reading R6): a linear table gives
-    the linear function, table nodes are hit exactly, values outside [0, 1]
-    clamp to the end entries, and v = 1 takes the last entry."""
+    the linear function, a random table agrees with numpy's interpolation,
+    table nodes are hit exactly, values outside [0, 1] clamp to the end
+    entries, and v = 1 takes the last entry."""
     for L in (2, 3, 256, 4096):
         c = np.array([0.25, -1.5, 3.0, 0.75])
         lut = np.arange(L)[:, None] / (L - 1) * c[None]
         for v in np.random.default_rng(L).uniform(0.0, 1.0, 50):
             assert np.allclose(RM.tf_lookup(lut, v), v * c, rtol=0, atol=1e-12)
         rnd = np.random.default_rng(L + 1).standard_normal((L, 4))
+        xk = np.arange(L) / (L - 1)
+        for v in np.random.default_rng(L + 2).uniform(0.0, 1.0, 50):  # numpy's interpolation
+            ref = [np.interp(v, xk, rnd[:, c]) for c in range(4)]
+            assert np.allclose(RM.tf_lookup(rnd, v), ref, rtol=0, atol=1e-12)
         for k in range(0, L, max(1, L // 7)):
             assert np.array_equal(RM.tf_lookup(rnd, k / (L - 1)), rnd[k])
         assert np.array_equal(RM.tf_lookup(rnd, -0.3), rnd[0])
