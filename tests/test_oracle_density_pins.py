@@ -46,6 +46,10 @@ def test_scene_extent_of_an_orbit():
     az = np.linspace(0, 2 * np.pi, 16, endpoint=False)
     c = np.stack([3 * np.sin(az), np.zeros(16), 3 * np.cos(az)], 1)
     assert D.scene_extent(c) == pytest.approx(3.3)
+    # distances are taken from the cameras' centroid, not from the origin
+    shifted = c + np.array([10.0, -4.0, 2.0])
+    assert D.scene_extent(shifted) == pytest.approx(3.3)
+    assert D.scene_extent([[10.0, 0, 0], [12.0, 0, 0]]) == pytest.approx(1.1)
 
 
 def _model(n, rng, ls=-4.0):
