@@ -206,3 +206,73 @@ def test_table_lookup_closed_forms():
         assert np.array_equal(RM.tf_lookup(rnd, -0.3), rnd[0])
         assert np.array_equal(RM.tf_lookup(rnd, 1.0), rnd[-1])
         assert np.array_equal(RM.tf_lookup(rnd, 7.0), rnd[-1])
+
+
+def test_camera_ray_reprojects_to_its_pixel():
+    """A point on the ray of pixel (i, j) projects back to (i, j) on a
+    non-square image (x = i along the width, y = j along the height), and the
+    ray starts at the camera centre."""
+    cam = S.orbit_camera(40.0, 15.0, 3.0, 61, 23)
+    w2c = np.asarray(cam.world_to_cam, np.float64)
+    for i, j in ((3, 17), (50, 2), (30, 11)):
+        eye, d = RM.camera_ray(cam, i, j)
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-12
+        assert np.allclose(w2c[:, :3] @ eye + w2c[:, 3], 0.0, atol=1e-6)
+        c = w2c[:, :3] @ (eye + 2.5 * d) + w2c[:, 3]
+        assert c[2] > 0
+        # to 1e-4 px: the stored rotation is float32, so its transpose is
+        # its inverse only to that rounding
+        assert abs(cam.fx * c[0] / c[2] + cam.cx - i) < 1e-4
+        assert abs(cam.fy * c[1] / c[2] + cam.cy - j) < 1e-4
+
+
+def test_trilinear_hits_vertices_on_every_face():
+    """At vertex positions, including those on the upper faces x, y or z = 1
+    (where the cell index is clamped), the value is the vertex value."""
+    R = 6
+    vol = np.random.default_rng(5).uniform(0.0, 1.0, (R, R, R))
+    x = grid(R)
+    for zi, yi, xi in ((R - 1, 2, 3), (1, R - 1, 4), (2, 3, R - 1), (R - 1, R - 1, R - 1),
+                       (0, 0, 0), (3, 1, 2)):
+        val, _ = RM.trilinear(vol, (x[xi], x[yi], x[zi]))
+        assert val == pytest.approx(vol[zi, yi, xi], abs=1e-12)
+
+
+def test_sample_count_of_a_fractional_segment():
+    """With the box crossing 2 long and Delta = 0.15 the ray takes
+    floor(2 / 0.15) = 13 samples at z_k = 1 - (k + 1/2) Delta."""
+    R = 17
+    vol = linear_volume(R, 0.0, 0.0, 0.4, 0.5)
+    x = np.arange(256) / 255
+    lut = np.stack([x, x, x, 0.02 + 0.1 * x], 1)[None]
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 33, 33)
+    h = 2.0 / (R - 1)
+    step = 0.15
+    out, _ = RM.march_pixel(cam, vol, lut, 16, 16, step, None)
+    C, T = 0.0, 1.0
+    for k in range(13):
+        v = 0.5 + 0.4 * (1.0 - (k + 0.5) * step)
+        a = 1.0 - (1.0 - (0.02 + 0.1 * v)) ** (step / h)
+        C += T * a * v
+        T *= 1.0 - a
+    assert out[0, 3] == pytest.approx(T, rel=1e-12)
+    assert out[0, 0] == pytest.approx(C, rel=1e-12)
+
+
+def test_no_specular_where_the_light_is_tangent():
+    """v = 0.3 x + 0.5 seen from (0, 0, 3): the normal -x is perpendicular
+    to the headlight (+z), so diffuse and specular vanish (reading R27) even
+    off axis, where n.h is not zero, and the colour is k_a C."""
+    R = 17
+    vol = linear_volume(R, 0.3, 0.0, 0.0, 0.5)
+    lut = S.constant_tf([0.2, 0.6, 0.9, 0.02]).astype(np.float64)[None]
+    cam = S.look_at_camera((0.0, 0.0, 3.0), 41, 41)
+    i, j = 5, 30
+    _, d = RM.camera_ray(cam, i, j)
+    light = -np.asarray(cam.world_to_cam, np.float64)[2, :3]
+    hv = (-d + light) / np.linalg.norm(-d + light)
+    assert abs(np.array([-1.0, 0, 0]) @ hv) > 0.05
+    plain, _ = RM.march_pixel(cam, vol, lut, i, j, 1.0 / 16, None)
+    lit, _ = RM.march_pixel(cam, vol, lut, i, j, 1.0 / 16, (0.3, 0.6, 0.25, 1.0))
+    assert lit[0, 3] == plain[0, 3]
+    assert np.allclose(lit[0, :3], 0.3 * plain[0, :3], rtol=1e-12, atol=0.0)
