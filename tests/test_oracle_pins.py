@@ -138,6 +138,43 @@ def test_off_axis_hand_derived_jacobian():
                                    rtol=1e-12)
 
 
+def test_jacobian_clamped_beyond_the_frustum():
+    """Reading R2: x/z in the Jacobian is clamped to 1.3 tan(fov/2).  A
+    large isotropic Gaussian centred right of the image (x/z = 1.2 times the
+    limit) still reaches it; its conic is the closed form with the clamped
+    x/z, about 5% away from the unclamped one."""
+    cam = S.look_at_camera((0, 0, 3), 64, 64)
+    f, Z = cam.fx, 3.0
+    lim = 1.3 * 32.0 / f
+    X = 1.2 * lim * Z
+    sigma = 0.4
+    ref = []
+    for xc in (lim, X / Z):
+        a = sigma ** 2 * f * f / Z ** 2 * (1.0 + xc * xc) + 0.3
+        c = sigma ** 2 * f * f / Z ** 2 + 0.3
+        ref.append(np.array([1.0 / a, 0.0, 1.0 / c]))
+    assert abs(ref[0][0] / ref[1][0] - 1.0) > 0.03
+    g = make_gs([[X, 0.0, 0.0]], math.log(sigma))
+    p32 = O.project32(cam, g)
+    p64 = O.project64(cam, np.array([[X, 0.0, 0.0]]), np.full((1, 3), math.log(sigma)),
+                      np.array([[1.0, 0, 0, 0]]))
+    assert p32["count"][0] > 0 and p32["geo"][0, 0] > cam.width  # centre off the image
+    np.testing.assert_allclose(p32["aux"][0, :3], ref[0], rtol=2e-5, atol=1e-9)
+    np.testing.assert_allclose(p64["conic"][0], ref[0], rtol=1e-10, atol=1e-14)
+
+
+def test_tf_cull_threshold():
+    """Reading R5: with the table given, a Gaussian is culled iff A(v) w <
+    1/255 (here A = 0.5 everywhere); without it nothing is culled for
+    opacity."""
+    cam = S.look_at_camera((0, 0, 3), 64, 64)
+    lut = S.constant_tf([1.0, 1.0, 1.0, 0.5])[None]
+    w = np.array([0.9, 1.1, 0.0, 4.0]) / 255 / 0.5
+    g = make_gs(np.zeros((4, 3)), -3.0, w=w)
+    assert list(O.project32(cam, g, lut)["count"] > 0) == [False, True, False, True]
+    assert np.all(O.project32(cam, g)["count"] > 0)
+
+
 def test_ewa_matches_monte_carlo_projection():
     """Projected samples of a small anisotropic 3D Gaussian have the EWA
     covariance Sigma' - 0.3 I (linearisation error ~ sigma/z)."""
