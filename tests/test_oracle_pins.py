@@ -333,6 +333,26 @@ def test_single_splat_closed_form():
     assert np.array_equal(fwd["n_contrib"][0, 0], (alpha > 0).astype(int))
 
 
+def test_positive_exponent_is_skipped():
+    """Reading R7: a pair whose exponent is positive is skipped.  With the
+    indefinite form (a, b, c) = (0.5, 0, -0.5) the exponent is
+    -(dx^2 - dy^2)/4: 0 at the centre, -1 two pixels to the side, +1 two
+    pixels above, where the pixel keeps the background."""
+    tf = S.constant_tf([0.9, 0.4, 0.1, 0.5])[None].astype(np.float64)
+    px, py = np.array([8.0, 10.0, 8.0]), np.array([8.0, 8.0, 10.0])
+    r = O.composite_tile(px, py, np.array([[8.0, 8.0]]), np.array([[0.5, 0.0, -0.5]]),
+                         np.array([0.5]), np.array([1.0]), tf, (0.2, 0.3, 0.4))
+    rgb, A = tf[0, 0, :3], tf[0, 0, 3]  # the table's float32 entries
+    alpha = np.array([A, A * math.exp(-1.0)])
+    for k in range(2):
+        np.testing.assert_allclose(r["out"][k, 0, :3],
+                                   alpha[k] * rgb + (1 - alpha[k]) * np.array([0.2, 0.3, 0.4]),
+                                   rtol=1e-12)
+        assert r["n_contrib"][k, 0] == 1
+    np.testing.assert_allclose(r["out"][2, 0], [0.2, 0.3, 0.4, 1.0], rtol=0, atol=0)
+    assert r["n_contrib"][2, 0] == 0
+
+
 def test_two_splats_in_depth_order():
     cam = S.look_at_camera((0, 0, 3), 33, 33)
     L5 = np.array([[0, 0, 0, 0], [1, 0, 0, 0.6], [0, 0, 0, 0], [0, 0, 1, 0.5], [0, 0, 0, 0]],
