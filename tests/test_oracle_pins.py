@@ -259,6 +259,19 @@ def test_bin_sort_matches_direct_tile_lists():
         assert [i for _, i in cand] == list(b["vals"][lo:hi].astype(int))
 
 
+def test_equal_depths_keep_index_order():
+    """Reading R4: equal keys (same tile, same depth bits) keep index order."""
+    cam = S.look_at_camera((0, 0, 3), 64, 64)
+    g = make_gs(np.zeros((400, 3)), -3.0)  # 400 identical Gaussians at the centre
+    p = O.project32(cam, g)
+    b = O.bin_sort([p], [cam])
+    for tile in range(cam.tiles_x * cam.tiles_y):
+        lo, hi = b["ranges"][0, tile]
+        lst = b["vals"][lo:hi].astype(int)
+        assert list(lst) == sorted(lst) and len(lst) in (0, 400)
+    assert b["vals"].size >= 400
+
+
 def test_multi_view_keys_carry_the_view():
     g, _, tf = S.plain_scene()
     g = g.subset(np.arange(300))
@@ -634,6 +647,12 @@ def test_shading_closed_forms():
     # on the axis the view direction equals the headlight: h = l, |n.h| = |n.l|
     np.testing.assert_allclose(f["s_d"], [0.7, 0.2, 0.7], atol=1e-12)
     np.testing.assert_allclose(f["s_s"], [0.7, 0.0, 0.7], atol=1e-12)
+    # off the axis a normal across the light still faces the half vector,
+    # yet with n.l = 0 there is no specular term (reading R16)
+    f = O.shade64(cam, l, np.array([[0.8, 0.0, 0.0]]), np.array([[1.0, 0, 0]]), ka[:1], kd[:1],
+                  ks[:1], np.array([1.0]))
+    assert f["nl"][0] == 0.0 and abs(f["ndh"][0]) > 0.05
+    assert f["s_d"][0] == 0.2 and f["s_s"][0] == 0.0
     # a lit single splat at the centre pixel: (s_d C + s_s) alpha, Eq. 1-3
     g = make_gs(np.zeros((1, 3)), math.log(0.05))
     tf = S.constant_tf([0.25, 0.5, 0.75, 0.5])[None]
