@@ -39,8 +39,11 @@ Readings where the paper is silent (each listed in the design notes):
   R8 output RGB = sum c a T + T_final bg and the final transmittance T_final.
   R9 derivatives are the true ones: zero through the 0.99 clamp and the skips.
   R12 pixels whose decisions sit within a relative 1e-5 (alpha tests) or 1e-3
-     (transmittance stop) of a threshold are flagged; float32 and float64 may
-     legitimately decide them differently.
+     (transmittance stop) of a threshold, or whose exponent is zero to within
+     1e-5 of its terms, are flagged; float32 and float64 may legitimately
+     decide them differently.  ``pixel_alternatives`` lists every outcome of
+     such a pixel (each flagged decision taken both ways), so a flagged pixel
+     is checked against the outcome with the same decisions, not dropped.
 """
 from __future__ import annotations
 
@@ -315,6 +318,13 @@ def _flag_near(x, ref, rel):
     return np.abs(x / ref - 1.0) < rel
 
 
+def _power_near_zero(qa, qc, qb, power):
+    """The exponent -(qa + qc)/2 - qb is zero to within 1e-5 of the size of
+    its terms: its sign (the skip of reading R7) is a rounding matter."""
+    scale = np.abs(qa) + np.abs(qc) + 2 * np.abs(qb)
+    return (np.abs(power) <= 1e-5 * scale) & (scale > 0)
+
+
 def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False, shade=None):
     """Front-to-back blending (Eq. 1) of one tile's depth-sorted splats for
     the pixel centres (px, py) and every transfer function in `luts`.
@@ -367,8 +377,7 @@ def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False, 
             with np.errstate(divide="ignore", invalid="ignore"):
                 near = (_flag_near(alpha, ALPHA_MIN, FLAG_ALPHA) | _flag_near(raw, ALPHA_MAX, FLAG_ALPHA)
                         | (ok & _flag_near(test, T_MIN, FLAG_T)))
-                scale = np.abs(qa) + np.abs(qc) + 2 * np.abs(qb)
-                near |= (np.abs(power) <= 1e-5 * scale)[:, None] & (scale > 0)[:, None]
+                near |= _power_near_zero(qa, qc, qb, power)[:, None]
             flag |= active & near
             active &= ~term
         else:
@@ -385,6 +394,122 @@ def composite_tile(px, py, u, conic, v, w, luts, bg, frozen=None, record=False, 
     out = np.concatenate([C + Tr[..., None] * np.asarray(bg, np.float64)[None, None],
                           Tr[..., None]], 2)
     return {"out": out, "n_contrib": last, "flag": flag, "stats": stats, "rec": rec}
+
+
+def pixel_alternatives(x, y, u, conic, v, w, lut, bg, shade=None, limit=64):
+    """Every outcome of Eq. 1 at the pixel centre (x, y) for one transfer
+    function `lut` when each decision that lies inside a window of reading
+    R12 may go either way: the skip of a positive exponent, the skip of
+    alpha < 1/255 and the stop at T (1 - alpha) < 1e-4.  The splats (u,
+    conic, v, w, shade) are the tile's list in order, as for composite_tile.
+
+    Outside the windows each decision is the float64 one, so a pixel with no
+    windowed decision has exactly one outcome, equal to composite_tile's.  A
+    pair inside the window of the 0.99 clamp gives alpha = 0.99 to within
+    1e-5 either way; it is not branched but marked (`clamp_near`), since its
+    gradient depends on the side taken.
+
+    Returns a list of dicts with out (4,) = (RGB + T bg, T_final), n_contrib,
+    blend (n,) and clamped (n,) decisions and clamp_near; None when more than
+    `limit` outcomes exist.
+    """
+    n = u.shape[0]
+    lut = np.asarray(lut, np.float64)
+    bg = np.asarray(bg, np.float64)
+    dx = u[:, 0] - float(x)
+    dy = u[:, 1] - float(y)
+    a, b, c = conic[:, 0], conic[:, 1], conic[:, 2]
+    qa, qc, qb = a * dx * dx, c * dy * dy, b * dx * dy
+    power = -0.5 * (qa + qc) - qb
+    pnear = _power_near_zero(qa, qc, qb, power)
+    G = np.exp(power)
+    vals = tf_eval64(lut, v)[0]  # (n, 4)
+    rgb = vals[:, :3]
+    if shade is not None:
+        rgb = shade[:, :1] * rgb + shade[:, 1:2]
+    raw = vals[:, 3] * w * G
+    alpha = np.minimum(ALPHA_MAX, raw)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        anear = _flag_near(alpha, ALPHA_MIN, FLAG_ALPHA)
+        cnear = _flag_near(raw, ALPHA_MAX, FLAG_ALPHA)
+    outs = []
+    # depth-first over the windowed decisions; a state is the next list
+    # position, T, the colour sum, n_contrib, the blended and clamped
+    # positions so far and whether a clamp window was met
+    stack = [(0, 1.0, np.zeros(3), 0, [], [], False)]
+    while stack:
+        i, T, C, last, bl, cl, cn = stack.pop()
+        while i < n:
+            evals = (False, True) if pnear[i] else (bool(power[i] <= 0.0),)
+            if len(evals) == 2:
+                stack.append((i + 1, T, C.copy(), last, list(bl), list(cl), cn))
+                if len(stack) + len(outs) > limit:
+                    return None
+            if not evals[-1]:
+                i += 1
+                continue
+            al = float(alpha[i])
+            passes = (False, True) if anear[i] else (al >= ALPHA_MIN,)
+            if len(passes) == 2:
+                stack.append((i + 1, T, C.copy(), last, list(bl), list(cl), cn))
+                if len(stack) + len(outs) > limit:
+                    return None
+            if not passes[-1]:
+                i += 1
+                continue
+            test = T * (1.0 - al)
+            if _flag_near(test, T_MIN, FLAG_T):
+                # the side that stops here ends this outcome
+                outs.append((T, C.copy(), last, list(bl), list(cl), cn))
+                if len(stack) + len(outs) > limit:
+                    return None
+            elif test < T_MIN:
+                break
+            C = C + al * T * rgb[i]
+            T = test
+            last = i + 1
+            bl.append(i)
+            if raw[i] > ALPHA_MAX:
+                cl.append(i)
+            cn = cn or bool(cnear[i])
+            i += 1
+        outs.append((T, C, last, bl, cl, cn))
+    res = []
+    for T, C, last, bl, cl, cn in outs:
+        blend = np.zeros(n, bool)
+        blend[bl] = True
+        clamped = np.zeros(n, bool)
+        clamped[cl] = True
+        res.append({"out": np.concatenate([C + T * bg, [T]]), "n_contrib": last,
+                    "blend": blend, "clamped": clamped, "clamp_near": cn})
+    return res
+
+
+def flag_alternatives(proj_views, cams, bins, luts, bg, fwd, limit=64):
+    """pixel_alternatives for every flagged (view, TF, y, x) of a forward
+    result `fwd` (composite_fwd); returns {(view, tf, y, x): list or None}."""
+    luts = np.asarray(luts, np.float64)
+    res = {}
+    cache = {}
+    for vi, t, y, x in zip(*np.nonzero(fwd["flag"])):
+        cam = cams[vi]
+        tile = (y // TILE) * cam.tiles_x + x // TILE
+        if (vi, tile) not in cache:
+            proj = proj_views[vi]
+            lo, hi = bins["ranges"][vi, tile]
+            idx, u, conic, v, w = _tile_splats(proj, bins["vals"], lo, hi, proj["geo"].shape[0])
+            cache[vi, tile] = (u, conic, v, w, _tile_shade(proj, idx))
+        u, conic, v, w, sh = cache[vi, tile]
+        res[int(vi), int(t), int(y), int(x)] = pixel_alternatives(x, y, u, conic, v, w, luts[t],
+                                                                  bg, sh, limit)
+    return res
+
+
+def tile_pixel_index(cam, tile, x, y):
+    """Position of pixel (x, y) in the pixel order of composite_tile (and of
+    the recorded decisions) for `tile`."""
+    px, py = _tile_pixels(cam, tile)
+    return int(np.nonzero((px == x) & (py == y))[0][0])
 
 
 def _tile_splats(proj, vals, lo, hi, n):

@@ -6,6 +6,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)  # the shared parity helpers (tests/parity.py)
 
 
 def pytest_configure(config):
@@ -25,3 +28,14 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Prints the parity report of the GPU tests: how many pixels straddled a
+    threshold and how each was resolved."""
+    try:
+        import parity
+    except ImportError:
+        return
+    for line in parity.summary_lines():
+        terminalreporter.write_line(line)
