@@ -5,7 +5,8 @@
 // one pixel and each warp an 8x4 pixel block.  The tile's list is staged in
 // batches of 256 splats through shared memory.  The stager evaluates every
 // splat's colour and opacity under each TF of the group once (linear
-// interpolation in TF tables held in shared memory), the exponent below which
+// interpolation in the TF tables: held in shared memory by the forward, read
+// through the L1 cache by the backward), the exponent below which
 // no TF of the group can reach alpha = 1/255, and a conservative mask of the
 // warp blocks that the splat's visible ellipse can touch.  Each warp then
 // compacts the batch into its own list (ballots) and walks only that list,
@@ -204,17 +205,25 @@ __device__ __forceinline__ void stage_luts(const CompArgs& A, int lut0, int ntg,
 }
 
 // Stages splat `i` of the tile list into batch slot threadIdx.x: geometry,
-// per-TF colour and A w (and, for the backward, slopes and A), the exponent
+// per-TF colour and A w (and, for the backward, the slopes), the exponent
 // cutoff and the warp-block mask.  Returns the record index.
+//
+// The forward (BWD = false) reads the group's tables from shared memory
+// (`lut`, TG tables of L entries, transparent where the group has no table).
+// The backward reads them from global memory through the L1 cache (`lut`
+// points at the group's first table; bit t of `valid` says whether table t
+// exists, a missing one reads as transparent): the 16 KB this frees at four
+// tables lets four backward CTAs share an SM instead of three.
 //
 // Shading (Eq. 2, LIT): the forward stages the shaded colour s_d C(v) + s_s;
 // the backward stages the unshaded C(v) and (s_d, s_s) in s_sh, with the
 // colour slopes already scaled by s_d.  Without shading s_sh is unused.
 template <int TG, bool BWD, bool LIT>
-__device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* s_lut,
-                                                float tx0, float ty0, float4* s_geo, float2* s_c,
-                                                float4* s_col, float4* s_slope, float* s_A,
-                                                float2* s_sh, unsigned char* s_mask) {
+__device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* lut,
+                                                unsigned valid, float tx0, float ty0,
+                                                float4* s_geo, float2* s_c, float4* s_col,
+                                                float4* s_slope, float2* s_sh,
+                                                unsigned char* s_mask) {
   const int L = A.lut_size;
   const int s = threadIdx.x;
   const uint32_t g = A.vals[i];
@@ -229,7 +238,15 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
   float max_aw = 0.0f;
 #pragma unroll
   for (int t = 0; t < TG; ++t) {
-    const float4 lo = s_lut[t * L + q.k], hi = s_lut[t * L + q.k + 1];
+    float4 lo, hi;
+    if (BWD) {
+      const bool ok = (valid >> t) & 1u;
+      lo = ok ? __ldg(&lut[t * L + q.k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      hi = ok ? __ldg(&lut[t * L + q.k + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      lo = lut[t * L + q.k];
+      hi = lut[t * L + q.k + 1];
+    }
     const float Aop = lerp_rn(lo.w, hi.w, q);
     const float aw = mul(Aop, ge.w);
     float r = lerp_rn(lo.x, hi.x, q), gc = lerp_rn(lo.y, hi.y, q), b = lerp_rn(lo.z, hi.z, q);
@@ -239,11 +256,9 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
       b = __fmaf_rn(sh.x, b, sh.y);
     }
     s_col[t * kBatch + s] = make_float4(r, gc, b, aw);
-    if (BWD) {
+    if (BWD)
       s_slope[t * kBatch + s] = make_float4(slc * (hi.x - lo.x), slc * (hi.y - lo.y),
                                             slc * (hi.z - lo.z), ge.w * sl * (hi.w - lo.w));
-      s_A[t * kBatch + s] = Aop;
-    }
     max_aw = fmaxf(max_aw, aw);
   }
   const float cut = power_cutoff(max_aw);
@@ -304,8 +319,8 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : (TG == 1 ? 5 : 4)))
     if (__syncthreads_count(act != 0u) == 0) break;
     const int cnt = min(kBatch, rg.y - start);
     if ((int)threadIdx.x < cnt)
-      stage_splat<TG, false, LIT>(A, start + threadIdx.x, s_lut, tx0, ty0, s_geo, s_c, s_col,
-                                    nullptr, nullptr, nullptr, s_mask);
+      stage_splat<TG, false, LIT>(A, start + threadIdx.x, s_lut, 0xffu, tx0, ty0, s_geo, s_c,
+                                  s_col, nullptr, nullptr, s_mask);
     else
       s_mask[threadIdx.x] = 0;
     __syncthreads();
@@ -480,14 +495,27 @@ __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c,
                : "memory");
 }
 
-// Replays each pixel's forward blend front to back.  With S_i the running
-// sum of (c_j . g) alpha_j T_j over blended j <= i and K = C_final . g +
-// T_final (bg . g + g_T), the gradient of the loss w.r.t. alpha_i is
-//   dL/dalpha_i = T_i (c_i . g) - (K - S_i) / (1 - alpha_i),
-// the prefix form of the suffix sum over later splats (no division chain to
-// recover T).  Per splat, the seven screen-space gradients are reduced over
-// the warp, summed over warps in shared memory and added to the per-record
-// gradient buffer once per tile.
+// Walks each pixel's list back to front, from its last contribution to the
+// first splat.  Below n_contrib a pair blends exactly when its exponent is in
+// range and alpha >= 1/255 (the stop only ends the list), so every decision
+// is recomputed bit for bit from the same float32 operations as the forward,
+// without the forward's transmittance.  With T_i the transmittance in front
+// of blended splat i and Suf_i = sum over blended j > i of (c_j . g) alpha_j
+// T_j + T_final (bg . g + g_T), the gradient of the loss w.r.t. alpha_i is
+//   dL/dalpha_i = T_i (c_i . g) - Suf_i / (1 - alpha_i).
+// Each pixel starts from T_final (the forward's output) and recovers
+// T_i = T_{i+1} / (1 - alpha_i) with the reciprocal that dL/dalpha_i needs
+// anyway; Suf grows from the back, so the small terms of deep splats are
+// summed first and keep their relative accuracy (a front-to-back prefix
+// K - S_i would leave them as a difference of two O(1) numbers).  Per splat,
+// the seven screen-space gradients are reduced over the warp, summed over
+// warps in shared memory and added to the per-record gradient buffer once
+// per tile.
+//
+// The weight needs no sum of its own: below the clamp alpha = A w e^power,
+// so dalpha/dw = alpha / w = (dalpha/dpower) / w and dL/dw is the summed
+// exponent gradient dL/dpower divided by w (applied at the flush; a splat
+// with w = 0 never blends and gets 0).
 //
 // Shaded (LIT): the blended colour is s_d C + s_s, so c.g = s_d (C.g) + s_s
 // (g_r + g_g + g_b), dL/dC = s_d alpha T g, and the pair adds alpha T (C.g)
@@ -499,8 +527,13 @@ __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c,
 // pixel's last contribution), iterated pairs, pairs above the cutoff, alpha
 // evaluations, blended pairs, blended pairs below the clamp, pairs with a
 // nonzero screen-space gradient.
+//
+// Resident CTAs per SM: 4 (64 registers; 8 warps per SM more than 3 CTAs
+// hide the walk's dependent-issue latency, 7% faster on the training step),
+// 3 for the shaded and instrumented builds of a 4-TF group, which would
+// spill at 64 registers.
 template <int TG, bool STATS, bool LIT>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
     composite_bwd_kernel(CompArgs A, const float4* __restrict__ out,
                          const int32_t* __restrict__ n_contrib, const float4* __restrict__ dout,
                          float4* __restrict__ grad2d, float2* __restrict__ grad_shade,
@@ -510,14 +543,12 @@ __global__ void __launch_bounds__(256, 3)
   unsigned long long n_rep = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0, n_free = 0,
                      n_grad = 0;
   extern __shared__ float4 smem[];
-  float4* s_lut = smem;                                     // [TG][L]
-  float4* s_col = s_lut + TG * A.lut_size;                  // [TG][kBatch]: rgb, A w
+  float4* s_col = smem;                                     // [TG][kBatch]: rgb, A w
   float4* s_slope = s_col + TG * kBatch;                    // [TG][kBatch]: drgb/dv, w dA/dv
   float4* s_geo = s_slope + TG * kBatch;                    // [kBatch]: u, -a/2, -b
   float2* s_c = reinterpret_cast<float2*>(s_geo + kBatch);  // [kBatch]: -c/2, cutoff
   float2* s_sh = s_c + kBatch;                              // [kBatch]: s_d, s_s (LIT)
-  float* s_A = reinterpret_cast<float*>(s_sh + (LIT ? kBatch : 0));  // [TG][kBatch]: A
-  float* s_acc = s_A + TG * kBatch;                         // [kBatch][kAcc] gradient sums
+  float* s_acc = reinterpret_cast<float*>(s_sh + (LIT ? kBatch : 0));  // [kBatch][kAcc]
   // record index of each staged splat (LIT keeps it in the staging thread)
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + kAcc * kBatch);
   unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + (LIT ? 0 : kBatch));
@@ -532,7 +563,11 @@ __global__ void __launch_bounds__(256, 3)
   const int n_out = A.view_tf ? 1 : A.n_tf;           // images per view
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* my_list = s_lists + warp * kBatch;
-  stage_luts<TG>(A, lut0, ntg, s_lut);
+  const float4* g_lut = A.lut + (int64_t)lut0 * A.lut_size;  // the group's tables
+  unsigned valid = 0u;
+#pragma unroll
+  for (int t = 0; t < TG; ++t)
+    if (t < ntg && lut0 + t >= 0 && lut0 + t < A.n_tf) valid |= 1u << t;
   for (int e = threadIdx.x; e < kAcc * kBatch; e += 256) s_acc[e] = 0.0f;
   if (threadIdx.x == 0) s_maxnc = 0;
   int px, py;
@@ -543,14 +578,15 @@ __global__ void __launch_bounds__(256, 3)
   const float2 fxy = make_float2((float)px, (float)py);
   const int2 rg = A.ranges[wi];
 
-  float T[TG], S[TG], K[TG], gr[TG], gg[TG], gb[TG], gs[TG];
+  // per TF: transmittance behind the splats walked so far, the suffix sum,
+  // the upstream colour gradient and n_contrib
+  float T[TG], Suf[TG], gr[TG], gg[TG], gb[TG], gs[TG];
   int nc[TG];
   int my_max = 0;
 #pragma unroll
   for (int t = 0; t < TG; ++t) {
     T[t] = 1.0f;
-    S[t] = 0.0f;
-    K[t] = 0.0f;
+    Suf[t] = 0.0f;
     gr[t] = gg[t] = gb[t] = gs[t] = 0.0f;
     nc[t] = 0;
     if (inside && t < ntg) {
@@ -561,16 +597,14 @@ __global__ void __launch_bounds__(256, 3)
       gg[t] = dv4.y;
       gb[t] = dv4.z;
       gs[t] = dv4.x + dv4.y + dv4.z;
-      const float Tn = ov.w;
-      const float cr = ov.x - Tn * A.bg0, cg = ov.y - Tn * A.bg1, cb = ov.z - Tn * A.bg2;
-      K[t] = cr * dv4.x + cg * dv4.y + cb * dv4.z +
-             Tn * (A.bg0 * dv4.x + A.bg1 * dv4.y + A.bg2 * dv4.z + dv4.w);
+      T[t] = ov.w;
+      Suf[t] = ov.w * (A.bg0 * dv4.x + A.bg1 * dv4.y + A.bg2 * dv4.z + dv4.w);
       my_max = max(my_max, nc[t]);
     }
   }
   if (STATS) n_rep = (unsigned long long)my_max;
-  // loop bounds: a warp walks until its last pixel is done (all lanes take
-  // part in the reductions); the block stages until its last warp is done
+  // loop bounds: a warp walks from its last contribution (all lanes take part
+  // in the reductions); the block stages from its last warp's
   int warp_max = my_max;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -580,22 +614,25 @@ __global__ void __launch_bounds__(256, 3)
   __syncthreads();
   const int block_max = s_maxnc;
 
-  for (int start = rg.x; start < rg.x + block_max; start += kBatch) {
-    const int i = start + threadIdx.x;
+  // batches from the back: list positions [bstart, bend), slot s = bstart + s
+  for (int bend = block_max; bend > 0; bend -= kBatch) {
+    const int bstart = max(0, bend - kBatch);
+    const int i = rg.x + bstart + threadIdx.x;
     uint32_t my_rec = 0;
-    if (i < rg.y) {
-      my_rec = stage_splat<TG, true, LIT>(A, i, s_lut, tx0, ty0, s_geo, s_c, s_col, s_slope, s_A,
-                                          s_sh, s_mask);
+    float my_w = 0.0f;  // weight of this thread's staged splat
+    if (i < rg.x + bend) {
+      my_rec = stage_splat<TG, true, LIT>(A, i, g_lut, valid, tx0, ty0, s_geo, s_c, s_col,
+                                          s_slope, s_sh, s_mask);
+      my_w = A.geo[my_rec].w;
       if (!LIT) s_idx[threadIdx.x] = my_rec;
     } else {
       s_mask[threadIdx.x] = 0;
     }
     __syncthreads();
     const int nw = build_warp_list(s_mask, my_list);
-    // replayed blend of splat j at list position idx for every TF of the
-    // group: accumulates dL/dG, dL/dv, dL/dw (and dL/ds_d, dL/ds_s) of this
-    // pixel
-    auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dww, float& dsd,
+    // blend of splat j at list position idx, undone for every TF of the
+    // group: accumulates dL/dG, dL/dv (and dL/ds_d, dL/ds_s) of this pixel
+    auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dsd,
                         float& dss) {
       float2 sh = make_float2(1.0f, 0.0f);
       if (LIT) sh = s_sh[j];
@@ -611,49 +648,51 @@ __global__ void __launch_bounds__(256, 3)
           ++n_blend;
           n_free += (raw <= kAlphaMax);
         }
-        const float wgt = mul(alpha, T[t]);
+        const float rr = rcp_approx(sub(1.0f, alpha));
+        const float Ti = T[t] * rr;  // transmittance in front of the splat
+        const float wgt = alpha * Ti;
         const float cgu = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
         const float cgd = LIT ? sh.x * cgu + sh.y * gs[t] : cgu;
         if (LIT) {
           dsd += wgt * cgu;
           dss += wgt * gs[t];
         }
-        S[t] += cgd * wgt;
-        const float one_m = sub(1.0f, alpha);
-        const float dalpha = T[t] * cgd - __fdividef(K[t] - S[t], one_m);
+        const float dalpha = Ti * cgd - Suf[t] * rr;
+        Suf[t] = __fmaf_rn(cgd, wgt, Suf[t]);
         const float4 sl = s_slope[t * kBatch + j];
         dvv += wgt * (gr[t] * sl.x + gg[t] * sl.y + gb[t] * sl.z);
         if (raw <= kAlphaMax) {
-          const float daw = dalpha * G;
-          dvv += daw * sl.w;
-          dww += daw * s_A[t * kBatch + j];
+          dvv += dalpha * G * sl.w;
           dG += dalpha * c.w;
         }
-        T[t] = mul(T[t], one_m);
+        T[t] = Ti;
       }
     };
-    // gradient parts of one pair: u_x, u_y, conic a, b, c, v, w (and s_d)
+    // gradient parts of one pair: u_x, u_y, conic a, b, c, v, the exponent
+    // (dL/dw times w) (and s_d)
     auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float2 d, float dvv,
-                          float dww, float dsd) {
+                          float dsd) {
       v[0] = dp * (2.0f * sg.z * d.x + sg.w * d.y);
       v[1] = dp * (2.0f * sc * d.y + sg.w * d.x);
       v[2] = dp * (-0.5f * d.x * d.x);
       v[3] = dp * (-d.x * d.y);
       v[4] = dp * (-0.5f * d.y * d.y);
       v[5] = dvv;
-      v[6] = dww;
+      v[6] = dp;
       v[7] = LIT ? dsd : 0.0f;
     };
-    // two splats per step: independent geometry and exponentials overlap,
-    // the replay stays in list order, and one 16-slot reduce-scatter sums
-    // both splats' gradients over the warp
-    for (int k = 0; k < nw; k += 2) {
+    // the warp's list is in list order: skip its entries past the warp's
+    // last contribution, then walk it backwards two splats per step (j0, the
+    // later one, first); independent geometry and exponentials overlap, and
+    // one 16-slot reduce-scatter sums both splats' gradients over the warp
+    int k = nw - 1;
+    while (k >= 0 && bstart + my_list[k] >= warp_max) --k;
+    for (; k >= 0; k -= 2) {
       const int j0 = my_list[k];
-      const int idx0 = start + j0 - rg.x;  // list position
-      if (idx0 >= warp_max) break;
-      const bool has1 = (k + 1 < nw) && (start + my_list[k + 1] - rg.x < warp_max);
-      const int j1 = has1 ? my_list[k + 1] : j0;
-      const int idx1 = start + j1 - rg.x;
+      const int idx0 = bstart + j0;  // list position
+      const bool has1 = k >= 1;
+      const int j1 = has1 ? my_list[k - 1] : j0;
+      const int idx1 = bstart + j1;
       if (STATS) n_it += 1 + (unsigned)has1;
       const float4 sg0 = s_geo[j0], sg1 = s_geo[j1];
       const float2 sc0 = s_c[j0], sc1 = s_c[j1];
@@ -665,19 +704,19 @@ __global__ void __launch_bounds__(256, 3)
       const bool ev1 = has1 && idx1 < my_max && p1 <= 0.0f && p1 >= sc1.y;
       const float G0 = ev0 ? gauss_of(p0) : 0.f;
       const float G1 = ev1 ? gauss_of(p1) : 0.f;
-      float dG0 = 0.f, dv0 = 0.f, dw0 = 0.f, dG1 = 0.f, dv1 = 0.f, dw1 = 0.f;
+      float dG0 = 0.f, dv0 = 0.f, dG1 = 0.f, dv1 = 0.f;
       float dd0 = 0.f, ds0 = 0.f, dd1 = 0.f, ds1 = 0.f;
-      if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dw0, dd0, ds0);
-      if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dw1, dd1, ds1);
+      if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dd0, ds0);
+      if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dd1, ds1);
       if (STATS) n_eval += (unsigned)ev0 + (unsigned)ev1;
       if (STATS) n_grad += (unsigned)(dG0 != 0.f) + (unsigned)(dG1 != 0.f);
       const float dp0 = dG0 * G0, dp1 = dG1 * G1;
-      bool nz = dp0 != 0.f || dv0 != 0.f || dw0 != 0.f || dp1 != 0.f || dv1 != 0.f || dw1 != 0.f;
+      bool nz = dp0 != 0.f || dv0 != 0.f || dp1 != 0.f || dv1 != 0.f;
       if (LIT) nz = nz || dd0 != 0.f || ds0 != 0.f || dd1 != 0.f || ds1 != 0.f;
       if (__any_sync(0xffffffffu, nz)) {
         float v[16];
-        pair_parts(v, dp0, sg0, sc0.x, d0, dv0, dw0, dd0);
-        pair_parts(v + 8, dp1, sg1, sc1.x, d1, dv1, dw1, dd1);
+        pair_parts(v, dp0, sg0, sc0.x, d0, dv0, dd0);
+        pair_parts(v + 8, dp1, sg1, sc1.x, d1, dv1, dd1);
         // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
         const float r = warp_reduce_scatter16(v, lane);
         const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
@@ -691,7 +730,7 @@ __global__ void __launch_bounds__(256, 3)
       }
     }
     __syncthreads();
-    if (i < rg.y) {
+    if (i < rg.x + bend) {
       float4* acc = reinterpret_cast<float4*>(s_acc) + (kAcc / 4) * threadIdx.x;
       const float4 a0 = acc[0], a1 = acc[1];
       const float4 a2 = LIT ? acc[2] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -703,8 +742,9 @@ __global__ void __launch_bounds__(256, 3)
       const uint32_t rec = LIT ? my_rec : s_idx[threadIdx.x];
       if (any) {
         float4* dst = grad2d + 2 * (int64_t)rec;
+        const float dw = my_w > 0.0f ? a1.z / my_w : 0.0f;
         red_add_v4(dst, a0.x, a0.y, a0.z, a0.w);
-        red_add_v4(dst + 1, a1.x, a1.y, a1.z, 0.0f);
+        red_add_v4(dst + 1, a1.x, a1.y, dw, 0.0f);
       }
       if (LIT && (a1.w != 0.f || a2.x != 0.f)) red_add_v2(grad_shade + rec, a1.w, a2.x);
     }
@@ -734,9 +774,11 @@ __global__ void __launch_bounds__(256, 3)
 }
 
 size_t bwd_smem_bytes(int TG, int L, bool lit) {
-  // lut, col + slope, geo, (c, cutoff), (s_d, s_s), A, acc, idx, mask, warp lists
-  return (size_t)TG * L * 16 + (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
-         (size_t)kBatch * 8 + (lit ? (size_t)kBatch * 8 : 0) + (size_t)TG * kBatch * 4 +
+  // col + slope, geo, (c, cutoff), (s_d, s_s), acc, idx, mask, warp lists (the
+  // tables stay in global memory)
+  (void)L;
+  return (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
+         (size_t)kBatch * 8 + (lit ? (size_t)kBatch * 8 : 0) +
          (size_t)(lit ? 12 : 8) * kBatch * 4 + (lit ? 0 : (size_t)kBatch * 4) + (size_t)kBatch +
          (size_t)kWarps * kBatch;
 }

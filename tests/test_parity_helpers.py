@@ -100,6 +100,7 @@ def test_a_pixel_off_the_bar_is_not_accepted():
 
 
 def test_elementwise_gradient_bound():
+    n0 = len(parity.GRAD_RATIOS)
     rng = np.random.default_rng(73)
     ref = rng.standard_normal(1000)
     ref[:10] *= 1e-5  # small entries
@@ -110,3 +111,4 @@ def test_elementwise_gradient_bound():
     assert np.abs(bad - ref).max() <= parity.GRAD_TOL * np.abs(ref).max()
     with pytest.raises(AssertionError):
         parity.grad_check(bad, ref, "planted")
+    del parity.GRAD_RATIOS[n0:]  # keep the run's report to the real tensors
