@@ -182,9 +182,13 @@ veg_status veg_tile_order(const int32_t* tile_ranges, int64_t count, int32_t* ti
  *   M > capacity means the binning overflowed (only the first `capacity`
  *   instances were binned).  There is no workspace header to pass to
  *   veg_sync_status.
- *   Set-up: the first call on each device looks up the array's device address
- *   (with that device current); make that first call before any stream
- *   capture begins.
+ *   Set-up: the first call in each CUDA context looks up the array's device
+ *   address with that context current and keeps it for later calls in the
+ *   same context; a device reset (or a primary context released and created
+ *   again) makes the next call look it up anew, since the array may then sit
+ *   elsewhere.  Make the first call of each context before any stream capture
+ *   begins: a lookup needed while `stream` is being captured returns
+ *   VEG_ERR_UNSUPPORTED without launching anything.
  *   Sharing: every call on a device uses the same array, which keeps the
  *   previous call's contents; each call writes every scratch word before it
  *   reads it, so no clearing is needed.  Calls whose work overlaps on the GPU

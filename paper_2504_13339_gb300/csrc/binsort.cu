@@ -820,6 +820,8 @@ extern "C" veg_status veg_sync_status(const void* workspace, cudaStream_t stream
 // device array instead of a caller workspace.
 // ---------------------------------------------------------------------------
 
+#include <cuda.h>  // driver types only; the functions are resolved at run time
+
 #include <mutex>
 
 namespace veg {
@@ -829,28 +831,80 @@ namespace {
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 constexpr int kMaxDevices = 64;
 
+// Address of the array per device, valid for the context it was looked up
+// in: a device reset (or a primary context released and created again)
+// reloads the library's module, and the array may then sit elsewhere.
+struct StaticScratch {
+  unsigned long long ctx_id;  // cuCtxGetId of the context, 0 = not looked up
+  void* ptr;
+};
 std::mutex g_static_mu;
-void* g_static_ptr[kMaxDevices] = {};
+StaticScratch g_static[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (the library links no
+// driver library: both driver functions are resolved through the runtime).
+veg_status current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (get_current == nullptr || get_id == nullptr) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault,
+                                         &q0) != cudaSuccess ||
+        q0 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || f0 == nullptr || f1 == nullptr)
+      return VEG_ERR_CUDA;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+    get_id = reinterpret_cast<CtxGetIdFn>(f1);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return VEG_ERR_CUDA;
+  if (get_id(ctx, id) != CUDA_SUCCESS || *id == 0) return VEG_ERR_CUDA;
+  return VEG_OK;
+}
 
 }  // namespace
 }  // namespace veg
 
 static __device__ __align__(256) unsigned char g_binsort_scratch[veg::kStaticScratchBytes];
 
-// The array's name is only a host-side handle: its device address has to be
-// looked up once per device, with that device current.
-static veg_status static_scratch_address(void** out) {
+// The array's name is only a host-side handle: its device address is looked
+// up with the device current, once per context.  A lookup is refused while
+// `stream` is being captured (it would run inside the caller's capture).
+static veg_status static_scratch_address(cudaStream_t stream, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return VEG_ERR_CUDA;
   if (dev < 0 || dev >= veg::kMaxDevices) return VEG_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(veg::g_static_mu);
-  if (veg::g_static_ptr[dev] == nullptr) {
+  unsigned long long ctx = 0;
+  if (veg::current_context_id(&ctx) != VEG_OK) {
+    // no context current on this thread yet: make the device's primary
+    // context current (the runtime creates it; nothing is allocated)
+    if (cudaSetDevice(dev) != cudaSuccess) return VEG_ERR_CUDA;
+    veg_status st = veg::current_context_id(&ctx);
+    if (st != VEG_OK) return st;
+  }
+  veg::StaticScratch& e = veg::g_static[dev];
+  if (e.ctx_id != ctx || e.ptr == nullptr) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess ||
+        cap != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();  // an implicit-capture error is not the caller's
+      return VEG_ERR_UNSUPPORTED;
+    }
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_binsort_scratch) != cudaSuccess || p == nullptr)
       return VEG_ERR_CUDA;
-    veg::g_static_ptr[dev] = p;
+    e.ptr = p;
+    e.ctx_id = ctx;
   }
-  *out = veg::g_static_ptr[dev];
+  *out = e.ptr;
   return VEG_OK;
 }
 
@@ -875,7 +929,7 @@ extern "C" veg_status veg_bin_sort_static(const veg_camera* cams, int32_t n_view
   if (binsort_ws_bytes(n, n_views, capacity, tpv) > kStaticScratchBytes)
     return VEG_ERR_UNSUPPORTED;
   void* ws = nullptr;
-  st = static_scratch_address(&ws);
+  st = static_scratch_address(stream, &ws);
   if (st != VEG_OK) return st;
   st = binsort_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
                       tiles_touched, reinterpret_cast<const short4*>(rect), ws, capacity, keys,
