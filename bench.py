@@ -1062,8 +1062,11 @@ def measure_serve(args):
         reqs = poisson_requests(models, 16, rate, duration, seed)
         if mode == "batching":
             srv.batch_sizes.clear()
+            srv.mixed_batches = srv.retries = 0
             res = latency_stats(srv.run(reqs))
             res["mean_batch"] = round(float(np.mean(srv.batch_sizes)), 3)
+            res["batches_of_mixed_resolution"] = int(srv.mixed_batches)
+            res["requests_retried_alone"] = int(srv.retries)
         else:
             res = latency_stats(fifo_serve(fsrv, reqs))
         return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in res.items()}
@@ -1074,8 +1077,9 @@ def measure_serve(args):
         best, rate, trail = None, args.rate, []
         while rate <= args.rate * 64:
             r = run(mode, rate, args.sat_duration, 43)
-            trail.append({"rate": rate, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
-                          "mpix_per_s": r["mpix_per_s"]})
+            trail.append({k: r[k] for k in ("p50_ms", "p99_ms", "mpix_per_s", "mean_batch")
+                          if k in r})
+            trail[-1]["rate"] = rate
             if r["p99_ms"] > args.p99_bound_ms:
                 break
             best = rate

@@ -27,7 +27,14 @@
  *   - Cameras (host structs, copied into kernel parameters): pinhole with
  *     OpenCV axes (x right, y down, z forward), world_to_cam = [R | t]
  *     row-major 3x4; pixel (i, j) is evaluated at the point (i, j) in
- *     pixel units.  All views of one call share width and height.
+ *     pixel units.  The views of one call may differ in image size (except
+ *     for the raymarcher, whose views share one size).
+ *   - Tiles and pixels of several views: view v's tiles (ceil(W_v/16) x
+ *     ceil(H_v/16), row-major) get the global ids off_v + tile with off_v
+ *     the tile count of the views before v; per-tile arrays (tile_ranges,
+ *     tile_order) are indexed by global id.  Per-pixel arrays hold, view
+ *     after view, each view's images of H_v x W_v pixels; for views of one
+ *     size these layouts are simply [V][tiles] and [V][images][H][W].
  *   - Gaussians: three float4 arrays of n rows: (mu_x, mu_y, mu_z, v),
  *     (log s_x, log s_y, log s_z, w), (q_w, q_x, q_y, q_z).  v and w are
  *     already activated into [0, 1] (the paper stores them via a sigmoid).
@@ -127,12 +134,13 @@ veg_status veg_project(const veg_camera* cams, int32_t n_views, veg_gaussians g,
  * increasing (depth, Gaussian index) order; equivalently the stable sort of
  * one key per (Gaussian, tile) pair,
  *     key = (view << (tb + 32)) | (tile << 32) | bits(depth_f32),
- * tb = max(1, ceil(log2(tiles per view))), emitted in Gaussian index order
- * with tiles row-major.  Outputs:
+ * tb = max(1, ceil(log2(tiles of the largest view))), emitted in Gaussian
+ * index order with tiles row-major.  Outputs:
  *   vals [capacity]: record index v*n + i of each instance, sorted
  *   keys [capacity] (optional, may be NULL): the sorted 64-bit keys above
- *   tile_ranges [V][tiles][2] int32: [start, end) of each tile's run in vals
- *       ((0, 0) for an empty tile); tiles = ceil(W/16) * ceil(H/16), row-major
+ *   tile_ranges [global tiles][2] int32: [start, end) of each tile's run in
+ *       vals ((0, 0) for an empty tile), indexed by global tile id (views
+ *       of one size: [V][tiles], tiles = ceil(W/16) * ceil(H/16))
  * The number of instances M is known only on the device; when M > capacity
  * only the first `capacity` instances (in emission order) are binned, the
  * header flag is set and veg_sync_status returns VEG_ERR_CAPACITY.
@@ -151,7 +159,7 @@ veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int64_t n,
 /*
  * veg_tile_order -- a processing order for the compositing kernels (a
  * scheduling aid of this library; the paper has no counterpart): the
- * indices 0..count-1 of tile_ranges [count][2] (count = views * tiles), the
+ * indices 0..count-1 of tile_ranges [count][2] (count = the global tiles), the
  * tiles with the longest lists first (bucketed by floor(log2(length)), empty
  * tiles last).  Passing it to veg_composite_fwd/bwd schedules the heaviest
  * tiles first, which shortens the tail of the launch; results do not depend
@@ -219,7 +227,9 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  *   skip if alpha < 1/255; stop this TF at this pixel if T (1 - alpha) <
  *   1e-4 (that splat not blended); else C += rgb alpha T, T *= 1 - alpha.
  * Writes out [V][n_tf][H][W][4] = (C + T bg, T_final) and n_contrib
- * [V][n_tf][H][W] = 1 + list position of the last blended splat (0 if none).
+ * [V][n_tf][H][W] = 1 + list position of the last blended splat (0 if none)
+ * (views of different sizes: view after view, n_tf images of H_v x W_v
+ * pixels each; with view_tf one image per view).
  * The scene representation is TF-independent, so one sort serves every TF.
  * tile_order: optional device int32 [V * tiles] from veg_tile_order (the
  * order in which tiles are scheduled; NULL = row-major; results do not
@@ -600,16 +610,23 @@ veg_status veg_train_step(const veg_train_args* args, int32_t view, int32_t map,
                           int32_t adam_step, int32_t accumulate_stats, cudaStream_t stream);
 
 /*
- * veg_render -- convenience forward: veg_project (with the TF cull), then
- * veg_bin_sort, then veg_composite_fwd, all scratch in `workspace`
- * (>= veg_render_workspace_size bytes).  Same outputs as
- * veg_composite_fwd.  Overflow of `capacity` is reported by veg_sync_status
- * on the same workspace.
+ * veg_render -- the forward render of Sec. 3.3 in one call: projection with
+ * the TF cull (veg_project), tile binning and depth sort (veg_bin_sort), the
+ * longest-first tile schedule (veg_tile_order) and Eq. 1 compositing
+ * (veg_composite_fwd), all scratch in `workspace` (device, 256-byte
+ * aligned, >= veg_render_workspace_size bytes; width and height there are
+ * the largest view's).  tf_group: TFs per compositing pass, 0 = the
+ * library's default (1), else 1, 2, 4 or 8; results do not depend on it.
+ * Outputs out and n_contrib as veg_composite_fwd (caller-owned device
+ * memory, overwritten).  Overflow of `capacity` is reported by
+ * veg_sync_status on the same workspace.  Returns VEG_ERR_INVALID_ARGUMENT
+ * before launching anything for malformed arguments or a workspace too
+ * small for these views.
  */
 veg_status veg_render_workspace_size(int64_t n, int32_t n_views, int64_t capacity,
                                      int32_t width, int32_t height, size_t* bytes);
 veg_status veg_render(const veg_camera* cams, int32_t n_views, veg_gaussians g, veg_tf tf,
-                      const float* bg, int64_t capacity, void* workspace,
+                      const float* bg, int32_t tf_group, int64_t capacity, void* workspace,
                       size_t workspace_bytes, float* out, int32_t* n_contrib,
                       cudaStream_t stream);
 

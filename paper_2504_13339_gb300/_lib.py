@@ -109,8 +109,8 @@ _SIGS = {
     "veg_l1_loss": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),
     "veg_render_workspace_size": (ctypes.c_int, [_I64, _I32, _I64, _I32, _I32,
                                                  ctypes.POINTER(_SZ)]),
-    "veg_render": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, veg_tf, _P, _I64, _P, _SZ, _P, _P,
-                                  _P]),
+    "veg_render": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, veg_tf, _P, _I32, _I64, _P, _SZ, _P,
+                                  _P, _P]),
     "veg_shade": (ctypes.c_int, [_CAMS, _I32, _P, _I64, _P, _P, _P, _P, _P]),
     "veg_l1_ssim_loss_workspace_size": (ctypes.c_int, [_I64, _I32, _I32, ctypes.POINTER(_SZ)]),
     "veg_l1_ssim_loss": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, ctypes.c_float, _P, _P, _P, _SZ,
@@ -459,9 +459,9 @@ def veg_render_workspace_size(n, n_views, capacity, width, height) -> int:
     return out.value
 
 
-def veg_render(cams, g, tf, bg, capacity, workspace, out, n_contrib, stream=None):
+def veg_render(cams, g, tf, bg, capacity, workspace, out, n_contrib, stream=None, tf_group=0):
     bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
     _check("veg_render",
-           load().veg_render(cams, len(cams), g, tf, ctypes.cast(bgc, ctypes.c_void_p), capacity,
-                             _ptr(workspace), workspace.numel(), _ptr(out), _ptr(n_contrib),
-                             _stream(stream)))
+           load().veg_render(cams, len(cams), g, tf, ctypes.cast(bgc, ctypes.c_void_p), tf_group,
+                             capacity, _ptr(workspace), workspace.numel(), _ptr(out),
+                             _ptr(n_contrib), _stream(stream)))

@@ -21,13 +21,21 @@ veg_status check_cameras(const veg_camera* cams, int32_t n_views) {
     const veg_camera& c = cams[v];
     if (c.width < 1 || c.height < 1 || c.width > VEG_MAX_IMAGE || c.height > VEG_MAX_IMAGE)
       return VEG_ERR_INVALID_ARGUMENT;
-    if (c.width != cams[0].width || c.height != cams[0].height) return VEG_ERR_INVALID_ARGUMENT;
     if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.cx) || !std::isfinite(c.cy) ||
         !std::isfinite(c.near_plane))
       return VEG_ERR_INVALID_ARGUMENT;
     for (int k = 0; k < 12; ++k)
       if (!std::isfinite(c.world_to_cam[k])) return VEG_ERR_INVALID_ARGUMENT;
   }
+  return VEG_OK;
+}
+
+veg_status check_cameras_one_size(const veg_camera* cams, int32_t n_views) {
+  veg_status st = check_cameras(cams, n_views);
+  if (st != VEG_OK) return st;
+  for (int v = 1; v < n_views; ++v)
+    if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+      return VEG_ERR_INVALID_ARGUMENT;
   return VEG_OK;
 }
 
@@ -104,11 +112,10 @@ struct RenderLayout {
   size_t bytes;
 };
 
-RenderLayout carve_render(void* ws, int64_t n, int n_views, int64_t capacity, int width,
-                          int height) {
-  const int tpv = tiles_x_of(width) * tiles_x_of(height);
+RenderLayout carve_render(void* ws, int64_t n, int n_views, int64_t capacity,
+                          int64_t total_tiles) {
   RenderLayout R;
-  R.binsort_bytes = binsort_ws_bytes(n, n_views, capacity, tpv);
+  R.binsort_bytes = binsort_ws_bytes(n, n_views, capacity);
   Carver c(ws);
   R.binsort_ws = c.take<char>(R.binsort_bytes);  // first: its header is at offset 0
   R.geo = c.take<float4>((size_t)n * n_views);
@@ -116,8 +123,8 @@ RenderLayout carve_render(void* ws, int64_t n, int n_views, int64_t capacity, in
   R.tiles = c.take<int32_t>((size_t)n * n_views);
   R.rect = c.take<short4>((size_t)n * n_views);
   R.vals = c.take<uint32_t>((size_t)capacity);
-  R.ranges = c.take<int2>((size_t)tpv * n_views);
-  R.order = c.take<int32_t>((size_t)tpv * n_views);
+  R.ranges = c.take<int2>((size_t)total_tiles);
+  R.order = c.take<int32_t>((size_t)total_tiles);
   R.bytes = c.bytes();
   return R;
 }
@@ -173,25 +180,30 @@ extern "C" veg_status veg_render_workspace_size(int64_t n, int32_t n_views, int6
       capacity >= ((int64_t)1 << 31) || width < 1 || height < 1 || width > VEG_MAX_IMAGE ||
       height > VEG_MAX_IMAGE)
     return VEG_ERR_INVALID_ARGUMENT;
-  *bytes = carve_render(nullptr, n, n_views, capacity, width, height).bytes;
+  // an upper bound for n_views views of at most width x height pixels
+  *bytes = carve_render(nullptr, n, n_views, capacity,
+                        (int64_t)n_views * tiles_x_of(width) * tiles_x_of(height))
+               .bytes;
   return VEG_OK;
 }
 
 extern "C" veg_status veg_render(const veg_camera* cams, int32_t n_views, veg_gaussians g,
-                                 veg_tf tf, const float* bg, int64_t capacity, void* workspace,
-                                 size_t workspace_bytes, float* out, int32_t* n_contrib,
-                                 cudaStream_t stream) {
+                                 veg_tf tf, const float* bg, int32_t tf_group, int64_t capacity,
+                                 void* workspace, size_t workspace_bytes, float* out,
+                                 int32_t* n_contrib, cudaStream_t stream) {
   veg_status st = check_cameras(cams, n_views);
   if (st != VEG_OK) return st;
   if (g.n < 0 || capacity < 0 || capacity >= ((int64_t)1 << 31) || !workspace || !out ||
-      !n_contrib || !tf.lut || tf.lut_size < 2 || tf.n_tf < 1)
+      !n_contrib || !tf.lut || tf.lut_size < 2 || tf.n_tf < 1 || tf_group < 0 || tf_group > 8)
     return VEG_ERR_INVALID_ARGUMENT;
+  const int64_t tiles = total_tiles_of(cams, n_views);
+  if (tiles >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
   if (g.n * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
   if (g.n > 0 && (!g.mean_v || !g.logscale_w || !g.quat)) return VEG_ERR_INVALID_ARGUMENT;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) || !aligned16(out) || !aligned16(tf.lut) ||
       !aligned16(g.mean_v) || !aligned16(g.logscale_w) || !aligned16(g.quat))
     return VEG_ERR_INVALID_ARGUMENT;
-  RenderLayout R = carve_render(workspace, g.n, n_views, capacity, cams[0].width, cams[0].height);
+  RenderLayout R = carve_render(workspace, g.n, n_views, capacity, tiles);
   if (workspace_bytes < R.bytes) return VEG_ERR_INVALID_ARGUMENT;
   CamSet cs;
   fill_camset(cams, n_views, &cs);
@@ -200,9 +212,9 @@ extern "C" veg_status veg_render(const veg_camera* cams, int32_t n_views, veg_ga
   st = binsort_launch(cams, n_views, g.n, R.geo, R.tiles, R.rect, R.binsort_ws, capacity, nullptr,
                       R.vals, R.ranges, stream);
   if (st != VEG_OK) return st;
-  const int count = tiles_x_of(cams[0].width) * tiles_x_of(cams[0].height) * n_views;
-  st = tile_order_launch(R.ranges, count, R.order, stream);
+  st = tile_order_launch(R.ranges, (int)tiles, R.order, stream);
   if (st != VEG_OK) return st;
   return composite_fwd_launch(cams, n_views, g.n, R.geo, R.aux, R.vals, R.ranges, R.order, tf, bg,
-                              nullptr, 0, reinterpret_cast<float4*>(out), n_contrib, nullptr, stream);
+                              nullptr, tf_group, reinterpret_cast<float4*>(out), n_contrib,
+                              nullptr, stream);
 }

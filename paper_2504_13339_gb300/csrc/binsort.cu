@@ -450,16 +450,18 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Writes the (view*tiles + tile, record) pairs of 32 consecutive records (in
-// depth order) per warp, tiles of a record row-major, below capacity.  The
+// Writes the (global tile id, record) pairs of 32 consecutive records (in
+// depth order) per warp, tiles of a record row-major, below capacity; the
+// global id of tile (tx, ty) of view v is vm.tile_off[v] + ty * tiles_x[v]
+// + tx.  The
 // warp's instances form one contiguous run; lanes write consecutive
 // positions of it, each finding the record that owns its position by a
 // binary search over the lanes' offsets (offsets increase with the lane).
 __global__ void __launch_bounds__(256)
     emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                Count visible, int64_t n_per_view, int tiles_x, int tiles_per_view,
-                int64_t capacity, uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
+                Count visible, int64_t n_per_view, ViewMap vm, int64_t capacity,
+                uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const int64_t nrec = visible.get();
@@ -479,7 +481,9 @@ __global__ void __launch_bounds__(256)
   if (first == 0xffffffffu || first >= (uint64_t)capacity) return;  // warp-uniform
   const uint32_t stop = (uint32_t)min(end, (unsigned long long)capacity);
   const int wx = rc.z - rc.x;
-  const uint32_t kb = (uint32_t)(g / (uint32_t)n_per_view) * (uint32_t)tiles_per_view;
+  const int view = (int)(g / (uint32_t)n_per_view);
+  const uint32_t kb = (uint32_t)vm.tile_off[view];
+  const int tx_v = vm.tiles_x[view];
   for (uint32_t base = first; base < stop; base += 32) {
     const uint32_t p = base + lane;
     // owner: the largest lane whose offset is <= p
@@ -494,6 +498,7 @@ __global__ void __launch_bounds__(256)
     const int o_x0 = __shfl_sync(0xffffffffu, (int)rc.x, lo);
     const int o_y0 = __shfl_sync(0xffffffffu, (int)rc.y, lo);
     const uint32_t o_kb = __shfl_sync(0xffffffffu, kb, lo);
+    const int o_tx = __shfl_sync(0xffffffffu, tx_v, lo);
     const uint32_t o_g = __shfl_sync(0xffffffffu, g, lo);
     if (p < stop) {
       const int local = (int)(p - o_off);
@@ -508,7 +513,7 @@ __global__ void __launch_bounds__(256)
         ++ry;
         rx -= o_wx;
       }
-      ikeys[p] = o_kb + (uint32_t)((o_y0 + ry) * tiles_x + o_x0 + rx);
+      ikeys[p] = o_kb + (uint32_t)((o_y0 + ry) * o_tx + o_x0 + rx);
       ivals[p] = o_g;
     }
   }
@@ -553,16 +558,18 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
   }
 }
 
+// key = (view << (tb + 32)) | (tile of the view << 32) | depth bits, with tb
+// the tile bits of the largest view.
 __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
-                              Count cnt, const float4* __restrict__ geo, int tiles_per_view, int tb,
+                              Count cnt, const float4* __restrict__ geo, ViewMap vm, int tb,
                               uint64_t* __restrict__ keys64) {
   pdl_enter();
   const int64_t n = cnt.get();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t tk = tkeys[i];
-  uint32_t view = tk / (uint32_t)tiles_per_view;
-  uint32_t tile = tk - view * (uint32_t)tiles_per_view;
+  uint32_t view = (uint32_t)view_of_tile(vm, (int)tk);
+  uint32_t tile = tk - (uint32_t)vm.tile_off[view];
   uint32_t depth = __float_as_uint(geo[vals[i]].z);
   keys64[i] = ((uint64_t)view << (tb + 32)) | ((uint64_t)tile << 32) | (uint64_t)depth;
 }
@@ -632,18 +639,16 @@ inline unsigned grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity, int tiles_per_view) {
-  (void)tiles_per_view;
+size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity) {
   return carve(nullptr, n * n_views, capacity).bytes;
 }
 
 veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const float4* geo,
                           const int32_t* tiles, const short4* rect, void* ws, int64_t capacity,
                           uint64_t* keys, uint32_t* vals, int2* ranges, cudaStream_t stream) {
-  const int W = cams[0].width, H = cams[0].height;
-  const int tiles_x = tiles_x_of(W), tiles_per_view = tiles_x * tiles_x_of(H);
+  const ViewMap vm = make_viewmap(cams, n_views, 1);
   const int64_t nrec = n * n_views;
-  const int64_t nranges = (int64_t)tiles_per_view * n_views;
+  const int64_t nranges = vm.tile_off[n_views];
   Layout L = carve(ws, nrec, capacity);
 
   launch_k(zero_ranges_kernel, grid_for(nranges, 256), 256, 0, stream, ranges, nranges);
@@ -691,8 +696,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
     vbuf[1] = vals;
   }
   launch_k(emit_kernel, grid_for(nrec, 256), 256, 0, stream, tiles, rect, order, L.offsets, cr, n,
-                                                       tiles_x, tiles_per_view, capacity, kbuf[0],
-                                                       vbuf[0]);
+           vm, capacity, kbuf[0], vbuf[0]);
   count_launch();
   Count ci{0, &L.hdr->n_instances, capacity};
   const int nb_inst = (int)std::max<int64_t>(1, (capacity + kTileItems - 1) / kTileItems);
@@ -708,8 +712,8 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   launch_k(ranges_kernel, grid_for(capacity, 1024), 256, 0, stream, fkeys, ci, ranges);
   count_launch();
   if (keys) {
-    launch_k(keys64_kernel, grid_for(capacity, 256), 256, 0, stream, 
-        fkeys, vals, ci, geo, tiles_per_view, tile_bits_of(tiles_per_view), keys);
+    launch_k(keys64_kernel, grid_for(capacity, 256), 256, 0, stream, fkeys, vals, ci, geo, vm,
+             tile_bits_of(vm.max_tiles), keys);
     count_launch();
   }
   return launch_status();
@@ -775,8 +779,7 @@ extern "C" veg_status veg_bin_sort_workspace_size(int64_t n, int32_t n_views, in
       capacity >= ((int64_t)1 << 31) || width < 1 || height < 1 || width > VEG_MAX_IMAGE ||
       height > VEG_MAX_IMAGE)
     return VEG_ERR_INVALID_ARGUMENT;
-  *bytes = veg::binsort_ws_bytes(n, n_views, capacity,
-                                 veg::tiles_x_of(width) * veg::tiles_x_of(height));
+  *bytes = veg::binsort_ws_bytes(n, n_views, capacity);
   return VEG_OK;
 }
 
@@ -795,9 +798,8 @@ extern "C" veg_status veg_bin_sort(const veg_camera* cams, int32_t n_views, int6
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) || !aligned16(splat_geo) ||
       (reinterpret_cast<uintptr_t>(rect) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
     return VEG_ERR_INVALID_ARGUMENT;
-  const int tpv = tiles_x_of(cams[0].width) * tiles_x_of(cams[0].height);
-  if ((int64_t)tpv * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
-  if (workspace_bytes < binsort_ws_bytes(n, n_views, capacity, tpv))
+  if (total_tiles_of(cams, n_views) >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
+  if (workspace_bytes < binsort_ws_bytes(n, n_views, capacity))
     return VEG_ERR_INVALID_ARGUMENT;
   return binsort_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
                         tiles_touched, reinterpret_cast<const short4*>(rect), workspace, capacity,
@@ -924,9 +926,8 @@ extern "C" veg_status veg_bin_sort_static(const veg_camera* cams, int32_t n_view
       (reinterpret_cast<uintptr_t>(tile_ranges) & 7) ||
       (reinterpret_cast<uintptr_t>(n_instances) & 7))
     return VEG_ERR_INVALID_ARGUMENT;
-  const int tpv = tiles_x_of(cams[0].width) * tiles_x_of(cams[0].height);
-  if ((int64_t)tpv * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
-  if (binsort_ws_bytes(n, n_views, capacity, tpv) > kStaticScratchBytes)
+  if (total_tiles_of(cams, n_views) >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
+  if (binsort_ws_bytes(n, n_views, capacity) > kStaticScratchBytes)
     return VEG_ERR_UNSUPPORTED;
   void* ws = nullptr;
   st = static_scratch_address(stream, &ws);

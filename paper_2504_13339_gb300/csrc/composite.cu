@@ -15,7 +15,7 @@ veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float* bg, const float* shade, int tf_group, float4* out,
                                 int32_t* n_contrib, unsigned long long* stats,
                                 cudaStream_t stream) {
-  CompArgs A = make_args(cams, geo, aux, vals, ranges, order, tf, bg, shade);
+  CompArgs A = make_args(cams, n_views, geo, aux, vals, ranges, order, tf, bg, shade);
   (void)n;
   const int TG =
       tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, false, tf.lut_size, shade != nullptr);
@@ -61,6 +61,7 @@ static veg_status check_composite_common(const veg_camera* cams, int32_t n_views
   if (st != VEG_OK) return st;
   if (n < 0 || !ranges || !tf.lut || tf.lut_size < 2 || tf.n_tf < 1 || tf.n_tf > 4096)
     return VEG_ERR_INVALID_ARGUMENT;
+  if (total_tiles_of(cams, n_views) >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
   if (tf.lut_size > 4096) return VEG_ERR_UNSUPPORTED;
   if (n > 0 && (!geo || !aux || !vals)) return VEG_ERR_INVALID_ARGUMENT;
   if (!aligned16(geo) || !aligned16(aux) || !aligned16(tf.lut) ||
@@ -143,7 +144,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
   if (lit && nrec2 > 0 &&
       cudaMemsetAsync(gsh, 0, (size_t)(nrec2 / 2) * sizeof(float2), stream) != cudaSuccess)
     return VEG_ERR_CUDA;
-  CompArgs A = make_args(cams, reinterpret_cast<const float4*>(splat_geo),
+  CompArgs A = make_args(cams, n_views, reinterpret_cast<const float4*>(splat_geo),
                          reinterpret_cast<const float4*>(splat_aux), vals,
                          reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
                          splat_shade);

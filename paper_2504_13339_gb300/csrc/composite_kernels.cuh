@@ -183,12 +183,12 @@ struct CompArgs {
   const float4* aux;
   const uint32_t* vals;
   const int2* ranges;
-  const int32_t* order;    // work-item order (view * tiles + tile) or null
+  const int32_t* order;    // work-item order (global tile ids) or null
   const int32_t* view_tf;  // per-view table index (one image per view) or null
   const float4* lut;
   const float2* shade;     // per-record Blinn-Phong factors (s_d, s_s) or null
   int lut_size, n_tf;
-  int width, height, tiles_x, tiles_per_view;
+  ViewMap vm;  // per-view tiles and output pixels (views may differ in size)
   float bg0, bg1, bg2;
 };
 
@@ -289,19 +289,20 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : (TG == 1 ? 5 : 4)))
   __shared__ float4 s_col[TG * kBatch];
   __shared__ __align__(8) unsigned char s_mask[kBatch];
   __shared__ unsigned char s_list[kWarps][kBatch];
-  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
-  const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
+  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // global tile id
+  const int view = view_of_tile(A.vm, wi), tile = wi - A.vm.tile_off[view];
+  const int tiles_x = A.vm.tiles_x[view], width = A.vm.width[view], height = A.vm.height[view];
+  const long long pix0 = A.vm.pix_off[view];  // the view's first output pixel
   const int t0 = blockIdx.z * TG;                     // first output image of the group
   const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
   const int ntg = A.view_tf ? 1 : min(TG, A.n_tf - t0);
-  const int n_out = A.view_tf ? 1 : A.n_tf;           // images per view
   const int warp = threadIdx.x >> 5;
   stage_luts<TG>(A, lut0, ntg, s_lut);
   int px, py;
-  pixel_of(tile, A.tiles_x, px, py);
-  const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
-  const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
-  const bool inside = px < A.width && py < A.height;
+  pixel_of(tile, tiles_x, px, py);
+  const float tx0 = (float)((tile % tiles_x) * VEG_TILE);
+  const float ty0 = (float)((tile / tiles_x) * VEG_TILE);
+  const bool inside = px < width && py < height;
   const float2 fxy = make_float2((float)px, (float)py);
   const int2 rg = A.ranges[wi];
   float T[TG], Cr[TG], Cg[TG], Cb[TG];
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : (TG == 1 ? 5 : 4)))
 #pragma unroll
     for (int t = 0; t < TG; ++t) {
       if (t >= ntg) break;
-      const int64_t o = (((int64_t)view * n_out + t0 + t) * A.height + py) * A.width + px;
+      const int64_t o = pix0 + ((int64_t)(t0 + t) * height + py) * width + px;
       out[o] = make_float4(add(Cr[t], mul(T[t], A.bg0)), add(Cg[t], mul(T[t], A.bg1)),
                            add(Cb[t], mul(T[t], A.bg2)), T[t]);
       n_contrib[o] = last[t];
@@ -555,12 +556,13 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
   unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
   __shared__ int s_maxnc;
 
-  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // view * tiles + tile
-  const int view = wi / A.tiles_per_view, tile = wi - view * A.tiles_per_view;
+  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // global tile id
+  const int view = view_of_tile(A.vm, wi), tile = wi - A.vm.tile_off[view];
+  const int tiles_x = A.vm.tiles_x[view], width = A.vm.width[view], height = A.vm.height[view];
+  const long long pix0 = A.vm.pix_off[view];  // the view's first output pixel
   const int t0 = blockIdx.z * TG;                     // first output image of the group
   const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
   const int ntg = A.view_tf ? 1 : min(TG, A.n_tf - t0);
-  const int n_out = A.view_tf ? 1 : A.n_tf;           // images per view
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* my_list = s_lists + warp * kBatch;
   const float4* g_lut = A.lut + (int64_t)lut0 * A.lut_size;  // the group's tables
@@ -571,10 +573,10 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
   for (int e = threadIdx.x; e < kAcc * kBatch; e += 256) s_acc[e] = 0.0f;
   if (threadIdx.x == 0) s_maxnc = 0;
   int px, py;
-  pixel_of(tile, A.tiles_x, px, py);
-  const float tx0 = (float)((tile % A.tiles_x) * VEG_TILE);
-  const float ty0 = (float)((tile / A.tiles_x) * VEG_TILE);
-  const bool inside = px < A.width && py < A.height;
+  pixel_of(tile, tiles_x, px, py);
+  const float tx0 = (float)((tile % tiles_x) * VEG_TILE);
+  const float ty0 = (float)((tile / tiles_x) * VEG_TILE);
+  const bool inside = px < width && py < height;
   const float2 fxy = make_float2((float)px, (float)py);
   const int2 rg = A.ranges[wi];
 
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
     gr[t] = gg[t] = gb[t] = gs[t] = 0.0f;
     nc[t] = 0;
     if (inside && t < ntg) {
-      const int64_t o = (((int64_t)view * n_out + t0 + t) * A.height + py) * A.width + px;
+      const int64_t o = pix0 + ((int64_t)(t0 + t) * height + py) * width + px;
       const float4 ov = out[o], dv4 = dout[o];
       nc[t] = n_contrib[o];
       gr[t] = dv4.x;
@@ -802,7 +804,7 @@ int pick_group(int tf_group, int n_tf, bool bwd, int lut_size, bool lit) {
   return g;
 }
 
-CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
+CompArgs make_args(const veg_camera* cams, int n_views, const float4* geo, const float4* aux,
                    const uint32_t* vals, const int2* ranges, const int32_t* order, veg_tf tf,
                    const float* bg, const float* shade) {
   CompArgs A;
@@ -816,10 +818,7 @@ CompArgs make_args(const veg_camera* cams, const float4* geo, const float4* aux,
   A.lut = reinterpret_cast<const float4*>(tf.lut);
   A.lut_size = tf.lut_size;
   A.n_tf = tf.n_tf;
-  A.width = cams[0].width;
-  A.height = cams[0].height;
-  A.tiles_x = tiles_x_of(A.width);
-  A.tiles_per_view = A.tiles_x * tiles_x_of(A.height);
+  A.vm = make_viewmap(cams, n_views, tf.view_tf ? 1 : tf.n_tf);
   A.bg0 = bg ? bg[0] : 0.f;
   A.bg1 = bg ? bg[1] : 0.f;
   A.bg2 = bg ? bg[2] : 0.f;
@@ -835,7 +834,7 @@ veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc
   veg_status st = prepare_smem(kern, smem, configured, true);
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
-  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
+  dim3 grid((unsigned)A.vm.tile_off[n_views], 1u, groups);
   launch_k(kern, grid, 256, smem, stream, A, out, nc, stats);
   count_launch();
   return launch_status();
@@ -851,7 +850,7 @@ veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const
   veg_status st = prepare_smem(kern, smem, configured, true);
   if (st != VEG_OK) return st;
   const unsigned groups = A.view_tf ? 1u : (unsigned)((A.n_tf + TG - 1) / TG);
-  dim3 grid((unsigned)(A.tiles_per_view * n_views), 1u, groups);
+  dim3 grid((unsigned)A.vm.tile_off[n_views], 1u, groups);
   launch_k(kern, grid, 256, smem, stream, A, out, nc, dout, grad2d, grad_shade, stats);
   count_launch();
   return launch_status();

@@ -368,7 +368,7 @@ extern "C" veg_status veg_raymarch_masked(const veg_camera* cams, int32_t n_view
                                           const float* bg, const uint32_t* cell_mask,
                                           int32_t cell, float* out, unsigned long long* stats,
                                           cudaStream_t stream) {
-  veg_status st = check_cameras(cams, n_views);
+  veg_status st = check_cameras_one_size(cams, n_views);
   if (st != VEG_OK) return st;
   if (!vol4 || !out || resolution < 2 || resolution > 2048 || !(step > 0.0f) || !tf.lut ||
       tf.lut_size < 2 || tf.n_tf < 1 || !aligned16(vol4) || !aligned16(out) ||

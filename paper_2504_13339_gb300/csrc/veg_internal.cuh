@@ -125,7 +125,24 @@ struct CamSet {
   CamParam c[VEG_MAX_VIEWS];
 };
 
+// Views of one call may differ in image size.  Their tiles are numbered
+// one view after another: view v owns the global tile ids [tile_off[v],
+// tile_off[v + 1]), row-major in its own tile grid, and its n_out images of
+// height[v] x width[v] pixels start at pixel pix_off[v] of the output.  For
+// views of one size this is the layout [V][tiles] and [V][T][H][W].
+struct ViewMap {
+  int n_views;
+  int tile_off[VEG_MAX_VIEWS + 1];
+  int tiles_x[VEG_MAX_VIEWS];
+  int width[VEG_MAX_VIEWS];
+  int height[VEG_MAX_VIEWS];
+  long long pix_off[VEG_MAX_VIEWS + 1];
+  int max_tiles;  // the largest view's tile count
+};
+
 veg_status check_cameras(const veg_camera* cams, int32_t n_views);
+// check_cameras, and every view of the size of the first
+veg_status check_cameras_one_size(const veg_camera* cams, int32_t n_views);
 void fill_camset(const veg_camera* cams, int32_t n_views, CamSet* out);
 
 inline int tiles_x_of(int w) { return (w + VEG_TILE - 1) / VEG_TILE; }
@@ -135,11 +152,52 @@ inline int tile_bits_of(int tiles) {
   return b;
 }
 
+// Tile total of the views (int64: callers check it against 2^31).
+inline int64_t total_tiles_of(const veg_camera* cams, int n_views) {
+  int64_t t = 0;
+  for (int v = 0; v < n_views; ++v)
+    t += (int64_t)tiles_x_of(cams[v].width) * tiles_x_of(cams[v].height);
+  return t;
+}
+
+// images_per_view: output images of each view (the TFs of the call, or one).
+inline ViewMap make_viewmap(const veg_camera* cams, int n_views, int images_per_view) {
+  ViewMap m;
+  m.n_views = n_views;
+  m.tile_off[0] = 0;
+  m.pix_off[0] = 0;
+  m.max_tiles = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const int tx = tiles_x_of(cams[v].width), t = tx * tiles_x_of(cams[v].height);
+    m.tiles_x[v] = tx;
+    m.width[v] = cams[v].width;
+    m.height[v] = cams[v].height;
+    m.tile_off[v + 1] = m.tile_off[v] + t;
+    m.pix_off[v + 1] = m.pix_off[v] + (long long)images_per_view * cams[v].width *
+                                          cams[v].height;
+    m.max_tiles = t > m.max_tiles ? t : m.max_tiles;
+  }
+  return m;
+}
+
+// The view owning global tile id g (binary search over the view offsets).
+__device__ __forceinline__ int view_of_tile(const ViewMap& m, int g) {
+  int lo = 0, hi = m.n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (m.tile_off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // Entry points shared between translation units (no argument validation).
 veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const veg_tf* cull_tf,
                           float4* geo, float4* aux, int32_t* tiles, short4* rect,
                           cudaStream_t stream);
-size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity, int tiles_per_view);
+size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity);
 veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const float4* geo,
                           const int32_t* tiles, const short4* rect, void* ws, int64_t capacity,
                           uint64_t* keys, uint32_t* vals, int2* ranges, cudaStream_t stream);

@@ -9,19 +9,28 @@ the device and admits render requests (model, camera, TF, resolution):
   up front (records, tile instances, pixels, views).  The number of slots is
   what the memory budget admits; nothing is allocated while serving.
 * Batching: a free slot takes the oldest waiting request and every other
-  waiting request for the same model and resolution that still fits its
-  buffers (records = views x Gaussians, pixels, estimated tile instances),
-  and renders them as one batch: one projection + binning + sort over all
-  the batch's views and one compositing launch in which view v uses its own
-  TF (`veg_tf.view_tf`).
+  waiting request for the same model, at any resolution, that still fits
+  its buffers (records = views x Gaussians, pixels, estimated tile
+  instances), and renders them as one batch: one projection + binning + sort
+  over all the batch's views, whose image sizes may differ, and one
+  compositing launch in which view v uses its own TF (`veg_tf.view_tf`) and
+  writes its own image.
 * Continuity: requests that arrive while batches run are admitted as soon as
   a slot frees; slots run on separate CUDA streams, so their work overlaps
   on the device.
 * Latency = result ready (the batch's completion event observed on the host)
-  minus arrival time.  The per-(model, resolution) instance estimate is
-  learned from completed batches; a batch that overflowed its instance
-  buffer is rendered again one request at a time, and a request whose own
-  render still overflows carries that status.
+  minus arrival time.  The tile instances of each (model, resolution) are
+  learned from completed batches (a batch's count is shared over its
+  requests in proportion to their pixels; a batch's estimate sums its
+  requests');
+  a batch that overflowed its instance buffer is not waited for again: its
+  requests go back to the front of the queue, each to be rendered alone
+  when a slot frees, and a request whose own render still overflows carries
+  that status.
+* Memory admission is by slots: the server builds as many slots as the
+  memory budget holds (at least one), and a request is admitted into a
+  batch when the batch's records, pixels and estimated instances fit the
+  slot's fixed buffers; nothing is allocated while serving.
 
 `fifo_serve` is the comparison path: one request at a time, in arrival order,
 each as a plain single-view render.
@@ -49,6 +58,7 @@ class Request:
     done: float = math.nan
     image: torch.Tensor | None = None  # [H][W][4] when kept
     status: int = 0  # VEG_OK, or VEG_ERR_CAPACITY if even its own render overflowed
+    solo: bool = False  # its batch overflowed: render it alone
 
     @property
     def latency(self):
@@ -100,6 +110,7 @@ class _Slot:
     bufs: _SlotBuffers
     event: torch.cuda.Event | None = None
     batch: list = field(default_factory=list)
+    offsets: list = field(default_factory=list)  # first pixel of each request's image
 
 
 class RenderServer:
@@ -124,75 +135,83 @@ class RenderServer:
             used += b.nbytes()
             self.slots.append(_Slot(torch.cuda.Stream(self.device), b))
         self.bytes = used
-        self.inst = {}  # (model, W, H) -> tile instances per view (largest seen)
+        self.inst = {}  # (model, W, H) -> tile instances of one view (largest seen)
         self.batch_sizes = []
+        self.mixed_batches = 0  # batches holding more than one resolution
+        self.retries = 0  # requests put back after their batch overflowed
 
     def _est(self, model, W, H):
         n = self.models[model][0].shape[0]
         return self.inst.get((model, W, H), min(16 * n, self.lim.instances))
 
-    def _fits(self, model, W, H, k):
-        n = self.models[model][0].shape[0]
-        return (k <= self.lim.views and k * n <= self.lim.records
-                and k * W * H <= self.lim.pixels
-                and k * self._est(model, W, H) <= self.lim.instances)
+    def _fits(self, batch):
+        """The batch's views, records, pixels and estimated instances fit a
+        slot's buffers."""
+        n = self.models[batch[0].model][0].shape[0]
+        k = len(batch)
+        pix = sum(r.camera.width * r.camera.height for r in batch)
+        inst = sum(self._est(r.model, r.camera.width, r.camera.height) for r in batch)
+        return (k <= self.lim.views and k * n <= self.lim.records and pix <= self.lim.pixels
+                and inst <= self.lim.instances)
 
     # -- one batch -------------------------------------------------------------
     def _launch(self, slot, batch):
         r0 = batch[0]
-        W, H = r0.camera.width, r0.camera.height
         b = slot.bufs
         k = len(batch)
         n = self.models[r0.model][0].shape[0]
         g = _lib.gaussians(*self.models[r0.model])
         cams = _lib.cameras([r.camera for r in batch])
-        tiles = ((W + 15) // 16) * ((H + 15) // 16)
+        offsets, tiles = [0], 0
         for i, r in enumerate(batch):
+            W, H = r.camera.width, r.camera.height
+            offsets.append(offsets[-1] + W * H)
+            tiles += ((W + 15) // 16) * ((H + 15) // 16)
             b.view_tf_host[i] = r.tf
+        npix = offsets[-1]
         s = slot.stream
         with torch.cuda.stream(s):
             b.view_tf[:k].copy_(b.view_tf_host[:k], non_blocking=True)
             tf = _lib.tf_desc(self.tf_bank, b.view_tf)
-            out = b.out[:k * H * W * 4].view(k, 1, H, W, 4)
-            nc = b.nc[:k * H * W].view(k, 1, H, W)
+            out = b.out[:npix * 4]
+            nc = b.nc[:npix]
             _lib.veg_project(cams, g, tf, b.geo, b.aux, b.count, b.rect, s)
             _lib.veg_bin_sort(cams, n, b.geo, b.count, b.rect, b.ws, self.lim.instances, None,
                               b.vals, b.ranges, s)
-            _lib.veg_tile_order(b.ranges[:k * tiles], b.order, s)
+            _lib.veg_tile_order(b.ranges[:tiles], b.order, s)
             _lib.veg_composite_fwd(cams, n, b.geo, b.aux, b.vals, b.ranges, tf, self.bg, 1, out,
                                    nc, None, s, tile_order=b.order)
             ev = torch.cuda.Event()
             ev.record(s)
-        slot.event, slot.batch = ev, batch
+        slot.event, slot.batch, slot.offsets = ev, batch, offsets
         self.batch_sizes.append(k)
-        return out
+        self.mixed_batches += len({(r.camera.width, r.camera.height) for r in batch}) > 1
 
     def _finish(self, slot):
+        """Completes a slot's finished batch; returns (completed requests,
+        requests to render again alone)."""
         b = slot.bufs
         st, m = _lib.veg_sync_status(b.ws, slot.stream)  # the stream is already done
-        batch = slot.batch
-        r0 = batch[0]
-        key = (r0.model, r0.camera.width, r0.camera.height)
-        self.inst[key] = max(self.inst.get(key, 0), int(m / len(batch) * 1.2) + 1)
-        if st != _lib.VEG_OK:  # overflow: render the batch again one request at a time
+        batch, offsets = slot.batch, slot.offsets
+        slot.event, slot.batch, slot.offsets = None, [], []
+        # the instances per view, shared over the batch in proportion to pixels
+        for i, r in enumerate(batch):
+            key = (r.model, r.camera.width, r.camera.height)
+            share = m * (offsets[i + 1] - offsets[i]) / offsets[-1]
+            self.inst[key] = max(self.inst.get(key, 0), int(share * 1.2) + 1)
+        if st != _lib.VEG_OK and len(batch) > 1:
             for r in batch:
-                out = self._launch(slot, [r])
-                slot.event.synchronize()
-                r.status = _lib.veg_sync_status(b.ws, slot.stream)[0]
-                self._complete(slot, [r], out)
-        else:
-            H, W = r0.camera.height, r0.camera.width
-            self._complete(slot, batch, b.out[:len(batch) * H * W * 4].view(len(batch), 1, H, W,
-                                                                            4))
-        slot.event, slot.batch = None, []
-        return batch
-
-    def _complete(self, slot, batch, out):
+                r.solo = True
+            self.retries += len(batch)
+            return [], batch
         now = self.clock()
         for i, r in enumerate(batch):
             r.done = now
+            r.status = st
             if self.keep:
-                r.image = out[i, 0].clone()
+                W, H = r.camera.width, r.camera.height
+                r.image = b.out[offsets[i] * 4:offsets[i + 1] * 4].view(H, W, 4).clone()
+        return batch, []
 
     # -- the loop --------------------------------------------------------------
     def clock(self):
@@ -200,12 +219,11 @@ class RenderServer:
 
     def _take_batch(self, pending):
         head = pending[0]
-        key = (head.model, head.camera.width, head.camera.height)
         batch = [head]
-        for r in list(pending)[1:]:
-            if (r.model, r.camera.width, r.camera.height) == key and \
-                    self._fits(head.model, key[1], key[2], len(batch) + 1):
-                batch.append(r)
+        if not head.solo:
+            for r in list(pending)[1:]:
+                if r.model == head.model and not r.solo and self._fits(batch + [r]):
+                    batch.append(r)
         for r in batch:
             pending.remove(r)
         return batch
@@ -225,7 +243,9 @@ class RenderServer:
                 nxt += 1
             for s in self.slots:
                 if s.event is not None and s.event.query():
-                    n_done += len(self._finish(s))
+                    done, retry = self._finish(s)
+                    n_done += len(done)
+                    pending.extendleft(reversed(retry))
             for s in self.slots:
                 if s.event is None and pending:
                     self._launch(s, self._take_batch(pending))

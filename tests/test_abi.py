@@ -109,6 +109,17 @@ def test_host_side_validation_needs_no_gpu(lib):
     assert lib.veg_raymarch_cells(fake, 16, tf16, 128, fake, None) == 1
     assert lib.veg_raymarch_masked(cams, 1, fake, 16, tf16, 0.1, None, None, fake, 3, fake,
                                    None, None) == 1
+    # the raymarcher's views share one size; the splatting entry points take
+    # views of different sizes
+    cams2 = (_lib.veg_camera * 2)()
+    for c, (w, h) in zip(cams2, ((64, 48), (32, 32))):
+        c.width, c.height, c.fx, c.fy = w, h, 40.0, 40.0
+    assert lib.veg_raymarch_masked(cams2, 2, fake, 16, tf16, 0.1, None, None, fake, 8, fake,
+                                   None, None) == 1
+    assert lib.veg_project(cams2, 2, _lib.veg_gaussians(0, 0, 0, 0), None, None, None, None,
+                           None, None) == 0  # n = 0: nothing to launch
+    # veg_render: the TF group is 0 (default) or 1..8
+    assert lib.veg_render(cams, 1, g, tf16, None, 9, 16, fake, 1 << 30, fake, fake, None) == 1
 
 
 def test_raymarch_cell_count_host_logic(lib):

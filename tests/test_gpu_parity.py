@@ -281,6 +281,86 @@ def test_render_entry_point_equals_pipeline():
     assert torch.equal(out, p.out) and torch.equal(nc, p.n_contrib)
 
 
+def test_views_of_different_sizes():
+    """Three views of different image sizes in one projection, binning and
+    compositing call (global tile ids view after view, images view after
+    view): each view's tile lists and images equal its own single-view render
+    bit for bit, its images and the summed gradients match the oracle."""
+    g = S.uniform_gaussians(1500, 141, logscale_mean=-2.8, logscale_std=0.4)
+    g.logscale_w[:, 3] = np.random.default_rng(140).uniform(0.3, 1.0, g.n)
+    sizes = [(100, 70), (64, 64), (37, 53)]
+    cams = [S.orbit_camera(20.0 + 40.0 * i, 10.0, 3.0, w, h) for i, (w, h) in enumerate(sizes)]
+    tfs = S.bump_tfs(2, 142)
+    bg = (0.05, 0.1, 0.0)
+    V, n, T = len(cams), g.n, len(tfs)
+    tens = (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))
+    luts = lut_tensor(tfs)
+    cc, gg, tf = _lib.cameras(cams), _lib.gaussians(*tens), _lib.tf_desc(luts)
+    f4 = lambda k: torch.empty(k, 4, device="cuda")
+    geo, aux = f4(V * n), f4(V * n)
+    tiles = torch.empty(V * n, dtype=torch.int32, device="cuda")
+    rect = torch.empty(V * n, 4, dtype=torch.int16, device="cuda")
+    _lib.veg_project(cc, gg, tf, geo, aux, tiles, rect)
+    ntile = [((w + 15) // 16) * ((h + 15) // 16) for w, h in sizes]
+    toff = np.concatenate([[0], np.cumsum(ntile)])
+    poff = np.concatenate([[0], np.cumsum([T * w * h for w, h in sizes])])
+    cap = 400_000
+    ws = torch.empty(_lib.veg_bin_sort_workspace_size(n, V, cap, 100, 70), dtype=torch.uint8,
+                     device="cuda")
+    ws[:256].zero_()
+    vals = torch.empty(cap, dtype=torch.int32, device="cuda")
+    keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+    ranges = torch.empty(int(toff[-1]), 2, dtype=torch.int32, device="cuda")
+    order = torch.empty(int(toff[-1]), dtype=torch.int32, device="cuda")
+    _lib.veg_bin_sort(cc, n, geo, tiles, rect, ws, cap, keys, vals, ranges)
+    _lib.veg_tile_order(ranges, order)
+    out = f4(int(poff[-1]))
+    nc = torch.empty(int(poff[-1]), dtype=torch.int32, device="cuda")
+    _lib.veg_composite_fwd(cc, n, geo, aux, vals, ranges, tf, bg, 0, out, nc, tile_order=order)
+    st, m = _lib.veg_sync_status(ws)
+    assert st == _lib.VEG_OK
+    rng_np, vals_np = ranges.cpu().numpy(), vals.cpu().numpy()
+    keys_np = keys[:m].cpu().numpy().view(np.uint64)
+    tb = max(1, int(np.ceil(np.log2(max(max(ntile), 2)))))
+    dout = np.random.default_rng(143).standard_normal((int(poff[-1]), 4))
+    gm_ref, gl_ref, gq_ref = np.zeros((n, 4)), np.zeros((n, 4)), np.zeros((n, 4))
+    for v, (w, h) in enumerate(sizes):
+        p, st1, m1, _, _ = gpu_forward(g, [cams[v]], tfs, bg=bg)
+        lo, hi = int(toff[v]), int(toff[v + 1])
+        r1 = p.ranges.cpu().numpy()
+        # the view's lists: the same records (offset by v n) in the same order
+        for t in range(hi - lo):
+            a, b = rng_np[lo + t]
+            a1, b1 = r1[t]
+            assert b - a == b1 - a1
+            assert np.array_equal(vals_np[a:b] - v * n, p.vals[a1:b1].cpu().numpy())
+            if b > a:
+                k = keys_np[a:b]
+                assert np.all(k >> np.uint64(tb + 32) == v)
+                assert np.all((k >> np.uint64(32)) & np.uint64((1 << tb) - 1) == t)
+        img = out[int(poff[v]):int(poff[v + 1])].view(T, h, w, 4)
+        assert torch.equal(img, p.out[0])
+        assert torch.equal(nc[int(poff[v]):int(poff[v + 1])].view(T, h, w), p.n_contrib[0])
+        proj, bins, fwd = O.render([cams[v]], g, tfs, bg=bg, record=True)
+        excl = check(f"sizes_view_{v}", p, fwd, proj, [cams[v]], bins, tfs, bg)
+        dv = dout[int(poff[v]):int(poff[v + 1])].reshape(1, T, h, w, 4)
+        dv[excl] = 0.0
+        g2 = O.composite_bwd(proj, [cams[v]], bins, tfs, bg, fwd, dv)
+        a, b, c = O.params_grad([cams[v]], g, proj, g2)
+        gm_ref += a
+        gl_ref += b
+        gq_ref += c
+    assert int(m) == int(np.diff(rng_np, axis=1).sum())  # every instance in some list
+    grads = [torch.zeros_like(t) for t in tens]
+    g2d = torch.empty(2 * V * n, 4, device="cuda")
+    _lib.veg_composite_bwd(cc, gg, geo, aux, tiles, vals, ranges, tf, bg, 0, out, nc,
+                           dev(dout.astype(np.float32)), None, *grads, g2d, tile_order=order)
+    torch.cuda.synchronize()
+    grad_check(grads[0].cpu().numpy(), gm_ref, "sizes mean_v")
+    grad_check(grads[1].cpu().numpy(), gl_ref, "sizes logscale_w")
+    grad_check(grads[2].cpu().numpy(), gq_ref, "sizes quat")
+
+
 # ----------------------------------------------------------------------------
 # backward
 # ----------------------------------------------------------------------------

@@ -49,6 +49,7 @@ def test_results_same_alone_and_in_the_mix():
     out_mix = mixed.run(reqs)
     assert all(r.image is not None for r in out_mix)
     assert max(mixed.batch_sizes) > 1  # requests were really batched together
+    assert mixed.mixed_batches > 0     # ... across resolutions
     # each request alone: fresh copies of the requests, one at a time
     alone = [Request(r.rid, r.model, r.camera, r.tf, 0.0) for r in reqs]
     single = RenderServer(models, tfs, n_slots=1, max_batch=1, limits=lim(), keep_images=True)
@@ -65,3 +66,38 @@ def test_results_same_alone_and_in_the_mix():
                       [Request(r.rid, r.model, r.camera, r.tf, r.arrival) for r in reqs])
     for f in fifo:
         assert torch.equal(f.image, by_id[f.rid].image)
+
+
+@pytest.mark.gpu
+def test_overflowing_batch_is_requeued_and_each_request_rendered_alone():
+    """A batch whose tile instances overflow the slot's buffer is not waited
+    for: its requests return to the queue and are rendered one at a time,
+    with the same images as alone, and every request completes."""
+    import __graft_entry__
+    __graft_entry__.build()
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    g, _ = S.field_gaussians(20000, 4, 2)
+    models = {"m": (dev(g.mean_v), dev(g.logscale_w), dev(g.quat))}
+    tfs = torch.as_tensor(S.bump_tfs(4, 5), device="cuda")
+    reqs = poisson_requests(models, 4, rate=20000.0, duration=0.002, seed=11,
+                            resolutions=(96, 128))
+    lim = lambda: SlotLimits(records=200_000, instances=120_000, pixels=1 << 20, views=6,
+                             max_side=128)
+    # one request alone needs 39,000-77,000 instances, any six together more
+    # than 120,000
+    single = RenderServer(models, tfs, n_slots=1, max_batch=1, limits=lim(), keep_images=True)
+    alone = [Request(r.rid, r.model, r.camera, r.tf, 0.0) for r in reqs]
+    for a in alone:
+        single.run([a])
+    assert all(a.status == _lib.VEG_OK for a in alone)
+    per_request = max(single.inst.values())
+    assert per_request * 6 > 120_000
+    srv = RenderServer(models, tfs, n_slots=2, max_batch=6, limits=lim(), keep_images=True)
+    for (m, w, h) in list(single.inst):  # estimates too low: batches form and overflow
+        srv.inst[(m, w, h)] = 1
+    out = srv.run([Request(r.rid, r.model, r.camera, r.tf, r.arrival) for r in reqs])
+    assert srv.retries > 0
+    by_id = {a.rid: a for a in alone}
+    for r in out:
+        assert r.status == _lib.VEG_OK and not np.isnan(r.done)
+        assert torch.equal(r.image, by_id[r.rid].image), r.rid
