@@ -500,6 +500,8 @@ def run_gpu(args):
                    "l2": "flushed between timed steps (512 MB write)",
                    "tf_group": {"fwd": p.tuned["fwd"], "bwd": p.tuned["bwd"],
                                 "source": "autotuned at setup (untimed)"},
+                   "tile_batch": {"fwd": p.tuned["fwd_batch"], "bwd": p.tuned["bwd_batch"],
+                                  "source": "autotuned at setup (untimed)"},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "execution": "value: the whole step (all library calls, gradient zeroing, "
                                 "Adam with a device step counter) replayed as one CUDA graph; "
@@ -866,7 +868,8 @@ def measure_sweep(args, reps=3):
            "batched_mpix_per_s": round(pix / (t_batched * 1e-3) / 1e6, 1),
            "plain_mpix_per_s": round(pix / (t_plain * 1e-3) / 1e6, 1),
            "speedup": round(t_plain / t_batched, 2), "images_bit_identical": same,
-           "tf_group": tuned["fwd"], "timing": f"CUDA events, mean of {reps} batched and "
+           "tf_group": tuned["fwd"], "tile_batch": tuned["fwd_batch"],
+           "timing": f"CUDA events, mean of {reps} batched and "
                                                 f"{max(1, reps - 1)} plain runs, L2 flushed "
                                                 "between runs", "clocks": clk}
     del p, q, outs, ref, tens, flush
@@ -948,6 +951,7 @@ def measure_batched(args, reps=5):
            "plain_mpix_per_s": round(pix / (t_plain * 1e-3) / 1e6, 1),
            "speedup_vs_plain": round(t_plain / graph, 2), "launches_per_step": cs.launches,
            "tf_group": {"fwd": tuned["fwd"], "bwd": tuned["bwd"]},
+           "tile_batch": {"fwd": tuned["fwd_batch"], "bwd": tuned["bwd_batch"]},
            "timing": f"CUDA events, mean of {reps} eager, {reps} graph and {max(1, reps // 2)} "
                      "plain steps, L2 flushed between steps; a step = projection, binning, "
                      "compositing of all views and TFs, L1, backward (no optimiser)",

@@ -231,11 +231,14 @@ veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* 
  * (views of different sizes: view after view, n_tf images of H_v x W_v
  * pixels each; with view_tf one image per view).
  * The scene representation is TF-independent, so one sort serves every TF.
- * tile_order: optional device int32 [V * tiles] from veg_tile_order (the
- * order in which tiles are scheduled; NULL = row-major; results do not
- * depend on it).
+ * tile_order: optional device int32 [global tiles] from veg_tile_order
+ * (the order in which tiles are scheduled; NULL = row-major; results do
+ * not depend on it).
  * tf_group: TFs composited per pass (1, 2, 4 or 8; 0 = library default, 1;
  * the autotuner of the Python package picks per shape).
+ * tile_batch: splats of a tile's list staged per pass through shared memory
+ * (128, 256 or 512; 0 = 256; the autotuner picks per shape); results do not
+ * depend on it.  The instrumented build (stats) stages 256.
  * splat_shade: optional device float [V][n][2] of Blinn-Phong factors
  * (s_d, s_s) from veg_shade (8-byte aligned); when given, each splat is
  * blended with the colour s_d rgb + s_s of Eq. 2 instead of rgb.  Opacity,
@@ -253,16 +256,17 @@ veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
                              const float* splat_shade, const uint32_t* vals,
                              const int32_t* tile_ranges,
                              const int32_t* tile_order, veg_tf tf, const float* bg,
-                             int32_t tf_group, float* out, int32_t* n_contrib,
-                             unsigned long long* stats, cudaStream_t stream);
+                             int32_t tf_group, int32_t tile_batch, float* out,
+                             int32_t* n_contrib, unsigned long long* stats,
+                             cudaStream_t stream);
 
 /*
  * veg_composite_bwd -- manual gradients of the render (Sec. 3.3, backward
  * pass through "the rasterizer", the transfer function and the projection).
  *
  * Given the forward inputs/outputs and dL_dout [V][n_tf][H][W][4] (gradient
- * with respect to (R, G, B, T_final)), replays each pixel's blend front to
- * back and ACCUMULATES (+=) into the caller's gradient arrays, packed like
+ * with respect to (R, G, B, T_final)), walks each pixel's blend back to
+ * front and ACCUMULATES (+=) into the caller's gradient arrays, packed like
  * the Gaussians: grad_mean_v [n][4] = (dL/dmu, dL/dv), grad_logscale_w
  * [n][4] = (dL/dlog s, dL/dw), grad_quat [n][4] = dL/dq, summed over views
  * and TFs.  Derivatives are exact: zero through the 0.99 clamp, the skips and
@@ -276,6 +280,8 @@ veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views, int64_t n,
  * dL/ds_d and dL/ds_s per record, and veg_shade_bwd chains them to the
  * normals, the material coefficients and the means; the colour slopes in dv
  * are scaled by s_d.  Shading with stats returns VEG_ERR_UNSUPPORTED.
+ * tf_group (1, 2 or 4; 0 = min(n_tf, 4)) and tile_batch (128, 256 or 512;
+ * 0 = 256) as in veg_composite_fwd; results do not depend on them.
  * stats: optional device uint64[7] accumulating (replayed pixel-splat pairs,
  * pairs walked after culling, pairs above the exponent cutoff, alpha
  * evaluations, blended pairs, blended pairs below the 0.99 clamp, pairs with
@@ -287,8 +293,8 @@ veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views, veg_gaussi
                              const float* splat_shade, const int32_t* tiles_touched,
                              const uint32_t* vals,
                              const int32_t* tile_ranges, const int32_t* tile_order, veg_tf tf,
-                             const float* bg, int32_t tf_group, const float* out,
-                             const int32_t* n_contrib,
+                             const float* bg, int32_t tf_group, int32_t tile_batch,
+                             const float* out, const int32_t* n_contrib,
                              const float* dL_dout, void* workspace, size_t workspace_bytes,
                              float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
                              float* grad2d, float* grad_shade, unsigned long long* stats,

@@ -98,11 +98,11 @@ _SIGS = {
                                            _P]),
     "veg_sync_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I64)]),
     "veg_composite_fwd": (ctypes.c_int, [_CAMS, _I32, _I64, _P, _P, _P, _P, _P, _P, veg_tf, _P,
-                                         _I32, _P, _P, _P, _P]),
+                                         _I32, _I32, _P, _P, _P, _P]),
     "veg_composite_bwd_workspace_size": (ctypes.c_int, [_I64, _I32, ctypes.POINTER(_SZ)]),
     "veg_composite_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P, _P,
-                                         veg_tf, _P, _I32, _P, _P, _P, _P, _SZ, _P, _P, _P, _P,
-                                         _P, _P, _P]),
+                                         veg_tf, _P, _I32, _I32, _P, _P, _P, _P, _SZ, _P, _P, _P,
+                                         _P, _P, _P, _P]),
     "veg_tile_order": (ctypes.c_int, [_P, _I64, _P, _P]),
     "veg_project_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P]),
     "veg_l1_loss_workspace_size": (ctypes.c_int, [ctypes.POINTER(_SZ)]),
@@ -255,13 +255,14 @@ def veg_tile_order(tile_ranges, tile_order, stream=None):
 
 
 def veg_composite_fwd(cams, n, splat_geo, splat_aux, vals, tile_ranges, tf, bg, tf_group, out,
-                      n_contrib, stats=None, stream=None, tile_order=None, splat_shade=None):
+                      n_contrib, stats=None, stream=None, tile_order=None, splat_shade=None,
+                      tile_batch=0):
     bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
     _check("veg_composite_fwd",
            load().veg_composite_fwd(cams, len(cams), n, _ptr(splat_geo), _ptr(splat_aux),
                                     _ptr(splat_shade), _ptr(vals), _ptr(tile_ranges), _ptr(tile_order), tf,
-                                    ctypes.cast(bgc, ctypes.c_void_p), tf_group, _ptr(out),
-                                    _ptr(n_contrib), _ptr(stats), _stream(stream)))
+                                    ctypes.cast(bgc, ctypes.c_void_p), tf_group, tile_batch,
+                                    _ptr(out), _ptr(n_contrib), _ptr(stats), _stream(stream)))
 
 
 def veg_composite_bwd_workspace_size(n, n_views) -> int:
@@ -274,15 +275,16 @@ def veg_composite_bwd_workspace_size(n, n_views) -> int:
 def veg_composite_bwd(cams, g, splat_geo, splat_aux, tiles_touched, vals, tile_ranges, tf, bg,
                       tf_group, out, n_contrib, dL_dout, workspace, grad_mean_v, grad_logscale_w,
                       grad_quat, grad2d=None, stats=None, stream=None, tile_order=None,
-                      splat_shade=None, grad_shade=None):
+                      splat_shade=None, grad_shade=None, tile_batch=0):
     bgc = (ctypes.c_float * 3)(*[float(b) for b in bg])
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check("veg_composite_bwd",
            load().veg_composite_bwd(cams, len(cams), g, _ptr(splat_geo), _ptr(splat_aux),
                                     _ptr(splat_shade), _ptr(tiles_touched), _ptr(vals), _ptr(tile_ranges),
                                     _ptr(tile_order), tf,
-                                    ctypes.cast(bgc, ctypes.c_void_p), tf_group, _ptr(out),
-                                    _ptr(n_contrib), _ptr(dL_dout), _ptr(workspace), ws_bytes,
+                                    ctypes.cast(bgc, ctypes.c_void_p), tf_group, tile_batch,
+                                    _ptr(out), _ptr(n_contrib), _ptr(dL_dout), _ptr(workspace),
+                                    ws_bytes,
                                     _ptr(grad_mean_v), _ptr(grad_logscale_w), _ptr(grad_quat),
                                     _ptr(grad2d), _ptr(grad_shade), _ptr(stats),
                                     _stream(stream)))

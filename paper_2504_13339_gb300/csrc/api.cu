@@ -215,6 +215,6 @@ extern "C" veg_status veg_render(const veg_camera* cams, int32_t n_views, veg_ga
   st = tile_order_launch(R.ranges, (int)tiles, R.order, stream);
   if (st != VEG_OK) return st;
   return composite_fwd_launch(cams, n_views, g.n, R.geo, R.aux, R.vals, R.ranges, R.order, tf, bg,
-                              nullptr, tf_group, reinterpret_cast<float4*>(out), n_contrib,
+                              nullptr, tf_group, 0, reinterpret_cast<float4*>(out), n_contrib,
                               nullptr, stream);
 }

@@ -12,35 +12,37 @@ veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
 veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float4* geo, const float4* aux, const uint32_t* vals,
                                 const int2* ranges, const int32_t* order, veg_tf tf,
-                                const float* bg, const float* shade, int tf_group, float4* out,
-                                int32_t* n_contrib, unsigned long long* stats,
-                                cudaStream_t stream) {
+                                const float* bg, const float* shade, int tf_group,
+                                int tile_batch, float4* out, int32_t* n_contrib,
+                                unsigned long long* stats, cudaStream_t stream) {
   CompArgs A = make_args(cams, n_views, geo, aux, vals, ranges, order, tf, bg, shade);
   (void)n;
-  const int TG =
-      tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, false, tf.lut_size, shade != nullptr);
+  const int B = pick_batch(tile_batch);
+  const int TG = tf.view_tf ? 1
+                            : pick_group(tf_group, tf.n_tf, false, tf.lut_size, shade != nullptr,
+                                         stats ? 256 : B);
   if (shade) {
     if (stats) return VEG_ERR_UNSUPPORTED;
     switch (TG) {
-      case 1: return launch_fwd_t<1, false, true>(A, n_views, out, n_contrib, nullptr, stream);
-      case 2: return launch_fwd_t<2, false, true>(A, n_views, out, n_contrib, nullptr, stream);
-      case 4: return launch_fwd_t<4, false, true>(A, n_views, out, n_contrib, nullptr, stream);
-      default: return launch_fwd_t<8, false, true>(A, n_views, out, n_contrib, nullptr, stream);
+      case 1: return fwd_batch<1, false, true>(B, A, n_views, out, n_contrib, nullptr, stream);
+      case 2: return fwd_batch<2, false, true>(B, A, n_views, out, n_contrib, nullptr, stream);
+      case 4: return fwd_batch<4, false, true>(B, A, n_views, out, n_contrib, nullptr, stream);
+      default: return fwd_batch<8, false, true>(B, A, n_views, out, n_contrib, nullptr, stream);
     }
   }
   if (stats) {
     switch (TG) {
-      case 1: return launch_fwd_t<1, true, false>(A, n_views, out, n_contrib, stats, stream);
-      case 2: return launch_fwd_t<2, true, false>(A, n_views, out, n_contrib, stats, stream);
-      case 4: return launch_fwd_t<4, true, false>(A, n_views, out, n_contrib, stats, stream);
-      default: return launch_fwd_t<8, true, false>(A, n_views, out, n_contrib, stats, stream);
+      case 1: return fwd_batch<1, true, false>(B, A, n_views, out, n_contrib, stats, stream);
+      case 2: return fwd_batch<2, true, false>(B, A, n_views, out, n_contrib, stats, stream);
+      case 4: return fwd_batch<4, true, false>(B, A, n_views, out, n_contrib, stats, stream);
+      default: return fwd_batch<8, true, false>(B, A, n_views, out, n_contrib, stats, stream);
     }
   }
   switch (TG) {
-    case 1: return launch_fwd_t<1, false, false>(A, n_views, out, n_contrib, nullptr, stream);
-    case 2: return launch_fwd_t<2, false, false>(A, n_views, out, n_contrib, nullptr, stream);
-    case 4: return launch_fwd_t<4, false, false>(A, n_views, out, n_contrib, nullptr, stream);
-    default: return launch_fwd_t<8, false, false>(A, n_views, out, n_contrib, nullptr, stream);
+    case 1: return fwd_batch<1, false, false>(B, A, n_views, out, n_contrib, nullptr, stream);
+    case 2: return fwd_batch<2, false, false>(B, A, n_views, out, n_contrib, nullptr, stream);
+    case 4: return fwd_batch<4, false, false>(B, A, n_views, out, n_contrib, nullptr, stream);
+    default: return fwd_batch<8, false, false>(B, A, n_views, out, n_contrib, nullptr, stream);
   }
 }
 
@@ -53,6 +55,8 @@ size_t composite_bwd_ws_bytes(int64_t n, int n_views) {
 }  // namespace veg
 
 using namespace veg;
+
+static bool batch_ok(int32_t b) { return b == 0 || b == 128 || b == 256 || b == 512; }
 
 static veg_status check_composite_common(const veg_camera* cams, int32_t n_views, int64_t n,
                                          const float* geo, const float* aux, const uint32_t* vals,
@@ -74,20 +78,20 @@ extern "C" veg_status veg_composite_fwd(const veg_camera* cams, int32_t n_views,
                                         const float* splat_geo, const float* splat_aux,
                                         const float* splat_shade, const uint32_t* vals,
                                         const int32_t* tile_ranges, const int32_t* tile_order,
-                                        veg_tf tf, const float* bg, int32_t tf_group, float* out,
-                                        int32_t* n_contrib, unsigned long long* stats,
-                                        cudaStream_t stream) {
+                                        veg_tf tf, const float* bg, int32_t tf_group,
+                                        int32_t tile_batch, float* out, int32_t* n_contrib,
+                                        unsigned long long* stats, cudaStream_t stream) {
   veg_status st =
       check_composite_common(cams, n_views, n, splat_geo, splat_aux, vals, tile_ranges, tf);
   if (st != VEG_OK) return st;
   if (!out || !n_contrib || !aligned16(out) || tf_group < 0 || tf_group > 8 ||
-      (reinterpret_cast<uintptr_t>(splat_shade) & 7))
+      !batch_ok(tile_batch) || (reinterpret_cast<uintptr_t>(splat_shade) & 7))
     return VEG_ERR_INVALID_ARGUMENT;
   return composite_fwd_launch(cams, n_views, n, reinterpret_cast<const float4*>(splat_geo),
                               reinterpret_cast<const float4*>(splat_aux), vals,
                               reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
-                              splat_shade, tf_group, reinterpret_cast<float4*>(out), n_contrib,
-                              stats, stream);
+                              splat_shade, tf_group, tile_batch, reinterpret_cast<float4*>(out),
+                              n_contrib, stats, stream);
 }
 
 extern "C" veg_status veg_composite_bwd_workspace_size(int64_t n, int32_t n_views,
@@ -103,7 +107,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
                                         const int32_t* tiles_touched, const uint32_t* vals,
                                         const int32_t* tile_ranges, const int32_t* tile_order,
                                         veg_tf tf, const float* bg, int32_t tf_group,
-                                        const float* out,
+                                        int32_t tile_batch, const float* out,
                                         const int32_t* n_contrib, const float* dL_dout,
                                         void* workspace, size_t workspace_bytes,
                                         float* grad_mean_v, float* grad_logscale_w,
@@ -113,7 +117,7 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
       check_composite_common(cams, n_views, g.n, splat_geo, splat_aux, vals, tile_ranges, tf);
   if (st != VEG_OK) return st;
   if (!out || !n_contrib || !dL_dout || !aligned16(out) || !aligned16(dL_dout) || tf_group < 0 ||
-      tf_group > 8)
+      tf_group > 8 || !batch_ok(tile_batch))
     return VEG_ERR_INVALID_ARGUMENT;
   const bool only_2d = !grad_mean_v && !grad_logscale_w && !grad_quat;
   if (only_2d && !grad2d) return VEG_ERR_INVALID_ARGUMENT;
@@ -148,26 +152,29 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
                          reinterpret_cast<const float4*>(splat_aux), vals,
                          reinterpret_cast<const int2*>(tile_ranges), tile_order, tf, bg,
                          splat_shade);
-  const int TG = tf.view_tf ? 1 : pick_group(tf_group, tf.n_tf, true, tf.lut_size, lit);
+  const int B = pick_batch(tile_batch);
+  const int TG = tf.view_tf ? 1
+                            : pick_group(tf_group, tf.n_tf, true, tf.lut_size, lit,
+                                         stats ? 256 : B);
   const float4* o4 = reinterpret_cast<const float4*>(out);
   const float4* d4 = reinterpret_cast<const float4*>(dL_dout);
   if (lit) {
     switch (TG) {
-      case 1: st = launch_bwd_t<1, false, true>(A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
-      case 2: st = launch_bwd_t<2, false, true>(A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
-      default: st = launch_bwd_t<4, false, true>(A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
+      case 1: st = bwd_batch<1, false, true>(B, A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
+      case 2: st = bwd_batch<2, false, true>(B, A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
+      default: st = bwd_batch<4, false, true>(B, A, n_views, o4, n_contrib, d4, g2, gsh, nullptr, stream); break;
     }
   } else if (stats) {
     switch (TG) {
-      case 1: st = launch_bwd_t<1, true, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
-      case 2: st = launch_bwd_t<2, true, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
-      default: st = launch_bwd_t<4, true, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
+      case 1: st = bwd_batch<1, true, false>(B, A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
+      case 2: st = bwd_batch<2, true, false>(B, A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
+      default: st = bwd_batch<4, true, false>(B, A, n_views, o4, n_contrib, d4, g2, nullptr, stats, stream); break;
     }
   } else {
     switch (TG) {
-      case 1: st = launch_bwd_t<1, false, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
-      case 2: st = launch_bwd_t<2, false, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
-      default: st = launch_bwd_t<4, false, false>(A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
+      case 1: st = bwd_batch<1, false, false>(B, A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
+      case 2: st = bwd_batch<2, false, false>(B, A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
+      default: st = bwd_batch<4, false, false>(B, A, n_views, o4, n_contrib, d4, g2, nullptr, nullptr, stream); break;
     }
   }
   if (st != VEG_OK || only_2d) return st;

@@ -1,9 +1,11 @@
 // Compositing kernels: front-to-back blending (Eq. 1) of depth-sorted splats
 // per 16x16 tile for a group of transfer functions, and its backward pass.
 //
-// One CTA of 256 threads owns one (view, tile, TF group); each thread owns
-// one pixel and each warp an 8x4 pixel block.  The tile's list is staged in
-// batches of 256 splats through shared memory.  The stager evaluates every
+// One CTA of 256 threads owns one (view, tile, TF group) work item, in the
+// longest-first order of the tiles; each thread owns one pixel and each warp
+// an 8x4 pixel block.  The tile's list is staged in batches of B splats (the
+// tile batch: 128, 256 or 512, chosen by the caller or its autotuner)
+// through shared memory.  The stager evaluates every
 // splat's colour and opacity under each TF of the group once (linear
 // interpolation in the TF tables: held in shared memory by the forward, read
 // through the L1 cache by the backward), the exponent below which
@@ -29,11 +31,20 @@ namespace veg {
 
 namespace {
 
-constexpr int kBatch = 256;
-constexpr int kWarps = 8;
-// One splat is staged per thread and the backward indexes its per-splat
-// shared arrays by thread: the batch must equal the 256-thread block.
-static_assert(kBatch == 32 * kWarps, "batch size must equal the block size");
+constexpr int kWarps = 8;  // 256 threads
+// Every per-splat shared array is indexed by the splat's batch slot, which
+// a thread loops over in steps of the block size (B / 256 slots per thread
+// for B = 512; threads past the slots stage nothing for B = 128).
+
+// A warp list entry is a batch slot: one byte for batches up to 256 splats.
+template <int B>
+struct ListEntry {
+  using T = unsigned char;
+};
+template <>
+struct ListEntry<512> {
+  using T = unsigned short;
+};
 
 // 2^x with the hardware approximation (ex2.approx.ftz), x = power * log2(e).
 __device__ __forceinline__ float gauss_of(float power) {
@@ -147,15 +158,31 @@ __device__ __forceinline__ unsigned lanemask_lt_() {
 }
 
 // Compacts the batch positions whose mask has this warp's bit, in order.
-// Lane l reads the masks of positions 8l .. 8l + 7 as one 64-bit word
-// (positions past the batch's count hold empty masks); an exclusive warp
-// scan of the per-lane hit counts places each lane's hits in the list.
-static_assert(kBatch == 32 * 8, "one 64-bit mask word per lane");
-__device__ __forceinline__ int build_warp_list(const unsigned char* s_mask, unsigned char* list) {
+// Lane l reads the masks of its P = B/32 consecutive positions P l .. P l +
+// P - 1 as one 32-bit word (B = 128) or P/8 64-bit words (positions past the
+// batch's count hold empty masks); an exclusive warp scan of the per-lane
+// hit counts places each lane's hits in the list.
+template <int B>
+__device__ __forceinline__ int build_warp_list(const unsigned char* s_mask,
+                                               typename ListEntry<B>::T* list) {
+  static_assert(B == 128 || B == 256 || B == 512, "tile batch of 128, 256 or 512 splats");
+  constexpr int P = B / 32;
+  constexpr int NW = P >= 8 ? P / 8 : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned long long m = reinterpret_cast<const unsigned long long*>(s_mask)[lane];
-  unsigned long long bits = (m >> warp) & 0x0101010101010101ull;  // bit 8k: position 8l + k
-  const int c = __popcll(bits);
+  unsigned long long bits[NW];
+  int c = 0;
+  if (P == 4) {
+    const unsigned m = reinterpret_cast<const unsigned*>(s_mask)[lane];
+    bits[0] = (m >> warp) & 0x01010101u;  // bit 8k: position 4l + k
+    c = __popc((unsigned)bits[0]);
+  } else {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const unsigned long long m = reinterpret_cast<const unsigned long long*>(s_mask)[lane * NW + w];
+      bits[w] = (m >> warp) & 0x0101010101010101ull;  // bit 8k: position P l + 8 w + k
+      c += __popcll(bits[w]);
+    }
+  }
   int incl = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -163,10 +190,14 @@ __device__ __forceinline__ int build_warp_list(const unsigned char* s_mask, unsi
     if (lane >= o) incl += t;
   }
   int pos = incl - c;
-  while (bits) {
-    const int b = __ffsll((long long)bits) - 1;
-    list[pos++] = (unsigned char)(8 * lane + (b >> 3));
-    bits &= bits - 1;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    unsigned long long bw = bits[w];
+    while (bw) {
+      const int bb = __ffsll((long long)bw) - 1;
+      list[pos++] = (typename ListEntry<B>::T)(P * lane + 8 * w + (bb >> 3));
+      bw &= bw - 1;
+    }
   }
   __syncwarp();
   return __shfl_sync(0xffffffffu, incl, 31);
@@ -204,7 +235,7 @@ __device__ __forceinline__ void stage_luts(const CompArgs& A, int lut0, int ntg,
   }
 }
 
-// Stages splat `i` of the tile list into batch slot threadIdx.x: geometry,
+// Stages splat `i` of the tile list into batch slot `s`: geometry,
 // per-TF colour and A w (and, for the backward, the slopes), the exponent
 // cutoff and the warp-block mask.  Returns the record index.
 //
@@ -218,14 +249,13 @@ __device__ __forceinline__ void stage_luts(const CompArgs& A, int lut0, int ntg,
 // Shading (Eq. 2, LIT): the forward stages the shaded colour s_d C(v) + s_s;
 // the backward stages the unshaded C(v) and (s_d, s_s) in s_sh, with the
 // colour slopes already scaled by s_d.  Without shading s_sh is unused.
-template <int TG, bool BWD, bool LIT>
-__device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const float4* lut,
+template <int TG, int B, bool BWD, bool LIT>
+__device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, int s, const float4* lut,
                                                 unsigned valid, float tx0, float ty0,
                                                 float4* s_geo, float2* s_c, float4* s_col,
                                                 float4* s_slope, float2* s_sh,
                                                 unsigned char* s_mask) {
   const int L = A.lut_size;
-  const int s = threadIdx.x;
   const uint32_t g = A.vals[i];
   const float4 ge = A.geo[g], au = A.aux[g];
   s_geo[s] = make_float4(ge.x, ge.y, -0.5f * au.x, -au.y);
@@ -255,9 +285,9 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
       gc = __fmaf_rn(sh.x, gc, sh.y);
       b = __fmaf_rn(sh.x, b, sh.y);
     }
-    s_col[t * kBatch + s] = make_float4(r, gc, b, aw);
+    s_col[t * B + s] = make_float4(r, gc, b, aw);
     if (BWD)
-      s_slope[t * kBatch + s] = make_float4(slc * (hi.x - lo.x), slc * (hi.y - lo.y),
+      s_slope[t * B + s] = make_float4(slc * (hi.x - lo.x), slc * (hi.y - lo.y),
                                             slc * (hi.z - lo.z), ge.w * sl * (hi.w - lo.w));
     max_aw = fmaxf(max_aw, aw);
   }
@@ -278,122 +308,129 @@ __device__ __forceinline__ uint32_t stage_splat(const CompArgs& A, int i, const 
 // Resident CTAs per SM: 5 for one TF (48 registers; the extra CTA hides the
 // batch barriers, 7% faster than 4 on the training step), 4 for 2-4 TFs,
 // 2 for 8.
-template <int TG, bool STATS, bool LIT>
+template <int TG, int B, bool STATS, bool LIT>
 __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : (TG == 1 ? 5 : 4)))
-    composite_fwd_kernel(CompArgs A, float4* __restrict__ out, int32_t* __restrict__ n_contrib,
-                         unsigned long long* __restrict__ stats) {
+    composite_fwd_kernel(CompArgs A, float4* __restrict__ out,
+                         int32_t* __restrict__ n_contrib, unsigned long long* __restrict__ stats) {
   pdl_enter();
   extern __shared__ float4 s_lut[];  // [TG][L]
-  __shared__ float4 s_geo[kBatch];   // u_x, u_y, -a/2, -b
-  __shared__ float2 s_c[kBatch];     // -c/2, exponent cutoff
-  __shared__ float4 s_col[TG * kBatch];
-  __shared__ __align__(8) unsigned char s_mask[kBatch];
-  __shared__ unsigned char s_list[kWarps][kBatch];
-  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // global tile id
-  const int view = view_of_tile(A.vm, wi), tile = wi - A.vm.tile_off[view];
-  const int tiles_x = A.vm.tiles_x[view], width = A.vm.width[view], height = A.vm.height[view];
-  const long long pix0 = A.vm.pix_off[view];  // the view's first output pixel
-  const int t0 = blockIdx.z * TG;                     // first output image of the group
-  const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
+  __shared__ float4 s_geo[B];        // u_x, u_y, -a/2, -b
+  __shared__ float2 s_c[B];          // -c/2, exponent cutoff
+  __shared__ float4 s_col[TG * B];
+  __shared__ __align__(16) unsigned char s_mask[B];
+  __shared__ typename ListEntry<B>::T s_list[kWarps][B];
+  const int t0 = blockIdx.z * TG;  // first output image of the group
   const int ntg = A.view_tf ? 1 : min(TG, A.n_tf - t0);
   const int warp = threadIdx.x >> 5;
-  stage_luts<TG>(A, lut0, ntg, s_lut);
-  int px, py;
-  pixel_of(tile, tiles_x, px, py);
-  const float tx0 = (float)((tile % tiles_x) * VEG_TILE);
-  const float ty0 = (float)((tile / tiles_x) * VEG_TILE);
-  const bool inside = px < width && py < height;
-  const float2 fxy = make_float2((float)px, (float)py);
-  const int2 rg = A.ranges[wi];
-  float T[TG], Cr[TG], Cg[TG], Cb[TG];
-  int last[TG];
-#pragma unroll
-  for (int t = 0; t < TG; ++t) {
-    T[t] = 1.0f;
-    Cr[t] = Cg[t] = Cb[t] = 0.0f;
-    last[t] = 0;
-  }
-  unsigned act = inside ? ((1u << ntg) - 1u) : 0u;
   unsigned long long n_vis = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0;
-
-  for (int start = rg.x; start < rg.y; start += kBatch) {
-    if (__syncthreads_count(act != 0u) == 0) break;
-    const int cnt = min(kBatch, rg.y - start);
-    if ((int)threadIdx.x < cnt)
-      stage_splat<TG, false, LIT>(A, start + threadIdx.x, s_lut, 0xffu, tx0, ty0, s_geo, s_c,
-                                  s_col, nullptr, nullptr, s_mask);
-    else
-      s_mask[threadIdx.x] = 0;
-    __syncthreads();
-    const int nw = build_warp_list(s_mask, s_list[warp]);
-    const bool act0 = act != 0u;
-    int jstop = cnt;  // 1 + batch position where this pixel terminated
-    // Eq. 1 update of every live TF of the group with splat j (exponent G).
-    auto blend = [&](int j, float G) {
-#pragma unroll
-      for (int t = 0; t < TG; ++t) {
-        if (!(act & (1u << t))) continue;
-        if (STATS) ++n_alpha;
-        const float4 c = s_col[t * kBatch + j];
-        const float alpha = fminf(kAlphaMax, mul(c.w, G));
-        if (alpha < kAlphaMin) continue;
-        const float test = mul(T[t], sub(1.0f, alpha));
-        if (test < kTMin) {
-          act &= ~(1u << t);
-          continue;
-        }
-        const float wgt = mul(alpha, T[t]);
-        Cr[t] = __fmaf_rn(c.x, wgt, Cr[t]);
-        Cg[t] = __fmaf_rn(c.y, wgt, Cg[t]);
-        Cb[t] = __fmaf_rn(c.z, wgt, Cb[t]);
-        T[t] = test;
-        last[t] = start + j - rg.x + 1;
-        if (STATS) ++n_blend;
-      }
-      if (STATS && !act) jstop = j + 1;
-    };
-    // two splats per step: their exponents are independent and overlap,
-    // the blends stay in list order
-    int k = 0;
-    for (; k + 1 < nw && act; k += 2) {
-      const int j0 = s_list[warp][k], j1 = s_list[warp][k + 1];
-      const float4 g0 = s_geo[j0], g1 = s_geo[j1];
-      const float2 c0 = s_c[j0], c1 = s_c[j1];
-      float2 d0, d1, q0, q1;
-      float x0, x1;
-      const float p0 = power_at(g0.x, g0.y, fxy, g0.z, g0.w, c0.x, d0, q0, x0);
-      const float p1 = power_at(g1.x, g1.y, fxy, g1.z, g1.w, c1.x, d1, q1, x1);
-      const bool e0 = !(p0 < c0.y || p0 > 0.0f), e1 = !(p1 < c1.y || p1 > 0.0f);
-      if (STATS) {
-        n_it += 2;
-        n_eval += (unsigned)e0 + (unsigned)e1;
-      }
-      if (e0) blend(j0, gauss_of(p0));
-      if (e1 && act) blend(j1, gauss_of(p1));
-    }
-    if (k < nw && act) {
-      const int j = s_list[warp][k];
-      const float4 sg = s_geo[j];
-      const float2 sc = s_c[j];
-      float2 d, d2;
-      float dxy;
-      const float power = power_at(sg.x, sg.y, fxy, sg.z, sg.w, sc.x, d, d2, dxy);
-      if (STATS) ++n_it;
-      if (!(power < sc.y || power > 0.0f)) {
-        if (STATS) ++n_eval;
-        blend(j, gauss_of(power));
-      }
-    }
-    if (STATS && act0) n_vis += (unsigned long long)jstop;
-  }
-  if (inside) {
+  {
+    const int item = (int)blockIdx.x;
+    const int wi = A.order ? A.order[item] : item;  // global tile id
+    const int view = view_of_tile(A.vm, wi), tile = wi - A.vm.tile_off[view];
+    const int tiles_x = A.vm.tiles_x[view], width = A.vm.width[view], height = A.vm.height[view];
+    const long long pix0 = A.vm.pix_off[view];          // the view's first output pixel
+    const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
+    stage_luts<TG>(A, lut0, ntg, s_lut);
+    int px, py;
+    pixel_of(tile, tiles_x, px, py);
+    const float tx0 = (float)((tile % tiles_x) * VEG_TILE);
+    const float ty0 = (float)((tile / tiles_x) * VEG_TILE);
+    const bool inside = px < width && py < height;
+    const float2 fxy = make_float2((float)px, (float)py);
+    const int2 rg = A.ranges[wi];
+    float T[TG], Cr[TG], Cg[TG], Cb[TG];
+    int last[TG];
 #pragma unroll
     for (int t = 0; t < TG; ++t) {
-      if (t >= ntg) break;
-      const int64_t o = pix0 + ((int64_t)(t0 + t) * height + py) * width + px;
-      out[o] = make_float4(add(Cr[t], mul(T[t], A.bg0)), add(Cg[t], mul(T[t], A.bg1)),
-                           add(Cb[t], mul(T[t], A.bg2)), T[t]);
-      n_contrib[o] = last[t];
+      T[t] = 1.0f;
+      Cr[t] = Cg[t] = Cb[t] = 0.0f;
+      last[t] = 0;
+    }
+    unsigned act = inside ? ((1u << ntg) - 1u) : 0u;
+
+    for (int start = rg.x; start < rg.y; start += B) {
+      if (__syncthreads_count(act != 0u) == 0) break;
+      const int cnt = min(B, rg.y - start);
+#pragma unroll
+      for (int r = 0; r < (B + 255) / 256; ++r) {
+        const int sl = (int)threadIdx.x + 256 * r;
+        if (sl < cnt)
+          stage_splat<TG, B, false, LIT>(A, start + sl, sl, s_lut, 0xffu, tx0, ty0, s_geo, s_c,
+                                         s_col, nullptr, nullptr, s_mask);
+        else if (sl < B)
+          s_mask[sl] = 0;
+      }
+      __syncthreads();
+      const int nw = build_warp_list<B>(s_mask, s_list[warp]);
+      const bool act0 = act != 0u;
+      int jstop = cnt;  // 1 + batch position where this pixel terminated
+      // Eq. 1 update of every live TF of the group with splat j (exponent G).
+      auto blend = [&](int j, float G) {
+#pragma unroll
+        for (int t = 0; t < TG; ++t) {
+          if (!(act & (1u << t))) continue;
+          if (STATS) ++n_alpha;
+          const float4 c = s_col[t * B + j];
+          const float alpha = fminf(kAlphaMax, mul(c.w, G));
+          if (alpha < kAlphaMin) continue;
+          const float test = mul(T[t], sub(1.0f, alpha));
+          if (test < kTMin) {
+            act &= ~(1u << t);
+            continue;
+          }
+          const float wgt = mul(alpha, T[t]);
+          Cr[t] = __fmaf_rn(c.x, wgt, Cr[t]);
+          Cg[t] = __fmaf_rn(c.y, wgt, Cg[t]);
+          Cb[t] = __fmaf_rn(c.z, wgt, Cb[t]);
+          T[t] = test;
+          last[t] = start + j - rg.x + 1;
+          if (STATS) ++n_blend;
+        }
+        if (STATS && !act) jstop = j + 1;
+      };
+      // two splats per step: their exponents are independent and overlap,
+      // the blends stay in list order
+      int k = 0;
+      for (; k + 1 < nw && act; k += 2) {
+        const int j0 = s_list[warp][k], j1 = s_list[warp][k + 1];
+        const float4 g0 = s_geo[j0], g1 = s_geo[j1];
+        const float2 c0 = s_c[j0], c1 = s_c[j1];
+        float2 d0, d1, q0, q1;
+        float x0, x1;
+        const float p0 = power_at(g0.x, g0.y, fxy, g0.z, g0.w, c0.x, d0, q0, x0);
+        const float p1 = power_at(g1.x, g1.y, fxy, g1.z, g1.w, c1.x, d1, q1, x1);
+        const bool e0 = !(p0 < c0.y || p0 > 0.0f), e1 = !(p1 < c1.y || p1 > 0.0f);
+        if (STATS) {
+          n_it += 2;
+          n_eval += (unsigned)e0 + (unsigned)e1;
+        }
+        if (e0) blend(j0, gauss_of(p0));
+        if (e1 && act) blend(j1, gauss_of(p1));
+      }
+      if (k < nw && act) {
+        const int j = s_list[warp][k];
+        const float4 sg = s_geo[j];
+        const float2 sc = s_c[j];
+        float2 d, d2;
+        float dxy;
+        const float power = power_at(sg.x, sg.y, fxy, sg.z, sg.w, sc.x, d, d2, dxy);
+        if (STATS) ++n_it;
+        if (!(power < sc.y || power > 0.0f)) {
+          if (STATS) ++n_eval;
+          blend(j, gauss_of(power));
+        }
+      }
+      if (STATS && act0) n_vis += (unsigned long long)jstop;
+    }
+    if (inside) {
+#pragma unroll
+      for (int t = 0; t < TG; ++t) {
+        if (t >= ntg) break;
+        const int64_t o = pix0 + ((int64_t)(t0 + t) * height + py) * width + px;
+        out[o] = make_float4(add(Cr[t], mul(T[t], A.bg0)), add(Cg[t], mul(T[t], A.bg1)),
+                             add(Cb[t], mul(T[t], A.bg2)), T[t]);
+        n_contrib[o] = last[t];
+      }
     }
   }
   if (STATS) {
@@ -533,7 +570,7 @@ __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c,
 // hide the walk's dependent-issue latency, 7% faster on the training step),
 // 3 for the shaded and instrumented builds of a 4-TF group, which would
 // spill at 64 registers.
-template <int TG, bool STATS, bool LIT>
+template <int TG, int B, bool STATS, bool LIT>
 __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
     composite_bwd_kernel(CompArgs A, const float4* __restrict__ out,
                          const int32_t* __restrict__ n_contrib, const float4* __restrict__ dout,
@@ -544,213 +581,219 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
   unsigned long long n_rep = 0, n_it = 0, n_eval = 0, n_alpha = 0, n_blend = 0, n_free = 0,
                      n_grad = 0;
   extern __shared__ float4 smem[];
-  float4* s_col = smem;                                     // [TG][kBatch]: rgb, A w
-  float4* s_slope = s_col + TG * kBatch;                    // [TG][kBatch]: drgb/dv, w dA/dv
-  float4* s_geo = s_slope + TG * kBatch;                    // [kBatch]: u, -a/2, -b
-  float2* s_c = reinterpret_cast<float2*>(s_geo + kBatch);  // [kBatch]: -c/2, cutoff
-  float2* s_sh = s_c + kBatch;                              // [kBatch]: s_d, s_s (LIT)
-  float* s_acc = reinterpret_cast<float*>(s_sh + (LIT ? kBatch : 0));  // [kBatch][kAcc]
-  // record index of each staged splat (LIT keeps it in the staging thread)
-  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + kAcc * kBatch);
-  unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + (LIT ? 0 : kBatch));
-  unsigned char* s_lists = s_mask + kBatch;  // [kWarps][kBatch]
+  using LT = typename ListEntry<B>::T;
+  float4* s_col = smem;                                // [TG][B]: rgb, A w
+  float4* s_slope = s_col + TG * B;                    // [TG][B]: drgb/dv, w dA/dv
+  float4* s_geo = s_slope + TG * B;                    // [B]: u, -a/2, -b
+  float2* s_c = reinterpret_cast<float2*>(s_geo + B);  // [B]: -c/2, cutoff
+  float2* s_sh = s_c + B;                              // [B]: s_d, s_s (LIT)
+  float* s_acc = reinterpret_cast<float*>(s_sh + (LIT ? B : 0));  // [B][kAcc] gradient sums
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_acc + kAcc * B);  // [B]: record index
+  unsigned char* s_mask = reinterpret_cast<unsigned char*>(s_idx + B);  // [B]
+  LT* s_lists = reinterpret_cast<LT*>(s_mask + B);  // [kWarps][B]
   __shared__ int s_maxnc;
 
-  const int wi = A.order ? A.order[blockIdx.x] : (int)blockIdx.x;  // global tile id
-  const int view = view_of_tile(A.vm, wi), tile = wi - A.vm.tile_off[view];
-  const int tiles_x = A.vm.tiles_x[view], width = A.vm.width[view], height = A.vm.height[view];
-  const long long pix0 = A.vm.pix_off[view];  // the view's first output pixel
-  const int t0 = blockIdx.z * TG;                     // first output image of the group
-  const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
+  const int t0 = blockIdx.z * TG;  // first output image of the group
   const int ntg = A.view_tf ? 1 : min(TG, A.n_tf - t0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* my_list = s_lists + warp * kBatch;
-  const float4* g_lut = A.lut + (int64_t)lut0 * A.lut_size;  // the group's tables
-  unsigned valid = 0u;
+  LT* my_list = s_lists + warp * B;
+  for (int e = threadIdx.x; e < kAcc * B; e += 256) s_acc[e] = 0.0f;
+  {
+    const int item = (int)blockIdx.x;
+    const int wi = A.order ? A.order[item] : item;  // global tile id
+    const int view = view_of_tile(A.vm, wi), tile = wi - A.vm.tile_off[view];
+    const int tiles_x = A.vm.tiles_x[view], width = A.vm.width[view], height = A.vm.height[view];
+    const long long pix0 = A.vm.pix_off[view];          // the view's first output pixel
+    const int lut0 = A.view_tf ? A.view_tf[view] : t0;  // first table of the group
+    const float4* g_lut = A.lut + (int64_t)lut0 * A.lut_size;  // the group's tables
+    unsigned valid = 0u;
 #pragma unroll
-  for (int t = 0; t < TG; ++t)
-    if (t < ntg && lut0 + t >= 0 && lut0 + t < A.n_tf) valid |= 1u << t;
-  for (int e = threadIdx.x; e < kAcc * kBatch; e += 256) s_acc[e] = 0.0f;
-  if (threadIdx.x == 0) s_maxnc = 0;
-  int px, py;
-  pixel_of(tile, tiles_x, px, py);
-  const float tx0 = (float)((tile % tiles_x) * VEG_TILE);
-  const float ty0 = (float)((tile / tiles_x) * VEG_TILE);
-  const bool inside = px < width && py < height;
-  const float2 fxy = make_float2((float)px, (float)py);
-  const int2 rg = A.ranges[wi];
+    for (int t = 0; t < TG; ++t)
+      if (t < ntg && lut0 + t >= 0 && lut0 + t < A.n_tf) valid |= 1u << t;
+    if (threadIdx.x == 0) s_maxnc = 0;
+    int px, py;
+    pixel_of(tile, tiles_x, px, py);
+    const float tx0 = (float)((tile % tiles_x) * VEG_TILE);
+    const float ty0 = (float)((tile / tiles_x) * VEG_TILE);
+    const bool inside = px < width && py < height;
+    const float2 fxy = make_float2((float)px, (float)py);
+    const int2 rg = A.ranges[wi];
 
-  // per TF: transmittance behind the splats walked so far, the suffix sum,
-  // the upstream colour gradient and n_contrib
-  float T[TG], Suf[TG], gr[TG], gg[TG], gb[TG], gs[TG];
-  int nc[TG];
-  int my_max = 0;
+    // per TF: transmittance behind the splats walked so far, the suffix sum,
+    // the upstream colour gradient and n_contrib
+    float T[TG], Suf[TG], gr[TG], gg[TG], gb[TG], gs[TG];
+    int nc[TG];
+    int my_max = 0;
 #pragma unroll
-  for (int t = 0; t < TG; ++t) {
-    T[t] = 1.0f;
-    Suf[t] = 0.0f;
-    gr[t] = gg[t] = gb[t] = gs[t] = 0.0f;
-    nc[t] = 0;
-    if (inside && t < ntg) {
-      const int64_t o = pix0 + ((int64_t)(t0 + t) * height + py) * width + px;
-      const float4 ov = out[o], dv4 = dout[o];
-      nc[t] = n_contrib[o];
-      gr[t] = dv4.x;
-      gg[t] = dv4.y;
-      gb[t] = dv4.z;
-      gs[t] = dv4.x + dv4.y + dv4.z;
-      T[t] = ov.w;
-      Suf[t] = ov.w * (A.bg0 * dv4.x + A.bg1 * dv4.y + A.bg2 * dv4.z + dv4.w);
-      my_max = max(my_max, nc[t]);
+    for (int t = 0; t < TG; ++t) {
+      T[t] = 1.0f;
+      Suf[t] = 0.0f;
+      gr[t] = gg[t] = gb[t] = gs[t] = 0.0f;
+      nc[t] = 0;
+      if (inside && t < ntg) {
+        const int64_t o = pix0 + ((int64_t)(t0 + t) * height + py) * width + px;
+        const float4 ov = out[o], dv4 = dout[o];
+        nc[t] = n_contrib[o];
+        gr[t] = dv4.x;
+        gg[t] = dv4.y;
+        gb[t] = dv4.z;
+        gs[t] = dv4.x + dv4.y + dv4.z;
+        T[t] = ov.w;
+        Suf[t] = ov.w * (A.bg0 * dv4.x + A.bg1 * dv4.y + A.bg2 * dv4.z + dv4.w);
+        my_max = max(my_max, nc[t]);
+      }
     }
-  }
-  if (STATS) n_rep = (unsigned long long)my_max;
-  // loop bounds: a warp walks from its last contribution (all lanes take part
-  // in the reductions); the block stages from its last warp's
-  int warp_max = my_max;
+    if (STATS) n_rep += (unsigned long long)my_max;
+    // loop bounds: a warp walks from its last contribution (all lanes take part
+    // in the reductions); the block stages from its last warp's
+    int warp_max = my_max;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    warp_max = max(warp_max, __shfl_xor_sync(0xffffffffu, warp_max, o));
-  __syncthreads();
-  if (lane == 0) atomicMax(&s_maxnc, warp_max);
-  __syncthreads();
-  const int block_max = s_maxnc;
+    for (int o = 16; o > 0; o >>= 1)
+      warp_max = max(warp_max, __shfl_xor_sync(0xffffffffu, warp_max, o));
+    __syncthreads();
+    if (lane == 0) atomicMax(&s_maxnc, warp_max);
+    __syncthreads();
+    const int block_max = s_maxnc;
 
-  // batches from the back: list positions [bstart, bend), slot s = bstart + s
-  for (int bend = block_max; bend > 0; bend -= kBatch) {
-    const int bstart = max(0, bend - kBatch);
-    const int i = rg.x + bstart + threadIdx.x;
-    uint32_t my_rec = 0;
-    float my_w = 0.0f;  // weight of this thread's staged splat
-    if (i < rg.x + bend) {
-      my_rec = stage_splat<TG, true, LIT>(A, i, g_lut, valid, tx0, ty0, s_geo, s_c, s_col,
-                                          s_slope, s_sh, s_mask);
-      my_w = A.geo[my_rec].w;
-      if (!LIT) s_idx[threadIdx.x] = my_rec;
-    } else {
-      s_mask[threadIdx.x] = 0;
-    }
-    __syncthreads();
-    const int nw = build_warp_list(s_mask, my_list);
-    // blend of splat j at list position idx, undone for every TF of the
-    // group: accumulates dL/dG, dL/dv (and dL/ds_d, dL/ds_s) of this pixel
-    auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dsd,
-                        float& dss) {
-      float2 sh = make_float2(1.0f, 0.0f);
-      if (LIT) sh = s_sh[j];
+    // batches from the back: list positions [bstart, bend), slot s = bstart + s
+    for (int bend = block_max; bend > 0; bend -= B) {
+      const int bstart = max(0, bend - B);
+      const int cnt = bend - bstart;
 #pragma unroll
-      for (int t = 0; t < TG; ++t) {
-        if (idx >= nc[t]) continue;
-        if (STATS) ++n_alpha;
-        const float4 c = s_col[t * kBatch + j];
-        const float raw = mul(c.w, G);
-        const float alpha = fminf(kAlphaMax, raw);
-        if (alpha < kAlphaMin) continue;
-        if (STATS) {
-          ++n_blend;
-          n_free += (raw <= kAlphaMax);
-        }
-        const float rr = rcp_approx(sub(1.0f, alpha));
-        const float Ti = T[t] * rr;  // transmittance in front of the splat
-        const float wgt = alpha * Ti;
-        const float cgu = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
-        const float cgd = LIT ? sh.x * cgu + sh.y * gs[t] : cgu;
-        if (LIT) {
-          dsd += wgt * cgu;
-          dss += wgt * gs[t];
-        }
-        const float dalpha = Ti * cgd - Suf[t] * rr;
-        Suf[t] = __fmaf_rn(cgd, wgt, Suf[t]);
-        const float4 sl = s_slope[t * kBatch + j];
-        dvv += wgt * (gr[t] * sl.x + gg[t] * sl.y + gb[t] * sl.z);
-        if (raw <= kAlphaMax) {
-          dvv += dalpha * G * sl.w;
-          dG += dalpha * c.w;
-        }
-        T[t] = Ti;
+      for (int r = 0; r < (B + 255) / 256; ++r) {
+        const int sl = (int)threadIdx.x + 256 * r;
+        if (sl < cnt)
+          s_idx[sl] = stage_splat<TG, B, true, LIT>(A, rg.x + bstart + sl, sl, g_lut, valid, tx0,
+                                                    ty0, s_geo, s_c, s_col, s_slope, s_sh, s_mask);
+        else if (sl < B)
+          s_mask[sl] = 0;
       }
-    };
-    // gradient parts of one pair: u_x, u_y, conic a, b, c, v, the exponent
-    // (dL/dw times w) (and s_d)
-    auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float2 d, float dvv,
-                          float dsd) {
-      v[0] = dp * (2.0f * sg.z * d.x + sg.w * d.y);
-      v[1] = dp * (2.0f * sc * d.y + sg.w * d.x);
-      v[2] = dp * (-0.5f * d.x * d.x);
-      v[3] = dp * (-d.x * d.y);
-      v[4] = dp * (-0.5f * d.y * d.y);
-      v[5] = dvv;
-      v[6] = dp;
-      v[7] = LIT ? dsd : 0.0f;
-    };
-    // the warp's list is in list order: skip its entries past the warp's
-    // last contribution, then walk it backwards two splats per step (j0, the
-    // later one, first); independent geometry and exponentials overlap, and
-    // one 16-slot reduce-scatter sums both splats' gradients over the warp
-    int k = nw - 1;
-    while (k >= 0 && bstart + my_list[k] >= warp_max) --k;
-    for (; k >= 0; k -= 2) {
-      const int j0 = my_list[k];
-      const int idx0 = bstart + j0;  // list position
-      const bool has1 = k >= 1;
-      const int j1 = has1 ? my_list[k - 1] : j0;
-      const int idx1 = bstart + j1;
-      if (STATS) n_it += 1 + (unsigned)has1;
-      const float4 sg0 = s_geo[j0], sg1 = s_geo[j1];
-      const float2 sc0 = s_c[j0], sc1 = s_c[j1];
-      float2 d0, d1, q0, q1;
-      float x0, x1;
-      const float p0 = power_at(sg0.x, sg0.y, fxy, sg0.z, sg0.w, sc0.x, d0, q0, x0);
-      const float p1 = power_at(sg1.x, sg1.y, fxy, sg1.z, sg1.w, sc1.x, d1, q1, x1);
-      const bool ev0 = idx0 < my_max && p0 <= 0.0f && p0 >= sc0.y;
-      const bool ev1 = has1 && idx1 < my_max && p1 <= 0.0f && p1 >= sc1.y;
-      const float G0 = ev0 ? gauss_of(p0) : 0.f;
-      const float G1 = ev1 ? gauss_of(p1) : 0.f;
-      float dG0 = 0.f, dv0 = 0.f, dG1 = 0.f, dv1 = 0.f;
-      float dd0 = 0.f, ds0 = 0.f, dd1 = 0.f, ds1 = 0.f;
-      if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dd0, ds0);
-      if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dd1, ds1);
-      if (STATS) n_eval += (unsigned)ev0 + (unsigned)ev1;
-      if (STATS) n_grad += (unsigned)(dG0 != 0.f) + (unsigned)(dG1 != 0.f);
-      const float dp0 = dG0 * G0, dp1 = dG1 * G1;
-      bool nz = dp0 != 0.f || dv0 != 0.f || dp1 != 0.f || dv1 != 0.f;
-      if (LIT) nz = nz || dd0 != 0.f || ds0 != 0.f || dd1 != 0.f || ds1 != 0.f;
-      if (__any_sync(0xffffffffu, nz)) {
-        float v[16];
-        pair_parts(v, dp0, sg0, sc0.x, d0, dv0, dd0);
-        pair_parts(v + 8, dp1, sg1, sc1.x, d1, dv1, dd1);
-        // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
-        const float r = warp_reduce_scatter16(v, lane);
-        const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
-        if ((lane & 1) == 0 && comp < (LIT ? 8 : 7) && (which == 0 || has1))
-          atomicAdd(&s_acc[(which ? j1 : j0) * kAcc + comp], r);
-        if (LIT) {
-          const float rs = warp_reduce_pair(ds0, ds1, lane);
-          if ((lane & 15) == 1 && (lane < 16 || has1))
-            atomicAdd(&s_acc[(lane < 16 ? j0 : j1) * kAcc + 8], rs);
+      __syncthreads();
+      const int nw = build_warp_list<B>(s_mask, my_list);
+      // blend of splat j at list position idx, undone for every TF of the
+      // group: accumulates dL/dG, dL/dv (and dL/ds_d, dL/ds_s) of this pixel
+      auto tf_grads = [&](int j, int idx, float G, float& dG, float& dvv, float& dsd,
+                          float& dss) {
+        float2 sh = make_float2(1.0f, 0.0f);
+        if (LIT) sh = s_sh[j];
+#pragma unroll
+        for (int t = 0; t < TG; ++t) {
+          if (idx >= nc[t]) continue;
+          if (STATS) ++n_alpha;
+          const float4 c = s_col[t * B + j];
+          const float raw = mul(c.w, G);
+          const float alpha = fminf(kAlphaMax, raw);
+          if (alpha < kAlphaMin) continue;
+          if (STATS) {
+            ++n_blend;
+            n_free += (raw <= kAlphaMax);
+          }
+          const float rr = rcp_approx(sub(1.0f, alpha));
+          const float Ti = T[t] * rr;  // transmittance in front of the splat
+          const float wgt = alpha * Ti;
+          const float cgu = c.x * gr[t] + c.y * gg[t] + c.z * gb[t];
+          const float cgd = LIT ? sh.x * cgu + sh.y * gs[t] : cgu;
+          if (LIT) {
+            dsd += wgt * cgu;
+            dss += wgt * gs[t];
+          }
+          const float dalpha = Ti * cgd - Suf[t] * rr;
+          Suf[t] = __fmaf_rn(cgd, wgt, Suf[t]);
+          const float4 sl = s_slope[t * B + j];
+          dvv += wgt * (gr[t] * sl.x + gg[t] * sl.y + gb[t] * sl.z);
+          if (raw <= kAlphaMax) {
+            dvv += dalpha * G * sl.w;
+            dG += dalpha * c.w;
+          }
+          T[t] = Ti;
+        }
+      };
+      // gradient parts of one pair: u_x, u_y, conic a, b, c, v, the exponent
+      // (dL/dw times w) (and s_d)
+      auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float2 d, float dvv,
+                            float dsd) {
+        v[0] = dp * (2.0f * sg.z * d.x + sg.w * d.y);
+        v[1] = dp * (2.0f * sc * d.y + sg.w * d.x);
+        v[2] = dp * (-0.5f * d.x * d.x);
+        v[3] = dp * (-d.x * d.y);
+        v[4] = dp * (-0.5f * d.y * d.y);
+        v[5] = dvv;
+        v[6] = dp;
+        v[7] = LIT ? dsd : 0.0f;
+      };
+      // the warp's list is in list order: skip its entries past the warp's
+      // last contribution, then walk it backwards two splats per step (j0, the
+      // later one, first); independent geometry and exponentials overlap, and
+      // one 16-slot reduce-scatter sums both splats' gradients over the warp
+      int k = nw - 1;
+      while (k >= 0 && bstart + my_list[k] >= warp_max) --k;
+      for (; k >= 0; k -= 2) {
+        const int j0 = my_list[k];
+        const int idx0 = bstart + j0;  // list position
+        const bool has1 = k >= 1;
+        const int j1 = has1 ? my_list[k - 1] : j0;
+        const int idx1 = bstart + j1;
+        if (STATS) n_it += 1 + (unsigned)has1;
+        const float4 sg0 = s_geo[j0], sg1 = s_geo[j1];
+        const float2 sc0 = s_c[j0], sc1 = s_c[j1];
+        float2 d0, d1, q0, q1;
+        float x0, x1;
+        const float p0 = power_at(sg0.x, sg0.y, fxy, sg0.z, sg0.w, sc0.x, d0, q0, x0);
+        const float p1 = power_at(sg1.x, sg1.y, fxy, sg1.z, sg1.w, sc1.x, d1, q1, x1);
+        const bool ev0 = idx0 < my_max && p0 <= 0.0f && p0 >= sc0.y;
+        const bool ev1 = has1 && idx1 < my_max && p1 <= 0.0f && p1 >= sc1.y;
+        const float G0 = ev0 ? gauss_of(p0) : 0.f;
+        const float G1 = ev1 ? gauss_of(p1) : 0.f;
+        float dG0 = 0.f, dv0 = 0.f, dG1 = 0.f, dv1 = 0.f;
+        float dd0 = 0.f, ds0 = 0.f, dd1 = 0.f, ds1 = 0.f;
+        if (ev0) tf_grads(j0, idx0, G0, dG0, dv0, dd0, ds0);
+        if (ev1) tf_grads(j1, idx1, G1, dG1, dv1, dd1, ds1);
+        if (STATS) n_eval += (unsigned)ev0 + (unsigned)ev1;
+        if (STATS) n_grad += (unsigned)(dG0 != 0.f) + (unsigned)(dG1 != 0.f);
+        const float dp0 = dG0 * G0, dp1 = dG1 * G1;
+        bool nz = dp0 != 0.f || dv0 != 0.f || dp1 != 0.f || dv1 != 0.f;
+        if (LIT) nz = nz || dd0 != 0.f || ds0 != 0.f || dd1 != 0.f || ds1 != 0.f;
+        if (__any_sync(0xffffffffu, nz)) {
+          float v[16];
+          pair_parts(v, dp0, sg0, sc0.x, d0, dv0, dd0);
+          pair_parts(v + 8, dp1, sg1, sc1.x, d1, dv1, dd1);
+          // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
+          const float r = warp_reduce_scatter16(v, lane);
+          const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
+          if ((lane & 1) == 0 && comp < (LIT ? 8 : 7) && (which == 0 || has1))
+            atomicAdd(&s_acc[(which ? j1 : j0) * kAcc + comp], r);
+          if (LIT) {
+            const float rs = warp_reduce_pair(ds0, ds1, lane);
+            if ((lane & 15) == 1 && (lane < 16 || has1))
+              atomicAdd(&s_acc[(lane < 16 ? j0 : j1) * kAcc + 8], rs);
+          }
         }
       }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < (B + 255) / 256; ++r) {
+        const int sl = (int)threadIdx.x + 256 * r;
+        if (sl >= cnt) break;
+        float4* acc = reinterpret_cast<float4*>(s_acc) + (kAcc / 4) * sl;
+        const float4 a0 = acc[0], a1 = acc[1];
+        const float4 a2 = LIT ? acc[2] : make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (LIT) acc[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool any = a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f ||
+                         a1.x != 0.f || a1.y != 0.f || a1.z != 0.f;
+        const uint32_t rec = s_idx[sl];
+        if (any) {
+          float4* dst = grad2d + 2 * (int64_t)rec;
+          const float w = A.geo[rec].w;
+          const float dw = w > 0.0f ? a1.z / w : 0.0f;
+          red_add_v4(dst, a0.x, a0.y, a0.z, a0.w);
+          red_add_v4(dst + 1, a1.x, a1.y, dw, 0.0f);
+        }
+        if (LIT && (a1.w != 0.f || a2.x != 0.f)) red_add_v2(grad_shade + rec, a1.w, a2.x);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (i < rg.x + bend) {
-      float4* acc = reinterpret_cast<float4*>(s_acc) + (kAcc / 4) * threadIdx.x;
-      const float4 a0 = acc[0], a1 = acc[1];
-      const float4 a2 = LIT ? acc[2] : make_float4(0.f, 0.f, 0.f, 0.f);
-      acc[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      acc[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (LIT) acc[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const bool any = a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f ||
-                       a1.x != 0.f || a1.y != 0.f || a1.z != 0.f;
-      const uint32_t rec = LIT ? my_rec : s_idx[threadIdx.x];
-      if (any) {
-        float4* dst = grad2d + 2 * (int64_t)rec;
-        const float dw = my_w > 0.0f ? a1.z / my_w : 0.0f;
-        red_add_v4(dst, a0.x, a0.y, a0.z, a0.w);
-        red_add_v4(dst + 1, a1.x, a1.y, dw, 0.0f);
-      }
-      if (LIT && (a1.w != 0.f || a2.x != 0.f)) red_add_v2(grad_shade + rec, a1.w, a2.x);
-    }
-    __syncthreads();
   }
   if (STATS) {
 #pragma unroll
@@ -775,29 +818,38 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
   }
 }
 
-size_t bwd_smem_bytes(int TG, int L, bool lit) {
+size_t bwd_smem_bytes(int TG, int L, bool lit, int B) {
   // col + slope, geo, (c, cutoff), (s_d, s_s), acc, idx, mask, warp lists (the
   // tables stay in global memory)
   (void)L;
-  return (size_t)TG * kBatch * 16 * 2 + (size_t)kBatch * 16 +
-         (size_t)kBatch * 8 + (lit ? (size_t)kBatch * 8 : 0) +
-         (size_t)(lit ? 12 : 8) * kBatch * 4 + (lit ? 0 : (size_t)kBatch * 4) + (size_t)kBatch +
-         (size_t)kWarps * kBatch;
+  return (size_t)TG * B * 16 * 2 + (size_t)B * 16 + (size_t)B * 8 +
+         (lit ? (size_t)B * 8 : 0) + (size_t)(lit ? 12 : 8) * B * 4 + (size_t)B * 4 +
+         (size_t)B + (size_t)kWarps * B * (B > 256 ? 2 : 1);
 }
+
+// Shared memory of a forward CTA: the group's tables (dynamic) and the
+// batch arrays (static).
+size_t fwd_smem_bytes(int TG, int L, int B) {
+  return (size_t)TG * L * 16 + (size_t)B * (16 + 8 + 1) + (size_t)TG * B * 16 +
+         (size_t)kWarps * B * (B > 256 ? 2 : 1);
+}
+
+// Tile batch: the caller's choice (128, 256 or 512 splats), else 256.
+int pick_batch(int tile_batch) { return tile_batch == 128 || tile_batch == 512 ? tile_batch : 256; }
 
 // TF group size: the caller's choice, else 1 for the forward (measured
 // fastest at the training-step and sweep shapes: each TF stops at its own
 // termination) and up to 4 for the backward (whose replay shares each
 // splat's geometry and reductions across the group); halved until the
-// group's shared memory fits one CTA (227 KB).  The group size changes no
-// result; one table of up to 4096 entries always fits.
-int pick_group(int tf_group, int n_tf, bool bwd, int lut_size, bool lit) {
+// group's shared memory fits one CTA (227 KB) at tile batch B.  The group
+// size changes no result; one table of up to 4096 entries always fits.
+int pick_group(int tf_group, int n_tf, bool bwd, int lut_size, bool lit, int B) {
   int g = tf_group;
   if (g <= 0) g = bwd ? std::min(n_tf, 4) : 1;
   g = g <= 1 ? 1 : g <= 2 ? 2 : (g <= 4 || bwd) ? 4 : 8;
   auto fits = [&](int tg) {
-    const size_t bytes = bwd ? bwd_smem_bytes(tg, lut_size, lit) + 1024
-                             : (size_t)tg * lut_size * 16 + (size_t)tg * kBatch * 16 + 9 * 1024;
+    const size_t bytes = bwd ? bwd_smem_bytes(tg, lut_size, lit, B) + 1024
+                             : fwd_smem_bytes(tg, lut_size, B) + 1024;
     return bytes <= (size_t)227 * 1024;
   };
   while (g > 1 && !fits(g)) g /= 2;
@@ -825,11 +877,11 @@ CompArgs make_args(const veg_camera* cams, int n_views, const float4* geo, const
   return A;
 }
 
-template <int TG, bool STATS, bool LIT>
+template <int TG, int B, bool STATS, bool LIT>
 veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc,
                         unsigned long long* stats, cudaStream_t stream) {
   const size_t smem = (size_t)TG * A.lut_size * sizeof(float4);
-  auto kern = composite_fwd_kernel<TG, STATS, LIT>;
+  auto kern = composite_fwd_kernel<TG, B, STATS, LIT>;
   static SmemRecord configured;
   veg_status st = prepare_smem(kern, smem, configured, true);
   if (st != VEG_OK) return st;
@@ -840,12 +892,12 @@ veg_status launch_fwd_t(const CompArgs& A, int n_views, float4* out, int32_t* nc
   return launch_status();
 }
 
-template <int TG, bool STATS, bool LIT>
+template <int TG, int B, bool STATS, bool LIT>
 veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const int32_t* nc,
                         const float4* dout, float4* grad2d, float2* grad_shade,
                         unsigned long long* stats, cudaStream_t stream) {
-  const size_t smem = bwd_smem_bytes(TG, A.lut_size, LIT);
-  auto kern = composite_bwd_kernel<TG, STATS, LIT>;
+  const size_t smem = bwd_smem_bytes(TG, A.lut_size, LIT, B);
+  auto kern = composite_bwd_kernel<TG, B, STATS, LIT>;
   static SmemRecord configured;
   veg_status st = prepare_smem(kern, smem, configured, true);
   if (st != VEG_OK) return st;
@@ -854,6 +906,34 @@ veg_status launch_bwd_t(const CompArgs& A, int n_views, const float4* out, const
   launch_k(kern, grid, 256, smem, stream, A, out, nc, dout, grad2d, grad_shade, stats);
   count_launch();
   return launch_status();
+}
+
+// Dispatch over the tile batch (the instrumented builds use 256: the pair
+// counts do not depend on the batch).
+template <int TG, bool STATS, bool LIT>
+veg_status fwd_batch(int B, const CompArgs& A, int n_views, float4* out, int32_t* nc,
+                     unsigned long long* stats, cudaStream_t stream) {
+  if constexpr (!STATS) {
+    if (B == 128) return launch_fwd_t<TG, 128, STATS, LIT>(A, n_views, out, nc, stats, stream);
+    if (B == 512) return launch_fwd_t<TG, 512, STATS, LIT>(A, n_views, out, nc, stats, stream);
+  }
+  return launch_fwd_t<TG, 256, STATS, LIT>(A, n_views, out, nc, stats, stream);
+}
+
+template <int TG, bool STATS, bool LIT>
+veg_status bwd_batch(int B, const CompArgs& A, int n_views, const float4* out, const int32_t* nc,
+                     const float4* dout, float4* grad2d, float2* grad_shade,
+                     unsigned long long* stats, cudaStream_t stream) {
+  if constexpr (!STATS) {
+    if (B == 128)
+      return launch_bwd_t<TG, 128, STATS, LIT>(A, n_views, out, nc, dout, grad2d, grad_shade,
+                                               stats, stream);
+    if (B == 512)
+      return launch_bwd_t<TG, 512, STATS, LIT>(A, n_views, out, nc, dout, grad2d, grad_shade,
+                                               stats, stream);
+  }
+  return launch_bwd_t<TG, 256, STATS, LIT>(A, n_views, out, nc, dout, grad2d, grad_shade, stats,
+                                           stream);
 }
 
 }  // namespace

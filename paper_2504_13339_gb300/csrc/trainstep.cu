@@ -45,7 +45,7 @@ extern "C" veg_status veg_train_step(const veg_train_args* a, int32_t view, int3
   const int tiles = veg::tiles_x_of(W) * veg::tiles_x_of(H);
   VEG_TRY(veg_tile_order(a->tile_ranges, tiles, a->tile_order, stream));
   VEG_TRY(veg_composite_fwd(cam, 1, a->n, a->splat_geo, a->splat_aux, shade, a->vals,
-                            a->tile_ranges, a->tile_order, tf, a->bg, a->tf_group, a->out,
+                            a->tile_ranges, a->tile_order, tf, a->bg, a->tf_group, 0, a->out,
                             a->n_contrib, nullptr, stream));
   const float* target = a->targets + ((int64_t)view * a->n_maps + map) * img;
   VEG_TRY(veg_l1_ssim_loss(a->out, target, 1, H, W, a->lambda, a->loss_grad, a->loss,
@@ -55,7 +55,7 @@ extern "C" veg_status veg_train_step(const veg_train_args* a, int32_t view, int3
         cudaMemsetAsync(a->grad[k], 0, (size_t)a->n * 16, stream) != cudaSuccess)
       return VEG_ERR_CUDA;
   VEG_TRY(veg_composite_bwd(cam, 1, g, a->splat_geo, a->splat_aux, shade, a->tiles_touched,
-                            a->vals, a->tile_ranges, a->tile_order, tf, a->bg, a->tf_group,
+                            a->vals, a->tile_ranges, a->tile_order, tf, a->bg, a->tf_group, 0,
                             a->out, a->n_contrib, a->loss_grad, nullptr, 0, a->grad[0],
                             a->grad[1], a->grad[2], a->grad2d, a->lit ? a->grad_shade : nullptr,
                             nullptr, stream));

@@ -204,9 +204,9 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
 veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float4* geo, const float4* aux, const uint32_t* vals,
                                 const int2* ranges, const int32_t* order, veg_tf tf,
-                                const float* bg, const float* shade, int tf_group, float4* out,
-                                int32_t* n_contrib, unsigned long long* stats,
-                                cudaStream_t stream);
+                                const float* bg, const float* shade, int tf_group,
+                                int tile_batch, float4* out, int32_t* n_contrib,
+                                unsigned long long* stats, cudaStream_t stream);
 veg_status tile_order_launch(const int2* ranges, int count, int32_t* order, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------

@@ -48,6 +48,8 @@ class SplatPipeline:
         self.n_tf = int(n_tf)
         self.tf_group = int(tf_group)      # TFs per compositing pass (forward)
         self.tf_group_bwd = int(tf_group)  # TFs per pass (backward)
+        self.tile_batch = 0                # splats staged per pass (forward; 0 = 256)
+        self.tile_batch_bwd = 0            # (backward)
         self.device = torch.device(device)
         self.c_cams = _lib.cameras(self.cams)
         nrec = self.V * self.n
@@ -177,7 +179,7 @@ class SplatPipeline:
         _lib.veg_composite_fwd(self.c_cams, self.n, self.geo, self.aux, self.vals, self.ranges,
                                _lib.tf_desc(luts), self._bg, self.tf_group, self.out,
                                self.n_contrib, stats, stream, tile_order=self.order,
-                               splat_shade=self._shade_buf())
+                               splat_shade=self._shade_buf(), tile_batch=self.tile_batch)
         return self.out
 
     def _shade_buf(self):
@@ -201,7 +203,7 @@ class SplatPipeline:
                                self.out, self.n_contrib, dL_dout, None, grad_mean_v,
                                grad_logscale_w, grad_quat, self.grad2d, None, stream,
                                tile_order=self.order, splat_shade=self._shade_buf(),
-                               grad_shade=self._grad_shade_buf())
+                               grad_shade=self._grad_shade_buf(), tile_batch=self.tile_batch_bwd)
         if self._lit is not None:
             self.shade_backward(grad_mean_v, grad_normal_beta, grad_k_ads, stream)
 
@@ -213,7 +215,8 @@ class SplatPipeline:
                                self.tf_group_bwd,
                                self.out, self.n_contrib, dL_dout, None, None, None, None,
                                self.grad2d, stats, stream, tile_order=self.order,
-                               splat_shade=self._shade_buf(), grad_shade=self._grad_shade_buf())
+                               splat_shade=self._shade_buf(), grad_shade=self._grad_shade_buf(),
+                               tile_batch=self.tile_batch_bwd)
 
     def project_backward(self, grad_mean_v, grad_logscale_w, grad_quat, stream=None):
         _lib.veg_project_bwd(self.c_cams, self._g, self.tiles, self.grad2d, grad_mean_v,

@@ -72,7 +72,7 @@ def test_host_side_validation_needs_no_gpu(lib):
     # null Gaussian arrays with n > 0
     assert lib.veg_project(cams, 1, g, None, None, None, None, None, None) == 1
     tf = _lib.veg_tf(0, 1, 1)
-    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, None, None, tf, None, 0,
+    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, None, None, tf, None, 0, 0,
                                  None, None, None, None) == 1
     assert lib.veg_tile_order(None, 5, None, None) == 1
     assert lib.veg_sync_status(None, None, None) == 1
@@ -83,6 +83,10 @@ def test_host_side_validation_needs_no_gpu(lib):
     assert lib.veg_bin_sort_static(cams, 1, -1, fake, fake, fake, 16, None, fake, fake, None,
                                    None) == 1
     assert lib.veg_l1_loss(None, None, 4, None, None, None, 0, None) == 1
+    # the tile batch is 0 (default), 128, 256 or 512
+    tf1 = _lib.veg_tf(fake, 16, 1)
+    assert lib.veg_composite_fwd(cams, 1, 0, None, None, None, None, fake, None, tf1, None, 0,
+                                 100, fake, fake, None, None) == 1
     # shading: light directions are checked on the host; n = 0 launches nothing
     light = (ctypes.c_float * 3)(0.0, 0.0, 1.0)
     zero = (ctypes.c_float * 3)(0.0, 0.0, 0.0)

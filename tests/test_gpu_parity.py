@@ -260,6 +260,60 @@ def test_batched_tfs_equal_single_tf_renders_bit_exact():
         assert np.array_equal(p.out.cpu().numpy()[0, 0].view(np.uint32), ref[0, t].view(np.uint32))
 
 
+def test_tile_batches_and_groups_give_the_same_results():
+    """Every tile batch (128, 256, 512 splats staged per pass) and TF group:
+    images and n_contrib bit-identical, gradients equal to float rounding
+    and, for one of them, within the bars against the oracle."""
+    g, cams = small_multiview()
+    g = g.subset(np.arange(900))
+    tfs = S.bump_tfs(3, 150)
+    bg = (0.05, 0.0, 0.1)
+    proj, bins, fwd = O.render(cams, g, tfs, bg=bg, record=True)
+    dout = np.random.default_rng(151).standard_normal(fwd["out"].shape)
+    ref = None
+    for group in (1, 2, 4):
+        for batch in (128, 256, 512):
+            p, st, m, tens, luts = gpu_forward(g, cams, tfs, bg=bg)
+            p.tf_group = p.tf_group_bwd = group
+            p.tile_batch = p.tile_batch_bwd = batch
+            p.composite(luts, bg)
+            grads = [torch.zeros_like(t) for t in tens]
+            if ref is None:
+                excl = check("batches", p, fwd, proj, cams, bins, tfs, bg)
+                dout[excl] = 0.0
+            p.backward(dev(dout.astype(np.float32)), *grads)
+            torch.cuda.synchronize()
+            got = (p.out.cpu().numpy(), p.n_contrib.cpu().numpy(),
+                   [t.cpu().numpy() for t in grads])
+            if ref is None:
+                ref = got
+                g2 = O.composite_bwd(proj, cams, bins, tfs, bg, fwd, dout)
+                gm, gl, gq = O.params_grad(cams, g, proj, g2)
+                for a, b, name in zip(got[2], (gm, gl, gq), ("mean_v", "logscale_w", "quat")):
+                    grad_check(a, b, f"batches {name}")
+                continue
+            assert np.array_equal(got[0].view(np.uint32), ref[0].view(np.uint32)), (group, batch)
+            assert np.array_equal(got[1], ref[1]), (group, batch)
+            for a, b in zip(got[2], ref[2]):
+                assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), (group, batch)
+
+
+def test_full_size_tile_batches_bit_identical(train_full):
+    """The 1M scene, whose tile lists span many batches of every size: the
+    forward at tile batches 128 and 512 equals the default bit for bit."""
+    g, cams, tfs, p, m, tens, luts = train_full
+    p.tile_batch = 0
+    p.composite(luts)
+    ref = p.out.clone()
+    for batch in (128, 512):
+        p.tile_batch = batch
+        p.composite(luts)
+        torch.cuda.synchronize()
+        assert torch.equal(p.out, ref), batch
+    p.tile_batch = 0
+    p.composite(luts)
+
+
 def test_tf_cull_is_lossless_bit_exact():
     g, cams, _ = S.plain_scene()
     tfs = S.bump_tfs(2, 38)
