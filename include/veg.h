@@ -209,11 +209,34 @@ veg_status veg_bin_sort_static(const veg_camera* cams, int32_t n_views, int64_t 
                                cudaStream_t stream);
 
 /*
+ * veg_radix_lookback_check -- a device check of the binning's radix sort (a
+ * diagnostic of this library; the paper has no counterpart).  Sorts of at
+ * most 64 chunks of 2048 items (small scenes; larger sorts take three
+ * kernels per pass with no waits) run each radix pass as one kernel in which
+ * a CTA waits for the digit counts that the CTAs of the earlier chunks
+ * publish; every such wait gives up after a bounded number of polls, sets a
+ * timeout flag in the workspace header and lets the kernel finish, so a
+ * fault in that chain shows as a status, never as a hang.  This call sorts n seeded keys (key i = (i * 2654435761) >> 4,
+ * mod 2^32; value i) with that sort, each wait limited to `spins` polls,
+ * and copies the sorted keys and values to keys_out and vals_out (device
+ * uint32 [n], overwritten).  With starve_first != 0 the first chunk is
+ * never taken, so the next chunk's wait runs out: veg_sync_status on the
+ * workspace then returns VEG_ERR_TIMEOUT (the outputs are void); otherwise
+ * VEG_OK and the stable sort.  workspace: device, 256-byte aligned, >=
+ * veg_bin_sort_workspace_size(n, 1, 0, 16, 16) bytes.  1 <= n <= 131072
+ * (64 chunks), spins >= 1; else VEG_ERR_INVALID_ARGUMENT.
+ */
+veg_status veg_radix_lookback_check(void* workspace, size_t workspace_bytes, int64_t n,
+                                    int32_t starve_first, int32_t spins, uint32_t* keys_out,
+                                    uint32_t* vals_out, cudaStream_t stream);
+
+/*
  * veg_sync_status -- waits for `stream`, then reads the status header of a
  * bin_sort / render workspace.  Writes the instance count M (even when it
  * exceeded the capacity) to *n_instances (host, may be NULL).  Returns
- * VEG_ERR_CAPACITY if the last binning overflowed, VEG_ERR_CUDA if the
- * stream reported an error, else VEG_OK.
+ * VEG_ERR_TIMEOUT if a bounded device-side wait of the last binning gave up
+ * (its outputs are then void), VEG_ERR_CAPACITY if the last binning
+ * overflowed, VEG_ERR_CUDA if the stream reported an error, else VEG_OK.
  */
 veg_status veg_sync_status(const void* workspace, cudaStream_t stream, int64_t* n_instances);
 
@@ -314,6 +337,21 @@ veg_status veg_project_bwd(const veg_camera* cams, int32_t n_views, veg_gaussian
                            const int32_t* tiles_touched, const float* grad2d,
                            float* grad_mean_v, float* grad_logscale_w, float* grad_quat,
                            cudaStream_t stream);
+
+/*
+ * veg_project_bwd_range -- veg_project_bwd for the Gaussians [first,
+ * first + count) only (0 <= first, 0 <= count, first + count <= g.n; else
+ * VEG_ERR_INVALID_ARGUMENT).  All arrays keep their full-model layout
+ * (grad2d [V][g.n][8], tiles_touched [V][g.n], gradients [g.n][4]); rows
+ * outside the range are neither read nor written.  Each Gaussian's result is
+ * the same as in the whole-model call, so a backward split into ranges is
+ * bit-identical to one call.  A data-parallel step uses it to start the
+ * gradient all-reduce of one range while the next range is still computed.
+ */
+veg_status veg_project_bwd_range(const veg_camera* cams, int32_t n_views, veg_gaussians g,
+                                 const int32_t* tiles_touched, const float* grad2d,
+                                 int64_t first, int64_t count, float* grad_mean_v,
+                                 float* grad_logscale_w, float* grad_quat, cudaStream_t stream);
 
 /*
  * veg_shade -- Blinn-Phong factors of Eq. 2-3 per view and Gaussian (Sec. 3.3,

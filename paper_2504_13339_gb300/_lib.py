@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libveg.so")
 VEG_OK = 0
 VEG_MAX_VIEWS = 64  # include/veg.h
 VEG_ERR_CAPACITY = 2
+VEG_ERR_TIMEOUT = 4
 STATUS_NAMES = {0: "VEG_OK", 1: "VEG_ERR_INVALID_ARGUMENT", 2: "VEG_ERR_CAPACITY",
                 3: "VEG_ERR_CUDA", 4: "VEG_ERR_TIMEOUT", 5: "VEG_ERR_UNSUPPORTED"}
 MAX_VIEWS = 64
@@ -104,7 +105,10 @@ _SIGS = {
                                          veg_tf, _P, _I32, _I32, _P, _P, _P, _P, _SZ, _P, _P, _P,
                                          _P, _P, _P, _P]),
     "veg_tile_order": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "veg_radix_lookback_check": (ctypes.c_int, [_P, _SZ, _I64, _I32, _I32, _P, _P, _P]),
     "veg_project_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P]),
+    "veg_project_bwd_range": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _I64, _I64, _P,
+                                             _P, _P, _P]),
     "veg_l1_loss_workspace_size": (ctypes.c_int, [ctypes.POINTER(_SZ)]),
     "veg_l1_loss": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),
     "veg_render_workspace_size": (ctypes.c_int, [_I64, _I32, _I64, _I32, _I32,
@@ -240,11 +244,20 @@ def veg_bin_sort_static(cams, n, splat_geo, tiles_touched, rect, capacity, keys,
                                       _ptr(tile_ranges), _ptr(n_instances), _stream(stream))
 
 
+def veg_radix_lookback_check(workspace, n, starve_first, spins, keys_out, vals_out,
+                             stream=None):
+    _check("veg_radix_lookback_check",
+           load().veg_radix_lookback_check(_ptr(workspace), workspace.numel(), n,
+                                           int(bool(starve_first)), spins, _ptr(keys_out),
+                                           _ptr(vals_out), _stream(stream)))
+
+
 def veg_sync_status(workspace, stream=None):
-    """Returns (status, n_instances); does not raise on VEG_ERR_CAPACITY."""
+    """Returns (status, n_instances); does not raise on VEG_ERR_CAPACITY or
+    VEG_ERR_TIMEOUT (the caller decides)."""
     n = _I64()
     st = load().veg_sync_status(_ptr(workspace), _stream(stream), ctypes.byref(n))
-    if st not in (VEG_OK, 2):
+    if st not in (VEG_OK, VEG_ERR_CAPACITY, VEG_ERR_TIMEOUT):
         raise VegError("veg_sync_status", st)
     return st, n.value
 
@@ -438,6 +451,14 @@ def veg_project_bwd(cams, g, tiles_touched, grad2d, grad_mean_v, grad_logscale_w
            load().veg_project_bwd(cams, len(cams), g, _ptr(tiles_touched), _ptr(grad2d),
                                   _ptr(grad_mean_v), _ptr(grad_logscale_w), _ptr(grad_quat),
                                   _stream(stream)))
+
+
+def veg_project_bwd_range(cams, g, tiles_touched, grad2d, first, count, grad_mean_v,
+                          grad_logscale_w, grad_quat, stream=None):
+    _check("veg_project_bwd_range",
+           load().veg_project_bwd_range(cams, len(cams), g, _ptr(tiles_touched), _ptr(grad2d),
+                                        int(first), int(count), _ptr(grad_mean_v),
+                                        _ptr(grad_logscale_w), _ptr(grad_quat), _stream(stream)))
 
 
 def veg_l1_loss_workspace_size() -> int:

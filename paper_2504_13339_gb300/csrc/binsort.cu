@@ -84,11 +84,41 @@ __device__ __forceinline__ T block_exclusive_scan256(T x, T* s_warp) {
 
 // ---------------------------------------------------------------------------
 // radix sort kernels (u32 keys, u32 values, one 1..8-bit digit per pass)
+//
+// A pass splits the items into chunks of 2048; a CTA ranks a chunk's items
+// among equal digits, stages the chunk in digit order in shared memory and
+// writes each digit run out contiguously.  A chunk's start in each digit's
+// run comes from one of two places:
+//  * a table (three kernels per pass: per-chunk digit counts, their scan
+//    along each digit, the scatter) -- for large inputs, where every CTA of
+//    a wave would otherwise wait on its neighbours;
+//  * a chained scan with decoupled look-back (one kernel per pass, after one
+//    histogram of all passes): the CTA takes its chunk by ticket, publishes
+//    its per-digit counts, then adds the earlier chunks' published values
+//    until it meets an inclusive prefix -- for inputs of a few chunks, where
+//    the walks are short and the launches dominate.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ int chunks_of(int64_t n) {
   return (int)((n + kTileItems - 1) / kTileItems);
 }
+
+constexpr int kMaxPasses = 4;
+struct PassDigits {
+  int passes;
+  int shift[kMaxPasses];
+  int nbits[kMaxPasses];
+};
+
+// Look-back word: state in the top two bits (0 not yet published, 1 the
+// chunk's own count, 2 the inclusive prefix of chunks 0..c), value below.
+constexpr unsigned long long kLbAgg = 1ull << 62;
+constexpr unsigned long long kLbInc = 2ull << 62;
+constexpr unsigned long long kLbValue = (1ull << 62) - 1ull;
+// Polls of a look-back word before a pass gives up and flags a timeout.
+constexpr int kLookbackSpins = 1 << 20;
+// Largest sort (in 2048-item chunks) that takes the look-back passes.
+constexpr int kLookbackMaxChunks = 64;
 
 // Per-chunk digit histograms; hist is [2^nbits][nblocks] (nblocks = the
 // chunk capacity), blocks stride over the chunks that hold items.
@@ -176,14 +206,63 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-// Stable scatter: rank every item among equal digits of its block (warp
-// order, then lane order = item order), stage the block in digit order in
-// shared memory, then write each digit run out contiguously.
+// Digit histograms of every pass over all n keys, added into ghist
+// [passes][256] (zeroed beforehand); also zeroes the first pass's look-back
+// words [chunks][256] (each pass zeroes the next one's).
+__global__ void __launch_bounds__(kThreads)
+    radix_global_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, PassDigits pd,
+                             uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look) {
+  pdl_enter();
+  __shared__ uint32_t s_hist[kMaxPasses][256];
+  const int64_t n = cnt.get();
+  const int nch = chunks_of(n);
+  for (int p = 0; p < kMaxPasses; ++p) s_hist[p][threadIdx.x] = 0u;
+  const int64_t nlook = (int64_t)nch * 256;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < nlook;
+       i += (int64_t)gridDim.x * kThreads)
+    look[i] = 0ull;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const uint32_t k = __ldg(&keys[i]);
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+      if (p < pd.passes) atomicAdd(&s_hist[p][(k >> pd.shift[p]) & ((1u << pd.nbits[p]) - 1u)], 1u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p)
+    if (p < pd.passes && (uint32_t)threadIdx.x < (1u << pd.nbits[p]) && s_hist[p][threadIdx.x])
+      atomicAdd(&ghist[p * 256 + threadIdx.x], s_hist[p][threadIdx.x]);
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// One stable pass: rank every item among equal digits of its chunk (warp
+// order, then lane order = item order), stage the chunk in digit order in
+// shared memory and write each digit run out contiguously.  The chunk's
+// start in each digit run is dtot-prefix + hist[digit][chunk] (TABLE; blocks
+// stride over the chunks) or found by look-back (blocks loop over tickets,
+// so a chunk's predecessors belong to blocks that are already running; a
+// look-back not answered within `spins` polls sets FLAG_TIMEOUT in the
+// header and stops waiting: the output is then void).  dtot: the digit
+// totals of the pass.
+template <bool TABLE>
 __global__ void __launch_bounds__(kThreads, 4)
     radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, Count cnt,
-                         int shift, int nbits, const uint32_t* __restrict__ hist,
-                         const uint32_t* __restrict__ totals, int nblocks) {
+                         int shift, int nbits, const uint32_t* __restrict__ dtot,
+                         const uint32_t* __restrict__ hist, int nblocks,
+                         unsigned long long* __restrict__ look, unsigned* __restrict__ ticket,
+                         WsHeader* __restrict__ hdr, int spins,
+                         unsigned long long* __restrict__ look_next) {
   pdl_enter();
   __shared__ uint32_t s_whist[8][256];
   __shared__ uint32_t s_dbase[256];
@@ -191,19 +270,37 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_keys[kTileItems];
   __shared__ uint32_t s_vals[kTileItems];
+  __shared__ int s_chunk;
   const int64_t n = cnt.get();
   const int nch = chunks_of(n);
-  if ((int)blockIdx.x >= nch) return;
+  if (TABLE && (int)blockIdx.x >= nch) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t mask = (1u << nbits) - 1u;
-  const bool digit = (uint32_t)tid <= mask;  // rows of hist and totals exist for digits only
-  const uint32_t dpre = block_exclusive_scan256<uint32_t>(digit ? totals[tid] : 0u, s_warp);
-  for (int b = blockIdx.x; b < nch; b += gridDim.x) {
-    const int64_t base = (int64_t)b * kTileItems;
+  const bool digit = (uint32_t)tid <= mask;  // rows of hist and dtot exist for digits only
+  // exclusive prefix of the digit totals: each digit's first output position
+  const uint32_t dpre = block_exclusive_scan256<uint32_t>(digit ? dtot[tid] : 0u, s_warp);
+  if (!TABLE && look_next) {  // the next pass's look-back words (unused during this pass)
+    const int64_t nl = (int64_t)nch * 256;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + tid; i < nl; i += (int64_t)gridDim.x * kThreads)
+      look_next[i] = 0ull;
+  }
+  for (int it = 0;; ++it) {
+    int b;
+    if (TABLE) {
+      b = (int)blockIdx.x + it * (int)gridDim.x;
+      if (b >= nch) break;  // block-uniform
+      if (digit) s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + b];
+    } else if (tid == 0) {
+      s_chunk = (int)atomicAdd(ticket, 1u);
+    }
 #pragma unroll
     for (int w = 0; w < 8; ++w) s_whist[w][tid] = 0;
-    if (digit) s_dbase[tid] = dpre + hist[(int64_t)tid * nblocks + b];
     __syncthreads();
+    if (!TABLE) {
+      b = s_chunk;
+      if (b >= nch) break;  // block-uniform
+    }
+    const int64_t base = (int64_t)b * kTileItems;
 
     uint32_t k[kItems], v[kItems], r[kItems];
     const unsigned lt = lanemask_lt();
@@ -222,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, and the block's digit count
+    // per digit: exclusive prefix over warps, and the chunk's digit count
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
@@ -230,17 +327,59 @@ __global__ void __launch_bounds__(kThreads, 4)
       s_whist[w][tid] = run;
       run += c;
     }
+    // the chunk in digit order in shared memory: needs only the chunk's own
+    // counts, so the item registers are free before the look-back below
     s_bstart[tid] = block_exclusive_scan256<uint32_t>(run, s_warp);
-    __syncthreads();
+    __syncthreads();  // every digit's start is read below
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
       int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
       if (i < n) {
         uint32_t d = (k[j] >> shift) & mask;
         uint32_t pos = s_bstart[d] + s_whist[warp][d] + r[j];
-        s_keys[pos] = k[j];
-        s_vals[pos] = v[j];
+        if (pos < (uint32_t)kTileItems) {  // always, when the counts agree
+          s_keys[pos] = k[j];
+          s_vals[pos] = v[j];
+        }
       }
+    }
+    if (!TABLE && digit) {
+      // publish the count, then add the earlier chunks' counts until an
+      // inclusive prefix is met, and publish this chunk's inclusive prefix
+      unsigned long long* mine = look + (int64_t)b * 256 + tid;
+      st_volatile_u64(mine, kLbAgg | run);
+      // the earlier chunks' words are read kWindow at a time (independent
+      // loads in flight together), then consumed in order: a count is added
+      // and the walk goes on, an inclusive prefix ends it, a word not yet
+      // published is polled again
+      constexpr int kWindow = 16;
+      unsigned long long prefix = 0;
+      int left = spins;
+      int j = b - 1;
+      bool done = j < 0;
+      while (!done) {
+        unsigned long long w[kWindow];
+#pragma unroll
+        for (int m = 0; m < kWindow; ++m)
+          w[m] = j - m >= 0 ? ld_volatile_u64(look + (int64_t)(j - m) * 256 + tid) : kLbInc;
+        int used = 0;
+#pragma unroll
+        for (int m = 0; m < kWindow; ++m) {
+          if (done || used < m) continue;  // stop at the first unpublished word
+          const unsigned long long st = w[m] & ~kLbValue;
+          if (st == 0ull) continue;
+          if (j - m >= 0) prefix += w[m] & kLbValue;
+          used = m + 1;
+          done = st == kLbInc;
+        }
+        j -= used;
+        if (!done && used < kWindow && --left <= 0) {
+          atomicOr(&hdr->flags, FLAG_TIMEOUT);
+          break;
+        }
+      }
+      st_volatile_u64(mine, kLbInc | (prefix + run));
+      s_dbase[tid] = dpre + (uint32_t)prefix;
     }
     __syncthreads();
     const int cnt_valid = (int)min((int64_t)kTileItems, n - base);
@@ -251,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       kout[g] = key;
       vout[g] = s_vals[p];
     }
-    __syncthreads();  // the next chunk reuses the shared arrays
+    __syncthreads();  // the next chunk reuses the shared arrays (and s_chunk)
   }
 }
 
@@ -419,7 +558,7 @@ __global__ void __launch_bounds__(1024)
   }
   if (threadIdx.x == 0) {
     hdr->n_instances = carry;
-    hdr->flags = carry > (unsigned long long)capacity ? FLAG_CAPACITY : 0u;
+    if (carry > (unsigned long long)capacity) atomicOr(&hdr->flags, FLAG_CAPACITY);
   }
 }
 
@@ -519,10 +658,18 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count) {
+// Empties the tile ranges; block 0 also clears the status flags and the
+// radix sorts' digit histograms and tickets (`small` words).
+__global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count,
+                                   uint32_t* __restrict__ small, int nsmall,
+                                   WsHeader* __restrict__ hdr) {
   pdl_enter();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) ranges[i] = make_int2(0, 0);
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < nsmall; k += blockDim.x) small[k] = 0u;
+    if (threadIdx.x == 0) hdr->flags = 0u;
+  }
 }
 
 // Four sorted keys per thread (one 16-byte load; the key array is 256-byte
@@ -579,10 +726,14 @@ struct Layout {
   uint32_t *dk0, *dv0, *dk1, *dv1, *offsets;
   unsigned long long* bsum;
   uint32_t *ik0, *ik1, *iv0;
-  uint32_t *hist, *totals;
+  uint32_t *hist, *totals;  // table passes: [256][nb_hist] per-chunk counts, [256] totals
+  uint32_t* small;  // look-back passes: [2 sorts][kMaxPasses][256] digit totals, then
+                    // [2][kMaxPasses] tickets
+  unsigned long long* look[2];  // look-back words of alternate passes, [chunks][256] each
   int nb_rec, nb_hist;
   size_t bytes;
 };
+constexpr int kSmallWords = 2 * kMaxPasses * 256 + 2 * kMaxPasses;
 
 Layout carve(void* ws, int64_t nrec, int64_t capacity) {
   Carver c(ws);
@@ -601,12 +752,17 @@ Layout carve(void* ws, int64_t nrec, int64_t capacity) {
   L.nb_hist = (int)std::max<int64_t>(L.nb_rec, (capacity + kTileItems - 1) / kTileItems);
   L.hist = c.take<uint32_t>((size_t)256 * L.nb_hist);
   L.totals = c.take<uint32_t>(256);
+  L.small = c.take<uint32_t>(kSmallWords);
+  // look-back words only for the sorts that take the look-back passes
+  const int64_t look_chunks = std::min<int64_t>(L.nb_hist, kLookbackMaxChunks);
+  L.look[0] = c.take<unsigned long long>((size_t)look_chunks * 256);
+  L.look[1] = c.take<unsigned long long>((size_t)look_chunks * 256);
   L.bytes = c.bytes();
   return L;
 }
 
-// Blocks for a pass over at most `nblocks` chunks: one wave of the scatter
-// (4 CTAs per SM) at most; the kernels stride over the chunks that hold items.
+// CTAs of a radix pass: one wave (4 per SM) at most; they take chunks by
+// ticket until none is left.
 int pass_grid(int nblocks) {
   static std::atomic<int> sms[64];  // per device, 0 until queried
   int dev = 0;
@@ -620,17 +776,54 @@ int pass_grid(int nblocks) {
   return std::max(1, std::min(nblocks, 4 * v));
 }
 
-void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
-                Count cnt, int shift, int nbits, int nblocks, const Layout& L,
-                cudaStream_t stream) {
-  const int grid = pass_grid(nblocks);
-  // the histogram kernel is light (28 registers, 1 KB): twice the blocks
-  launch_k(radix_hist_kernel, std::min(nblocks, 2 * grid), kThreads, 0, stream, kin, cnt, shift, nbits,
-                                                                         L.hist, nblocks);
-  launch_k(radix_scan_rows_kernel, 1 << nbits, 1024, 0, stream, L.hist, nblocks, L.totals, cnt);
-  launch_k(radix_scatter_kernel, grid, kThreads, 0, stream, kin, vin, kout, vout, cnt, shift, nbits,
-                                                      L.hist, L.totals, nblocks);
-  count_launch(3);
+// Stable LSD sort of (key, value) pairs by the key bits [0, bits), in
+// passes of balanced digit widths (at most 8 bits).  Buffers ping-pong
+// k[p % 2] -> k[(p + 1) % 2], the result in k[passes % 2], v[passes % 2].
+// Up to kLookbackMaxChunks chunks (max_chunks, known on the host: the item
+// count itself lives on the device) the passes are look-back kernels after
+// one histogram of all passes (`sort`, 0 or 1, picks their digit totals and
+// tickets); above, three table kernels per pass.
+int radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int bits, int max_chunks,
+               const Layout& L, int sort, cudaStream_t stream, int spins = kLookbackSpins) {
+  PassDigits pd;
+  pd.passes = std::max(1, (bits + 7) / 8);
+  int shift = 0;
+  for (int p = 0; p < pd.passes; ++p) {
+    const int nb = (bits - shift + (pd.passes - p) - 1) / (pd.passes - p);  // balanced widths
+    pd.shift[p] = shift;
+    pd.nbits[p] = std::max(1, nb);
+    shift += nb;
+  }
+  const int grid = pass_grid(max_chunks);
+  if (max_chunks > kLookbackMaxChunks) {
+    for (int p = 0; p < pd.passes; ++p) {
+      const uint32_t* kin = k[p & 1];
+      const uint32_t* vin = v[p & 1];
+      // the histogram kernel is light (28 registers, 1 KB): twice the blocks
+      launch_k(radix_hist_kernel, std::min(max_chunks, 2 * grid), kThreads, 0, stream, kin, cnt,
+               pd.shift[p], pd.nbits[p], L.hist, max_chunks);
+      launch_k(radix_scan_rows_kernel, 1 << pd.nbits[p], 1024, 0, stream, L.hist, max_chunks,
+               L.totals, cnt);
+      launch_k(radix_scatter_kernel<true>, grid, kThreads, 0, stream, kin, vin, k[(p + 1) & 1],
+               v[(p + 1) & 1], cnt, pd.shift[p], pd.nbits[p], (const uint32_t*)L.totals,
+               (const uint32_t*)L.hist, max_chunks, (unsigned long long*)nullptr,
+               (unsigned*)nullptr, L.hdr, spins, (unsigned long long*)nullptr);
+    }
+    count_launch(3 * pd.passes);
+    return pd.passes;
+  }
+  uint32_t* ghist = L.small + sort * kMaxPasses * 256;
+  unsigned* tickets = L.small + 2 * kMaxPasses * 256 + sort * kMaxPasses;
+  launch_k(radix_global_hist_kernel, grid, kThreads, 0, stream, (const uint32_t*)k[0], cnt, pd,
+           ghist, L.look[0]);
+  for (int p = 0; p < pd.passes; ++p)
+    launch_k(radix_scatter_kernel<false>, grid, kThreads, 0, stream, (const uint32_t*)k[p & 1],
+             (const uint32_t*)v[p & 1], k[(p + 1) & 1], v[(p + 1) & 1], cnt, pd.shift[p],
+             pd.nbits[p], (const uint32_t*)(ghist + p * 256), (const uint32_t*)nullptr, 0,
+             L.look[p & 1], tickets + p, L.hdr, spins,
+             p + 1 < pd.passes ? L.look[(p + 1) & 1] : (unsigned long long*)nullptr);
+  count_launch(1 + pd.passes);
+  return pd.passes;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -651,7 +844,8 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   const int64_t nranges = vm.tile_off[n_views];
   Layout L = carve(ws, nrec, capacity);
 
-  launch_k(zero_ranges_kernel, grid_for(nranges, 256), 256, 0, stream, ranges, nranges);
+  launch_k(zero_ranges_kernel, grid_for(nranges, 256), 256, 0, stream, ranges, nranges, L.small,
+           kSmallWords, L.hdr);
   count_launch();
   if (nrec == 0) {
     cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), stream);
@@ -672,10 +866,11 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
                                                               L.dv0);
     count_launch(3);
   }
-  radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 0, 8, L.nb_rec, L, stream);
-  radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 8, 8, L.nb_rec, L, stream);
-  radix_pass(L.dk0, L.dv0, L.dk1, L.dv1, cr, 16, 8, L.nb_rec, L, stream);
-  radix_pass(L.dk1, L.dv1, L.dk0, L.dv0, cr, 24, 8, L.nb_rec, L, stream);
+  {
+    uint32_t* const dk[2] = {L.dk0, L.dk1};
+    uint32_t* const dv[2] = {L.dv0, L.dv1};
+    radix_sort(dk, dv, cr, 32, L.nb_rec, L, 0, stream);  // 4 passes: the result in dk0, dv0
+  }
   const uint32_t* order = L.dv0;
   // 2. instance offsets in depth order, total into the header
   launch_k(count_reduce_kernel, L.nb_rec, kThreads, 0, stream, tiles, order, cr, L.bsum);
@@ -700,13 +895,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   count_launch();
   Count ci{0, &L.hdr->n_instances, capacity};
   const int nb_inst = (int)std::max<int64_t>(1, (capacity + kTileItems - 1) / kTileItems);
-  int shift = 0;
-  for (int p = 0; p < passes; ++p) {
-    int nb = (bits - shift + (passes - p) - 1) / (passes - p);  // balanced digit widths
-    radix_pass(kbuf[p & 1], vbuf[p & 1], kbuf[(p + 1) & 1], vbuf[(p + 1) & 1], ci, shift, nb,
-               nb_inst, L, stream);
-    shift += nb;
-  }
+  radix_sort(kbuf, vbuf, ci, bits, nb_inst, L, 1, stream);
   const uint32_t* fkeys = kbuf[passes & 1];
   // 4. per-tile ranges and optional 64-bit keys
   launch_k(ranges_kernel, grid_for(capacity, 1024), 256, 0, stream, fkeys, ci, ranges);
@@ -814,7 +1003,59 @@ extern "C" veg_status veg_sync_status(const void* workspace, cudaStream_t stream
     return VEG_ERR_CUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return VEG_ERR_CUDA;
   if (n_instances) *n_instances = (int64_t)h.n_instances;
+  if (h.flags & veg::FLAG_TIMEOUT) return VEG_ERR_TIMEOUT;
   return (h.flags & veg::FLAG_CAPACITY) ? VEG_ERR_CAPACITY : VEG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A check of the radix passes' bounded waits on the device.
+// ---------------------------------------------------------------------------
+
+namespace veg {
+namespace {
+
+// Seeded keys (a multiplicative hash of the index, with repeats) and their
+// indices; with `starve`, pass 0's first ticket is taken in advance so that
+// chunk 0 is never sorted and never published.
+__global__ void lookback_check_keys_kernel(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                           int64_t n, unsigned* __restrict__ ticket0, int starve) {
+  pdl_enter();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    keys[i] = ((uint32_t)i * 2654435761u) >> 4;
+    vals[i] = (uint32_t)i;
+  }
+  if (i == 0 && starve) *ticket0 = 1u;
+}
+
+}  // namespace
+}  // namespace veg
+
+extern "C" veg_status veg_radix_lookback_check(void* workspace, size_t workspace_bytes, int64_t n,
+                                               int32_t starve_first, int32_t spins,
+                                               uint32_t* keys_out, uint32_t* vals_out,
+                                               cudaStream_t stream) {
+  using namespace veg;
+  if (!workspace || n < 1 || n > (int64_t)kLookbackMaxChunks * kTileItems || spins < 1 ||
+      !keys_out || !vals_out || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return VEG_ERR_INVALID_ARGUMENT;
+  Layout L = carve(workspace, n, 0);
+  if (workspace_bytes < L.bytes) return VEG_ERR_INVALID_ARGUMENT;
+  if (cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), stream) != cudaSuccess ||
+      cudaMemsetAsync(L.small, 0, kSmallWords * sizeof(uint32_t), stream) != cudaSuccess)
+    return VEG_ERR_CUDA;
+  launch_k(lookback_check_keys_kernel, grid_for(n, 256), 256, 0, stream, L.dk0, L.dv0, n,
+           L.small + 2 * kMaxPasses * 256, (int)(starve_first != 0));
+  count_launch();
+  uint32_t* const dk[2] = {L.dk0, L.dk1};
+  uint32_t* const dv[2] = {L.dv0, L.dv1};
+  radix_sort(dk, dv, Count{n, nullptr, 0}, 32, L.nb_rec, L, 0, stream, spins);  // into dk0, dv0
+  if (cudaMemcpyAsync(keys_out, L.dk0, (size_t)n * 4, cudaMemcpyDeviceToDevice, stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(vals_out, L.dv0, (size_t)n * 4, cudaMemcpyDeviceToDevice, stream) !=
+          cudaSuccess)
+    return VEG_ERR_CUDA;
+  return launch_status();
 }
 
 // ---------------------------------------------------------------------------

@@ -7,7 +7,8 @@ namespace veg {
 
 veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
                               const int32_t* tiles, const float4* grad2d, float4* gm, float4* gl,
-                              float4* gq, cudaStream_t stream);
+                              float4* gq, cudaStream_t stream, int64_t first = 0,
+                              int64_t count = -1);
 
 veg_status composite_fwd_launch(const veg_camera* cams, int n_views, int64_t n,
                                 const float4* geo, const float4* aux, const uint32_t* vals,
@@ -186,15 +187,18 @@ extern "C" veg_status veg_composite_bwd(const veg_camera* cams, int32_t n_views,
                             reinterpret_cast<float4*>(grad_quat), stream);
 }
 
-extern "C" veg_status veg_project_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
-                                      const int32_t* tiles_touched, const float* grad2d,
-                                      float* grad_mean_v, float* grad_logscale_w,
-                                      float* grad_quat, cudaStream_t stream) {
+namespace {
+veg_status project_bwd_checked(const veg_camera* cams, int32_t n_views, veg_gaussians g,
+                               const int32_t* tiles_touched, const float* grad2d, int64_t first,
+                               int64_t count, float* grad_mean_v, float* grad_logscale_w,
+                               float* grad_quat, cudaStream_t stream) {
   veg_status st = check_cameras(cams, n_views);
   if (st != VEG_OK) return st;
   if (g.n < 0 || g.n * n_views >= ((int64_t)1 << 31)) return VEG_ERR_INVALID_ARGUMENT;
-  if (g.n > 0 && (!g.mean_v || !g.logscale_w || !g.quat || !tiles_touched || !grad2d ||
-                  !grad_mean_v || !grad_logscale_w || !grad_quat))
+  if (first < 0 || count < 0 || first > g.n || count > g.n - first)
+    return VEG_ERR_INVALID_ARGUMENT;
+  if (count > 0 && (!g.mean_v || !g.logscale_w || !g.quat || !tiles_touched || !grad2d ||
+                    !grad_mean_v || !grad_logscale_w || !grad_quat))
     return VEG_ERR_INVALID_ARGUMENT;
   if (!aligned16(grad2d) || !aligned16(grad_mean_v) || !aligned16(grad_logscale_w) ||
       !aligned16(grad_quat) || !aligned16(g.mean_v) || !aligned16(g.logscale_w) ||
@@ -206,5 +210,23 @@ extern "C" veg_status veg_project_bwd(const veg_camera* cams, int32_t n_views, v
                             reinterpret_cast<const float4*>(grad2d),
                             reinterpret_cast<float4*>(grad_mean_v),
                             reinterpret_cast<float4*>(grad_logscale_w),
-                            reinterpret_cast<float4*>(grad_quat), stream);
+                            reinterpret_cast<float4*>(grad_quat), stream, first, count);
+}
+}  // namespace
+
+extern "C" veg_status veg_project_bwd(const veg_camera* cams, int32_t n_views, veg_gaussians g,
+                                      const int32_t* tiles_touched, const float* grad2d,
+                                      float* grad_mean_v, float* grad_logscale_w,
+                                      float* grad_quat, cudaStream_t stream) {
+  return project_bwd_checked(cams, n_views, g, tiles_touched, grad2d, 0, g.n < 0 ? 0 : g.n,
+                             grad_mean_v, grad_logscale_w, grad_quat, stream);
+}
+
+extern "C" veg_status veg_project_bwd_range(const veg_camera* cams, int32_t n_views,
+                                            veg_gaussians g, const int32_t* tiles_touched,
+                                            const float* grad2d, int64_t first, int64_t count,
+                                            float* grad_mean_v, float* grad_logscale_w,
+                                            float* grad_quat, cudaStream_t stream) {
+  return project_bwd_checked(cams, n_views, g, tiles_touched, grad2d, first, count, grad_mean_v,
+                             grad_logscale_w, grad_quat, stream);
 }

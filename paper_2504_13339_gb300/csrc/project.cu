@@ -266,12 +266,12 @@ __device__ __forceinline__ void project_bwd_one(const CamParam& cp, const Proj& 
 __global__ void __launch_bounds__(128, 6)
     project_bwd_kernel(CamSet cams, int n_views, const float4* __restrict__ mean_v,
                        const float4* __restrict__ logscale_w, const float4* __restrict__ quat,
-                       int64_t n, const int32_t* __restrict__ tiles,
+                       int64_t n, int64_t first, int64_t end, const int32_t* __restrict__ tiles,
                        const float4* __restrict__ grad2d, float4* __restrict__ grad_mean_v,
                        float4* __restrict__ grad_logscale_w, float4* __restrict__ grad_quat) {
   pdl_enter();
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= end) return;
   float4 mv = mean_v[i], lw = logscale_w[i], q = quat[i];
   float dm[3] = {0.f, 0.f, 0.f}, dl[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
   float dvv = 0.f, dww = 0.f;
@@ -319,13 +319,14 @@ veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const 
 
 veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
                               const int32_t* tiles, const float4* grad2d, float4* gm, float4* gl,
-                              float4* gq, cudaStream_t stream) {
-  if (g.n == 0) return VEG_OK;
-  dim3 grid((unsigned)((g.n + 127) / 128));
+                              float4* gq, cudaStream_t stream, int64_t first, int64_t count) {
+  if (count < 0) count = g.n - first;
+  if (count == 0) return VEG_OK;
+  dim3 grid((unsigned)((count + 127) / 128));
   launch_k(project_bwd_kernel, grid, 128, 0, stream, 
       cs, n_views, reinterpret_cast<const float4*>(g.mean_v),
       reinterpret_cast<const float4*>(g.logscale_w), reinterpret_cast<const float4*>(g.quat), g.n,
-      tiles, grad2d, gm, gl, gq);
+      first, first + count, tiles, grad2d, gm, gl, gq);
   count_launch();
   return launch_status();
 }

@@ -112,6 +112,7 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
 constexpr unsigned int FLAG_CAPACITY = 1u;
+constexpr unsigned int FLAG_TIMEOUT = 2u;  // a bounded device-side wait gave up
 
 struct CamParam {
   float r[9];

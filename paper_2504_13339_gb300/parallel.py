@@ -16,6 +16,15 @@ The collective is torch.distributed's all_reduce on one flat buffer (NCCL
 between GPUs, gloo on the CPU); the gradient arrays of `TrainParams` are
 views into that buffer (`TrainParams.use_flat_gradients`), so a step needs
 one collective and no packing.
+
+`backward_allreduce` overlaps that exchange with the last stage of the
+backward instead: the projection backward (one thread per Gaussian, summing
+its views) runs over contiguous ranges of Gaussians ("buckets"), and as soon
+as a bucket's rows are final their all-reduce starts asynchronously (on
+NCCL's stream, ordered after the work queued so far), while the next
+bucket's projection backward runs.  The gradients are the same as with one
+collective after the whole backward: each row is summed over the ranks once,
+after every contribution to it.
 """
 from __future__ import annotations
 
@@ -74,3 +83,49 @@ def sync_step(params, group=None) -> None:
     dist.all_reduce(hi, op=dist.ReduceOp.MAX, group=group)
     if int(lo) != int(hi):
         raise RuntimeError(f"ranks are at different steps ({int(lo)} .. {int(hi)})")
+
+
+def buckets(n: int, n_buckets: int) -> list:
+    """Contiguous ranges of rows splitting [0, n) into at most n_buckets
+    non-empty parts whose sizes differ by at most one, in order."""
+    if n < 0 or n_buckets < 1:
+        raise ValueError("buckets: need n >= 0 and n_buckets >= 1")
+    k = min(n_buckets, n)
+    return [range(b * n // k, (b + 1) * n // k) for b in range(k)]
+
+
+def backward_allreduce(produce, grads, n: int, n_buckets: int = 4, group=None) -> None:
+    """For each bucket of the rows [0, n) in order: `produce(first, count)`
+    completes the gradient rows [first, first + count) of every array in
+    `grads` (on the current stream), then the sum over the ranks of those
+    rows starts asynchronously, one collective per array, overlapping the
+    next bucket's `produce`.  Returns once every collective has been waited
+    for (for NCCL: the current stream waits for them; on the CPU the call
+    blocks).  With one rank only `produce` runs."""
+    live = [g for g in grads if g is not None]
+    multi = dist.is_initialized() and dist.get_world_size(group) > 1
+    pending = []
+    for b in buckets(n, n_buckets):
+        produce(b.start, len(b))
+        if multi:
+            for g in live:
+                pending.append(dist.all_reduce(g[b.start:b.stop], op=dist.ReduceOp.SUM,
+                                               group=group, async_op=True))
+    for w in pending:
+        w.wait()
+
+
+def project_allreduce(pipe, grads, n_buckets: int = 4, group=None, stream=None) -> None:
+    """The bucketed projection backward of a SplatPipeline whose screen-space
+    gradients are current (`pipe.backward_2d`, and the shading backward when
+    shaded), with the all-reduce of each bucket's rows of `grads` = (mean_v,
+    logscale_w, quat[, normal_beta, k_ads]) overlapping the next bucket."""
+    import torch
+
+    def produce(first, count):
+        pipe.project_backward(grads[0], grads[1], grads[2], stream, first=first, count=count)
+    if stream is None:
+        backward_allreduce(produce, grads, pipe.n, n_buckets, group)
+        return
+    with torch.cuda.stream(stream):
+        backward_allreduce(produce, grads, pipe.n, n_buckets, group)

@@ -169,8 +169,12 @@ class SplatPipeline:
         _lib.veg_tile_order(self.ranges, self.order, stream)
 
     def status(self, stream=None):
-        """(status, instance count) after waiting for the stream."""
-        return _lib.veg_sync_status(self.ws, stream)
+        """(status, instance count) after waiting for the stream; raises if a
+        bounded device-side wait of the binning gave up (its lists are void)."""
+        st, m = _lib.veg_sync_status(self.ws, stream)
+        if st == _lib.VEG_ERR_TIMEOUT:
+            raise _lib.VegError("veg_bin_sort", st)
+        return st, m
 
     def composite(self, luts, bg=(0.0, 0.0, 0.0), stats=None, stream=None):
         self.generation += 1
@@ -218,9 +222,17 @@ class SplatPipeline:
                                splat_shade=self._shade_buf(), grad_shade=self._grad_shade_buf(),
                                tile_batch=self.tile_batch_bwd)
 
-    def project_backward(self, grad_mean_v, grad_logscale_w, grad_quat, stream=None):
-        _lib.veg_project_bwd(self.c_cams, self._g, self.tiles, self.grad2d, grad_mean_v,
-                             grad_logscale_w, grad_quat, stream)
+    def project_backward(self, grad_mean_v, grad_logscale_w, grad_quat, stream=None,
+                         first=0, count=None):
+        """Accumulates the projection backward of Gaussians [first, first +
+        count) (all by default) from self.grad2d into the gradients."""
+        if first == 0 and count is None:
+            _lib.veg_project_bwd(self.c_cams, self._g, self.tiles, self.grad2d, grad_mean_v,
+                                 grad_logscale_w, grad_quat, stream)
+            return
+        count = self.n - first if count is None else count
+        _lib.veg_project_bwd_range(self.c_cams, self._g, self.tiles, self.grad2d, first, count,
+                                   grad_mean_v, grad_logscale_w, grad_quat, stream)
 
     def shade_backward(self, grad_mean_v, grad_normal_beta, grad_k_ads, stream=None):
         if grad_normal_beta is None or grad_k_ads is None:
@@ -243,11 +255,13 @@ class SplatPipeline:
         return self.composite(luts, bg, stream=stream)
 
     def train_step(self, mean_v, logscale_w, quat, luts, target, grads, bg=(0.0, 0.0, 0.0),
-                   lighting=None, stream=None):
+                   lighting=None, stream=None, project_grads=True):
         """One pass of the hot path: project, bin, sort, (shade,) composite,
         L1 loss, composite backward, projection (and shading) backward.
         grads = (mean_v, logscale_w, quat[, normal_beta, k_ads]) gradient
-        buffers, zeroed first; lighting = (normal_beta, k_ads, light_dirs)."""
+        buffers, zeroed first; lighting = (normal_beta, k_ads, light_dirs).
+        With project_grads=False the projection backward is left to the
+        caller (e.g. a bucketed one overlapping the gradient all-reduce)."""
         for gbuf in grads:
             gbuf.zero_()
         self.project(mean_v, logscale_w, quat, luts, stream)
@@ -258,7 +272,12 @@ class SplatPipeline:
         self.bin_sort(stream=stream)
         self.composite(luts, bg, stream=stream)
         self.l1(target, stream)
-        self.backward(self.loss_grad, *grads, stream=stream)
+        if project_grads:
+            self.backward(self.loss_grad, *grads, stream=stream)
+        else:
+            self.backward_2d(self.loss_grad, stream=stream)
+            if self._lit is not None:
+                self.shade_backward(grads[0], grads[3], grads[4], stream)
         return self.loss
 
 

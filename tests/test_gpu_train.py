@@ -342,3 +342,42 @@ def test_graph_replayed_training_step_matches_eager():
     assert np.allclose(la, lb, rtol=1e-5)
     for a, (x, y) in enumerate(zip(pa, pb)):
         assert np.all(np.abs(x - y) <= 2 * 3 * lr[a][None, :] + 1e-6), a
+
+
+def test_bucketed_projection_backward_is_bit_identical():
+    """The projection backward split into Gaussian ranges (as the
+    data-parallel step runs it, each range's all-reduce overlapping the
+    next range) gives the same bits as one call, for several bucket counts,
+    including one range per Gaussian at the tail; rows outside a range are
+    left untouched; an out-of-range request is refused."""
+    from paper_2504_13339_gb300 import parallel
+    from paper_2504_13339_gb300.render import SplatPipeline
+    g, lt, cams, luts, tg = small_training_set(seed=99)
+    lut = lut_tensor(luts[:2])
+    P = TrainParams(g)
+    p = SplatPipeline(P.n, cams[:2], n_tf=2)
+    p.project(P.mean_v, P.logscale_w, P.raw[2], lut)
+    p.bin_sort()
+    p.composite(lut)
+    p.l1(dev(tg[:2, :2]))
+    p.backward_2d(p.loss_grad)
+    whole = [torch.zeros_like(t) for t in P.raw[:3]]
+    p.project_backward(*whole)
+    for nb in (1, 3, 7, P.n):
+        parts = [torch.zeros_like(t) for t in P.raw[:3]]
+        parallel.project_allreduce(p, parts, n_buckets=nb)
+        for a, b in zip(whole, parts):
+            assert torch.equal(a, b), nb
+    # one range only: rows outside it stay as they were
+    first, count = P.n // 3, P.n // 4
+    sentinel = [torch.full_like(t, 7.0) for t in P.raw[:3]]
+    for t in sentinel:
+        t[first:first + count] = 0.0
+    p.project_backward(*sentinel, first=first, count=count)
+    for s, w in zip(sentinel, whole):
+        assert bool((s[:first] == 7.0).all()) and bool((s[first + count:] == 7.0).all())
+        assert torch.equal(s[first:first + count], w[first:first + count])
+    with pytest.raises(_lib.VegError):
+        p.project_backward(*sentinel, first=P.n - 2, count=3)
+    with pytest.raises(_lib.VegError):
+        p.project_backward(*sentinel, first=-1, count=2)

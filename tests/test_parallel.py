@@ -1,7 +1,9 @@
 """Data-parallel training host logic on CPU (two gloo ranks): view shards,
 the one all-reduce of the flat gradient buffer against the oracle's
-gradient summed over all views, the densification statistic, and the
-parameter broadcast."""
+gradient summed over all views, the bucketed all-reduce overlapping the
+projection backward (its order and its sums), the densification statistic,
+and the parameter broadcast.  The library's own gradient kernels need a GPU:
+here the oracle's per-shard gradients stand in for them."""
 import os
 import socket
 
@@ -170,3 +172,88 @@ def test_ranks_at_different_steps_are_reported_on_every_rank():
         assert p.exitcode == 0
     for r in range(world):
         assert "different steps (5 .. 6)" in out[r]
+
+
+def test_buckets_partition_the_rows():
+    from paper_2504_13339_gb300.parallel import buckets
+    for n in range(0, 40):
+        for k in range(1, 9):
+            bs = buckets(n, k)
+            assert [i for b in bs for i in b] == list(range(n))
+            assert all(len(b) > 0 for b in bs) and len(bs) == min(n, k)
+            if bs:
+                assert max(map(len, bs)) - min(map(len, bs)) <= 1
+    with pytest.raises(ValueError):
+        buckets(5, 0)
+
+
+def _rank_buckets(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2504_13339_gb300 import parallel
+        from paper_2504_13339_gb300.train import TrainParams
+        g, cams, tfs = _scene()
+        P = TrainParams(g, device="cpu")
+        P.use_flat_gradients()
+        grads = P.grads[:3]
+        mine = [torch.as_tensor(a, dtype=torch.float32)
+                for a in _view_grads(g, cams, tfs, view_shard(len(cams), rank, world))]
+        log, produced = [], set()
+        bases = [(gr.data_ptr(), gr.data_ptr() + gr.numel() * 4) for gr in grads]
+
+        def produce(first, count):
+            log.append(("p", first, count))
+            for gr, part in zip(grads, mine):
+                gr[first:first + count] = part[first:first + count]
+            produced.update(range(first, first + count))
+
+        real = dist.all_reduce
+
+        def logged(t, *a, **kw):
+            arr = next(i for i, (lo, hi) in enumerate(bases) if lo <= t.data_ptr() < hi)
+            row = (t.data_ptr() - bases[arr][0]) // 16
+            rows = range(row, row + t.shape[0])
+            log.append(("r", arr, row, t.shape[0], set(rows) <= produced, kw.get("async_op")))
+            return real(t, *a, **kw)
+        dist.all_reduce = logged
+        try:
+            parallel.backward_allreduce(produce, grads, g.n, n_buckets=4)
+        finally:
+            dist.all_reduce = real
+        full = _view_grads(g, cams, tfs, range(len(cams)))
+        errs = [float(np.abs(gr.numpy() - f).max() / max(np.abs(f).max(), 1e-30))
+                for gr, f in zip(grads, full)]
+        out[rank] = (log, errs)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(300)
+def test_bucketed_allreduce_follows_each_bucket_and_sums_the_views():
+    """Each bucket's rows are all-reduced (asynchronously, one collective per
+    gradient array) right after that bucket is produced and before the next
+    bucket is, never before its rows are final; the summed gradients equal
+    the oracle's gradient over all views."""
+    from paper_2504_13339_gb300 import build
+    build.build()
+    world = 2
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_buckets, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(280)
+        assert p.exitcode == 0
+    n = _scene()[0].n
+    from paper_2504_13339_gb300.parallel import buckets
+    want = []
+    for b in buckets(n, 4):
+        want.append(("p", b.start, len(b)))
+        want += [("r", a, b.start, len(b), True, True) for a in range(3)]
+    for r in range(world):
+        log, errs = out[r]
+        assert log == want
+        assert max(errs) <= 1e-5, errs
