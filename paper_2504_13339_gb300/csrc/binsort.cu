@@ -110,6 +110,47 @@ struct PassDigits {
   int nbits[kMaxPasses];
 };
 
+// Key range of a sort (the depth sort: the range of its keys, folded into
+// the header by the kernels that write them).  Digits are taken of
+// key - key_min, and a pass whose digits are then all zero (its shift at or
+// beyond the bit length of key_max - key_min) is an identity and does no
+// work.  Such passes form a suffix of the passes.  Null: plain keys, no
+// pass skipped.
+__device__ __forceinline__ uint32_t range_base(const WsHeader* h) {
+  return h ? h->key_min : 0u;
+}
+__device__ __forceinline__ bool pass_skipped(const WsHeader* h, int shift) {
+  if (!h) return false;
+  const uint32_t lo = h->key_min, hi = h->key_max;
+  return hi <= lo || ((hi - lo) >> shift) == 0u;
+}
+
+// The values of a sort whose trailing passes may have been skipped: buffer
+// v[q % 2], q = the passes that ran.
+struct SortedVals {
+  const uint32_t* v[2];
+  const WsHeader* krange;
+  PassDigits pd;
+  __device__ __forceinline__ const uint32_t* get() const {
+    int q = 0;
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+      if (p < pd.passes && !pass_skipped(krange, pd.shift[p])) ++q;
+    return (q & 1) ? v[1] : v[0];
+  }
+};
+
+// Folds each lane's key range [kmin, kmax] (empty when kmin > kmax) into the
+// header: one atomic pair per warp.  Every lane of the warp must call.
+__device__ __forceinline__ void fold_key_range(uint32_t kmin, uint32_t kmax, WsHeader* hdr) {
+  kmin = __reduce_min_sync(0xffffffffu, kmin);
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
+  if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
+    atomicMin(&hdr->key_min, kmin);
+    atomicMax(&hdr->key_max, kmax);
+  }
+}
+
 // Look-back word: state in the top two bits (0 not yet published, 1 the
 // chunk's own count, 2 the inclusive prefix of chunks 0..c), value below.
 constexpr unsigned long long kLbAgg = 1ull << 62;
@@ -124,9 +165,11 @@ constexpr int kLookbackMaxChunks = 64;
 // chunk capacity), blocks stride over the chunks that hold items.
 __global__ void __launch_bounds__(kThreads)
     radix_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, int shift, int nbits,
-                      uint32_t* __restrict__ hist, int nblocks) {
+                      uint32_t* __restrict__ hist, int nblocks, const WsHeader* krange) {
   pdl_enter();
   __shared__ uint32_t s_hist[256];
+  if (pass_skipped(krange, shift)) return;
+  const uint32_t kb = range_base(krange);
   const int64_t n = cnt.get();
   const int nch = chunks_of(n);
   const uint32_t mask = (1u << nbits) - 1u;
@@ -142,10 +185,10 @@ __global__ void __launch_bounds__(kThreads)
       const uint4 a = __ldg(src), c = __ldg(src + 1);
       const uint32_t k[kItems] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-      for (int j = 0; j < kItems; ++j) atomicAdd(&s_hist[(k[j] >> shift) & mask], 1u);
+      for (int j = 0; j < kItems; ++j) atomicAdd(&s_hist[((k[j] - kb) >> shift) & mask], 1u);
     } else {
       for (int j = 0; j < kItems; ++j)
-        if (i0 + j < n) atomicAdd(&s_hist[(__ldg(&keys[i0 + j]) >> shift) & mask], 1u);
+        if (i0 + j < n) atomicAdd(&s_hist[((__ldg(&keys[i0 + j]) - kb) >> shift) & mask], 1u);
     }
     __syncthreads();
     if (digit) hist[(int64_t)threadIdx.x * nblocks + b] = s_hist[threadIdx.x];
@@ -156,10 +199,11 @@ __global__ void __launch_bounds__(kThreads)
 // counts (the chunks that hold items), and the digit total.
 __global__ void __launch_bounds__(1024)
     radix_scan_rows_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ totals,
-                           Count cnt) {
+                           Count cnt, int shift, const WsHeader* krange) {
   pdl_enter();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_total;
+  if (pass_skipped(krange, shift)) return;
   uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
   nblocks = chunks_of(cnt.get());
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -211,9 +255,11 @@ __global__ void __launch_bounds__(1024)
 // words [chunks][256] (each pass zeroes the next one's).
 __global__ void __launch_bounds__(kThreads)
     radix_global_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, PassDigits pd,
-                             uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look) {
+                             uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look,
+                             const WsHeader* krange) {
   pdl_enter();
   __shared__ uint32_t s_hist[kMaxPasses][256];
+  const uint32_t kb = range_base(krange);
   const int64_t n = cnt.get();
   const int nch = chunks_of(n);
   for (int p = 0; p < kMaxPasses; ++p) s_hist[p][threadIdx.x] = 0u;
@@ -224,7 +270,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
-    const uint32_t k = __ldg(&keys[i]);
+    const uint32_t k = __ldg(&keys[i]) - kb;
 #pragma unroll
     for (int p = 0; p < kMaxPasses; ++p)
       if (p < pd.passes) atomicAdd(&s_hist[p][(k >> pd.shift[p]) & ((1u << pd.nbits[p]) - 1u)], 1u);
@@ -262,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 4)
                          const uint32_t* __restrict__ hist, int nblocks,
                          unsigned long long* __restrict__ look, unsigned* __restrict__ ticket,
                          WsHeader* __restrict__ hdr, int spins,
-                         unsigned long long* __restrict__ look_next) {
+                         unsigned long long* __restrict__ look_next, const WsHeader* krange) {
   pdl_enter();
   __shared__ uint32_t s_whist[8][256];
   __shared__ uint32_t s_dbase[256];
@@ -271,6 +317,8 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ uint32_t s_keys[kTileItems];
   __shared__ uint32_t s_vals[kTileItems];
   __shared__ int s_chunk;
+  if (pass_skipped(krange, shift)) return;  // then so is every later pass
+  const uint32_t kb = range_base(krange);
   const int64_t n = cnt.get();
   const int nch = chunks_of(n);
   if (TABLE && (int)blockIdx.x >= nch) return;
@@ -310,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       bool valid = i < n;
       k[j] = valid ? kin[i] : 0u;
       v[j] = valid ? vin[i] : 0u;
-      uint32_t d = valid ? ((k[j] >> shift) & mask) : 256u;
+      uint32_t d = valid ? (((k[j] - kb) >> shift) & mask) : 256u;
       unsigned peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
       r[j] = before + __popc(peers & lt);
@@ -335,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     for (int j = 0; j < kItems; ++j) {
       int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
       if (i < n) {
-        uint32_t d = (k[j] >> shift) & mask;
+        uint32_t d = ((k[j] - kb) >> shift) & mask;
         uint32_t pos = s_bstart[d] + s_whist[warp][d] + r[j];
         if (pos < (uint32_t)kTileItems) {  // always, when the counts agree
           s_keys[pos] = k[j];
@@ -385,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int cnt_valid = (int)min((int64_t)kTileItems, n - base);
     for (int p = tid; p < cnt_valid; p += kThreads) {
       uint32_t key = s_keys[p];
-      uint32_t d = (key >> shift) & mask;
+      uint32_t d = ((key - kb) >> shift) & mask;
       uint32_t g = s_dbase[d] + (uint32_t)p - s_bstart[d];
       kout[g] = key;
       vout[g] = s_vals[p];
@@ -403,12 +451,17 @@ __global__ void __launch_bounds__(kThreads, 4)
 // launch costs more than sorting the culled records.
 __global__ void depth_keys_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
                                   int64_t nrec, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ vals) {
+                                  uint32_t* __restrict__ vals, WsHeader* __restrict__ hdr) {
   pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrec) return;
-  keys[i] = tiles[i] > 0 ? __float_as_uint(geo[i].z) : 0xffffffffu;
-  vals[i] = (uint32_t)i;
+  uint32_t key = 0xffffffffu, kmax = 0u;
+  if (i < nrec) {
+    key = tiles[i] > 0 ? __float_as_uint(geo[i].z) : 0xffffffffu;
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+    kmax = key;
+  }
+  fold_key_range(key, kmax, hdr);
 }
 
 // Per-chunk counts of the records that touch a tile (index order).
@@ -437,7 +490,8 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     visible_scatter_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
                            int64_t nrec, const unsigned long long* __restrict__ bsum,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           WsHeader* __restrict__ hdr) {
   pdl_enter();
   __shared__ unsigned long long s_warp[8];
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
@@ -449,13 +503,18 @@ __global__ void __launch_bounds__(kThreads)
     c += vis[k] ? 1ull : 0ull;
   }
   unsigned long long run = bsum[blockIdx.x] + block_exclusive_scan256<unsigned long long>(c, s_warp);
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     if (!vis[k]) continue;
-    keys[run] = __float_as_uint(geo[base + k].z);
+    const uint32_t key = __float_as_uint(geo[base + k].z);
+    keys[run] = key;
     vals[run] = (uint32_t)(base + k);
+    kmin = min(kmin, key);
+    kmax = max(kmax, key);
     ++run;
   }
+  fold_key_range(kmin, kmax, hdr);
 }
 
 // Exclusive scan of per-chunk counts in one block; the total to *total.
@@ -499,9 +558,10 @@ __global__ void __launch_bounds__(1024)
 
 // Per-block sums of tiles_touched taken in depth order.
 __global__ void __launch_bounds__(kThreads)
-    count_reduce_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
-                        Count cnt, unsigned long long* __restrict__ bsum) {
+    count_reduce_kernel(const int32_t* __restrict__ tiles, SortedVals sorted, Count cnt,
+                        unsigned long long* __restrict__ bsum) {
   pdl_enter();
+  const uint32_t* __restrict__ order = sorted.get();
   __shared__ unsigned long long s[kThreads];
   const int64_t nrec = cnt.get();
   const int64_t base = (int64_t)blockIdx.x * kTileItems;
@@ -565,10 +625,10 @@ __global__ void __launch_bounds__(1024)
 // Instance offsets (exclusive prefix of tiles_touched in depth order),
 // saturated to 0xffffffff (any value >= capacity is never emitted).
 __global__ void __launch_bounds__(kThreads)
-    count_down_kernel(const int32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
-                      Count cnt, const unsigned long long* __restrict__ bsum,
-                      uint32_t* __restrict__ offsets) {
+    count_down_kernel(const int32_t* __restrict__ tiles, SortedVals sorted, Count cnt,
+                      const unsigned long long* __restrict__ bsum, uint32_t* __restrict__ offsets) {
   pdl_enter();
+  const uint32_t* __restrict__ order = sorted.get();
   __shared__ unsigned long long s_warp[8];
   const int64_t nrec = cnt.get();
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
@@ -598,10 +658,11 @@ __global__ void __launch_bounds__(kThreads)
 // binary search over the lanes' offsets (offsets increase with the lane).
 __global__ void __launch_bounds__(256)
     emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
-                const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                Count visible, int64_t n_per_view, ViewMap vm, int64_t capacity,
-                uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
+                SortedVals sorted, const uint32_t* __restrict__ offsets, Count visible,
+                int64_t n_per_view, ViewMap vm, int64_t capacity, uint32_t* __restrict__ ikeys,
+                uint32_t* __restrict__ ivals) {
   pdl_enter();
+  const uint32_t* __restrict__ order = sorted.get();
   const int lane = threadIdx.x & 31;
   const int64_t nrec = visible.get();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -668,7 +729,11 @@ __global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count,
   if (i < count) ranges[i] = make_int2(0, 0);
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < nsmall; k += blockDim.x) small[k] = 0u;
-    if (threadIdx.x == 0) hdr->flags = 0u;
+    if (threadIdx.x == 0) {
+      hdr->flags = 0u;
+      hdr->key_min = 0xffffffffu;  // empty range, widened by the depth keys' writers
+      hdr->key_max = 0u;
+    }
   }
 }
 
@@ -778,13 +843,17 @@ int pass_grid(int nblocks) {
 
 // Stable LSD sort of (key, value) pairs by the key bits [0, bits), in
 // passes of balanced digit widths (at most 8 bits).  Buffers ping-pong
-// k[p % 2] -> k[(p + 1) % 2], the result in k[passes % 2], v[passes % 2].
-// Up to kLookbackMaxChunks chunks (max_chunks, known on the host: the item
-// count itself lives on the device) the passes are look-back kernels after
-// one histogram of all passes (`sort`, 0 or 1, picks their digit totals and
-// tickets); above, three table kernels per pass.
-int radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int bits, int max_chunks,
-               const Layout& L, int sort, cudaStream_t stream, int spins = kLookbackSpins) {
+// k[p % 2] -> k[(p + 1) % 2]; with `krange` (the depth sort) trailing passes
+// over constant digits are skipped on the device, so the result's buffer is
+// known there only: the returned SortedVals names it (without `krange`,
+// v[passes % 2]).  Up to kLookbackMaxChunks chunks (max_chunks, known on the
+// host: the item count itself lives on the device) the passes are
+// look-back kernels after one histogram of all passes (`sort`, 0 or 1,
+// picks their digit totals and tickets); above, three table kernels per
+// pass.
+SortedVals radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int bits,
+                      int max_chunks, const Layout& L, int sort, const WsHeader* krange,
+                      cudaStream_t stream, int spins = kLookbackSpins) {
   PassDigits pd;
   pd.passes = std::max(1, (bits + 7) / 8);
   int shift = 0;
@@ -794,6 +863,7 @@ int radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int bits, 
     pd.nbits[p] = std::max(1, nb);
     shift += nb;
   }
+  SortedVals out{{v[0], v[1]}, krange, pd};
   const int grid = pass_grid(max_chunks);
   if (max_chunks > kLookbackMaxChunks) {
     for (int p = 0; p < pd.passes; ++p) {
@@ -801,29 +871,29 @@ int radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int bits, 
       const uint32_t* vin = v[p & 1];
       // the histogram kernel is light (28 registers, 1 KB): twice the blocks
       launch_k(radix_hist_kernel, std::min(max_chunks, 2 * grid), kThreads, 0, stream, kin, cnt,
-               pd.shift[p], pd.nbits[p], L.hist, max_chunks);
+               pd.shift[p], pd.nbits[p], L.hist, max_chunks, krange);
       launch_k(radix_scan_rows_kernel, 1 << pd.nbits[p], 1024, 0, stream, L.hist, max_chunks,
-               L.totals, cnt);
+               L.totals, cnt, pd.shift[p], krange);
       launch_k(radix_scatter_kernel<true>, grid, kThreads, 0, stream, kin, vin, k[(p + 1) & 1],
                v[(p + 1) & 1], cnt, pd.shift[p], pd.nbits[p], (const uint32_t*)L.totals,
                (const uint32_t*)L.hist, max_chunks, (unsigned long long*)nullptr,
-               (unsigned*)nullptr, L.hdr, spins, (unsigned long long*)nullptr);
+               (unsigned*)nullptr, L.hdr, spins, (unsigned long long*)nullptr, krange);
     }
     count_launch(3 * pd.passes);
-    return pd.passes;
+    return out;
   }
   uint32_t* ghist = L.small + sort * kMaxPasses * 256;
   unsigned* tickets = L.small + 2 * kMaxPasses * 256 + sort * kMaxPasses;
   launch_k(radix_global_hist_kernel, grid, kThreads, 0, stream, (const uint32_t*)k[0], cnt, pd,
-           ghist, L.look[0]);
+           ghist, L.look[0], krange);
   for (int p = 0; p < pd.passes; ++p)
     launch_k(radix_scatter_kernel<false>, grid, kThreads, 0, stream, (const uint32_t*)k[p & 1],
              (const uint32_t*)v[p & 1], k[(p + 1) & 1], v[(p + 1) & 1], cnt, pd.shift[p],
              pd.nbits[p], (const uint32_t*)(ghist + p * 256), (const uint32_t*)nullptr, 0,
              L.look[p & 1], tickets + p, L.hdr, spins,
-             p + 1 < pd.passes ? L.look[(p + 1) & 1] : (unsigned long long*)nullptr);
+             p + 1 < pd.passes ? L.look[(p + 1) & 1] : (unsigned long long*)nullptr, krange);
   count_launch(1 + pd.passes);
-  return pd.passes;
+  return out;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -856,22 +926,21 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   //    (same order, fewer launches)
   Count cr{0, &L.hdr->n_visible, nrec};
   if (nrec <= kSmallRecords) {
-    launch_k(depth_keys_kernel, grid_for(nrec, 256), 256, 0, stream, geo, tiles, nrec, L.dk0, L.dv0);
+    launch_k(depth_keys_kernel, grid_for(nrec, 256), 256, 0, stream, geo, tiles, nrec, L.dk0, L.dv0,
+             L.hdr);
     count_launch();
     cr = Count{nrec, nullptr, 0};
   } else {
     launch_k(visible_count_kernel, L.nb_rec, kThreads, 0, stream, tiles, nrec, L.bsum);
     launch_k(chunk_scan_kernel, 1, 1024, 0, stream, L.bsum, L.nb_rec, &L.hdr->n_visible);
     launch_k(visible_scatter_kernel, L.nb_rec, kThreads, 0, stream, geo, tiles, nrec, L.bsum, L.dk0,
-                                                              L.dv0);
+             L.dv0, L.hdr);
     count_launch(3);
   }
-  {
-    uint32_t* const dk[2] = {L.dk0, L.dk1};
-    uint32_t* const dv[2] = {L.dv0, L.dv1};
-    radix_sort(dk, dv, cr, 32, L.nb_rec, L, 0, stream);  // 4 passes: the result in dk0, dv0
-  }
-  const uint32_t* order = L.dv0;
+  // (the passes above the depth keys' span are skipped on the device)
+  uint32_t* const dk[2] = {L.dk0, L.dk1};
+  uint32_t* const dv[2] = {L.dv0, L.dv1};
+  const SortedVals order = radix_sort(dk, dv, cr, 32, L.nb_rec, L, 0, L.hdr, stream);
   // 2. instance offsets in depth order, total into the header
   launch_k(count_reduce_kernel, L.nb_rec, kThreads, 0, stream, tiles, order, cr, L.bsum);
   launch_k(count_top_kernel, 1, 1024, 0, stream, L.bsum, L.nb_rec, L.hdr, capacity);
@@ -895,7 +964,7 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   count_launch();
   Count ci{0, &L.hdr->n_instances, capacity};
   const int nb_inst = (int)std::max<int64_t>(1, (capacity + kTileItems - 1) / kTileItems);
-  radix_sort(kbuf, vbuf, ci, bits, nb_inst, L, 1, stream);
+  radix_sort(kbuf, vbuf, ci, bits, nb_inst, L, 1, nullptr, stream);
   const uint32_t* fkeys = kbuf[passes & 1];
   // 4. per-tile ranges and optional 64-bit keys
   launch_k(ranges_kernel, grid_for(capacity, 1024), 256, 0, stream, fkeys, ci, ranges);
@@ -1049,7 +1118,8 @@ extern "C" veg_status veg_radix_lookback_check(void* workspace, size_t workspace
   count_launch();
   uint32_t* const dk[2] = {L.dk0, L.dk1};
   uint32_t* const dv[2] = {L.dv0, L.dv1};
-  radix_sort(dk, dv, Count{n, nullptr, 0}, 32, L.nb_rec, L, 0, stream, spins);  // into dk0, dv0
+  radix_sort(dk, dv, Count{n, nullptr, 0}, 32, L.nb_rec, L, 0, nullptr, stream,
+             spins);  // 4 passes: into dk0, dv0
   if (cudaMemcpyAsync(keys_out, L.dk0, (size_t)n * 4, cudaMemcpyDeviceToDevice, stream) !=
           cudaSuccess ||
       cudaMemcpyAsync(vals_out, L.dv0, (size_t)n * 4, cudaMemcpyDeviceToDevice, stream) !=

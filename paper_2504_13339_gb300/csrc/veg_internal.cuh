@@ -108,7 +108,8 @@ struct WsHeader {
   unsigned int flags;              // VEG_FLAG_* bits
   unsigned int pad0;
   unsigned long long n_visible;    // records that touch a tile (last binning)
-  unsigned int pad[58];
+  unsigned int key_min, key_max;   // range of the depth sort's keys (last binning)
+  unsigned int pad[56];
 };
 static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
 constexpr unsigned int FLAG_CAPACITY = 1u;

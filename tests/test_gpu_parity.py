@@ -186,6 +186,75 @@ def test_bins_and_capacity_overflow_across_sizes_and_views(n, views, W, H, cut):
     assert np.array_equal(p.ranges.cpu().numpy().reshape(-1, 2), ranges)
 
 
+def _sorted_lists(dbits, tiles, rect, tiles_x, tb):
+    """The tile lists by their definition: visible records in (depth bits,
+    index) order, each record's tiles row-major, stably sorted by tile."""
+    vis = np.nonzero(tiles > 0)[0]
+    order = vis[np.lexsort((vis, dbits[vis]))]
+    keys, vals = [], []
+    for i in order:
+        x0, y0, x1, y1 = (int(v) for v in rect[i])
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                keys.append(((ty * tiles_x + tx) << 32) | int(dbits[i]))
+                vals.append(i)
+    keys = np.array(keys, np.uint64)
+    vals = np.array(vals, np.uint32)
+    srt = np.argsort(keys >> np.uint64(32), kind="stable")
+    return keys[srt], vals[srt]
+
+
+@pytest.mark.parametrize("span,passes_run", [(0, 0), (200, 1), (60_000, 2), (1 << 20, 3),
+                                             (None, 4)])
+def test_depth_sort_skips_the_passes_above_the_key_span(span, passes_run):
+    """The depth sort takes its digits of depth bits minus their minimum and
+    skips the passes above the span of the visible records' keys (found on
+    the device): for spans needing 0-4 of the 8-bit passes, on 70,000
+    records (the compaction path) with a fifth culled, the lists equal their
+    definition bit for bit, keys included."""
+    n, W = 70_000, 256
+    rng = np.random.default_rng(180 + passes_run)
+    cam = S.look_at_camera((0.0, 0.0, 3.0), W, W)
+    tx = cam.tiles_x
+    x0 = rng.integers(0, tx - 2, n)
+    y0 = rng.integers(0, tx - 2, n)
+    rect = np.stack([x0, y0, x0 + rng.integers(1, 3, n), y0 + rng.integers(1, 3, n)],
+                    axis=1).astype(np.int16)
+    tiles = ((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])).astype(np.int32)
+    culled = rng.random(n) < 0.2
+    tiles[culled] = 0
+    rect[culled] = 0
+    base = np.float32(3.7).view(np.uint32)
+    if span is None:
+        dbits = rng.uniform(0.3, 90.0, n).astype(np.float32).view(np.uint32)
+    else:
+        dbits = (base + rng.integers(0, span + 1, n)).astype(np.uint32)
+    vis = tiles > 0
+    real_span = int(dbits[vis].max()) - int(dbits[vis].min())
+    assert (real_span.bit_length() + 7) // 8 == passes_run
+    geo = np.zeros((n, 4), np.float32)
+    geo[:, 2] = dbits.view(np.float32)
+    keys_ref, vals_ref = _sorted_lists(dbits, tiles, rect, tx, tb=8)
+    M = vals_ref.size
+    c = _lib.cameras([cam])
+    ws = torch.empty(_lib.veg_bin_sort_workspace_size(n, 1, M, W, W), dtype=torch.uint8,
+                     device="cuda")
+    keys = torch.empty(M, dtype=torch.int64, device="cuda")
+    vals = torch.empty(M, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(tx * tx, 2, dtype=torch.int32, device="cuda")
+    _lib.veg_bin_sort(c, n, dev(geo), torch.as_tensor(tiles, device="cuda"),
+                      torch.as_tensor(rect, device="cuda"), ws, M, keys, vals, ranges)
+    st, m = _lib.veg_sync_status(ws)
+    assert st == _lib.VEG_OK and m == M
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), vals_ref)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_ref)
+    lists = (keys_ref >> np.uint64(32)).astype(np.int64)
+    rr = ranges.cpu().numpy()
+    for t in range(tx * tx):
+        w = np.nonzero(lists == t)[0]
+        assert tuple(rr[t]) == ((w[0], w[-1] + 1) if w.size else (0, 0))
+
+
 def test_empty_and_fully_culled():
     g, cams, tfs = S.plain_scene()
     empty = g.subset(np.arange(0))
