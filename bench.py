@@ -86,6 +86,12 @@ def parse():
                     help="serving: seconds of arrivals per rate of the sustainable-rate search")
     ap.add_argument("--p99-bound-ms", type=float, default=20.0,
                     help="serving: the p99 latency bound of the sustainable-rate search")
+    ap.add_argument("--batch-window-ms", type=float, default=4.0,
+                    help="serving: the windowed-batching mode's window (waiting requests of "
+                         "any model launch together once --min-batch of them wait or the "
+                         "oldest waited this)")
+    ap.add_argument("--min-batch", type=int, default=3,
+                    help="serving: the windowed-batching mode's batch that launches at once")
     ap.add_argument("--no-extras", action="store_true",
                     help="default run: skip the batched, sweep and serving records")
     return ap.parse_args()
@@ -1047,8 +1053,8 @@ def measure_serve(args):
 
     import __graft_entry__
     from paper_2504_13339_gb300 import scenes as S
-    from paper_2504_13339_gb300.serve import (RenderServer, fifo_serve, latency_stats,
-                                              poisson_requests)
+    from paper_2504_13339_gb300.serve import (RenderServer, SlotLimits, fifo_serve,
+                                              latency_stats, poisson_requests)
     __graft_entry__.build()
     models = {}
     for i, n in enumerate((200_000, 500_000, 1_000_000, 3_000_000, 6_000_000)):
@@ -1056,30 +1062,45 @@ def measure_serve(args):
         models[f"{n // 1000}k"] = _dev_tensors(g, "cuda")
     tfs = torch.as_tensor(S.bump_tfs(16, 32), device="cuda")
     srv = RenderServer(models, tfs, n_slots=4, max_batch=8)
+    # batches across models hold views x the largest model's records: room for 4 views of 6M
+    wsrv = RenderServer(models, tfs, n_slots=4, max_batch=8, batch_window_ms=args.batch_window_ms,
+                        min_batch=args.min_batch, cross_model=True,
+                        limits=SlotLimits(records=24_000_000))
     fsrv = RenderServer(models, tfs, n_slots=1)
     warm = poisson_requests(models, 16, args.rate, 2.0, 40)
     srv.run(warm)
+    wsrv.run(warm)
     fifo_serve(fsrv, warm)
     clocks = ClockSampler(torch.cuda.current_device())
     torch.cuda.synchronize()
     clocks.start()
 
+    names = {"batching": "continuous_batching", "windowed": "windowed_batching",
+             "fifo": "fifo_plain"}
+
     def run(mode, rate, duration, seed):
         reqs = poisson_requests(models, 16, rate, duration, seed)
-        if mode == "batching":
-            srv.batch_sizes.clear()
-            srv.mixed_batches = srv.retries = 0
-            res = latency_stats(srv.run(reqs))
-            res["mean_batch"] = round(float(np.mean(srv.batch_sizes)), 3)
-            res["batches_of_mixed_resolution"] = int(srv.mixed_batches)
-            res["requests_retried_alone"] = int(srv.retries)
+        if mode in ("batching", "windowed"):
+            sv = srv if mode == "batching" else wsrv
+            sv.batch_sizes.clear()
+            sv.mixed_batches = sv.retries = sv.multi_model_batches = 0
+            res = latency_stats(sv.run(reqs))
+            res["mean_batch"] = round(float(np.mean(sv.batch_sizes)), 3)
+            res["batches_of_mixed_resolution"] = int(sv.mixed_batches)
+            res["requests_retried_alone"] = int(sv.retries)
+            res["batches_of_several_models"] = int(sv.multi_model_batches)
         else:
             res = latency_stats(fifo_serve(fsrv, reqs))
         return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in res.items()}
-    at_rate = {"continuous_batching": run("batching", args.rate, args.serve_duration, 41),
-               "fifo_plain": run("fifo", args.rate, args.serve_duration, 41)}
+    at_rate = {names[m]: run(m, args.rate, args.serve_duration, 41)
+               for m in ("batching", "windowed", "fifo")}
+    # the windowed mode's point: batches at a moderate rate (4x the configured one)
+    at_rate["windowed_batching_at_4x_rate"] = run("windowed", 4 * args.rate,
+                                                  args.serve_duration, 42)
+    at_rate["continuous_batching_at_4x_rate"] = run("batching", 4 * args.rate,
+                                                    args.serve_duration, 42)
     sustain = {}
-    for mode in ("batching", "fifo"):
+    for mode in ("batching", "windowed", "fifo"):
         best, rate, trail = None, args.rate, []
         while rate <= args.rate * 64:
             r = run(mode, rate, args.sat_duration, 43)
@@ -1090,8 +1111,7 @@ def measure_serve(args):
                 break
             best = rate
             rate *= 2
-        sustain["continuous_batching" if mode == "batching" else "fifo_plain"] = {
-            "highest_rate": best, "runs": trail}
+        sustain[names[mode]] = {"highest_rate": best, "runs": trail}
     clk = clocks.stop()
     res = {"workload": "serving: 5 resident models (200k-6M Gaussians), Poisson arrivals, "
                        "random model/view/TF/resolution in {256,512,1024,2048}^2",
@@ -1101,9 +1121,13 @@ def measure_serve(args):
                            "rates": "doubled from the configured rate until p99 exceeds the "
                                     "bound", **sustain},
            "slots": len(srv.slots), "slot_bytes": srv.bytes,
+           "windowed_batching": f"waiting requests of any model batch together (each view "
+                                f"projects its own model); they launch once "
+                                f"{args.min_batch} wait, a batch is full, or the oldest has "
+                                f"waited {args.batch_window_ms:g} ms",
            "latency": "arrival to the result ready on the host (its completion event "
                       "observed)", "clocks": clk}
-    del srv, fsrv, models, tfs
+    del srv, wsrv, fsrv, models, tfs
     torch.cuda.empty_cache()
     return res
 

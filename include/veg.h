@@ -127,6 +127,26 @@ veg_status veg_project(const veg_camera* cams, int32_t n_views, veg_gaussians g,
                        int32_t* tiles_touched, int16_t* rect, cudaStream_t stream);
 
 /*
+ * veg_project_views -- veg_project where each view shows its own model
+ * (a server batching requests for different models into one binning and one
+ * compositing call; the paper renders one model per frame, Sec. 3.3).
+ * models: host [n_views]; view v projects models[v] (any model, the same
+ * one in several views allowed).  n: the record stride, >= every
+ * models[v].n.  View v's records are [v*n, v*n + models[v].n), written
+ * exactly as veg_project writes them; its records [v*n + models[v].n,
+ * (v+1)*n) get tiles_touched = 0 and their other arrays are left untouched
+ * (the binning reads nothing else of a record that touches no tile).
+ * Downstream calls take n as the Gaussian count: veg_bin_sort and
+ * veg_composite_fwd treat the padding records as culled, so each view's
+ * image is the one its model renders alone.  Errors as veg_project, and
+ * VEG_ERR_INVALID_ARGUMENT when models is NULL or a models[v].n exceeds n.
+ */
+veg_status veg_project_views(const veg_camera* cams, int32_t n_views,
+                             const veg_gaussians* models, int64_t n, const veg_tf* cull_tf,
+                             float* splat_geo, float* splat_aux, int32_t* tiles_touched,
+                             int16_t* rect, cudaStream_t stream);
+
+/*
  * veg_bin_sort -- tile binning and depth ordering (Sec. 3.3: "the efficient
  * tile-based rasterizer", alpha-blending "in front-to-back order").
  *

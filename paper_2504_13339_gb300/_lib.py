@@ -107,6 +107,8 @@ _SIGS = {
     "veg_tile_order": (ctypes.c_int, [_P, _I64, _P, _P]),
     "veg_radix_lookback_check": (ctypes.c_int, [_P, _SZ, _I64, _I32, _I32, _P, _P, _P]),
     "veg_project_bwd": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _P, _P, _P, _P]),
+    "veg_project_views": (ctypes.c_int, [_CAMS, _I32, ctypes.POINTER(veg_gaussians), _I64,
+                                         ctypes.POINTER(veg_tf), _P, _P, _P, _P, _P]),
     "veg_project_bwd_range": (ctypes.c_int, [_CAMS, _I32, veg_gaussians, _P, _P, _I64, _I64, _P,
                                              _P, _P, _P]),
     "veg_l1_loss_workspace_size": (ctypes.c_int, [ctypes.POINTER(_SZ)]),
@@ -217,6 +219,19 @@ def veg_project(cams, g, cull_tf, splat_geo, splat_aux, tiles_touched, rect, str
     tf = ctypes.byref(cull_tf) if cull_tf is not None else None
     _check("veg_project", lib.veg_project(cams, len(cams), g, tf, _ptr(splat_geo), _ptr(splat_aux),
                                           _ptr(tiles_touched), _ptr(rect), _stream(stream)))
+
+
+def veg_project_views(cams, models, n, cull_tf, splat_geo, splat_aux, tiles_touched, rect,
+                      stream=None):
+    """models: one veg_gaussians per view (len(cams) of them); n: the record
+    stride (>= every model's n)."""
+    lib = load()
+    arr = (veg_gaussians * len(models))(*models)
+    tf = ctypes.byref(cull_tf) if cull_tf is not None else None
+    _check("veg_project_views",
+           lib.veg_project_views(cams, len(cams), arr, int(n), tf, _ptr(splat_geo),
+                                 _ptr(splat_aux), _ptr(tiles_touched), _ptr(rect),
+                                 _stream(stream)))
 
 
 def veg_bin_sort_workspace_size(n, n_views, capacity, width, height) -> int:

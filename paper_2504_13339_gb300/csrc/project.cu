@@ -117,20 +117,14 @@ __device__ __forceinline__ bool project_one(const CamParam& cp, float4 mv, float
   return ok;
 }
 
-__global__ void __launch_bounds__(256)
-    project_fwd_kernel(CamSet cams, const float4* __restrict__ mean_v,
-                       const float4* __restrict__ logscale_w, const float4* __restrict__ quat,
-                       int64_t n, const float4* __restrict__ cull_lut, int lut_size, int n_tf,
-                       const int32_t* __restrict__ view_tf, float4* __restrict__ geo,
-                       float4* __restrict__ aux,
-                       int32_t* __restrict__ tiles, short4* __restrict__ rect) {
-  pdl_enter();
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int view = blockIdx.y;
-  const CamParam& cp = cams.c[view];
-  const int64_t o = (int64_t)view * n + i;
-  float4 mv = mean_v[i], lw = logscale_w[i], q = quat[i];
+// Record o of `view`: the projection of Gaussian (mv, lw, q).
+__device__ __forceinline__ void project_record(const CamParam& cp, int view, float4 mv, float4 lw,
+                                               float4 q, int64_t o,
+                                               const float4* __restrict__ cull_lut, int lut_size,
+                                               int n_tf, const int32_t* __restrict__ view_tf,
+                                               float4* __restrict__ geo, float4* __restrict__ aux,
+                                               int32_t* __restrict__ tiles,
+                                               short4* __restrict__ rect) {
   Proj P;
   bool ok = project_one(cp, mv, lw, q, P);
   // radius from the larger eigenvalue of Sigma'
@@ -173,6 +167,45 @@ __global__ void __launch_bounds__(256)
   aux[o] = make_float4(P.ca, P.cb, P.cc, mv.w);
   tiles[o] = (int32_t)(x1 - x0) * (int32_t)(y1 - y0);
   rect[o] = make_short4(x0, y0, x1, y1);
+}
+
+__global__ void __launch_bounds__(256)
+    project_fwd_kernel(CamSet cams, const float4* __restrict__ mean_v,
+                       const float4* __restrict__ logscale_w, const float4* __restrict__ quat,
+                       int64_t n, const float4* __restrict__ cull_lut, int lut_size, int n_tf,
+                       const int32_t* __restrict__ view_tf, float4* __restrict__ geo,
+                       float4* __restrict__ aux,
+                       int32_t* __restrict__ tiles, short4* __restrict__ rect) {
+  pdl_enter();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int view = blockIdx.y;
+  project_record(cams.c[view], view, mean_v[i], logscale_w[i], quat[i], (int64_t)view * n + i,
+                 cull_lut, lut_size, n_tf, view_tf, geo, aux, tiles, rect);
+}
+
+// Each view its own model: view v projects models.n[v] Gaussians into its
+// records [v n, v n + models.n[v]); its records up to (v + 1) n only get
+// tiles_touched = 0 (the binning reads nothing else of a record that
+// touches no tile).
+__global__ void __launch_bounds__(256)
+    project_views_kernel(CamSet cams, const __grid_constant__ ViewModels models, int64_t n,
+                         const float4* __restrict__ cull_lut, int lut_size, int n_tf,
+                         const int32_t* __restrict__ view_tf, float4* __restrict__ geo,
+                         float4* __restrict__ aux, int32_t* __restrict__ tiles,
+                         short4* __restrict__ rect) {
+  pdl_enter();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int view = blockIdx.y;
+  const int64_t o = (int64_t)view * n + i;
+  if (i >= models.n[view]) {
+    tiles[o] = 0;
+    return;
+  }
+  project_record(cams.c[view], view, models.mean_v[view][i], models.logscale_w[view][i],
+                 models.quat[view][i], o, cull_lut, lut_size, n_tf, view_tf, geo, aux, tiles,
+                 rect);
 }
 
 // dL/d(u, conic) of one view chained to the 3D parameters (accumulated).
@@ -317,6 +350,19 @@ veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const 
   return launch_status();
 }
 
+veg_status project_views_launch(const CamSet& cs, int n_views, const ViewModels& models,
+                                int64_t n, const veg_tf* cull_tf, float4* geo, float4* aux,
+                                int32_t* tiles, short4* rect, cudaStream_t stream) {
+  if (n == 0) return VEG_OK;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)n_views);
+  const float4* lut = cull_tf ? reinterpret_cast<const float4*>(cull_tf->lut) : nullptr;
+  launch_k(project_views_kernel, grid, 256, 0, stream, cs, models, n, lut,
+           cull_tf ? cull_tf->lut_size : 0, cull_tf ? cull_tf->n_tf : 0,
+           cull_tf ? cull_tf->view_tf : nullptr, geo, aux, tiles, rect);
+  count_launch();
+  return launch_status();
+}
+
 veg_status project_bwd_launch(const CamSet& cs, int n_views, veg_gaussians g,
                               const int32_t* tiles, const float4* grad2d, float4* gm, float4* gl,
                               float4* gq, cudaStream_t stream, int64_t first, int64_t count) {
@@ -354,4 +400,39 @@ extern "C" veg_status veg_project(const veg_camera* cams, int32_t n_views, veg_g
   return project_launch(cs, n_views, g, cull_tf, reinterpret_cast<float4*>(splat_geo),
                         reinterpret_cast<float4*>(splat_aux), tiles_touched,
                         reinterpret_cast<short4*>(rect), stream);
+}
+
+extern "C" veg_status veg_project_views(const veg_camera* cams, int32_t n_views,
+                                        const veg_gaussians* models, int64_t n,
+                                        const veg_tf* cull_tf, float* splat_geo,
+                                        float* splat_aux, int32_t* tiles_touched, int16_t* rect,
+                                        cudaStream_t stream) {
+  using namespace veg;
+  veg_status st = check_cameras(cams, n_views);
+  if (st != VEG_OK) return st;
+  if (!models || n < 0 || n > ((int64_t)1 << 31) / n_views) return VEG_ERR_INVALID_ARGUMENT;
+  if (n > 0 && (!splat_geo || !splat_aux || !tiles_touched || !rect))
+    return VEG_ERR_INVALID_ARGUMENT;
+  if (!aligned16(splat_geo) || !aligned16(splat_aux) || (reinterpret_cast<uintptr_t>(rect) & 7))
+    return VEG_ERR_INVALID_ARGUMENT;
+  ViewModels vm;
+  for (int v = 0; v < n_views; ++v) {
+    const veg_gaussians& g = models[v];
+    if (g.n < 0 || g.n > n) return VEG_ERR_INVALID_ARGUMENT;
+    if (g.n > 0 && (!g.mean_v || !g.logscale_w || !g.quat || !aligned16(g.mean_v) ||
+                    !aligned16(g.logscale_w) || !aligned16(g.quat)))
+      return VEG_ERR_INVALID_ARGUMENT;
+    vm.mean_v[v] = reinterpret_cast<const float4*>(g.mean_v);
+    vm.logscale_w[v] = reinterpret_cast<const float4*>(g.logscale_w);
+    vm.quat[v] = reinterpret_cast<const float4*>(g.quat);
+    vm.n[v] = g.n;
+  }
+  if (cull_tf && (!cull_tf->lut || cull_tf->lut_size < 2 || cull_tf->n_tf < 1 ||
+                  !aligned16(cull_tf->lut)))
+    return VEG_ERR_INVALID_ARGUMENT;
+  CamSet cs;
+  fill_camset(cams, n_views, &cs);
+  return project_views_launch(cs, n_views, vm, n, cull_tf, reinterpret_cast<float4*>(splat_geo),
+                              reinterpret_cast<float4*>(splat_aux), tiles_touched,
+                              reinterpret_cast<short4*>(rect), stream);
 }

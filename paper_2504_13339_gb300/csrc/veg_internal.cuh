@@ -196,6 +196,14 @@ __device__ __forceinline__ int view_of_tile(const ViewMap& m, int g) {
 }
 
 // Entry points shared between translation units (no argument validation).
+// Per-view models of one projection call (views may show different models).
+struct ViewModels {
+  const float4* mean_v[VEG_MAX_VIEWS];
+  const float4* logscale_w[VEG_MAX_VIEWS];
+  const float4* quat[VEG_MAX_VIEWS];
+  int64_t n[VEG_MAX_VIEWS];
+};
+
 veg_status project_launch(const CamSet& cs, int n_views, veg_gaussians g, const veg_tf* cull_tf,
                           float4* geo, float4* aux, int32_t* tiles, short4* rect,
                           cudaStream_t stream);

@@ -31,6 +31,20 @@ the device and admits render requests (model, camera, TF, resolution):
   memory budget holds (at least one), and a request is admitted into a
   batch when the batch's records, pixels and estimated instances fit the
   slot's fixed buffers; nothing is allocated while serving.
+* Batching window (optional, `batch_window_ms` > 0): a free slot launches a
+  model's waiting requests only once they are `min_batch` or more, fill a
+  batch, or the oldest of them has waited the window; until then the slot
+  stays free for another model.  This trades up to a window of latency for
+  larger batches when arrivals are sparse (the immediate policy launches
+  whatever waits as soon as a slot frees, which at moderate rates is one
+  request).
+* Batches across models (optional, `cross_model`): a batch may hold views
+  of different models (`veg_project_views`: each view projects its own
+  model into records of a common stride, the largest model's size; a
+  smaller model's remaining records touch no tile), so waiting requests
+  batch whatever model they ask for, as long as at most half of a batch's
+  records are such padding.  With the window, all waiting requests form
+  one group.
 
 `fifo_serve` is the comparison path: one request at a time, in arrival order,
 each as a plain single-view render.
@@ -117,7 +131,8 @@ class RenderServer:
     """Continuous-batching render server (see module docstring)."""
 
     def __init__(self, models, tf_bank, n_slots=4, max_batch=8, limits=None,
-                 mem_budget=None, bg=(0.0, 0.0, 0.0), keep_images=False, device="cuda"):
+                 mem_budget=None, bg=(0.0, 0.0, 0.0), keep_images=False, device="cuda",
+                 batch_window_ms=0.0, min_batch=2, cross_model=False):
         _lib.load()
         self.device = torch.device(device)
         self.models = {k: tuple(t.contiguous() for t in v) for k, v in models.items()}
@@ -139,16 +154,25 @@ class RenderServer:
         self.batch_sizes = []
         self.mixed_batches = 0  # batches holding more than one resolution
         self.retries = 0  # requests put back after their batch overflowed
+        self.multi_model_batches = 0  # batches holding more than one model
+        self.window = max(0.0, float(batch_window_ms)) * 1e-3
+        self.min_batch = max(1, int(min_batch))
+        self.cross_model = bool(cross_model)
 
     def _est(self, model, W, H):
         n = self.models[model][0].shape[0]
         return self.inst.get((model, W, H), min(16 * n, self.lim.instances))
 
     def _fits(self, batch):
-        """The batch's views, records, pixels and estimated instances fit a
-        slot's buffers."""
-        n = self.models[batch[0].model][0].shape[0]
+        """The batch's views, records (views x the largest model's size),
+        pixels and estimated instances fit a slot's buffers; across models,
+        at most half the records are padding (a small model's view beside a
+        large one projects the large one's record count)."""
+        sizes = [self.models[r.model][0].shape[0] for r in batch]
+        n = max(sizes)
         k = len(batch)
+        if k > 1 and k * n > 2 * sum(sizes):
+            return False
         pix = sum(r.camera.width * r.camera.height for r in batch)
         inst = sum(self._est(r.model, r.camera.width, r.camera.height) for r in batch)
         return (k <= self.lim.views and k * n <= self.lim.records and pix <= self.lim.pixels
@@ -159,7 +183,8 @@ class RenderServer:
         r0 = batch[0]
         b = slot.bufs
         k = len(batch)
-        n = self.models[r0.model][0].shape[0]
+        one_model = all(r.model == r0.model for r in batch)
+        n = max(self.models[r.model][0].shape[0] for r in batch)
         g = _lib.gaussians(*self.models[r0.model])
         cams = _lib.cameras([r.camera for r in batch])
         offsets, tiles = [0], 0
@@ -175,7 +200,12 @@ class RenderServer:
             tf = _lib.tf_desc(self.tf_bank, b.view_tf)
             out = b.out[:npix * 4]
             nc = b.nc[:npix]
-            _lib.veg_project(cams, g, tf, b.geo, b.aux, b.count, b.rect, s)
+            if one_model:
+                _lib.veg_project(cams, g, tf, b.geo, b.aux, b.count, b.rect, s)
+            else:
+                _lib.veg_project_views(cams, [_lib.gaussians(*self.models[r.model])
+                                              for r in batch], n, tf, b.geo, b.aux, b.count,
+                                       b.rect, s)
             _lib.veg_bin_sort(cams, n, b.geo, b.count, b.rect, b.ws, self.lim.instances, None,
                               b.vals, b.ranges, s)
             _lib.veg_tile_order(b.ranges[:tiles], b.order, s)
@@ -186,6 +216,7 @@ class RenderServer:
         slot.event, slot.batch, slot.offsets = ev, batch, offsets
         self.batch_sizes.append(k)
         self.mixed_batches += len({(r.camera.width, r.camera.height) for r in batch}) > 1
+        self.multi_model_batches += not one_model
 
     def _finish(self, slot):
         """Completes a slot's finished batch; returns (completed requests,
@@ -217,13 +248,36 @@ class RenderServer:
     def clock(self):
         return time.perf_counter() - self.t0
 
-    def _take_batch(self, pending):
-        head = pending[0]
+    def _gather(self, pending, head):
+        """`head` and every later waiting request of its model (of any model
+        with cross_model) that fits."""
         batch = [head]
         if not head.solo:
-            for r in list(pending)[1:]:
-                if r.model == head.model and not r.solo and self._fits(batch + [r]):
+            for r in pending:
+                if r is not head and not r.solo and (self.cross_model or r.model == head.model) \
+                        and self._fits(batch + [r]):
                     batch.append(r)
+        return batch
+
+    def _take_batch(self, pending):
+        """The next batch to launch, removed from `pending`, or None when the
+        batching window holds every model's requests back."""
+        if self.window <= 0.0:
+            batch = self._gather(pending, pending[0])
+        else:
+            now, batch, seen = self.clock(), None, set()
+            for r in pending:  # oldest first: the first model ready goes
+                if (r.model in seen or (self.cross_model and seen)) and not r.solo:
+                    continue
+                seen.add(r.model)
+                b = self._gather(pending, r)
+                # no room for one more request like the last: launch now
+                full = len(b) >= self.lim.views or not self._fits(b + [b[-1]])
+                if r.solo or full or len(b) >= self.min_batch or now - r.arrival >= self.window:
+                    batch = b
+                    break
+            if batch is None:
+                return None
         for r in batch:
             pending.remove(r)
         return batch
@@ -248,7 +302,10 @@ class RenderServer:
                     pending.extendleft(reversed(retry))
             for s in self.slots:
                 if s.event is None and pending:
-                    self._launch(s, self._take_batch(pending))
+                    batch = self._take_batch(pending)
+                    if batch is None:
+                        break  # the window holds the waiting requests back
+                    self._launch(s, batch)
             if not pending and nxt < len(reqs) and all(s.event is None for s in self.slots):
                 wait = reqs[nxt].arrival - self.clock()
                 if wait > 2e-4:

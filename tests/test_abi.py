@@ -122,6 +122,17 @@ def test_host_side_validation_needs_no_gpu(lib):
                                    None, None) == 1
     assert lib.veg_project(cams2, 2, _lib.veg_gaussians(0, 0, 0, 0), None, None, None, None,
                            None, None) == 0  # n = 0: nothing to launch
+    # per-view models: the list must be given and each model fit the stride
+    ms = (_lib.veg_gaussians * 2)(_lib.veg_gaussians(fake, fake, fake, 10),
+                                  _lib.veg_gaussians(fake, fake, fake, 30))
+    assert lib.veg_project_views(cams2, 2, None, 30, None, fake, fake, fake, fake, None) == 1
+    assert lib.veg_project_views(cams2, 2, ms, 20, None, fake, fake, fake, fake, None) == 1
+    ms[1] = _lib.veg_gaussians(0, 0, 0, 30)  # null arrays with n > 0
+    assert lib.veg_project_views(cams2, 2, ms, 30, None, fake, fake, fake, fake, None) == 1
+    ms[1] = _lib.veg_gaussians(fake + 4, fake, fake, 30)  # misaligned
+    assert lib.veg_project_views(cams2, 2, ms, 30, None, fake, fake, fake, fake, None) == 1
+    ms[0] = ms[1] = _lib.veg_gaussians(0, 0, 0, 0)
+    assert lib.veg_project_views(cams2, 2, ms, 0, None, None, None, None, None, None) == 0
     # veg_render: the TF group is 0 (default) or 1..8
     assert lib.veg_render(cams, 1, g, tf16, None, 9, 16, fake, 1 << 30, fake, fake, None) == 1
 

@@ -255,6 +255,33 @@ def test_depth_sort_skips_the_passes_above_the_key_span(span, passes_run):
         assert tuple(rr[t]) == ((w[0], w[-1] + 1) if w.size else (0, 0))
 
 
+def test_views_of_different_models_project_as_each_model_alone():
+    """veg_project_views: each view's records are those veg_project writes
+    for its own model, the records past a smaller model's size touch no
+    tile, and the binned lists of the batch equal each view's own."""
+    ga = S.uniform_gaussians(300, 185, logscale_mean=-2.5)
+    gb = S.uniform_gaussians(500, 186, logscale_mean=-2.5)
+    cams = S.orbit_cameras(2, 187, 64, 48)
+    tfs = lut_tensor(S.bump_tfs(2, 188))
+    tens = [tuple(dev(a) for a in (g.mean_v, g.logscale_w, g.quat)) for g in (ga, gb)]
+    n = 500
+    geo = torch.zeros(2 * n, 4, device="cuda")
+    aux = torch.zeros(2 * n, 4, device="cuda")
+    tiles = torch.full((2 * n,), 7, dtype=torch.int32, device="cuda")
+    rect = torch.zeros(2 * n, 4, dtype=torch.int16, device="cuda")
+    _lib.veg_project_views(_lib.cameras(cams), [_lib.gaussians(*t) for t in tens], n,
+                           _lib.tf_desc(tfs), geo, aux, tiles, rect)
+    for v, (g, t) in enumerate(zip((ga, gb), tens)):
+        p = SplatPipeline(g.n, [cams[v]], n_tf=2)
+        p.project(*t, tfs)
+        sl = slice(v * n, v * n + g.n)
+        assert torch.equal(geo[sl], p.geo.view(-1, 4)[:g.n])
+        assert torch.equal(aux[sl], p.aux.view(-1, 4)[:g.n])
+        assert torch.equal(tiles[sl], p.tiles.view(-1)[:g.n])
+        assert torch.equal(rect[sl], p.rect.view(-1, 4)[:g.n])
+    assert int(tiles[300:500].abs().sum()) == 0
+
+
 def test_empty_and_fully_culled():
     g, cams, tfs = S.plain_scene()
     empty = g.subset(np.arange(0))
