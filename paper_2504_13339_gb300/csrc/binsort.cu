@@ -906,6 +906,297 @@ size_t binsort_ws_bytes(int64_t n, int n_views, int64_t capacity) {
   return carve(nullptr, n * n_views, capacity).bytes;
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// One-CTA binning for small inputs (at most kOneCtaRecords records and
+// kOneCtaLists tile lists): the whole path of the kernels above in one
+// launch of 1024 threads, with the records in shared memory.  Same output,
+// bit for bit: the visible records in index order, their stable radix sort
+// by depth bits (passes above the keys' span skipped), the instance offsets
+// in depth order, then the stable sort of the first `capacity` instances by
+// list as a counting sort: each warp owns a contiguous run of 128 sorted
+// records, counts its instances per list, and after a scan over (list,
+// warp) writes them at their places in emission order.  Every warp
+// collective sits in a loop whose trip count is the same for all lanes of
+// the warp.
+// ---------------------------------------------------------------------------
+
+constexpr int kOneCtaThreads = 1024;
+constexpr int kOneCtaWarps = kOneCtaThreads / 32;
+constexpr int kOneCtaRecords = 4096;                    // 4 per thread, 128 per warp
+constexpr int kOneCtaLists = 256;
+constexpr int kOneCtaPerWarp = kOneCtaRecords / kOneCtaWarps;
+
+struct OneCtaSmem {
+  uint32_t key[2][kOneCtaRecords];
+  uint32_t rec[2][kOneCtaRecords];
+  uint32_t off[kOneCtaRecords + 1];            // instance offsets of the sorted records
+  uint32_t lbase[kOneCtaRecords];              // list of each sorted record's first tile
+  uint32_t shape[kOneCtaRecords];              // its rect width | view's tiles_x << 16
+  uint16_t wcnt[kOneCtaWarps][256];           // per warp: digit counts, then list counts
+  uint32_t lmask[kOneCtaWarps][kOneCtaLists];  // per warp and list: lanes touching the list
+  uint32_t lstart[kOneCtaLists];               // first instance of each list
+  uint32_t ltotal[kOneCtaLists];
+  uint32_t scan[kOneCtaWarps];
+  uint32_t kmin, kmax, nvis;
+};
+
+// Exclusive scan of one value per thread over the 1024-thread block; the
+// total to *total (read after the call's last barrier).
+__device__ __forceinline__ uint32_t onecta_scan(uint32_t x, uint32_t* s_warp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = s_warp[lane];
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  const uint32_t r = s_warp[warp] + inc - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kOneCtaThreads, 1)
+    bin_one_cta_kernel(const float4* __restrict__ geo, const int32_t* __restrict__ tiles,
+                       const short4* __restrict__ rect, int nrec, int64_t n_per_view, ViewMap vm,
+                       int nlists, int64_t capacity, int tb, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ vals, int2* __restrict__ ranges,
+                       WsHeader* __restrict__ hdr) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char onecta_raw[];
+  OneCtaSmem& S = *reinterpret_cast<OneCtaSmem*>(onecta_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = lanemask_lt();
+  if (tid == 0) {
+    S.kmin = 0xffffffffu;
+    S.kmax = 0u;
+  }
+  // 1. the visible records in index order (4 consecutive records per thread)
+  uint32_t vis[4], key[4];
+  uint32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = tid * 4 + k;
+    vis[k] = i < nrec && tiles[i] > 0;
+    key[k] = vis[k] ? __float_as_uint(geo[i].z) : 0u;
+    c += vis[k];
+  }
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (vis[k]) {
+      kmin = min(kmin, key[k]);
+      kmax = max(kmax, key[k]);
+    }
+  kmin = __reduce_min_sync(0xffffffffu, kmin);
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
+  __syncthreads();  // S.kmin / S.kmax initialised
+  if (lane == 0) {
+    atomicMin(&S.kmin, kmin);
+    atomicMax(&S.kmax, kmax);
+  }
+  uint32_t pos = onecta_scan(c, S.scan, &S.nvis);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (vis[k]) {
+      S.key[0][pos] = key[k];
+      S.rec[0][pos] = (uint32_t)(tid * 4 + k);
+      ++pos;
+    }
+  __syncthreads();
+  const int nvis = (int)S.nvis;
+  const uint32_t kb = S.kmin;
+  const uint32_t span = S.kmax > S.kmin ? S.kmax - S.kmin : 0u;
+
+  // 2. stable LSD sort by (key - kmin), 8-bit digits, passes within the span
+  int cur = 0;
+  for (int shift = 0; shift < 32 && (span >> shift) != 0u; shift += 8) {
+    for (int e = tid; e < kOneCtaWarps * 256; e += kOneCtaThreads)
+      S.wcnt[e >> 8][e & 255] = 0;
+    __syncthreads();
+    uint32_t d[4], r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = warp * kOneCtaPerWarp + j * 32 + lane;
+      d[j] = i < nvis ? ((S.key[cur][i] - kb) >> shift) & 255u : 256u;
+      const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
+      const uint32_t before = d[j] < 256u ? S.wcnt[warp][d[j]] : 0u;
+      r[j] = before + __popc(peers & lt);
+      __syncwarp();
+      if (d[j] < 256u && (peers & lt) == 0u)
+        S.wcnt[warp][d[j]] = (uint16_t)(before + __popc(peers));
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: prefix over warps, then over digits
+    uint32_t run = 0;
+    if (tid < 256)
+      for (int w = 0; w < kOneCtaWarps; ++w) {
+        const uint32_t x = S.wcnt[w][tid];
+        S.wcnt[w][tid] = (uint16_t)run;
+        run += x;
+      }
+    uint32_t unused;
+    const uint32_t dstart = onecta_scan(tid < 256 ? run : 0u, S.scan, &unused);
+    if (tid < 256) S.lstart[tid] = dstart;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = warp * kOneCtaPerWarp + j * 32 + lane;
+      if (d[j] < 256u) {
+        const uint32_t q = S.lstart[d[j]] + S.wcnt[warp][d[j]] + r[j];
+        if (q < (uint32_t)kOneCtaRecords) {  // always, when the counts agree
+          S.key[cur ^ 1][q] = S.key[cur][i];
+          S.rec[cur ^ 1][q] = S.rec[cur][i];
+        }
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  const uint32_t* order = S.rec[cur];
+
+  // 3. instance offsets in depth order (4 consecutive sorted records per
+  //    thread), and each record's list geometry, gathered once
+  uint32_t cnt[4], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = tid * 4 + k;
+    cnt[k] = 0u;
+    if (j < nvis) {
+      const uint32_t g = order[j];
+      const short4 rc = rect[g];
+      const int view = (int)(g / (uint32_t)n_per_view);
+      const int tx = vm.tiles_x[view];
+      cnt[k] = (uint32_t)tiles[g];
+      S.lbase[j] = (uint32_t)(vm.tile_off[view] + rc.y * tx + rc.x);
+      S.shape[j] = (uint32_t)(rc.z - rc.x) | ((uint32_t)tx << 16);
+    }
+    sum += cnt[k];
+  }
+  uint32_t total;
+  {
+    uint32_t o = onecta_scan(sum, S.scan, &S.off[kOneCtaRecords]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      S.off[tid * 4 + k] = o;
+      o += cnt[k];
+    }
+  }
+  __syncthreads();
+  total = S.off[kOneCtaRecords];
+  const uint32_t m_cap = (uint32_t)min((int64_t)total, capacity);
+  if (tid == 0) {
+    hdr->n_instances = total;
+    hdr->n_visible = (unsigned long long)nvis;
+    hdr->flags = (int64_t)total > capacity ? FLAG_CAPACITY : 0u;
+  }
+
+  // 4. the first m_cap instances sorted by list.  Warp w owns the sorted
+  //    records [128 w, 128 w + 128), 32 at a time, one per lane.  A record
+  //    adds at most one instance to a list, so a lane's place among its
+  //    round's instances of list l is the number of lower lanes whose
+  //    record touches l too: each lane sets its bit in the warp's mask of
+  //    every list it touches (shared memory), then reads the masks.  The
+  //    lowest lane of a mask adds its count and clears it.  Only __syncwarp
+  //    sits between the lanes' own loops.
+  for (int e = tid; e < kOneCtaWarps * kOneCtaLists; e += kOneCtaThreads) {
+    S.wcnt[e / kOneCtaLists][e % kOneCtaLists] = 0;
+    S.lmask[e / kOneCtaLists][e % kOneCtaLists] = 0u;
+  }
+  __syncthreads();
+  const uint32_t bit = 1u << lane;
+  for (int pass = 0; pass < 2; ++pass) {  // count, then place
+    if (pass == 1) {
+      // per list: prefix over warps, then the lists' starts
+      uint32_t lrun = 0;
+      if (tid < nlists)
+        for (int w = 0; w < kOneCtaWarps; ++w) {
+          const uint32_t x = S.wcnt[w][tid];
+          S.wcnt[w][tid] = (uint16_t)lrun;
+          lrun += x;
+        }
+      uint32_t unused;
+      const uint32_t ls = onecta_scan(tid < nlists ? lrun : 0u, S.scan, &unused);
+      if (tid < nlists) {
+        S.lstart[tid] = ls;
+        S.ltotal[tid] = lrun;
+      }
+      __syncthreads();
+    }
+    for (int round = 0; round < kOneCtaPerWarp / 32; ++round) {
+      const int j = warp * kOneCtaPerWarp + round * 32 + lane;
+      int ntk = 0;
+      uint32_t lb = 0, g = 0;
+      int wx = 1, tx = 0;
+      if (j < nvis) {
+        const uint32_t e0 = S.off[j];
+        const uint32_t e1 = min(S.off[j + 1], m_cap);
+        ntk = e1 > e0 ? (int)(e1 - e0) : 0;
+        lb = S.lbase[j];
+        wx = (int)(S.shape[j] & 0xffffu);
+        tx = (int)(S.shape[j] >> 16);
+        g = order[j];
+      }
+      // the record's lists, tiles row-major: lb + ry * tx + rx
+      for (int t = 0, rx = 0, ry = 0; t < ntk; ++t) {
+        atomicOr(&S.lmask[warp][lb + ry * tx + rx], bit);
+        if (++rx == wx) rx = 0, ++ry;
+      }
+      __syncwarp();
+      if (pass == 1) {
+        for (int t = 0, rx = 0, ry = 0; t < ntk; ++t) {
+          const uint32_t l = lb + (uint32_t)(ry * tx + rx);
+          const uint32_t q = S.lstart[l] + S.wcnt[warp][l] + __popc(S.lmask[warp][l] & lt);
+          if (q < m_cap) {  // always, when the counts agree
+            vals[q] = g;
+            if (keys) {
+              const uint32_t view = (uint32_t)view_of_tile(vm, (int)l);
+              const uint32_t tile = l - (uint32_t)vm.tile_off[view];
+              keys[q] = ((uint64_t)view << (tb + 32)) | ((uint64_t)tile << 32) |
+                        (uint64_t)__float_as_uint(geo[g].z);
+            }
+          }
+          if (++rx == wx) rx = 0, ++ry;
+        }
+        __syncwarp();
+      }
+      for (int t = 0, rx = 0, ry = 0; t < ntk; ++t) {
+        const uint32_t l = lb + (uint32_t)(ry * tx + rx);
+        const uint32_t m = S.lmask[warp][l];
+        if ((m & lt) == 0u) {  // the lowest lane of the list's mask
+          S.wcnt[warp][l] = (uint16_t)(S.wcnt[warp][l] + __popc(m));
+          S.lmask[warp][l] = 0u;
+        }
+        if (++rx == wx) rx = 0, ++ry;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  // 5. the ranges of every list
+  for (int l = tid; l < nlists; l += kOneCtaThreads)
+    ranges[l] = S.ltotal[l] ? make_int2((int)S.lstart[l], (int)(S.lstart[l] + S.ltotal[l]))
+                            : make_int2(0, 0);
+}
+
+}  // namespace
+
 veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const float4* geo,
                           const int32_t* tiles, const short4* rect, void* ws, int64_t capacity,
                           uint64_t* keys, uint32_t* vals, int2* ranges, cudaStream_t stream) {
@@ -914,6 +1205,17 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   const int64_t nranges = vm.tile_off[n_views];
   Layout L = carve(ws, nrec, capacity);
 
+  // small inputs: the whole binning in one CTA
+  if (nrec >= 1 && nrec <= kOneCtaRecords && nranges <= kOneCtaLists) {
+    static SmemRecord one_cta;
+    if (prepare_smem(bin_one_cta_kernel, sizeof(OneCtaSmem), one_cta, true) == VEG_OK) {
+      launch_k(bin_one_cta_kernel, 1, kOneCtaThreads, sizeof(OneCtaSmem), stream, geo, tiles,
+               rect, (int)nrec, n, vm, (int)nranges, capacity, tile_bits_of(vm.max_tiles), keys,
+               vals, ranges, L.hdr);
+      count_launch();
+      return launch_status();
+    }
+  }
   launch_k(zero_ranges_kernel, grid_for(nranges, 256), 256, 0, stream, ranges, nranges, L.small,
            kSmallWords, L.hdr);
   count_launch();
