@@ -47,8 +47,12 @@ FP32_LANES_PER_SM = 128
 # The "visited"/"replayed" counts are the method's own pair counts; pairs
 # that the per-warp lists skip cost nothing and carry no flops.
 FWD_FLOPS = {"visited": 0, "iterated": 12, "evaluated": 2, "alpha": 3, "blended": 10}
+# A pair with a screen gradient: dp = dL/dG G, its five offset moments dp
+# (dx, dy, dx^2, dx dy, dy^2) and the warp sums of the seven per-splat
+# slots (one add per pair each); the per-splat coefficients applied at the
+# flush are not counted.
 BWD_FLOPS = {"replayed": 0, "iterated": 12, "evaluated": 2, "alpha": 3, "blended": 21,
-             "free": 7, "grad": 26}
+             "free": 7, "grad": 14}
 # shaded backward: per blended pair c.g = s_d (C.g) + s_s (g_r + g_g + g_b)
 # (+3) and the two shading sums (+4)
 BWD_FLOPS_LIT = dict(BWD_FLOPS, blended=28)

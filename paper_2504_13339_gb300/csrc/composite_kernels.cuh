@@ -708,15 +708,19 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
           T[t] = Ti;
         }
       };
-      // gradient parts of one pair: u_x, u_y, conic a, b, c, v, the exponent
-      // (dL/dw times w) (and s_d)
-      auto pair_parts = [&](float* v, float dp, float4 sg, float sc, float2 d, float dvv,
+      // gradient parts of one pair: the exponent gradient dp = dL/dpower
+      // times the offset moments dx, dy, dx^2, dx dy, dy^2 (d = u - pixel),
+      // dL/dv, dp itself (dL/dw times w) (and s_d).  The screen gradients
+      // are linear in these moments with per-splat coefficients (power =
+      // -a/2 dx^2 - b dx dy - c/2 dy^2), applied once per splat at the flush.
+      auto pair_parts = [&](float* v, float dp, float2 d, float2 d2, float dxy, float dvv,
                             float dsd) {
-        v[0] = dp * (2.0f * sg.z * d.x + sg.w * d.y);
-        v[1] = dp * (2.0f * sc * d.y + sg.w * d.x);
-        v[2] = dp * (-0.5f * d.x * d.x);
-        v[3] = dp * (-d.x * d.y);
-        v[4] = dp * (-0.5f * d.y * d.y);
+        const float2 m = mul2(make_float2(dp, dp), d);
+        v[0] = m.x;
+        v[1] = m.y;
+        v[2] = dp * d2.x;
+        v[3] = dp * dxy;
+        v[4] = dp * d2.y;
         v[5] = dvv;
         v[6] = dp;
         v[7] = LIT ? dsd : 0.0f;
@@ -755,8 +759,8 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
         if (LIT) nz = nz || dd0 != 0.f || ds0 != 0.f || dd1 != 0.f || ds1 != 0.f;
         if (__any_sync(0xffffffffu, nz)) {
           float v[16];
-          pair_parts(v, dp0, sg0, sc0.x, d0, dv0, dd0);
-          pair_parts(v + 8, dp1, sg1, sc1.x, d1, dv1, dd1);
+          pair_parts(v, dp0, d0, q0, x0, dv0, dd0);
+          pair_parts(v + 8, dp1, d1, q1, x1, dv1, dd1);
           // lane l ends with slot l >> 1 (splat (l >> 4), component (l >> 1) & 7)
           const float r = warp_reduce_scatter16(v, lane);
           const int slot = lane >> 1, which = slot >> 3, comp = slot & 7;
@@ -784,11 +788,17 @@ __global__ void __launch_bounds__(256, ((LIT || STATS) && TG >= 4) ? 3 : 4)
                          a1.x != 0.f || a1.y != 0.f || a1.z != 0.f;
         const uint32_t rec = s_idx[sl];
         if (any) {
+          // moments (S_x, S_y, S_xx, S_xy, S_yy) of dp to the screen
+          // gradients: du = (-a S_x - b S_y, -b S_x - c S_y), dconic =
+          // (-S_xx / 2, -S_xy, -S_yy / 2); s_geo holds (u, -a/2, -b), s_c -c/2
+          const float4 sg = s_geo[sl];
+          const float sc = s_c[sl].x;
           float4* dst = grad2d + 2 * (int64_t)rec;
           const float w = A.geo[rec].w;
           const float dw = w > 0.0f ? a1.z / w : 0.0f;
-          red_add_v4(dst, a0.x, a0.y, a0.z, a0.w);
-          red_add_v4(dst + 1, a1.x, a1.y, dw, 0.0f);
+          red_add_v4(dst, 2.0f * sg.z * a0.x + sg.w * a0.y, 2.0f * sc * a0.y + sg.w * a0.x,
+                     -0.5f * a0.z, -a0.w);
+          red_add_v4(dst + 1, -0.5f * a1.x, a1.y, dw, 0.0f);
         }
         if (LIT && (a1.w != 0.f || a2.x != 0.f)) red_add_v2(grad_shade + rec, a1.w, a2.x);
       }
