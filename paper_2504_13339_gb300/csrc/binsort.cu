@@ -556,27 +556,26 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0) *total = carry;
 }
 
-// Per-block sums of tiles_touched taken in depth order.
-__global__ void __launch_bounds__(kThreads)
+// Sums of tiles_touched over blocks of 256 records taken in depth order (the
+// blocks of the emission kernel).
+__global__ void __launch_bounds__(256)
     count_reduce_kernel(const int32_t* __restrict__ tiles, SortedVals sorted, Count cnt,
                         unsigned long long* __restrict__ bsum) {
   pdl_enter();
   const uint32_t* __restrict__ order = sorted.get();
-  __shared__ unsigned long long s[kThreads];
+  __shared__ unsigned long long s_warp[8];
   const int64_t nrec = cnt.get();
-  const int64_t base = (int64_t)blockIdx.x * kTileItems;
-  unsigned long long acc = 0;
-  for (int j = 0; j < kItems; ++j) {
-    int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
-    if (i < nrec) acc += (unsigned)tiles[order[i]];
-  }
-  s[threadIdx.x] = acc;
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  unsigned long long acc = i < nrec ? (unsigned)tiles[order[i]] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = acc;
   __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += s_warp[w];
+    bsum[blockIdx.x] = t;
   }
-  if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
 }
 
 // Exclusive scan of the block sums (one block of 1024 threads); writes the
@@ -622,33 +621,6 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Instance offsets (exclusive prefix of tiles_touched in depth order),
-// saturated to 0xffffffff (any value >= capacity is never emitted).
-__global__ void __launch_bounds__(kThreads)
-    count_down_kernel(const int32_t* __restrict__ tiles, SortedVals sorted, Count cnt,
-                      const unsigned long long* __restrict__ bsum, uint32_t* __restrict__ offsets) {
-  pdl_enter();
-  const uint32_t* __restrict__ order = sorted.get();
-  __shared__ unsigned long long s_warp[8];
-  const int64_t nrec = cnt.get();
-  const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
-  uint32_t c[kItems];
-  unsigned long long sum = 0;
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    int64_t i = base + k;
-    c[k] = i < nrec ? (uint32_t)tiles[order[i]] : 0u;
-    sum += c[k];
-  }
-  unsigned long long run = bsum[blockIdx.x] + block_exclusive_scan256<unsigned long long>(sum, s_warp);
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    int64_t i = base + k;
-    if (i < nrec) offsets[i] = run < 0xffffffffull ? (uint32_t)run : 0xffffffffu;
-    run += c[k];
-  }
-}
-
 // Writes the (global tile id, record) pairs of 32 consecutive records (in
 // depth order) per warp, tiles of a record row-major, below capacity; the
 // global id of tile (tx, ty) of view v is vm.tile_off[v] + ty * tiles_x[v]
@@ -658,22 +630,28 @@ __global__ void __launch_bounds__(kThreads)
 // binary search over the lanes' offsets (offsets increase with the lane).
 __global__ void __launch_bounds__(256)
     emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
-                SortedVals sorted, const uint32_t* __restrict__ offsets, Count visible,
+                SortedVals sorted, const unsigned long long* __restrict__ bsum, Count visible,
                 int64_t n_per_view, ViewMap vm, int64_t capacity, uint32_t* __restrict__ ikeys,
                 uint32_t* __restrict__ ivals) {
   pdl_enter();
+  __shared__ unsigned long long s_warp[8];
   const uint32_t* __restrict__ order = sorted.get();
   const int lane = threadIdx.x & 31;
   const int64_t nrec = visible.get();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t g = 0, cnt = 0, off = 0xffffffffu;
+  uint32_t g = 0, cnt = 0;
   short4 rc = make_short4(0, 0, 0, 0);
   if (i < nrec) {
     g = order[i];
     cnt = (uint32_t)tiles[g];
-    off = offsets[i];  // saturated at 0xffffffff beyond 2^32 instances
     if (cnt) rc = rect[g];
   }
+  // the record's first instance: the block's offset (scanned block sums)
+  // plus the block's exclusive scan, saturated at 0xffffffff beyond 2^32
+  // instances; records past the count get 0xffffffff
+  const unsigned long long off64 =
+      bsum[blockIdx.x] + block_exclusive_scan256<unsigned long long>(cnt, s_warp);
+  const uint32_t off = i < nrec && off64 < 0xffffffffull ? (uint32_t)off64 : 0xffffffffu;
   const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
   unsigned long long end = off == 0xffffffffu ? 0ull : (unsigned long long)off + cnt;
 #pragma unroll
@@ -788,14 +766,15 @@ __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t
 
 struct Layout {
   WsHeader* hdr;
-  uint32_t *dk0, *dv0, *dk1, *dv1, *offsets;
+  uint32_t *dk0, *dv0, *dk1, *dv1;
+  unsigned long long* esum;  // instances per 256-record block in depth order, then their scan
   unsigned long long* bsum;
   uint32_t *ik0, *ik1, *iv0;
   uint32_t *hist, *totals;  // table passes: [256][nb_hist] per-chunk counts, [256] totals
   uint32_t* small;  // look-back passes: [2 sorts][kMaxPasses][256] digit totals, then
                     // [2][kMaxPasses] tickets
   unsigned long long* look[2];  // look-back words of alternate passes, [chunks][256] each
-  int nb_rec, nb_hist;
+  int nb_rec, nb_hist, nb_emit;
   size_t bytes;
 };
 constexpr int kSmallWords = 2 * kMaxPasses * 256 + 2 * kMaxPasses;
@@ -808,7 +787,8 @@ Layout carve(void* ws, int64_t nrec, int64_t capacity) {
   L.dv0 = c.take<uint32_t>(nrec);
   L.dk1 = c.take<uint32_t>(nrec);
   L.dv1 = c.take<uint32_t>(nrec);
-  L.offsets = c.take<uint32_t>(nrec);
+  L.nb_emit = (int)std::max<int64_t>(1, (nrec + 255) / 256);
+  L.esum = c.take<unsigned long long>(L.nb_emit);
   L.nb_rec = (int)std::max<int64_t>(1, (nrec + kTileItems - 1) / kTileItems);
   L.bsum = c.take<unsigned long long>(L.nb_rec);
   L.ik0 = c.take<uint32_t>(capacity);
@@ -1244,10 +1224,9 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   uint32_t* const dv[2] = {L.dv0, L.dv1};
   const SortedVals order = radix_sort(dk, dv, cr, 32, L.nb_rec, L, 0, L.hdr, stream);
   // 2. instance offsets in depth order, total into the header
-  launch_k(count_reduce_kernel, L.nb_rec, kThreads, 0, stream, tiles, order, cr, L.bsum);
-  launch_k(count_top_kernel, 1, 1024, 0, stream, L.bsum, L.nb_rec, L.hdr, capacity);
-  launch_k(count_down_kernel, L.nb_rec, kThreads, 0, stream, tiles, order, cr, L.bsum, L.offsets);
-  count_launch(3);
+  launch_k(count_reduce_kernel, L.nb_emit, 256, 0, stream, tiles, order, cr, L.esum);
+  launch_k(count_top_kernel, 1, 1024, 0, stream, L.esum, L.nb_emit, L.hdr, capacity);
+  count_launch(2);
   // 3. emit (tile key, record) pairs, then stable sort by tile key
   int bits = 1;
   while (((int64_t)1 << bits) < nranges) ++bits;
@@ -1261,7 +1240,8 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
     vbuf[0] = L.iv0;
     vbuf[1] = vals;
   }
-  launch_k(emit_kernel, grid_for(nrec, 256), 256, 0, stream, tiles, rect, order, L.offsets, cr, n,
+  launch_k(emit_kernel, L.nb_emit, 256, 0, stream, tiles, rect, order,
+           (const unsigned long long*)L.esum, cr, n,
            vm, capacity, kbuf[0], vbuf[0]);
   count_launch();
   Count ci{0, &L.hdr->n_instances, capacity};
