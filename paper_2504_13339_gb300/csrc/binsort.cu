@@ -352,12 +352,18 @@ __global__ void __launch_bounds__(kThreads, 4)
 
     uint32_t k[kItems], v[kItems], r[kItems];
     const unsigned lt = lanemask_lt();
+    // every load in flight before the ranking (whose warp barriers would
+    // otherwise wait for each load in turn)
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+      k[j] = i < n ? kin[i] : 0u;
+      v[j] = i < n ? vin[i] : 0u;
+    }
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
       int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
       bool valid = i < n;
-      k[j] = valid ? kin[i] : 0u;
-      v[j] = valid ? vin[i] : 0u;
       uint32_t d = valid ? (((k[j] - kb) >> shift) & mask) : 256u;
       unsigned peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = d < 256u ? s_whist[warp][d] : 0u;
@@ -496,18 +502,22 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ unsigned long long s_warp[8];
   const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)threadIdx.x * kItems;
   bool vis[kItems];
+  uint32_t dk[kItems];
   unsigned long long c = 0;
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     vis[k] = base + k < nrec && tiles[base + k] > 0;
     c += vis[k] ? 1ull : 0ull;
   }
+  // the depth loads in flight across the scan's barriers
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) dk[k] = vis[k] ? __float_as_uint(geo[base + k].z) : 0u;
   unsigned long long run = bsum[blockIdx.x] + block_exclusive_scan256<unsigned long long>(c, s_warp);
   uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     if (!vis[k]) continue;
-    const uint32_t key = __float_as_uint(geo[base + k].z);
+    const uint32_t key = dk[k];
     keys[run] = key;
     vals[run] = (uint32_t)(base + k);
     kmin = min(kmin, key);

@@ -388,9 +388,31 @@ __global__ void __launch_bounds__(256, (TG >= 8 ? 2 : (TG == 1 ? 5 : 4)))
         }
         if (STATS && !act) jstop = j + 1;
       };
-      // two splats per step: their exponents are independent and overlap,
-      // the blends stay in list order
+      // four (then two, then one) splats per step: their exponents are
+      // independent and overlap, the blends stay in list order
       int k = 0;
+      for (; k + 3 < nw && act; k += 4) {
+        const int j0 = s_list[warp][k], j1 = s_list[warp][k + 1];
+        const int j2 = s_list[warp][k + 2], j3 = s_list[warp][k + 3];
+        const float4 g0 = s_geo[j0], g1 = s_geo[j1], g2 = s_geo[j2], g3 = s_geo[j3];
+        const float2 c0 = s_c[j0], c1 = s_c[j1], c2 = s_c[j2], c3 = s_c[j3];
+        float2 d0, d1, d2, d3, q0, q1, q2, q3;
+        float x0, x1, x2, x3;
+        const float p0 = power_at(g0.x, g0.y, fxy, g0.z, g0.w, c0.x, d0, q0, x0);
+        const float p1 = power_at(g1.x, g1.y, fxy, g1.z, g1.w, c1.x, d1, q1, x1);
+        const float p2 = power_at(g2.x, g2.y, fxy, g2.z, g2.w, c2.x, d2, q2, x2);
+        const float p3 = power_at(g3.x, g3.y, fxy, g3.z, g3.w, c3.x, d3, q3, x3);
+        const bool e0 = !(p0 < c0.y || p0 > 0.0f), e1 = !(p1 < c1.y || p1 > 0.0f);
+        const bool e2 = !(p2 < c2.y || p2 > 0.0f), e3 = !(p3 < c3.y || p3 > 0.0f);
+        if (STATS) {
+          n_it += 4;
+          n_eval += (unsigned)e0 + (unsigned)e1 + (unsigned)e2 + (unsigned)e3;
+        }
+        if (e0) blend(j0, gauss_of(p0));
+        if (e1 && act) blend(j1, gauss_of(p1));
+        if (e2 && act) blend(j2, gauss_of(p2));
+        if (e3 && act) blend(j3, gauss_of(p3));
+      }
       for (; k + 1 < nw && act; k += 2) {
         const int j0 = s_list[warp][k], j1 = s_list[warp][k + 1];
         const float4 g0 = s_geo[j0], g1 = s_geo[j1];
