@@ -99,8 +99,10 @@ __device__ __forceinline__ T block_exclusive_scan256(T x, T* s_warp) {
 //    the walks are short and the launches dominate.
 // ---------------------------------------------------------------------------
 
+// Chunks of `ITEMS` items per thread of a 256-thread block.
+template <int ITEMS = kItems>
 __device__ __forceinline__ int chunks_of(int64_t n) {
-  return (int)((n + kTileItems - 1) / kTileItems);
+  return (int)((n + kThreads * ITEMS - 1) / (kThreads * ITEMS));
 }
 
 constexpr int kMaxPasses = 4;
@@ -163,6 +165,7 @@ constexpr int kLookbackMaxChunks = 64;
 
 // Per-chunk digit histograms; hist is [2^nbits][nblocks] (nblocks = the
 // chunk capacity), blocks stride over the chunks that hold items.
+template <int ITEMS>
 __global__ void __launch_bounds__(kThreads)
     radix_hist_kernel(const uint32_t* __restrict__ keys, Count cnt, int shift, int nbits,
                       uint32_t* __restrict__ hist, int nblocks, const WsHeader* krange) {
@@ -171,23 +174,30 @@ __global__ void __launch_bounds__(kThreads)
   if (pass_skipped(krange, shift)) return;
   const uint32_t kb = range_base(krange);
   const int64_t n = cnt.get();
-  const int nch = chunks_of(n);
+  const int nch = chunks_of<ITEMS>(n);
   const uint32_t mask = (1u << nbits) - 1u;
   const bool digit = threadIdx.x <= mask;
   for (int b = blockIdx.x; b < nch; b += gridDim.x) {
     s_hist[threadIdx.x] = 0;
     __syncthreads();
-    // each thread counts 8 consecutive keys, loaded as two 16-byte vectors
+    // each thread counts ITEMS consecutive keys, loaded as 16-byte vectors
     // (the key arrays are 256-byte aligned) before any shared-memory update
-    const int64_t i0 = (int64_t)b * kTileItems + (int64_t)threadIdx.x * kItems;
-    if (i0 + kItems <= n) {
+    const int64_t i0 = (int64_t)b * (kThreads * ITEMS) + (int64_t)threadIdx.x * ITEMS;
+    if (i0 + ITEMS <= n) {
       const uint4* src = reinterpret_cast<const uint4*>(keys + i0);
-      const uint4 a = __ldg(src), c = __ldg(src + 1);
-      const uint32_t k[kItems] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+      uint32_t k[ITEMS];
 #pragma unroll
-      for (int j = 0; j < kItems; ++j) atomicAdd(&s_hist[((k[j] - kb) >> shift) & mask], 1u);
+      for (int q = 0; q < ITEMS / 4; ++q) {
+        const uint4 a = __ldg(src + q);
+        k[4 * q] = a.x;
+        k[4 * q + 1] = a.y;
+        k[4 * q + 2] = a.z;
+        k[4 * q + 3] = a.w;
+      }
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) atomicAdd(&s_hist[((k[j] - kb) >> shift) & mask], 1u);
     } else {
-      for (int j = 0; j < kItems; ++j)
+      for (int j = 0; j < ITEMS; ++j)
         if (i0 + j < n) atomicAdd(&s_hist[((__ldg(&keys[i0 + j]) - kb) >> shift) & mask], 1u);
     }
     __syncthreads();
@@ -197,6 +207,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // One block per digit: exclusive scan in place of that digit's per-chunk
 // counts (the chunks that hold items), and the digit total.
+template <int ITEMS>
 __global__ void __launch_bounds__(1024)
     radix_scan_rows_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ totals,
                            Count cnt, int shift, const WsHeader* krange) {
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(1024)
   __shared__ uint32_t s_total;
   if (pass_skipped(krange, shift)) return;
   uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
-  nblocks = chunks_of(cnt.get());
+  nblocks = chunks_of<ITEMS>(cnt.get());
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t carry = 0;
   for (int base = 0; base < nblocks; base += 1024 * 4) {
@@ -300,8 +311,8 @@ __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned 
 // look-back not answered within `spins` polls sets FLAG_TIMEOUT in the
 // header and stops waiting: the output is then void).  dtot: the digit
 // totals of the pass.
-template <bool TABLE>
-__global__ void __launch_bounds__(kThreads, 4)
+template <bool TABLE, int ITEMS>
+__global__ void __launch_bounds__(kThreads, ITEMS == 4 ? 6 : 4)
     radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, Count cnt,
                          int shift, int nbits, const uint32_t* __restrict__ dtot,
@@ -314,13 +325,13 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ uint32_t s_dbase[256];
   __shared__ uint32_t s_bstart[256];
   __shared__ uint32_t s_warp[8];
-  __shared__ uint32_t s_keys[kTileItems];
-  __shared__ uint32_t s_vals[kTileItems];
+  __shared__ uint32_t s_keys[kThreads * ITEMS];
+  __shared__ uint32_t s_vals[kThreads * ITEMS];
   __shared__ int s_chunk;
   if (pass_skipped(krange, shift)) return;  // then so is every later pass
   const uint32_t kb = range_base(krange);
   const int64_t n = cnt.get();
-  const int nch = chunks_of(n);
+  const int nch = chunks_of<ITEMS>(n);
   if (TABLE && (int)blockIdx.x >= nch) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t mask = (1u << nbits) - 1u;
@@ -348,21 +359,21 @@ __global__ void __launch_bounds__(kThreads, 4)
       b = s_chunk;
       if (b >= nch) break;  // block-uniform
     }
-    const int64_t base = (int64_t)b * kTileItems;
+    const int64_t base = (int64_t)b * (kThreads * ITEMS);
 
-    uint32_t k[kItems], v[kItems], r[kItems];
+    uint32_t k[ITEMS], v[ITEMS], r[ITEMS];
     const unsigned lt = lanemask_lt();
     // every load in flight before the ranking (whose warp barriers would
     // otherwise wait for each load in turn)
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      const int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+    for (int j = 0; j < ITEMS; ++j) {
+      const int64_t i = base + warp * (ITEMS * 32) + j * 32 + lane;
       k[j] = i < n ? kin[i] : 0u;
       v[j] = i < n ? vin[i] : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+    for (int j = 0; j < ITEMS; ++j) {
+      int64_t i = base + warp * (ITEMS * 32) + j * 32 + lane;
       bool valid = i < n;
       uint32_t d = valid ? (((k[j] - kb) >> shift) & mask) : 256u;
       unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -386,12 +397,12 @@ __global__ void __launch_bounds__(kThreads, 4)
     s_bstart[tid] = block_exclusive_scan256<uint32_t>(run, s_warp);
     __syncthreads();  // every digit's start is read below
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      int64_t i = base + warp * (kItems * 32) + j * 32 + lane;
+    for (int j = 0; j < ITEMS; ++j) {
+      int64_t i = base + warp * (ITEMS * 32) + j * 32 + lane;
       if (i < n) {
         uint32_t d = ((k[j] - kb) >> shift) & mask;
         uint32_t pos = s_bstart[d] + s_whist[warp][d] + r[j];
-        if (pos < (uint32_t)kTileItems) {  // always, when the counts agree
+        if (pos < (uint32_t)(kThreads * ITEMS)) {  // always, when the counts agree
           s_keys[pos] = k[j];
           s_vals[pos] = v[j];
         }
@@ -436,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       s_dbase[tid] = dpre + (uint32_t)prefix;
     }
     __syncthreads();
-    const int cnt_valid = (int)min((int64_t)kTileItems, n - base);
+    const int cnt_valid = (int)min((int64_t)(kThreads * ITEMS), n - base);
     for (int p = tid; p < cnt_valid; p += kThreads) {
       uint32_t key = s_keys[p];
       uint32_t d = ((key - kb) >> shift) & mask;
@@ -804,7 +815,9 @@ Layout carve(void* ws, int64_t nrec, int64_t capacity) {
   L.ik0 = c.take<uint32_t>(capacity);
   L.ik1 = c.take<uint32_t>(capacity);
   L.iv0 = c.take<uint32_t>(capacity);
-  L.nb_hist = (int)std::max<int64_t>(L.nb_rec, (capacity + kTileItems - 1) / kTileItems);
+  // the depth sort's table passes take chunks of 1024 records
+  L.nb_hist = (int)std::max<int64_t>(2 * (int64_t)L.nb_rec,
+                                     (capacity + kTileItems - 1) / kTileItems);
   L.hist = c.take<uint32_t>((size_t)256 * L.nb_hist);
   L.totals = c.take<uint32_t>(256);
   L.small = c.take<uint32_t>(kSmallWords);
@@ -818,7 +831,7 @@ Layout carve(void* ws, int64_t nrec, int64_t capacity) {
 
 // CTAs of a radix pass: one wave (4 per SM) at most; they take chunks by
 // ticket until none is left.
-int pass_grid(int nblocks) {
+int pass_grid(int nblocks, int per_sm = 4) {
   static std::atomic<int> sms[64];  // per device, 0 until queried
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
@@ -828,7 +841,31 @@ int pass_grid(int nblocks) {
       v = 1;
     sms[dev].store(v, std::memory_order_relaxed);
   }
-  return std::max(1, std::min(nblocks, 4 * v));
+  return std::max(1, std::min(nblocks, per_sm * v));
+}
+
+// The three table kernels of every pass, ITEMS items per thread (chunks of
+// 256 ITEMS items; `chunks` of them at most).
+template <int ITEMS>
+void table_passes(uint32_t* const k[2], uint32_t* const v[2], Count cnt, const PassDigits& pd,
+                  int chunks, const Layout& L, const WsHeader* krange, cudaStream_t stream,
+                  int spins) {
+  const int grid = pass_grid(chunks, ITEMS == 4 ? 6 : 4);  // the scatter's CTAs per SM
+  for (int p = 0; p < pd.passes; ++p) {
+    const uint32_t* kin = k[p & 1];
+    const uint32_t* vin = v[p & 1];
+    // the histogram kernel is light (28 registers, 1 KB): twice the blocks
+    launch_k(radix_hist_kernel<ITEMS>, std::min(chunks, 2 * grid), kThreads, 0, stream, kin, cnt,
+             pd.shift[p], pd.nbits[p], L.hist, chunks, krange);
+    launch_k(radix_scan_rows_kernel<ITEMS>, 1 << pd.nbits[p], 1024, 0, stream, L.hist, chunks,
+             L.totals, cnt, pd.shift[p], krange);
+    launch_k(radix_scatter_kernel<true, ITEMS>, grid, kThreads, 0, stream, kin, vin,
+             k[(p + 1) & 1], v[(p + 1) & 1], cnt, pd.shift[p], pd.nbits[p],
+             (const uint32_t*)L.totals, (const uint32_t*)L.hist, chunks,
+             (unsigned long long*)nullptr, (unsigned*)nullptr, L.hdr, spins,
+             (unsigned long long*)nullptr, krange);
+  }
+  count_launch(3 * pd.passes);
 }
 
 // Stable LSD sort of (key, value) pairs by the key bits [0, bits), in
@@ -854,30 +891,24 @@ SortedVals radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int
     shift += nb;
   }
   SortedVals out{{v[0], v[1]}, krange, pd};
-  const int grid = pass_grid(max_chunks);
   if (max_chunks > kLookbackMaxChunks) {
-    for (int p = 0; p < pd.passes; ++p) {
-      const uint32_t* kin = k[p & 1];
-      const uint32_t* vin = v[p & 1];
-      // the histogram kernel is light (28 registers, 1 KB): twice the blocks
-      launch_k(radix_hist_kernel, std::min(max_chunks, 2 * grid), kThreads, 0, stream, kin, cnt,
-               pd.shift[p], pd.nbits[p], L.hist, max_chunks, krange);
-      launch_k(radix_scan_rows_kernel, 1 << pd.nbits[p], 1024, 0, stream, L.hist, max_chunks,
-               L.totals, cnt, pd.shift[p], krange);
-      launch_k(radix_scatter_kernel<true>, grid, kThreads, 0, stream, kin, vin, k[(p + 1) & 1],
-               v[(p + 1) & 1], cnt, pd.shift[p], pd.nbits[p], (const uint32_t*)L.totals,
-               (const uint32_t*)L.hist, max_chunks, (unsigned long long*)nullptr,
-               (unsigned*)nullptr, L.hdr, spins, (unsigned long long*)nullptr, krange);
-    }
-    count_launch(3 * pd.passes);
+    // the depth sort (about one item per Gaussian, L2-resident) in chunks of
+    // 1024: twice the CTAs, each with half the ranking chain; the tile sort
+    // in chunks of 2048
+    if (sort == 0)
+      table_passes<4>(k, v, cnt, pd, 2 * max_chunks, L, krange, stream, spins);
+    else
+      table_passes<8>(k, v, cnt, pd, max_chunks, L, krange, stream, spins);
     return out;
   }
+  const int grid = pass_grid(max_chunks);
   uint32_t* ghist = L.small + sort * kMaxPasses * 256;
   unsigned* tickets = L.small + 2 * kMaxPasses * 256 + sort * kMaxPasses;
   launch_k(radix_global_hist_kernel, grid, kThreads, 0, stream, (const uint32_t*)k[0], cnt, pd,
            ghist, L.look[0], krange);
   for (int p = 0; p < pd.passes; ++p)
-    launch_k(radix_scatter_kernel<false>, grid, kThreads, 0, stream, (const uint32_t*)k[p & 1],
+    launch_k(radix_scatter_kernel<false, kItems>, grid, kThreads, 0, stream,
+             (const uint32_t*)k[p & 1],
              (const uint32_t*)v[p & 1], k[(p + 1) & 1], v[(p + 1) & 1], cnt, pd.shift[p],
              pd.nbits[p], (const uint32_t*)(ghist + p * 256), (const uint32_t*)nullptr, 0,
              L.look[p & 1], tickets + p, L.hdr, spins,
