@@ -9,10 +9,10 @@ sort, compositing of all 4 TFs, L1 loss, compositing backward, projection
 backward, and the Adam step on the raw parameters (sigmoid-activated scalar
 and weight).  Inputs are resident in HBM when the timed region starts; L2 is
 flushed (512 MB write) between timed steps, outside the timed spans.  Prints
-one JSON line, which also carries (one GPU, unless --no-extras) the batched
-training launch, the 64-TF sweep and the serving loop, each against its
-plain one-TF-per-launch path with its own clock record, and the oracle on the
-host's cores.
+one JSON line, which also carries (one GPU, unless --no-extras) the small
+plain render, the batched training launch, the 64-TF sweep and the serving
+loop, each against its plain one-TF-per-launch path with its own clock
+record, and the oracle on the host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -546,8 +546,10 @@ def run_gpu(args):
         "roofline": roofline,
     }
     if world == 1 and not args.no_extras:
-        # the batched, multi-TF and serving forms against their plain paths on
-        # the same GPU, each with its own clock record
+        # the plain render (C1) and the batched, multi-TF and serving forms
+        # against their plain paths on the same GPU, each with its own clock
+        # record
+        line["plain"] = measure_plain(args)
         line["batched"] = measure_batched(args)
         line["sweep"] = measure_sweep(args)
         line["serve"] = measure_serve(args)
@@ -787,8 +789,11 @@ def _event_time(fn, reps, flush=None):
     return tot / reps
 
 
-def run_plain(args):
-    """4096 Gaussians, 128x128, one TF: render latency, eager and graph-replayed."""
+def measure_plain(args, reps=200):
+    """C1: 4096 Gaussians, 128x128, one TF: project, bin and composite,
+    eager and replayed as a CUDA graph, CUDA events around each render with
+    L2 flushed (a 512 MB write) before it.  Returns the record with its
+    clocks."""
     import torch
 
     import __graft_entry__
@@ -801,6 +806,7 @@ def run_plain(args):
     luts = lut_tensor(tfs)
     p = SplatPipeline(g.n, cams, n_tf=1)
     p.render(*tens, luts)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
         p.project(*tens, luts)
@@ -808,15 +814,29 @@ def run_plain(args):
         p.composite(luts)
     for _ in range(max(args.warmup, 3)):
         step()
-    eager = _event_time(step, args.steps)
     cs = CapturedStep(step)
-    graph = _event_time(cs.replay, args.steps)
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    eager = _event_time(step, reps, flush)
+    graph = _event_time(cs.replay, reps, flush)
+    clk = clocks.stop()
     px = 128 * 128
-    print(json.dumps({"workload": "plain render: 4096 Gaussians, 128x128, 1 TF",
-                      "us_per_render_eager": round(eager * 1e3, 2),
-                      "us_per_render_graph": round(graph * 1e3, 2),
-                      "mpix_per_s_graph": round(px / (graph * 1e-3) / 1e6, 2),
-                      "launches_per_render": cs.launches}))
+    res = {"workload": "plain render: 4096 Gaussians, 128x128, 1 TF",
+           "us_per_render_eager": round(eager * 1e3, 2),
+           "us_per_render_graph": round(graph * 1e3, 2),
+           "mpix_per_s_graph": round(px / (graph * 1e-3) / 1e6, 2),
+           "launches_per_render": cs.launches,
+           "timing": f"CUDA events around each of {reps} renders, L2 flushed before each",
+           "clocks": clk}
+    del p, flush, tens
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_plain(args):
+    """C1 on its own (measure_plain)."""
+    print(json.dumps(measure_plain(args, reps=max(args.steps, 20))))
 
 
 def measure_sweep(args, reps=3):
