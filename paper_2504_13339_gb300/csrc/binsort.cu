@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS == 4 ? 6 : 4)
     for (int j = 0; j < ITEMS; ++j) {
       const int64_t i = base + warp * (ITEMS * 32) + j * 32 + lane;
       k[j] = i < n ? kin[i] : 0u;
-      v[j] = i < n ? vin[i] : 0u;
+      v[j] = i < n && vin ? vin[i] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS == 4 ? 6 : 4)
       uint32_t d = ((key - kb) >> shift) & mask;
       uint32_t g = s_dbase[d] + (uint32_t)p - s_bstart[d];
       kout[g] = key;
-      vout[g] = s_vals[p];
+      if (vout) vout[g] = s_vals[p];  // keys-only sorts carry no values
     }
     __syncthreads();  // the next chunk reuses the shared arrays (and s_chunk)
   }
@@ -642,6 +642,8 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+// With rec_bits > 0 (records and list ids fit one 32-bit word together) each
+// pair is written as one word, list id << rec_bits | record, into ikeys.
 // Writes the (global tile id, record) pairs of 32 consecutive records (in
 // depth order) per warp, tiles of a record row-major, below capacity; the
 // global id of tile (tx, ty) of view v is vm.tile_off[v] + ty * tiles_x[v]
@@ -652,8 +654,8 @@ __global__ void __launch_bounds__(1024)
 __global__ void __launch_bounds__(256)
     emit_kernel(const int32_t* __restrict__ tiles, const short4* __restrict__ rect,
                 SortedVals sorted, const unsigned long long* __restrict__ bsum, Count visible,
-                int64_t n_per_view, ViewMap vm, int64_t capacity, uint32_t* __restrict__ ikeys,
-                uint32_t* __restrict__ ivals) {
+                int64_t n_per_view, ViewMap vm, int64_t capacity, int rec_bits,
+                uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
   pdl_enter();
   __shared__ unsigned long long s_warp[8];
   const uint32_t* __restrict__ order = sorted.get();
@@ -712,8 +714,13 @@ __global__ void __launch_bounds__(256)
         ++ry;
         rx -= o_wx;
       }
-      ikeys[p] = o_kb + (uint32_t)((o_y0 + ry) * o_tx + o_x0 + rx);
-      ivals[p] = o_g;
+      const uint32_t key = o_kb + (uint32_t)((o_y0 + ry) * o_tx + o_x0 + rx);
+      if (rec_bits > 0) {
+        ikeys[p] = (key << rec_bits) | o_g;  // one packed word: list id, record
+      } else {
+        ikeys[p] = key;
+        ivals[p] = o_g;
+      }
     }
   }
 }
@@ -741,24 +748,32 @@ __global__ void zero_ranges_kernel(int2* __restrict__ ranges, int64_t count,
 // ends where it differs from its successor.  Keys are < 2^31, so 0xffffffff
 // marks "no neighbour".
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
-                              int2* __restrict__ ranges) {
+                              int2* __restrict__ ranges, int key_shift,
+                              uint32_t* __restrict__ vals) {
   pdl_enter();
   const int64_t n = cnt.get();
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= n) return;
-  uint32_t k[6];
-  k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+  // packed words (key_shift > 0): the list id above key_shift, the record
+  // below it (written to vals); 0xffffffff marks "no neighbour" after the
+  // shift (list ids are below 2^31)
+  uint32_t w[4];
   if (i0 + 4 <= n) {
     const uint4 q = *reinterpret_cast<const uint4*>(keys + i0);
-    k[1] = q.x;
-    k[2] = q.y;
-    k[3] = q.z;
-    k[4] = q.w;
+    w[0] = q.x;
+    w[1] = q.y;
+    w[2] = q.z;
+    w[3] = q.w;
   } else {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) k[1 + t] = i0 + t < n ? keys[i0 + t] : 0xffffffffu;
+    for (int t = 0; t < 4; ++t) w[t] = i0 + t < n ? keys[i0 + t] : 0u;
   }
-  k[5] = i0 + 4 < n ? keys[i0 + 4] : 0xffffffffu;
+  uint32_t k[6];
+  k[0] = i0 > 0 ? keys[i0 - 1] >> key_shift : 0xffffffffu;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) k[1 + t] = i0 + t < n ? w[t] >> key_shift : 0xffffffffu;
+  k[5] = i0 + 4 < n ? keys[i0 + 4] >> key_shift : 0xffffffffu;
+  const uint32_t rmask = key_shift > 0 ? (0xffffffffu >> (32 - key_shift)) : 0u;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const int64_t i = i0 + t;
@@ -766,6 +781,7 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
     const uint32_t kk = k[1 + t];
     if (kk != k[t]) ranges[kk].x = (int)i;
     if (kk != k[2 + t]) ranges[kk].y = (int)(i + 1);
+    if (vals) vals[i] = w[t] & rmask;
   }
 }
 
@@ -773,12 +789,12 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, Count cnt,
 // the tile bits of the largest view.
 __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
                               Count cnt, const float4* __restrict__ geo, ViewMap vm, int tb,
-                              uint64_t* __restrict__ keys64) {
+                              int key_shift, uint64_t* __restrict__ keys64) {
   pdl_enter();
   const int64_t n = cnt.get();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t tk = tkeys[i];
+  uint32_t tk = tkeys[i] >> key_shift;
   uint32_t view = (uint32_t)view_of_tile(vm, (int)tk);
   uint32_t tile = tk - (uint32_t)vm.tile_off[view];
   uint32_t depth = __float_as_uint(geo[vals[i]].z);
@@ -868,8 +884,9 @@ void table_passes(uint32_t* const k[2], uint32_t* const v[2], Count cnt, const P
   count_launch(3 * pd.passes);
 }
 
-// Stable LSD sort of (key, value) pairs by the key bits [0, bits), in
-// passes of balanced digit widths (at most 8 bits).  Buffers ping-pong
+// Stable LSD sort of (key, value) pairs by the key bits [base_shift,
+// base_shift + bits), in passes of balanced digit widths (at most 8 bits);
+// with v[0] and v[1] null the keys alone are sorted.  Buffers ping-pong
 // k[p % 2] -> k[(p + 1) % 2]; with `krange` (the depth sort) trailing passes
 // over constant digits are skipped on the device, so the result's buffer is
 // known there only: the returned SortedVals names it (without `krange`,
@@ -880,12 +897,13 @@ void table_passes(uint32_t* const k[2], uint32_t* const v[2], Count cnt, const P
 // pass.
 SortedVals radix_sort(uint32_t* const k[2], uint32_t* const v[2], Count cnt, int bits,
                       int max_chunks, const Layout& L, int sort, const WsHeader* krange,
-                      cudaStream_t stream, int spins = kLookbackSpins) {
+                      cudaStream_t stream, int spins = kLookbackSpins, int base_shift = 0) {
   PassDigits pd;
   pd.passes = std::max(1, (bits + 7) / 8);
-  int shift = 0;
+  int shift = base_shift;
   for (int p = 0; p < pd.passes; ++p) {
-    const int nb = (bits - shift + (pd.passes - p) - 1) / (pd.passes - p);  // balanced widths
+    const int nb = (bits - (shift - base_shift) + (pd.passes - p) - 1) /
+                   (pd.passes - p);  // balanced widths
     pd.shift[p] = shift;
     pd.nbits[p] = std::max(1, nb);
     shift += nb;
@@ -1268,33 +1286,38 @@ veg_status binsort_launch(const veg_camera* cams, int n_views, int64_t n, const 
   launch_k(count_reduce_kernel, L.nb_emit, 256, 0, stream, tiles, order, cr, L.esum);
   launch_k(count_top_kernel, 1, 1024, 0, stream, L.esum, L.nb_emit, L.hdr, capacity);
   count_launch(2);
-  // 3. emit (tile key, record) pairs, then stable sort by tile key
+  // 3. emit (tile key, record) pairs, then stable sort by tile key.  When
+  //    record indices and list ids fit one 32-bit word together, each pair
+  //    is one packed word and the sort moves keys only (half the bytes);
+  //    the ranges kernel then writes the records into vals.
   int bits = 1;
   while (((int64_t)1 << bits) < nranges) ++bits;
+  int rec_bits = 1;
+  while (((int64_t)1 << rec_bits) < nrec) ++rec_bits;
+  const bool packed = rec_bits + bits <= 32;
+  if (!packed) rec_bits = 0;
   const int passes = (bits + 7) / 8;
   uint32_t* kbuf[2] = {L.ik0, L.ik1};
-  uint32_t* vbuf[2];
-  if (passes % 2 == 0) {
-    vbuf[0] = vals;
-    vbuf[1] = L.iv0;
-  } else {
-    vbuf[0] = L.iv0;
-    vbuf[1] = vals;
+  uint32_t* vbuf[2] = {nullptr, nullptr};
+  if (!packed) {
+    vbuf[passes % 2 == 0 ? 0 : 1] = vals;
+    vbuf[passes % 2 == 0 ? 1 : 0] = L.iv0;
   }
   launch_k(emit_kernel, L.nb_emit, 256, 0, stream, tiles, rect, order,
-           (const unsigned long long*)L.esum, cr, n,
-           vm, capacity, kbuf[0], vbuf[0]);
+           (const unsigned long long*)L.esum, cr, n, vm, capacity, rec_bits, kbuf[0], vbuf[0]);
   count_launch();
   Count ci{0, &L.hdr->n_instances, capacity};
   const int nb_inst = (int)std::max<int64_t>(1, (capacity + kTileItems - 1) / kTileItems);
-  radix_sort(kbuf, vbuf, ci, bits, nb_inst, L, 1, nullptr, stream);
+  radix_sort(kbuf, vbuf, ci, bits, nb_inst, L, 1, nullptr, stream, kLookbackSpins, rec_bits);
   const uint32_t* fkeys = kbuf[passes & 1];
-  // 4. per-tile ranges and optional 64-bit keys
-  launch_k(ranges_kernel, grid_for(capacity, 1024), 256, 0, stream, fkeys, ci, ranges);
+  // 4. per-tile ranges (and the records, from packed words) and optional
+  //    64-bit keys
+  launch_k(ranges_kernel, grid_for(capacity, 1024), 256, 0, stream, fkeys, ci, ranges, rec_bits,
+           packed ? vals : (uint32_t*)nullptr);
   count_launch();
   if (keys) {
     launch_k(keys64_kernel, grid_for(capacity, 256), 256, 0, stream, fkeys, vals, ci, geo, vm,
-             tile_bits_of(vm.max_tiles), keys);
+             tile_bits_of(vm.max_tiles), rec_bits, keys);
     count_launch();
   }
   return launch_status();
