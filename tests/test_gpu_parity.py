@@ -204,15 +204,19 @@ def _sorted_lists(dbits, tiles, rect, tiles_x, tb):
     return keys[srt], vals[srt]
 
 
-@pytest.mark.parametrize("span,passes_run", [(0, 0), (200, 1), (60_000, 2), (1 << 20, 3),
-                                             (None, 4)])
-def test_depth_sort_skips_the_passes_above_the_key_span(span, passes_run):
+@pytest.mark.parametrize("span,passes_run,W", [(0, 0, 256), (200, 1, 256), (60_000, 2, 256),
+                                               (1 << 20, 3, 256), (None, 4, 256),
+                                               (None, 4, 4096)])
+def test_depth_sort_skips_the_passes_above_the_key_span(span, passes_run, W):
     """The depth sort takes its digits of depth bits minus their minimum and
     skips the passes above the span of the visible records' keys (found on
     the device): for spans needing 0-4 of the 8-bit passes, on 70,000
     records (the compaction path) with a fifth culled, the lists equal their
-    definition bit for bit, keys included."""
-    n, W = 70_000, 256
+    definition bit for bit, keys included.  At 256 x 256 the tile sort runs
+    on packed words (17 record bits + 8 list bits); at 4096 x 4096 (65,536
+    lists, 16 bits) record and list do not fit one word and it sorts
+    (key, value) pairs."""
+    n = 70_000
     rng = np.random.default_rng(180 + passes_run)
     cam = S.look_at_camera((0.0, 0.0, 3.0), W, W)
     tx = cam.tiles_x
@@ -250,9 +254,11 @@ def test_depth_sort_skips_the_passes_above_the_key_span(span, passes_run):
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_ref)
     lists = (keys_ref >> np.uint64(32)).astype(np.int64)
     rr = ranges.cpu().numpy()
-    for t in range(tx * tx):
-        w = np.nonzero(lists == t)[0]
-        assert tuple(rr[t]) == ((w[0], w[-1] + 1) if w.size else (0, 0))
+    ids = np.arange(tx * tx)
+    lo = np.searchsorted(lists, ids, "left")
+    hi = np.searchsorted(lists, ids, "right")
+    want = np.where((hi > lo)[:, None], np.stack([lo, hi], axis=1), 0)
+    assert np.array_equal(rr.astype(np.int64), want)
 
 
 def test_views_of_different_models_project_as_each_model_alone():
