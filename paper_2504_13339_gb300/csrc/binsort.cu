@@ -5,18 +5,23 @@
 // index order.  Rather than radix-sorting 44-60 bit keys over all M pairs,
 // the path sorts in two stages that give the same order:
 //   1. sort the V*n (view, Gaussian) records by their float32 depth bits
-//      (stable, so ties keep index order) -- 4 passes over V*n items;
+//      (stable, so ties keep index order), digits taken of the bits minus
+//      their minimum, the passes above the keys' span skipped on the device;
 //   2. emit the pairs in that depth order with key = view * tiles + tile and
-//      stable-sort them by that key alone -- ceil(bits/8) passes over M.
+//      stable-sort them by that key alone -- ceil(bits/8) passes over M
+//      (one packed word per pair when record and key fit 32 bits together).
 // A stable sort by tile of a sequence already ordered by (depth, index)
 // yields (view, tile, depth, index) order.  Records that touch no tile
 // (culled) are dropped first by a stable compaction, so only the visible
 // ones are depth-sorted (inputs of at most 2^16 records instead sort the
-// culled ones last: the same order with fewer launches).  Both stages use one hand-written LSD radix sort
-// (reduce / scan / stable scatter, 8-bit digits, 2048-item chunks, grid-
-// stride blocks).  The visible and instance counts live only on the device;
-// later kernels read them from the workspace header, so no host round trip
-// is needed and no block works past them.
+// culled ones last: the same order with fewer launches).  Both stages use
+// one hand-written LSD radix sort of 8-bit digits in three forms by size:
+// the whole binning in one CTA (at most 4096 records and 256 lists), one
+// look-back kernel per pass (at most 64 chunks of 2048 items), or per-chunk
+// counts, their scan and a stable scatter per pass.  The visible and
+// instance counts live only on the device; later kernels read them from the
+// workspace header, so no host round trip is needed and no block works past
+// them.
 #include <algorithm>
 
 #include "veg_internal.cuh"
